@@ -1,0 +1,323 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+of the paper's definitions on Fourier modes, the Taylor remainder, textbook
+reductions (gamma -> 0 gives the classical leap-frog), and the numbers the
+paper prints (Table 3).  A plausible slip anywhere in the oracle (a dropped
+term, a wrong sign or index, a transposed axis, a missing 1/N) fails one of
+them.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+
+def _mode_closed_form(shape, modes, s_field, lo=None, hi=None):
+    """sum_i a_i |mu_{k_i}|^{2 s(x)} cos(mu_{k_i}.(x-a) + phi_i): the image of a
+    cosine sum under the dense operator (Eq. (2.12)): each mode +-k_i is
+    multiplied pointwise by |mu_{k_i}|^{2 s(x_j)}."""
+    d = len(shape)
+    lo = [-np.pi] * d if lo is None else lo
+    hi = [np.pi] * d if hi is None else hi
+    grids = S.mesh(shape, lo, hi)
+    out = np.zeros(shape)
+    for amp, ks, phi in modes:
+        arg = np.zeros(shape)
+        m2 = 0.0
+        for i in range(d):
+            mu = 2 * np.pi * ks[i] / (hi[i] - lo[i])
+            arg = arg + mu * (grids[i] - lo[i])
+            m2 += mu * mu
+        out = out + amp * (m2 ** s_field(m2)) * np.cos(arg + phi)
+    return out
+
+
+# --------------------------------------------------------------------------
+# P1: dense operator on Fourier modes (Eq. (2.3), Eq. (2.12))
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,lo,hi", [
+    ((32,), [-np.pi], [np.pi]),
+    ((24,), [-32.0], [32.0]),
+    ((12, 16), [-np.pi, -np.pi], [np.pi, np.pi]),
+    ((8, 6, 10), [0.0, -1.0, -np.pi], [2.0, 3.0, np.pi]),
+])
+def test_dense_operator_modes(shape, lo, hi):
+    d = len(shape)
+    rng = np.random.default_rng(11)
+    modes = []
+    for _ in range(3):
+        ks = [int(rng.integers(-shape[d - 1 - i] // 2 + 1, shape[d - 1 - i] // 2))
+              for i in range(d)]
+        if all(k == 0 for k in ks):
+            ks[0] = 1
+        modes.append((float(rng.uniform(0.5, 2)), ks, float(rng.uniform(0, 6))))
+    u = S.cosine_modes(shape, modes, lo, hi)
+    grids = S.mesh(shape, lo, hi)
+    s = 0.6 + 0.5 * np.sin(grids[0] * 0.7 + 0.2) ** 2
+    for g in grids[1:]:
+        s = s + 0.1 * np.cos(g)
+    got = O.dense_operator(u, s, lo, hi)
+    ref = _mode_closed_form(shape, modes, lambda m2: s, lo, hi)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_dense_operator_nyquist_real_and_sampled_points():
+    """The Nyquist row of the asymmetric index set is kept (k = -J/2, |mu| =
+    pi J/(b-a)); on the mode cos(pi j) the operator is |mu_N|^{2 s_j} cos(pi j)."""
+    n = 16
+    x = S.axis(n)
+    u = np.cos(np.pi * np.arange(n))  # pure Nyquist mode
+    s = 1.0 + 0.2 * np.sin(x)
+    got = O.dense_operator(u, s)
+    ref = (n / 2.0) ** (2 * s) * u
+    assert np.allclose(got, ref, rtol=1e-13, atol=0)
+    pts = np.array([0, 5, 11])
+    assert np.allclose(O.dense_operator(u, s, points=pts), ref[pts], rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# P2: matrix-free scheme closed form (Eq. (2.10), Eq. (2.13))
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("M", [0, 1, 2, 5, 8, 16])
+def test_matrix_free_truncated_exponential(M):
+    shape = (20, 16)
+    modes = [(1.0, (3, 2), 0.3), (0.5, (-5, 1), 1.1), (0.25, (0, 7), -0.4),
+             (0.7, (1, 0), 0.0)]  # |mu| = 1: ln|mu|^2 = 0
+    u = S.cosine_modes(shape, modes)
+    x, y = S.mesh(shape)
+    s = 1.0 + 0.3 * np.sin(x) * np.cos(2 * y)
+    got = O.matrix_free_operator(u, s, M)
+    s0 = s.mean()
+    delta = s - s0
+
+    # |mu|^{2 s0} e_M(delta ln|mu|^2) per mode
+    ref = np.zeros(shape)
+    for amp, ks, phi in modes:
+        m2 = ks[0] ** 2 + ks[1] ** 2
+        L = math.log(m2)
+        eM = sum((delta * L) ** m / math.factorial(m) for m in range(M + 1))
+        ref += amp * m2 ** s0 * eM * np.cos(ks[0] * (x + np.pi) + ks[1] * (y + np.pi) + phi)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_matrix_free_uses_grid_mean_s0():
+    """Any s0 gives a valid expansion; the paper's choice is the domain
+    average.  With an explicit, different s0 the M -> large limit is the same
+    dense result, while the default must equal an explicit grid mean."""
+    shape = (32,)
+    x = S.axis(32)
+    u = S.random_field(shape, 3)
+    s = 1.0 + 0.25 * np.sin(x)
+    a = O.matrix_free_operator(u, s, 6)
+    b = O.matrix_free_operator(u, s, 6, s0=float(np.mean(s)))
+    assert np.array_equal(a, b)
+    dense = O.dense_operator(u, s)
+    c = O.matrix_free_operator(u, s, 40, s0=0.8)
+    assert np.max(np.abs(c - dense)) <= 1e-9 * np.max(np.abs(dense))
+
+
+# --------------------------------------------------------------------------
+# P3: matrix-free -> dense as M grows, within the Taylor remainder (Eq. (2.8))
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(64,), (16, 16), (8, 8, 8)])
+def test_matrix_free_converges_to_dense_within_remainder(shape):
+    u = S.random_field(shape, 5)
+    grids = S.mesh(shape)
+    s = 1.0 + 0.3 * np.sin(grids[0])
+    for g in grids[1:]:
+        s = s * (1.0 + 0.1 * np.cos(g))
+    dense = O.dense_operator(u, s)
+    errs = []
+    for M in (2, 4, 8, 12, 20):
+        mf = O.matrix_free_operator(u, s, M)
+        bound = O.taylor_remainder_bound(u, s, M)
+        err = np.abs(mf - dense)
+        assert np.all(err <= bound * (1 + 1e-9) + 1e-10 * np.max(np.abs(dense)))
+        errs.append(err.max())
+    assert errs[-1] <= 1e-10 * np.max(np.abs(dense))
+    assert all(a > b for a, b in zip(errs[:-2], errs[1:-1]))
+
+
+# --------------------------------------------------------------------------
+# P4: special cases
+# --------------------------------------------------------------------------
+def test_constant_order_is_the_plain_multiplier():
+    """Constant s: Eq. (2.13) collapses to F^{-1}[|mu|^{2s} F u] (Eq. (1.3)),
+    which for a cosine sum is the closed form; dense and matrix-free agree."""
+    shape = (16, 24)
+    modes = [(1.0, (2, 3), 0.1), (2.0, (-4, 5), 0.7)]
+    u = S.cosine_modes(shape, modes)
+    ref = _mode_closed_form(shape, modes, lambda m2: 1.37)
+    for M in (0, 3, 9):
+        got = O.matrix_free_operator(u, np.full(shape, 1.37), M)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    got = O.dense_operator(u, np.full(shape, 1.37))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_constant_field_maps_to_zero_and_linearity():
+    shape = (12, 10)
+    x, y = S.mesh(shape)
+    s = 0.8 + 0.2 * np.cos(x + y)
+    assert np.max(np.abs(O.matrix_free_operator(np.full(shape, 3.0), s, 8))) < 1e-11
+    assert np.max(np.abs(O.dense_operator(np.full(shape, 3.0), s))) < 1e-11
+    u, v = S.random_field(shape, 1), S.random_field(shape, 2)
+    lhs = O.matrix_free_operator(2.0 * u - 0.5 * v, s, 7)
+    rhs = 2.0 * O.matrix_free_operator(u, s, 7) - 0.5 * O.matrix_free_operator(v, s, 7)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(lhs))
+
+
+def test_second_order_is_minus_laplacian():
+    """s = 1: the operator is -Delta; on sin(3x) cos(2y) that is 13 times it."""
+    shape = (16, 16)
+    x, y = S.mesh(shape)
+    u = np.sin(3 * x) * np.cos(2 * y)
+    assert np.allclose(O.dense_operator(u, np.ones(shape)), 13 * u, atol=1e-11)
+    assert np.allclose(O.matrix_free_operator(u, np.ones(shape), 4), 13 * u, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# seismic coefficients (Sec. 1)
+# --------------------------------------------------------------------------
+def test_seismic_coefficients_limits_and_invariants():
+    Q = np.array([1e-3, 0.5, 1.0, 5.0, 20.0, 100.0, 1e12])
+    c0, w0 = 1.7, 2 * np.pi
+    co = O.seismic_coefficients(Q, c0, w0)
+    g = co["gamma"]
+    assert np.all((g > 0) & (g < 0.5))
+    assert abs(g[2] - 0.25) < 1e-15  # arctan(1) = pi/4
+    # gamma -> 0: the classical acoustic wave equation (c = c0, eta = -1, tau = 0)
+    assert abs(co["c"][-1] - c0) < 1e-12 and abs(co["eta"][-1] + 1) < 1e-10
+    assert abs(co["tau"][-1]) < 1e-10
+    # eta and tau are the cos/sin pair of the same angle pi*gamma, with
+    # scale c0^{2g} w0^{-2g} (tau has one extra 1/c0)
+    scale = c0 ** (2 * g) * w0 ** (-2 * g)
+    assert np.allclose((co["eta"] / scale) ** 2 + (co["tau"] * c0 / scale) ** 2, 1.0)
+    assert np.allclose(np.arctan2(-co["tau"] * c0, -co["eta"]), np.pi * g)
+    # half-angle: 2 (c/c0)^2 - 1 = cos(pi gamma)
+    assert np.allclose(2 * (co["c"] / c0) ** 2 - 1, -co["eta"] / scale)
+    with pytest.raises(ValueError):
+        O.seismic_coefficients(np.array([1.0, 0.0]), 1.0, 1.0)
+
+
+# --------------------------------------------------------------------------
+# P5 / P6: the seismic LFFP stepper on a single Fourier mode
+# --------------------------------------------------------------------------
+def test_seismic_lffp_gamma_zero_is_classical_leapfrog():
+    """gamma = 0: u_tt = c0^2 Delta u; on one mode the leap-frog solution is
+    cos(n theta) u0 with cos(theta) = 1 - dt^2 c0^2 |mu|^2 / 2, and the Taylor
+    start gives u1 = cos(theta) u0 exactly."""
+    n = 32
+    x = S.axis(n)
+    k, c0, dt, steps = 5, 1.3, 0.02, 60
+    u0 = np.cos(k * (x + np.pi))
+    u = O.seismic_lffp(np.zeros(n), c0, 2 * np.pi, u0, None, dt, steps, M=4)
+    theta = math.acos(1 - 0.5 * dt * dt * c0 * c0 * k * k)
+    assert np.allclose(u, math.cos(steps * theta) * u0, atol=1e-11)
+
+
+@pytest.mark.parametrize("gamma,k,dt", [(0.05, 3, 0.01), (0.2, 6, 0.004), (0.4, 2, 0.05)])
+def test_seismic_lffp_constant_gamma_damped_recurrence(gamma, k, dt):
+    """Constant gamma: one mode obeys a_{n+1} = (2-al-be) a_n - (1-be) a_{n-1}
+    with al = dt^2 c^2|eta| |mu|^{2+2g}, be = dt c^2 |tau| |mu|^{1+2g} and
+    a_1 = (1 - al/2) a_0; solved through the characteristic roots."""
+    n, c0, w0, steps = 32, 1.0, 2 * np.pi, 40
+    x = S.axis(n)
+    u0 = np.cos(k * (x + np.pi))
+    u = O.seismic_lffp(np.full(n, gamma), c0, w0, u0, None, dt, steps, M=3)
+    c = c0 * math.cos(math.pi * gamma / 2)
+    eta = c0 ** (2 * gamma) * w0 ** (-2 * gamma) * math.cos(math.pi * gamma)
+    tau = c0 ** (2 * gamma - 1) * w0 ** (-2 * gamma) * math.sin(math.pi * gamma)
+    al = dt * dt * c * c * eta * k ** (2 + 2 * gamma)
+    be = dt * c * c * tau * k ** (1 + 2 * gamma)
+    r = np.roots([1.0, -(2 - al - be), 1 - be]).astype(complex)
+    a0, a1 = 1.0, 1 - al / 2
+    C2 = (a1 - r[0] * a0) / (r[1] - r[0])
+    C1 = a0 - C2
+    an = (C1 * r[0] ** steps + C2 * r[1] ** steps).real
+    assert np.allclose(u, an * u0, atol=1e-11)
+
+
+def test_seismic_lffp_source_and_velocity_start():
+    """Taylor start with v0 and a source (reading of Eq. (3.4c) for Eq. (1.1)):
+    gamma = 0, u0 = 0, v0 = cos(kx): u1 = dt v0 + dt^2/2 * (source term);
+    the source adds dt^2/2 r_0 / h at the source node only."""
+    n = 16
+    x = S.axis(n)
+    v0 = np.cos(2 * (x + np.pi))
+    dt = 0.01
+    u1 = O.seismic_lffp(np.zeros(n), 1.0, 1.0, np.zeros(n), v0, dt, 1, M=2,
+                        src_idx=(3,), src=np.array([2.0]))
+    h = 2 * np.pi / n
+    ref = dt * v0.copy()
+    ref[3] += 0.5 * dt * dt * 2.0 / h
+    assert np.allclose(u1, ref, atol=1e-14)
+
+
+def test_seismic_lffp_dense_vs_matrix_free_variable_gamma():
+    """Tiny 2D grid, variable gamma: the O2-driven run converges to the
+    O1-driven run (the schemes differ only by the truncation of Eq. (2.9))."""
+    shape = (8, 8)
+    x, y = S.mesh(shape)
+    Q = 5.0 + 20.0 * (1 + np.sin(x) * np.cos(y))
+    gam = np.arctan(1.0 / Q) / np.pi
+    u0 = S.gaussian_pulse(shape, 1.5)
+    a = O.seismic_lffp(gam, 1.0, 2 * np.pi, u0, None, 2e-3, 20, M=10, method="matrix_free")
+    b = O.seismic_lffp(gam, 1.0, 2 * np.pi, u0, None, 2e-3, 20, M=10, method="dense")
+    assert O.rel_l2(a, b) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# P7: the paper's printed LFFP temporal errors (Table 3)
+# --------------------------------------------------------------------------
+def _table3(golden_dir):
+    rows = {}
+    with open(os.path.join(golden_dir, "table3_lffp_temporal_errors.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[int(p[0])] = [None if v == "unstable" else float(v) for v in p[1:]]
+    return rows
+
+
+def test_paper_table3_lffp_variable_order(golden_dir):
+    """Column s1(x) = 1 + 0.3 sin(pi x/8) of Table 3: errors at dt = 2^-9,
+    2^-10, 2^-11 against the dt = 1e-4 reference reproduce the printed four
+    digits, and dt = 2^-7, 2^-8 blow up ("unstable")."""
+    rows = _table3(golden_dir)
+    J, lo, hi = 4096, [-32.0], [32.0]
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s1 = 1.0 + 0.3 * np.sin(np.pi * x / 8)
+    cube = lambda u: u ** 3  # noqa: E731
+    ref = O.general_lffp(s1, 1.0, cube, phi, None, 1e-4, 10000, 15, lo, hi)
+    for p in (9, 10, 11):
+        u = O.general_lffp(s1, 1.0, cube, phi, None, 2.0 ** -p, 2 ** p, 15, lo, hi)
+        err = O.l2_error(u, ref, [1.0 / 64])
+        printed = rows[p][3]
+        assert abs(err - printed) <= 0.0006 * printed, (p, err, printed)
+    for p in (7, 8):
+        assert rows[p][3] is None
+        with np.errstate(all="ignore"):
+            u = O.general_lffp(s1, 1.0, cube, phi, None, 2.0 ** -p, 2 ** p, 15, lo, hi)
+        assert not np.all(np.isfinite(u)) or np.max(np.abs(u)) > 1e3
+
+
+def test_paper_table3_lffp_constant_order_column(golden_dir):
+    """Column s = 0.5 of Table 3 (M irrelevant: delta = 0)."""
+    rows = _table3(golden_dir)
+    J, lo, hi = 4096, [-32.0], [32.0]
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s = np.full(J, 0.5)
+    cube = lambda u: u ** 3  # noqa: E731
+    ref = O.general_lffp(s, 1.0, cube, phi, None, 1e-4, 10000, 0, lo, hi)
+    u = O.general_lffp(s, 1.0, cube, phi, None, 2.0 ** -8, 2 ** 8, 0, lo, hi)
+    err = O.l2_error(u, ref, [1.0 / 64])
+    assert abs(err - rows[8][0]) <= 0.0006 * rows[8][0], err
