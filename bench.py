@@ -1,0 +1,380 @@
+"""Benchmark of the fused GB300 path on the headline workload.
+
+Workload ("2D 1024^2, M = 16"): periodic [-pi,pi)^2 on 1024 x 1024 points,
+Q(x, y) = seeded low-passed noise mapped to [5, 100], c0 = 1, omega0 = 2 pi,
+Ricker source (f0 = 10) at the centre, u0 = u_t = 0, dt = 5e-4, 1000
+leap-frog steps of Eq. (1.1) with both operators by Eq. (2.13), M = 16.
+
+One bench "step" = one complete run of that workload (model precompute from
+Q, state and source set-up, start step + 999 leap-frog steps).  The metric
+is Mpoint-steps/s = 1024^2 * 1000 * runs / time.
+
+  value  device-resident inputs (Q, u0, source samples already in HBM);
+  e2e    the same run through the C ABI with host buffers: the H2D copies of
+         Q, u0 and the samples and the D2H copy of the final wavefield are
+         inside the timed region;
+  plain  the cuFFT + elementwise baseline on the same run.
+
+L2 is flushed (256 MiB write) before every timed run.  Times are CUDA events
+on the context stream.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 1024
+NSTEPS = 1000
+M = 16
+DT = 5e-4
+METRIC = "Mpoint-steps/s (2D 1024², M=16) fused vs plain at ≤1e-5 rel L2; serve p50/p99"
+UNIT = "Mpoint-steps/s"
+WORKLOAD = "2D periodic 1024x1024, FP32, M=16, Q low-passed noise in [5,100] (seed 2), Ricker f0=10 at centre, dt=5e-4, 1000 steps"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _config(extra=None):
+    c = {"workload": WORKLOAD, "grid": [NY, NX], "M": M, "steps_per_run": NSTEPS, "dt": DT,
+         "parallelism": "replicas (one independent run per GPU)",
+         "l2": "flushed between timed runs (256 MiB write)", "step_unit": "one full 1000-step run"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.p = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.p.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle, as it stands
+# ---------------------------------------------------------------------------
+def _oracle_sample(w, gamma, nsteps):
+    import oracle as O
+    t0 = time.perf_counter()
+    O.seismic_lffp(gamma, w["c0"], w["omega0"], w["u0"], None, w["dt"], nsteps, w["M"],
+                   src_idx=w["src_idx"], src=w["src"])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(nsteps=3):
+    import oracle as O
+    import synthetic as S
+    w = S.workload_2d_1024(nsteps=NSTEPS)
+    gamma = O.seismic_coefficients(w["Q"], w["c0"], w["omega0"])["gamma"]
+    _oracle_sample(w, gamma, 1)  # warm the multiplier-table cache
+    t = _oracle_sample(w, gamma, nsteps)
+    return {"value": NX * NY * nsteps / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} leap-frog steps of the 1024^2 M=16 workload (FP64 NumPy, pocketfft, 1 thread), "
+                      f"{t:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    import oracle as O
+    import synthetic as S
+    w = S.workload_2d_1024(nsteps=NSTEPS)
+    gamma = O.seismic_coefficients(w["Q"], w["c0"], w["omega0"])["gamma"]
+    per = 2  # oracle leap-frog steps per bench step (bounded sample)
+    for _ in range(args.warmup):
+        _oracle_sample(w, gamma, 1)
+    times = [_oracle_sample(w, gamma, per) for _ in range(args.steps)]
+    tot = sum(times)
+    value = NX * NY * per * args.steps / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": _config({"reference": "FP64 NumPy oracle (oracle/), each bench step = "
+                                             f"{per} leap-frog steps of the workload on the host"}),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                             "sample": f"{per} oracle leap-frog steps per bench step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    import oracle as O
+    import paper_2311_13049_gb300 as V
+    import synthetic as S
+    from paper_2311_13049_gb300 import build as B
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+
+    w = S.workload_2d_1024(nsteps=NSTEPS)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    Q_host = torch.from_numpy(w["Q"]).pin_memory()
+    u0_host = torch.zeros((NY, NX), dtype=torch.float32).pin_memory()
+    src_host = torch.from_numpy(w["src"]).pin_memory()
+    out_host = torch.empty((NY, NX), dtype=torch.float32).pin_memory()
+    Q_dev = Q_host.cuda()
+    u0_dev = u0_host.cuda()
+    src_dev = src_host.cuda()
+    idx = w["src_idx"]
+
+    def make(impl):
+        s = V.Solver((NY, NX), prec=V.F32, impl=impl, stream=stream.cuda_stream)
+        s.set_M(M)
+        return s
+
+    def run_once(s, host):
+        if host:
+            s.set_q(Q_host, w["c0"], w["omega0"])
+            s.set_state(u0_host)
+            s.set_source(idx, src_host)
+            s.step(NSTEPS, DT)
+            s.get_state(out_host)
+        else:
+            s.set_q(Q_dev, w["c0"], w["omega0"])
+            s.set_state(u0_dev)
+            s.set_source(idx, src_dev)
+            s.step(NSTEPS, DT)
+
+    def run_once_steps(s, n):
+        s.set_q(Q_dev, w["c0"], w["omega0"])
+        s.set_state(u0_dev)
+        s.set_source(idx, src_dev)
+        s.step(n, DT)
+
+    def steady_step_ms(s, n=200):
+        """Average time of one leap-frog step inside a run (graph replays)."""
+        with torch.cuda.stream(stream):
+            run_once_steps(s, 10)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(n, DT)
+            e1.record(stream)
+            e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def timed(s, host, k, wu):
+        with torch.cuda.stream(stream):
+            for _ in range(wu):
+                run_once(s, host)
+            stream.synchronize()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            tot = 0.0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(k):
+                flush.zero_()
+                stream.synchronize()
+                e0.record(stream)
+                run_once(s, host)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            torch.cuda.synchronize()
+        ms = tot
+        if dist:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    fused = make(V.IMPL_FUSED)
+    if args.ncu_steps:
+        # short run for profilers: set-up, then ncu_steps leap-frog steps
+        with torch.cuda.stream(stream):
+            run_once_steps(fused, args.ncu_steps)
+        stream.synchronize()
+        fused.close()
+        return 0
+    clocks = ClockSampler(local)
+    launches0 = V.kernel_launches()
+    clocks.start()
+    ms_dev = timed(fused, False, args.steps, args.warmup)
+    clk = clocks.stop()
+    launches = V.kernel_launches() - launches0
+    # launches in the timed region only: subtract the warm-up runs' share
+    per_run = launches / (args.steps + args.warmup)
+    gpu_launches = int(round(per_run * args.steps))
+    ms_e2e = timed(fused, True, args.steps, 1)
+    final = fused.get_state()  # wavefield after the last run (host)
+
+    lffp_fused = steady_step_ms(fused)
+    plain = make(V.IMPL_PLAIN)
+    kp = max(1, min(args.steps, 3))
+    ms_plain = timed(plain, False, kp, 1)
+    lffp_plain = steady_step_ms(plain, 50)
+
+    pts = NX * NY * NSTEPS
+    value = ws * pts * args.steps / (ms_dev * 1e-3) / 1e6
+    e2e = ws * pts * args.steps / (ms_e2e * 1e-3) / 1e6
+    plain_value = ws * pts * kp / (ms_plain * 1e-3) / 1e6
+
+    # --- roofline of the dominant kernel (isolated launches, CUDA events on the context stream)
+    prof = fused.profile_kernels(reps=20)
+    groups = -(-(M + 1) // 6)
+    launches_per_step = {"k2d_fwd_rows": 1, "k2d_fwd_cols": 1, "k2d_inv_cols": groups, "k2d_inv_rows": groups}
+    share = {nm: ms * launches_per_step.get(nm, 1) for nm, ms, _ in prof}
+    dom = max(share, key=share.get)
+    dom_ms, dom_units = [(ms, u) for nm, ms, u in prof if nm == dom][0]
+    # algorithmic flops of a complex line FFT of length L: 5 L log2 L
+    flops = dom_units * 5.0 * 1024 * 10
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x sm_max_mhz",
+            "flops_per_launch": flops, "ms_per_launch": dom_ms,
+            "kernels": {nm: {"ms": ms, "units": u, "launches_per_step": launches_per_step.get(nm, 1)}
+                        for nm, ms, u in prof}}
+
+    # --- accuracy of one operator apply on the final wavefield (outside the timed region)
+    acc = None
+    if rank == 0 and not args.skip_accuracy:
+        gamma = O.seismic_coefficients(w["Q"], w["c0"], w["omega0"])["gamma"]
+        ut = torch.from_numpy(final).cuda()
+        res = {}
+        for nm, s in (("fused", fused), ("plain", plain)):
+            o1 = torch.empty_like(ut)
+            o2 = torch.empty_like(ut)
+            s.apply_pair(ut, o1, o2)
+            s.sync()
+            res[nm] = (o1.cpu().numpy().astype(np.float64), o2.cpu().numpy().astype(np.float64))
+        r1, r2 = O.seismic_operators(final.astype(np.float64), gamma, M)
+        acc = {f"{nm}_apply_rel_l2": [O.rel_l2(res[nm][0], r1), O.rel_l2(res[nm][1], r2)] for nm in res}
+        acc["input"] = "final wavefield of the timed run (FP32), oracle FP64 on the same input"
+
+    cpu = cpu_baseline() if (rank == 0 and not args.skip_cpu) else None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_dev / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _config(), "impl": "fused",
+                "e2e": {"value": e2e, "unit": UNIT, "ms_per_step": ms_e2e / args.steps,
+                        "h2d_bytes_per_step": int(Q_host.numel() * 8 + u0_host.numel() * 4 + src_host.numel() * 8),
+                        "d2h_bytes_per_step": int(out_host.numel() * 4)},
+                "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": ms_plain / kp, "steps": kp,
+                          "ms_per_lffp_step": lffp_plain},
+                "ms_per_lffp_step": lffp_fused,
+                "fused_over_plain": value / plain_value,
+                "accuracy": acc, "gpu_launches": gpu_launches, "roofline": roof,
+                "cpu_baseline": cpu, "clocks": clk, "serve": None}
+        print(json.dumps(line))
+    fused.close()
+    plain.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
+    ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--ncu-steps", type=int, default=0,
+                    help="profiling mode: set up the workload, run this many leap-frog steps, print nothing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * vofl.h -- C ABI of the GB300 (sm_103a) variable-order fractional Laplacian
+ * wave solver, after arXiv 2311.13049 ("Fourier pseudospectral methods for the
+ * variable-order space fractional wave equations").
+ *
+ * What it computes
+ *   The seismic viscoacoustic model of Eq. (1.1),
+ *       u_tt / c^2 = eta (-Delta)^{1+gamma(x)} u + tau d/dt[(-Delta)^{1/2+gamma(x)} u],
+ *   with c = c0 cos(pi gamma/2), eta = -c0^{2 gamma} w0^{-2 gamma} cos(pi gamma),
+ *   tau = -c0^{2 gamma - 1} w0^{-2 gamma} sin(pi gamma), gamma = arctan(1/Q)/pi
+ *   (Sec. 1), on a periodic grid (Sec. 2, Sec. 2.3).  Each variable-order
+ *   operator is applied with the accelerated matrix-free scheme of Eq. (2.13):
+ *       (-Delta)^{s(x_j)} u_j ~= sum_{m=0}^{M} [s(x_j)-s0]^m
+ *              sum_{k != 0} (ln|mu_k|^2)^m / m! |mu_k|^{2 s0} u_hat_k e^{i mu_k.(x_j-a)},
+ *   s0 = grid mean of s.  Time stepping is the leap-frog (LFFP) scheme of
+ *   Eq. (3.4) extended to Eq. (1.1) (damping term by a backward difference).
+ *
+ * Conventions (all entry points)
+ *   - Every function returns a vofl_status (0 = success, < 0 = error); none
+ *     aborts or throws.  vofl_last_error() gives a message for the last error
+ *     on a context.
+ *   - Arrays are dense, C order, indexed [z][y][x] (x fastest); grid sizes
+ *     n[] and box bounds lo[], hi[] are given in (x, y, z) order.
+ *   - Grid sizes must be even (Sec. 2: "J even").  The fused kernels accept
+ *     powers of two 64..1024 per axis in 2D; other sizes and dimensions run on
+ *     the plain cuFFT path (VOFL_IMPL_PLAIN) or return VOFL_EUNSUPPORTED.
+ *   - "_dev" pointers are device pointers on the GPU current when the context
+ *     was created; others are host pointers unless an `on_device` flag says so.
+ *     Inputs are copied in (the caller keeps ownership); outputs go to caller
+ *     buffers.  Element type follows the context precision (float for
+ *     VOFL_F32, double for VOFL_F64) except where a prototype says double.
+ *   - Work is queued on the context's CUDA stream and is asynchronous unless
+ *     stated; errors of queued work are sticky and reported by vofl_sync().
+ *   - A context is not thread-safe; distinct contexts may be used concurrently.
+ */
+#ifndef VOFL_H
+#define VOFL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VOFL_API __attribute__((visibility("default")))
+#else
+#define VOFL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vofl_ctx vofl_ctx;
+
+typedef enum {
+  VOFL_OK = 0,
+  VOFL_EINVAL = -1,        /* bad argument */
+  VOFL_ENOMEM = -2,        /* device allocation failed */
+  VOFL_ECUDA = -3,         /* a CUDA / cuFFT call failed */
+  VOFL_ETIMEDOUT = -4,     /* a bounded device wait gave up */
+  VOFL_ESTATE = -5,        /* call out of order (e.g. step before set_q) */
+  VOFL_EUNSUPPORTED = -6   /* size / dimension / precision not built */
+} vofl_status;
+
+typedef enum { VOFL_F32 = 0, VOFL_F64 = 1 } vofl_prec;
+
+/* The two operators of Eq. (1.1). */
+typedef enum {
+  VOFL_OP_1PG = 0, /* (-Delta)^{1+gamma(x)}   */
+  VOFL_OP_HPG = 1  /* (-Delta)^{1/2+gamma(x)} */
+} vofl_op;
+
+/* Implementation of the operator/step: the fused hand-written kernels, or
+ * the plain baseline (cuFFT transforms + separate multiply / accumulate /
+ * update kernels, same arithmetic). */
+typedef enum { VOFL_IMPL_FUSED = 0, VOFL_IMPL_PLAIN = 1 } vofl_impl;
+
+/* Create a context for a periodic box prod_m [lo_m, hi_m) with n_m points
+ * per axis (Sec. 2.3: x_j = a + j h, h = (b-a)/J).  ndim in {1,2,3}.
+ * prec: VOFL_F32 or VOFL_F64 arithmetic for transforms and updates (the
+ * per-model coefficients are always computed in double).  stream: a
+ * cudaStream_t, or NULL for a stream the context creates itself (a blocking
+ * stream, hence ordered with the legacy default stream).  On success *out
+ * owns all device state; free it with vofl_destroy. */
+VOFL_API int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo,
+                         const double* hi, int prec, int impl, void* stream);
+VOFL_API void vofl_destroy(vofl_ctx* ctx);
+
+/* Quality-factor model (Sec. 1): gamma = arctan(1/Q)/pi, then c, eta, tau
+ * with scalar c0, omega0.  Q has prod(n) doubles, host or device; all Q > 0.
+ * Derives, in double on the GPU: gamma0 = grid mean of gamma (the s0 of
+ * Eq. (2.13) for both operators, s0 = 1+gamma0 and 1/2+gamma0),
+ * delta = gamma - gamma0, A = c^2 eta, B = c^2 tau, and the spectral tables
+ * |mu_k|^{2 s0}, ln|mu_k|^2.  Resets the time stepper. */
+VOFL_API int vofl_set_q(vofl_ctx* ctx, const double* Q, int on_device, double c0,
+               double omega0);
+
+/* As vofl_set_q with gamma given directly (gamma = 0 allowed: the classical
+ * acoustic wave equation, Sec. 1).  c0_field (prod(n) doubles or NULL) lets
+ * c0 vary in space as in the paper's two-layer example (Sec. 4.3, Example 3);
+ * when NULL the scalar c0 is used. */
+VOFL_API int vofl_set_gamma(vofl_ctx* ctx, const double* gamma, const double* c0_field,
+                   int on_device, double c0, double omega0);
+
+/* Highest Taylor power M of Eq. (2.13): each operator apply runs the M+1
+ * terms m = 0..M.  0 <= M <= 40.  Default 8. */
+VOFL_API int vofl_set_M(vofl_ctx* ctx, int M);
+
+/* out_dev = (-Delta)_h^{s(x)} u_dev for op (Eq. (2.13)), s = 1+gamma or
+ * 1/2+gamma.  u_dev, out_dev: device arrays of prod(n) elements of the
+ * context precision; they may not alias the context's state.  Async. */
+VOFL_API int vofl_apply(vofl_ctx* ctx, int op, const void* u_dev, void* out_dev);
+
+/* Both operators on the same input (one forward transform, both sums). */
+VOFL_API int vofl_apply_pair(vofl_ctx* ctx, const void* u_dev, void* out1_dev,
+                    void* out2_dev);
+
+/* Initial state u(x,0) = phi, u_t(x,0) = psi (Eq. (3.4b-c) start data);
+ * psi may be NULL (zero).  Arrays of the context precision, host or device.
+ * Resets the step counter. */
+VOFL_API int vofl_set_state(vofl_ctx* ctx, const void* u0, const void* v0,
+                   int on_device);
+
+/* Point source: adds r_n / h^d at grid index idx (x,y,z order) to the right
+ * hand side of Eq. (1.1) at t_n = n dt, where r_n = samples[n] (double) for
+ * n < nsamples and 0 afterwards; n counts from the start of the run.
+ * nsamples = 0 removes the source.  Host or device samples. */
+VOFL_API int vofl_set_source(vofl_ctx* ctx, const int64_t* idx, const double* samples,
+                    int64_t nsamples, int on_device);
+
+/* Advance nsteps leap-frog steps of size dt (Eq. (3.4a) for Eq. (1.1)):
+ *   u^{n+1} = 2u^n - u^{n-1} + dt^2 [A L1 u^n + B (L2 u^n - L2 u^{n-1})/dt + f_n],
+ * the first step of a run being the Taylor start
+ *   u^1 = u^0 + dt psi + dt^2/2 [A L1 u^0 + B L2 psi + f_0]   (Eq. (3.4c)).
+ * dt must stay the same for the whole run.  Async (steps are replayed from
+ * a captured CUDA graph when the path allows it). */
+VOFL_API int vofl_step(vofl_ctx* ctx, int64_t nsteps, double dt);
+
+/* Copy the current wavefield u^n (n = steps taken) to u_out (host or device,
+ * context precision).  Synchronises the stream when the target is host
+ * memory. */
+VOFL_API int vofl_get_state(vofl_ctx* ctx, void* u_out, int on_device);
+
+/* Number of steps taken in the current run. */
+VOFL_API int64_t vofl_steps_taken(const vofl_ctx* ctx);
+
+/* Wait for queued work; returns the first sticky error of that work. */
+VOFL_API int vofl_sync(vofl_ctx* ctx);
+
+VOFL_API const char* vofl_last_error(const vofl_ctx* ctx);
+
+/* Device bytes a context of this shape needs (for admission by footprint). */
+VOFL_API size_t vofl_footprint_bytes(int ndim, const int64_t* n, int prec, int impl,
+                            int M);
+
+/* Number of kernels this library has launched in the calling process
+ * (counted at the launch sites; a captured graph counts its kernels each
+ * time it is replayed). */
+VOFL_API uint64_t vofl_kernel_launches(void);
+
+/* Time each kernel kind of one fused step in isolation (CUDA events on the
+ * context stream, reps launches each, after one warm-up).  names_out gets a
+ * ';'-separated list of kernel names (cap bytes), ms_out (cap entries) the
+ * average milliseconds per launch, units_out the lines (1D transforms)
+ * each launch processes.  Returns the number of entries written, or < 0. */
+VOFL_API int vofl_profile_kernels(vofl_ctx* ctx, int reps, char* names_out,
+                         size_t names_cap, double* ms_out,
+                         double* units_out, int cap);
+
+/* Library version string. */
+VOFL_API const char* vofl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOFL_H */

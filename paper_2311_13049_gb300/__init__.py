@@ -1,0 +1,231 @@
+"""Python binding of libvofl (include/vofl.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+(host) and torch CUDA tensors (device) to pointers and checks return codes.
+There is no CPU fallback: the first call fails loudly when the library has
+not been built (``python -m paper_2311_13049_gb300.build``).
+
+Shapes are given in array order (slowest axis first, as numpy/torch); box
+bounds ``lo``/``hi`` in (x, y, z) order, as in the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libvofl.so")
+
+_LIB = None
+
+F32, F64 = 0, 1
+OP_1PG, OP_HPG = 0, 1
+IMPL_FUSED, IMPL_PLAIN = 0, 1
+_STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ESTATE",
+           -6: "EUNSUPPORTED"}
+
+_i64p = C.POINTER(C.c_int64)
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+# exported symbols and their signatures: name -> (restype, argtypes)
+SIGNATURES = {
+    "vofl_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _i64p, _dp, _dp, C.c_int, C.c_int, _vp]),
+    "vofl_destroy": (None, [_vp]),
+    "vofl_set_q": (C.c_int, [_vp, _vp, C.c_int, C.c_double, C.c_double]),
+    "vofl_set_gamma": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_double]),
+    "vofl_set_M": (C.c_int, [_vp, C.c_int]),
+    "vofl_apply": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "vofl_apply_pair": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "vofl_set_state": (C.c_int, [_vp, _vp, _vp, C.c_int]),
+    "vofl_set_source": (C.c_int, [_vp, _i64p, _vp, C.c_int64, C.c_int]),
+    "vofl_step": (C.c_int, [_vp, C.c_int64, C.c_double]),
+    "vofl_get_state": (C.c_int, [_vp, _vp, C.c_int]),
+    "vofl_steps_taken": (C.c_int64, [_vp]),
+    "vofl_sync": (C.c_int, [_vp]),
+    "vofl_last_error": (C.c_char_p, [_vp]),
+    "vofl_footprint_bytes": (C.c_size_t, [C.c_int, _i64p, C.c_int, C.c_int, C.c_int]),
+    "vofl_kernel_launches": (C.c_uint64, []),
+    "vofl_profile_kernels": (C.c_int, [_vp, C.c_int, C.c_char_p, C.c_size_t, _dp, _dp, C.c_int]),
+    "vofl_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded libvofl.so (loaded on first use).  Raises if the library
+    has not been built: there is no fallback implementation."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"libvofl.so not found at {LIB_PATH}; build it with "
+                "`python -m paper_2311_13049_gb300.build` (needs nvcc)")
+        handle = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(handle, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = handle
+    return _LIB
+
+
+class VoflError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def version() -> str:
+    return lib().vofl_version().decode()
+
+
+def kernel_launches() -> int:
+    return int(lib().vofl_kernel_launches())
+
+
+def footprint_bytes(shape, prec=F32, impl=IMPL_FUSED, M=8) -> int:
+    n = (C.c_int64 * 3)(*[int(v) for v in reversed(shape)])
+    return int(lib().vofl_footprint_bytes(len(shape), n, prec, impl, M))
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype, what):
+    """(pointer, on_device) of a numpy array (host) or torch CUDA tensor."""
+    if a is None:
+        return None, 0
+    if _is_torch(a):
+        import torch
+        want = torch.float32 if dtype == np.float32 else torch.float64
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"{what}: expected a contiguous {want} tensor")
+        # a CPU tensor is host memory owned by the caller
+        return C.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+    if not isinstance(a, np.ndarray):
+        raise TypeError(f"{what}: expected a numpy array or a torch tensor")
+    arr = a
+    if arr.dtype != dtype or not arr.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"{what}: expected a C-contiguous {np.dtype(dtype).name} array")
+    return C.c_void_p(arr.ctypes.data), 0
+
+
+class Solver:
+    """One simulation context (vofl_ctx)."""
+
+    def __init__(self, shape, lo=None, hi=None, prec=F32, impl=IMPL_FUSED, stream=None):
+        self.shape = tuple(int(v) for v in shape)
+        d = len(self.shape)
+        lo = [-np.pi] * d if lo is None else [float(v) for v in lo]
+        hi = [np.pi] * d if hi is None else [float(v) for v in hi]
+        self.ndim, self.prec, self.impl = d, prec, impl
+        self.dtype = np.float32 if prec == F32 else np.float64
+        n = (C.c_int64 * 3)(*[v for v in reversed(self.shape)])
+        lo_c = (C.c_double * 3)(*lo)
+        hi_c = (C.c_double * 3)(*hi)
+        h = C.c_void_p()
+        s = C.c_void_p(stream) if stream else None
+        rc = lib().vofl_create(C.byref(h), d, n, lo_c, hi_c, prec, impl, s)
+        if rc != 0:
+            raise VoflError(rc, "vofl_create failed")
+        self._h = h
+        self._keep = []
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise VoflError(rc, lib().vofl_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vofl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- model -------------------------------------------------------------
+    def set_q(self, Q, c0=1.0, omega0=2 * np.pi):
+        p, dev = _ptr(Q, np.float64, "Q")
+        self._check(lib().vofl_set_q(self._h, p, dev, float(c0), float(omega0)))
+
+    def set_gamma(self, gamma, c0=1.0, omega0=2 * np.pi, c0_field=None):
+        p, dev = _ptr(gamma, np.float64, "gamma")
+        pc, devc = _ptr(c0_field, np.float64, "c0_field")
+        if c0_field is not None and devc != dev:
+            raise TypeError("gamma and c0_field must both be host or both be device arrays")
+        self._check(lib().vofl_set_gamma(self._h, p, pc, dev, float(c0), float(omega0)))
+
+    def set_M(self, M):
+        self._check(lib().vofl_set_M(self._h, int(M)))
+
+    # -- operators (device tensors) ------------------------------------------
+    def apply(self, op, u, out):
+        pu, du = _ptr(u, self.dtype, "u")
+        po, do = _ptr(out, self.dtype, "out")
+        if not (du and do):
+            raise TypeError("apply takes device tensors")
+        self._check(lib().vofl_apply(self._h, int(op), pu, po))
+
+    def apply_pair(self, u, out1, out2):
+        pu, du = _ptr(u, self.dtype, "u")
+        p1, _ = _ptr(out1, self.dtype, "out1")
+        p2, _ = _ptr(out2, self.dtype, "out2")
+        self._check(lib().vofl_apply_pair(self._h, pu, p1, p2))
+
+    # -- time stepping -------------------------------------------------------
+    def set_state(self, u0, v0=None):
+        p0, d0 = _ptr(u0, self.dtype, "u0")
+        p1, d1 = _ptr(v0, self.dtype, "v0")
+        if v0 is not None and d1 != d0:
+            raise TypeError("u0 and v0 must both be host or both be device arrays")
+        self._check(lib().vofl_set_state(self._h, p0, p1, d0))
+
+    def set_source(self, idx, samples):
+        """idx in (x, y, z) order; samples r_n (float64) for n = 0.."""
+        if samples is None or len(samples) == 0:
+            self._check(lib().vofl_set_source(self._h, None, None, 0, 0))
+            return
+        i = (C.c_int64 * 3)(*[int(v) for v in idx])
+        p, dev = _ptr(samples, np.float64, "samples")
+        self._check(lib().vofl_set_source(self._h, i, p, len(samples), dev))
+
+    def step(self, nsteps, dt):
+        self._check(lib().vofl_step(self._h, int(nsteps), float(dt)))
+
+    def steps_taken(self):
+        return int(lib().vofl_steps_taken(self._h))
+
+    def get_state(self, out=None):
+        """Current u^n into `out` (torch CUDA tensor or numpy array), or a new
+        numpy array."""
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        p, dev = _ptr(out, self.dtype, "out")
+        self._check(lib().vofl_get_state(self._h, p, dev))
+        return out
+
+    def sync(self):
+        self._check(lib().vofl_sync(self._h))
+
+    def profile_kernels(self, reps=20):
+        names = C.create_string_buffer(1024)
+        ms = (C.c_double * 16)()
+        units = (C.c_double * 16)()
+        k = lib().vofl_profile_kernels(self._h, int(reps), names, 1024, ms, units, 16)
+        if k < 0:
+            self._check(k)
+        nm = names.value.decode().split(";") if k > 0 else []
+        return [(nm[i], ms[i], units[i]) for i in range(k)]

@@ -1,0 +1,108 @@
+"""Build the CUDA library libvofl.so in-tree (no cmake, no pip).
+
+Each translation unit under csrc/ is compiled by nvcc for sm_103a in parallel,
+then linked with cuFFT into paper_2311_13049_gb300/_build/libvofl.so.  A
+rebuild only recompiles units whose source or headers changed.
+
+    python -m paper_2311_13049_gb300.build [--verbose-ptxas] [--force]
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(PKG, "_build")
+LIB = os.path.join(BUILD, "libvofl.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+              "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
+
+
+def _nvcc():
+    cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cand):
+        raise RuntimeError("nvcc not found (CUDA 13 toolkit required)")
+    return cand
+
+
+def _sources():
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def _headers():
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    hs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
+    return sorted(hs)
+
+
+def _digest(paths, extra=""):
+    h = hashlib.sha256(extra.encode())
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(p.encode())
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _compile(src, verbose_ptxas):
+    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    stamp = obj + ".sha"
+    flags = NVCC_FLAGS + (["-Xptxas", "-v"] if verbose_ptxas else [])
+    dig = _digest([src] + _headers(), " ".join(ARCH + flags))
+    if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == dig:
+        return obj, ""
+    cmd = [_nvcc()] + ARCH + flags + ["-c", src, "-o", obj]
+    p = subprocess.run(cmd, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{p.stderr}")
+    with open(stamp, "w") as f:
+        f.write(dig)
+    return obj, p.stderr
+
+
+def build(verbose_ptxas: bool = False, force: bool = False, quiet: bool = True) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libvofl.so; returns its path."""
+    os.makedirs(BUILD, exist_ok=True)
+    if force:
+        for f in os.listdir(BUILD):
+            os.remove(os.path.join(BUILD, f))
+    srcs = _sources()
+    logs = []
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        futs = [ex.submit(_compile, s, verbose_ptxas) for s in srcs]
+        objs = []
+        for fu in futs:
+            o, log = fu.result()
+            objs.append(o)
+            if log:
+                logs.append(log)
+    link_dig = _digest(objs)
+    stamp = LIB + ".sha"
+    if not (os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == link_dig):
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcufft", "-lcudart"]
+        p = subprocess.run(cmd, capture_output=True, text=True)
+        if p.returncode != 0:
+            raise RuntimeError(f"link failed:\n{p.stderr}")
+        with open(stamp, "w") as f:
+            f.write(link_dig)
+    if logs and not quiet:
+        sys.stderr.write("".join(logs))
+    return LIB
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--verbose-ptxas", action="store_true")
+    ap.add_argument("--force", action="store_true")
+    a = ap.parse_args()
+    print(build(verbose_ptxas=a.verbose_ptxas, force=a.force, quiet=False))

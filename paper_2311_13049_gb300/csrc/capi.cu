@@ -1,0 +1,389 @@
+// capi.cu -- the C ABI declared in include/vofl.h: context lifecycle,
+// argument checks, host/device copies, the leap-frog run state machine and
+// CUDA-graph replay of steps.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+using namespace vofl;
+
+namespace {
+
+const char* kVersion = "vofl 0.1.0 (sm_103a)";
+
+size_t elem_size(const vofl_ctx* c) { return c->prec == VOFL_F64 ? 8 : 4; }
+
+void drop_graphs(vofl_ctx* c) {
+  for (auto& g : c->step_graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+void reset_run(vofl_ctx* c) {
+  c->steps = 0;
+  c->cur = 0;
+}
+
+vofl_ctx::GraphKey current_key(const vofl_ctx* c) {
+  vofl_ctx::GraphKey k;
+  k.dt = c->dt;
+  k.M = c->M;
+  k.src_flat = c->nsrc > 0 ? c->src_flat : -1;
+  k.d_src = c->d_src;
+  k.nsrc = c->nsrc;
+  return k;
+}
+
+int check_ctx(vofl_ctx* c) { return c ? VOFL_OK : VOFL_EINVAL; }
+
+int upload(vofl_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
+  VOFL_CUDA(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               c->stream));
+  if (!on_device) VOFL_CUDA(c, cudaStreamSynchronize(c->stream));  // host buffer may be pageable/transient
+  return VOFL_OK;
+}
+
+// Capture one STEP of the engine into a graph for the current `cur`.
+int capture_step(vofl_ctx* c) {
+  const uint64_t before = g_kernel_launches.load();
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return VOFL_EUNSUPPORTED;
+  }
+  int st = c->eng->step(c, EPI_STEP, true);
+  e = cudaStreamEndCapture(c->stream, &g);
+  g_kernel_launches.store(before);  // captured launches are counted when replayed
+  if (st != VOFL_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return VOFL_EUNSUPPORTED;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return VOFL_EUNSUPPORTED;
+  }
+  c->step_graph[c->cur] = ex;
+  c->step_graph_kernels = c->eng->kernels_per_step(c);
+  return VOFL_OK;
+}
+
+int one_step(vofl_ctx* c) {
+  const vofl_ctx::GraphKey key = current_key(c);
+  if (!(key == c->graph_key)) {
+    drop_graphs(c);
+    c->graph_key = key;
+  }
+  if (c->graphs_ok && !c->step_graph[c->cur]) {
+    if (capture_step(c) != VOFL_OK) c->graphs_ok = false;
+  }
+  if (c->graphs_ok && c->step_graph[c->cur]) {
+    VOFL_CUDA(c, cudaGraphLaunch(c->step_graph[c->cur], c->stream));
+    count_launch(c->step_graph_kernels);
+  } else {
+    int st = c->eng->step(c, EPI_STEP, true);
+    if (st) return st;
+  }
+  c->cur ^= 1;
+  c->steps += 1;
+  return VOFL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vofl_version(void) { return kVersion; }
+
+uint64_t vofl_kernel_launches(void) { return g_kernel_launches.load(); }
+
+size_t vofl_footprint_bytes(int ndim, const int64_t* n, int prec, int impl, int M) {
+  if (ndim < 1 || ndim > 3 || !n) return 0;
+  long long N = 1;
+  for (int i = 0; i < ndim; ++i) N *= n[i];
+  const size_t r = prec == VOFL_F64 ? 8 : 4;
+  size_t b = r * (size_t)N * 6 + sizeof(double) * (size_t)N + 8192;  // delta A B u0 u1 l2p, gamma
+  if (impl == VOFL_IMPL_FUSED && fused2d_supported(ndim, n, prec))
+    b += fused2d_footprint(n, M);
+  else
+    b += plain_footprint(ndim, n, prec);
+  return b;
+}
+
+int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, const double* hi, int prec, int impl,
+                void* stream) {
+  if (!out) return VOFL_EINVAL;
+  *out = nullptr;
+  if (ndim < 1 || ndim > 3 || !n || !lo || !hi) return VOFL_EINVAL;
+  if (prec != VOFL_F32 && prec != VOFL_F64) return VOFL_EINVAL;
+  if (impl != VOFL_IMPL_FUSED && impl != VOFL_IMPL_PLAIN) return VOFL_EINVAL;
+  long long N = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (n[i] < 2 || (n[i] % 2) != 0 || n[i] > (1 << 20)) return VOFL_EINVAL;
+    if (!(hi[i] > lo[i]) || !std::isfinite(lo[i]) || !std::isfinite(hi[i])) return VOFL_EINVAL;
+    N *= n[i];
+  }
+  if (N > (1LL << 34)) return VOFL_EINVAL;
+  if (impl == VOFL_IMPL_FUSED && !fused2d_supported(ndim, n, prec)) return VOFL_EUNSUPPORTED;
+
+  vofl_ctx* c = new vofl_ctx();
+  c->ndim = ndim;
+  c->N = N;
+  c->prec = prec;
+  c->impl = impl;
+  for (int i = 0; i < ndim; ++i) {
+    c->n[i] = n[i];
+    c->lo[i] = lo[i];
+    c->hi[i] = hi[i];
+  }
+  cudaGetDevice(&c->device);
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else if (cudaStreamCreate(&c->stream) != cudaSuccess) {  // blocking: ordered with the legacy stream
+    delete c;
+    return VOFL_ECUDA;
+  } else {
+    c->own_stream = true;
+  }
+  const size_t r = elem_size(c);
+  bool ok = true;
+  ok &= cudaMalloc(&c->delta, r * N) == cudaSuccess;
+  ok &= cudaMalloc(&c->A, r * N) == cudaSuccess;
+  ok &= cudaMalloc(&c->B, r * N) == cudaSuccess;
+  ok &= cudaMalloc(&c->u[0], r * N) == cudaSuccess;
+  ok &= cudaMalloc(&c->u[1], r * N) == cudaSuccess;
+  ok &= cudaMalloc(&c->l2p, r * N) == cudaSuccess;
+  ok &= cudaMalloc(&c->d_gamma, sizeof(double) * N) == cudaSuccess;
+  ok &= cudaMalloc(&c->d_scratch, sizeof(double) * 1024) == cudaSuccess;
+  ok &= cudaMalloc(&c->d_step, sizeof(int) * 4) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    vofl_destroy(c);
+    return VOFL_ENOMEM;
+  }
+  cudaMemsetAsync(c->u[0], 0, r * N, c->stream);
+  cudaMemsetAsync(c->u[1], 0, r * N, c->stream);
+  cudaMemsetAsync(c->l2p, 0, r * N, c->stream);
+  cudaMemsetAsync(c->d_step, 0, sizeof(int) * 4, c->stream);
+  int st = VOFL_OK;
+  if (impl == VOFL_IMPL_FUSED)
+    c->eng = make_fused2d(c, &st);
+  else
+    c->eng = make_plain(c, &st);
+  if (!c->eng) {
+    vofl_destroy(c);
+    return st ? st : VOFL_ECUDA;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    vofl_destroy(c);
+    return VOFL_ECUDA;
+  }
+  *out = c;
+  return VOFL_OK;
+}
+
+void vofl_destroy(vofl_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  delete c->eng;
+  cudaFree(c->delta);
+  cudaFree(c->A);
+  cudaFree(c->B);
+  cudaFree(c->u[0]);
+  cudaFree(c->u[1]);
+  cudaFree(c->l2p);
+  cudaFree(c->d_gamma);
+  cudaFree(c->d_scratch);
+  cudaFree(c->d_step);
+  cudaFree(c->d_src);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* vofl_last_error(const vofl_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+static int finish_model(vofl_ctx* c, const double* d_c0field, double c0, double omega0) {
+  int st = model_from_gamma(c, c->d_gamma, d_c0field, c0, omega0);
+  if (st) return st;
+  st = c->eng->set_model(c);
+  if (st) return st;
+  c->model_set = true;
+  reset_run(c);
+  return VOFL_OK;
+}
+
+int vofl_set_q(vofl_ctx* c, const double* Q, int on_device, double c0, double omega0) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (!Q) return set_err(c, VOFL_EINVAL, "Q is null");
+  if (!(c0 > 0) || !(omega0 > 0)) return set_err(c, VOFL_EINVAL, "c0 and omega0 must be positive");
+  int st = upload(c, c->d_gamma, Q, sizeof(double) * c->N, on_device);
+  if (st) return st;
+  st = model_gamma_from_q(c, c->d_gamma, c->d_gamma);
+  if (st) return st;
+  return finish_model(c, nullptr, c0, omega0);
+}
+
+int vofl_set_gamma(vofl_ctx* c, const double* gamma, const double* c0_field, int on_device, double c0,
+                   double omega0) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (!gamma) return set_err(c, VOFL_EINVAL, "gamma is null");
+  if (!(omega0 > 0) || (!c0_field && !(c0 > 0))) return set_err(c, VOFL_EINVAL, "c0 and omega0 must be positive");
+  int st = upload(c, c->d_gamma, gamma, sizeof(double) * c->N, on_device);
+  if (st) return st;
+  double* d_c0 = nullptr;
+  if (c0_field) {
+    VOFL_CUDA(c, cudaMalloc(&d_c0, sizeof(double) * c->N));
+    st = upload(c, d_c0, c0_field, sizeof(double) * c->N, on_device);
+    if (st) {
+      cudaFree(d_c0);
+      return st;
+    }
+  }
+  st = finish_model(c, d_c0, c0, omega0);
+  if (d_c0) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(d_c0);
+  }
+  return st;
+}
+
+int vofl_set_M(vofl_ctx* c, int M) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (M < 0 || M > 40) return set_err(c, VOFL_EINVAL, "M must be in [0, 40]");
+  c->M = M;  // captured graphs are re-keyed on the next step
+  return VOFL_OK;
+}
+
+int vofl_apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (!c->model_set) return set_err(c, VOFL_ESTATE, "set_q / set_gamma first");
+  if (!u || (!o1 && !o2)) return set_err(c, VOFL_EINVAL, "null array");
+  return c->eng->apply_pair(c, u, o1, o2);
+}
+
+int vofl_apply(vofl_ctx* c, int op, const void* u, void* out) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (op != VOFL_OP_1PG && op != VOFL_OP_HPG) return set_err(c, VOFL_EINVAL, "unknown operator");
+  return vofl_apply_pair(c, u, op == VOFL_OP_1PG ? out : nullptr, op == VOFL_OP_HPG ? out : nullptr);
+}
+
+int vofl_set_state(vofl_ctx* c, const void* u0, const void* v0, int on_device) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (!u0) return set_err(c, VOFL_EINVAL, "u0 is null");
+  const size_t b = elem_size(c) * c->N;
+  reset_run(c);
+  int st = upload(c, c->u[0], u0, b, on_device);
+  if (st) return st;
+  if (v0) {
+    st = upload(c, c->u[1], v0, b, on_device);
+    if (st) return st;
+    c->psi_nonzero = true;
+  } else {
+    VOFL_CUDA(c, cudaMemsetAsync(c->u[1], 0, b, c->stream));
+    c->psi_nonzero = false;
+  }
+  VOFL_CUDA(c, cudaMemsetAsync(c->l2p, 0, b, c->stream));
+  c->state_set = true;
+  return VOFL_OK;
+}
+
+int vofl_set_source(vofl_ctx* c, const int64_t* idx, const double* samples, int64_t nsamples, int on_device) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (nsamples <= 0) {
+    c->nsrc = 0;
+    c->src_flat = -1;
+    return VOFL_OK;
+  }
+  if (!idx || !samples) return set_err(c, VOFL_EINVAL, "null source argument");
+  long long flat = 0, stride = 1;
+  for (int i = 0; i < c->ndim; ++i) {
+    if (idx[i] < 0 || idx[i] >= c->n[i]) return set_err(c, VOFL_EINVAL, "source index outside the grid");
+    flat += idx[i] * stride;
+    stride *= c->n[i];
+  }
+  if (nsamples > c->src_cap) {
+    drop_graphs(c);  // graphs hold the old pointer
+    VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_src);
+    c->d_src = nullptr;
+    VOFL_CUDA(c, cudaMalloc(&c->d_src, sizeof(double) * nsamples));
+    c->src_cap = nsamples;
+  }
+  int st = upload(c, c->d_src, samples, sizeof(double) * nsamples, on_device);
+  if (st) return st;
+  c->nsrc = nsamples;
+  c->src_flat = flat;
+  return VOFL_OK;
+}
+
+int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
+  if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return set_err(c, VOFL_EINVAL, "bad nsteps or dt");
+  if (nsteps == 0) return VOFL_OK;
+  if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");
+  if (c->steps == 0) {
+    c->dt = dt;
+    VOFL_CUDA(c, cudaMemsetAsync(c->d_step, 0, sizeof(int), c->stream));
+    if (c->psi_nonzero) {
+      // L2 psi for the Taylor start, into the l2p buffer
+      int st = c->eng->apply_pair(c, c->u[1], nullptr, c->l2p);
+      if (st) return st;
+    }
+    int st = c->eng->step(c, EPI_START, false);
+    if (st) return st;
+    c->cur ^= 1;
+    c->steps = 1;
+    --nsteps;
+  }
+  for (int64_t i = 0; i < nsteps; ++i) {
+    int st = one_step(c);
+    if (st) return st;
+  }
+  return VOFL_OK;
+}
+
+int64_t vofl_steps_taken(const vofl_ctx* c) { return c ? c->steps : -1; }
+
+int vofl_get_state(vofl_ctx* c, void* u_out, int on_device) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (!u_out) return set_err(c, VOFL_EINVAL, "null output");
+  const size_t b = elem_size(c) * c->N;
+  VOFL_CUDA(c, cudaMemcpyAsync(u_out, c->u[c->cur], b, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               c->stream));
+  if (!on_device) VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VOFL_OK;
+}
+
+int vofl_sync(vofl_ctx* c) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  VOFL_CUDA(c, cudaGetLastError());
+  return VOFL_OK;
+}
+
+int vofl_profile_kernels(vofl_ctx* c, int reps, char* names_out, size_t names_cap, double* ms_out, double* units_out,
+                         int cap) {
+  if (check_ctx(c)) return VOFL_EINVAL;
+  if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
+  if (reps < 1 || !names_out || !ms_out || !units_out) return set_err(c, VOFL_EINVAL, "bad profile arguments");
+  std::string names;
+  int k = c->eng->profile(c, reps, names, ms_out, units_out, cap);
+  if (k < 0) return k;
+  if (names.size() + 1 > names_cap) return set_err(c, VOFL_EINVAL, "names buffer too small");
+  std::memcpy(names_out, names.c_str(), names.size() + 1);
+  return k;
+}
+
+}  // extern "C"

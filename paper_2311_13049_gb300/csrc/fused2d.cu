@@ -1,0 +1,605 @@
+// fused2d.cu -- fused FP32 kernels for the 2D matrix-free operator pair
+// (-Delta)^{1+gamma(x)} u, (-Delta)^{1/2+gamma(x)} u (Eq. (2.13) of
+// arXiv 2311.13049) and the leap-frog step of Eq. (1.1) (Eq. (3.4)).
+//
+// Data path of one step on an nx * ny grid (x fastest), H = nx/2:
+//   F1 k2d_fwd_rows   u (ny x nx f32) -> T (ny x (H+1) c64)
+//        one warp-line per PAIR of rows: the complex FFT of u[y0] + i u[y0+1]
+//        is split into the two half spectra (real-data two-for-one);
+//   F2 k2d_fwd_cols   T -> Uh ((H+1) x ny c64, column-major)
+//        complex FFT along y of each of the H+1 columns; Uh = N * u_hat;
+//   then for Taylor groups g = K-1 .. 0 (terms [m_lo, m_hi)):
+//   I1 k2d_inv_cols   Uh -> Z[g] (per term and operator, ny x (H+1) c64)
+//        multiplier P_op(k) ln|mu_k|^{2m}/m! (P_op = |mu|^{2 s0_op}/N) applied
+//        in registers by the recurrence t_m = t_{m-1} ln|mu|^2 / m, then the
+//        inverse FFT along y; the M+1 multiplied spectra never exist in memory;
+//   I2 k2d_inv_rows   Z[g] -> accumulators / epilogue
+//        inverse FFT along x of BOTH operators at once: the row spectra A
+//        (operator 1) and B (operator 2) are Hermitian, so one complex
+//        inverse FFT of A + iB returns L1-term + i L2-term; the delta^m
+//        weights of Eq. (2.13) are applied by Horner's rule in registers
+//        (acc = Y_m + delta * acc, m descending), and the last group runs the
+//        pointwise leap-frog update (or writes the operator values).
+// Only the between-group partial sums (2 fields) and one group of spectra
+// (G terms) are stored: storage O(N) in M, against O(MN) for storing every
+// term.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fft_warp.cuh"
+#include "internal.h"
+
+namespace vofl {
+
+namespace {
+
+constexpr int WARPS = 8;           // warps per CTA in every fused kernel
+constexpr int THREADS = WARPS * 32;
+
+template <int N>
+constexpr int warp_stride() {
+  // consecutive warp buffers start 2 (mod 16) float2 slots apart, so a
+  // half-warp reading one element from each of 8 warp buffers for 2
+  // consecutive rows touches 16 distinct bank pairs
+  return (LineFFT<N>::WARP_SLOTS + 15) / 16 * 16 + 2;
+}
+template <int N>
+constexpr size_t dyn_smem() {
+  return (size_t)WARPS * warp_stride<N>() * sizeof(float2);
+}
+
+// -------------------------------------------------------------------------
+// F1: forward FFT along x of two rows at once, split into half spectra.
+// -------------------------------------------------------------------------
+template <int NX>
+__global__ void __launch_bounds__(THREADS) k2d_fwd_rows(const float* __restrict__ u, float2* __restrict__ T, int ny,
+                                                        int pT, float ryy, const float2* __restrict__ twx,
+                                                        int* step_ctr, int inc_step) {
+  using F = LineFFT<NX>;
+  constexpr int E = F::E, LANES = F::LANES, H = NX / 2;
+  __shared__ float2 s_tw[NX];
+  extern __shared__ float2 s_buf[];
+  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
+  if (inc_step && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = lane % LANES, line = lane / LANES;
+  float2* wbuf = s_buf + warp * warp_stride<NX>();
+  const int pair = (blockIdx.x * WARPS + warp) * F::LPW + line;
+  const bool active = pair < ny / 2;
+  const int y0 = 2 * (active ? pair : 0);
+  const float* r0 = u + (size_t)y0 * NX;
+  const float* r1 = r0 + NX;
+  const float* rm = u + (size_t)(y0 == 0 ? ny - 1 : y0 - 1) * NX;
+  const float* rp = u + (size_t)(y0 + 2 == ny ? 0 : y0 + 2) * NX;
+  // w = D_xx u + (h_x/h_y)^2 D_yy u (second differences, no 1/h^2): its DFT is
+  // lambda_k u_hat_k exactly, with lambda_k = -4 sin^2(pi k1/nx) - 4 (h_x/h_y)^2
+  // sin^2(pi k2/ny); 1/lambda_k is folded into the multiplier table.  On FP32
+  // data the neighbour differences are exact or carry a rounding relative to
+  // themselves, so w's transform keeps the high-wavenumber content that an
+  // FP32 transform of u would bury under round-off of size eps*|u|.
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int x = li + LANES * m;
+    const int xm = (x - 1) & (NX - 1), xp = (x + 1) & (NX - 1);
+    const float a = __ldg(r0 + x), b = __ldg(r1 + x);
+    const float dxa = (__ldg(r0 + xp) - a) - (a - __ldg(r0 + xm));
+    const float dxb = (__ldg(r1 + xp) - b) - (b - __ldg(r1 + xm));
+    const float dya = (b - a) - (a - __ldg(rm + x));
+    const float dyb = (__ldg(rp + x) - b) - (b - a);
+    v[m] = make_float2(dxa + ryy * dya, dxb + ryy * dyb);
+  }
+  fft_line<NX, false>(v, wbuf, s_tw, li, line);
+  float2* lb = wbuf + line * F::PAD_LINE;
+#pragma unroll
+  for (int m = 0; m < E; ++m) lb[F::pad(li + LANES * m)] = v[m];
+  __syncwarp();
+  float2* t0 = T + (size_t)y0 * pT;
+  float2* t1 = t0 + pT;
+  for (int k = li; k <= H; k += LANES) {
+    const float2 a = lb[F::pad(k)];
+    const float2 b = lb[F::pad((NX - k) & (NX - 1))];
+    // A = (X_k + conj X_{-k})/2 (row y0), B = (X_k - conj X_{-k})/(2i) (row y0+1)
+    if (active) {
+      t0[k] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+      t1[k] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+    }
+  }
+}
+
+// -------------------------------------------------------------------------
+// F2: forward FFT along y of each half-spectrum column.
+// -------------------------------------------------------------------------
+template <int NY>
+__global__ void __launch_bounds__(THREADS) k2d_fwd_cols(const float2* __restrict__ T, int pT, float2* __restrict__ Uh,
+                                                        int ncols, const float2* __restrict__ twy) {
+  using F = LineFFT<NY>;
+  constexpr int E = F::E, LANES = F::LANES;
+  __shared__ float2 s_tw[NY];
+  extern __shared__ float2 s_buf[];
+  for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = lane % LANES, line = lane / LANES;
+  float2* wbuf = s_buf + warp * warp_stride<NY>();
+  const int c = (blockIdx.x * WARPS + warp) * F::LPW + line;
+  const bool active = c < ncols;
+  const int cc = active ? c : 0;
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = T[(size_t)(li + LANES * m) * pT + cc];
+  fft_line<NY, false>(v, wbuf, s_tw, li, line);
+  if (active) {
+    float2* dst = Uh + (size_t)c * NY;
+#pragma unroll
+    for (int m = 0; m < E; ++m) dst[li + LANES * m] = v[m];
+  }
+}
+
+// -------------------------------------------------------------------------
+// I1: multiplier + inverse FFT along y, for terms [m_lo, m_hi) of one
+// operator (blockIdx.y).  Output Z[s][op][y][c], s = m - m_lo.
+// -------------------------------------------------------------------------
+template <int NY>
+__global__ void __launch_bounds__(THREADS) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
+                                                        const float* __restrict__ Lg, float2* __restrict__ Z,
+                                                        long long zslot, int pZ, int ncols, int m_lo, int m_hi,
+                                                        const float2* __restrict__ twy) {
+  using F = LineFFT<NY>;
+  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW;
+  constexpr int CW = WARPS * LPW;  // columns per CTA
+  __shared__ float2 s_tw[NY];
+  extern __shared__ float2 s_buf[];
+  for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
+  __syncthreads();
+  const int op = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = lane % LANES, line = lane / LANES;
+  float2* wbuf = s_buf + warp * warp_stride<NY>();
+  const int c0 = blockIdx.x * CW;
+  const int c = c0 + warp * LPW + line;
+  const bool active = c < ncols;
+  const int cc = active ? c : 0;
+  const long long tot = (long long)ncols * NY;
+  const float2* uh_col = Uh + (size_t)cc * NY;
+  const float* p_col = P + op * tot + (size_t)cc * NY;
+  const float* l_col = Lg + (size_t)cc * NY;
+  float2 uh[E];
+  float tm[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int y = li + LANES * m;
+    uh[m] = uh_col[y];
+    float t = p_col[y];
+    const float l = l_col[y];
+    for (int j = 1; j <= m_lo; ++j) t = t * (l * (1.0f / (float)j));
+    tm[m] = t;
+  }
+  for (int mt = m_lo; mt < m_hi; ++mt) {
+    float2 x[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = cscale(uh[m], tm[m]);
+    fft_line<NY, true>(x, wbuf, s_tw, li, line);
+    float2* lb = wbuf + line * F::PAD_LINE;
+#pragma unroll
+    for (int m = 0; m < E; ++m) lb[F::pad(li + LANES * m)] = x[m];
+    __syncthreads();
+    // cooperative, row-segment-coalesced store of the CTA's [NY][CW] tile:
+    // THREADS is a multiple of CW, so each thread keeps one column k and
+    // walks rows y = y0 + RSTEP*i with constant address increments.
+    {
+      constexpr int RSTEP = THREADS / CW;
+      const int k = threadIdx.x % CW, y0 = threadIdx.x / CW;
+      const float2* colbuf = s_buf + (k / LPW) * warp_stride<NY>() + (k % LPW) * F::PAD_LINE;
+      float2* dst = Z + (long long)((mt - m_lo) * 2 + op) * zslot + (size_t)y0 * pZ + c0 + k;
+      if (c0 + k < ncols) {
+#pragma unroll 8
+        for (int i = 0; i < NY / RSTEP; ++i) dst[(size_t)i * RSTEP * pZ] = colbuf[F::pad(y0 + RSTEP * i)];
+      }
+    }
+    __syncthreads();
+    if (mt + 1 < m_hi) {
+      const float rinv = 1.0f / (float)(mt + 1);
+#pragma unroll
+      for (int m = 0; m < E; ++m) tm[m] = tm[m] * (l_col[li + LANES * m] * rinv);
+    }
+  }
+}
+
+// -------------------------------------------------------------------------
+// I2: inverse FFT along x of both operators (A + iB), Horner accumulation
+// over the group's terms, then partial store or epilogue.
+// -------------------------------------------------------------------------
+template <int NX>
+__global__ void __launch_bounds__(THREADS) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ, int ny,
+                                                        int m_lo, int m_hi, int top, const float* __restrict__ delta,
+                                                        float* __restrict__ part1, float* __restrict__ part2,
+                                                        EpiArgs<float> epi, float inv_lambda,
+                                                        const float2* __restrict__ twx) {
+  using F = LineFFT<NX>;
+  constexpr int E = F::E, LANES = F::LANES, H = NX / 2;
+  __shared__ float2 s_tw[NX];
+  extern __shared__ float2 s_buf[];
+  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = lane % LANES, line = lane / LANES;
+  float2* wbuf = s_buf + warp * warp_stride<NX>();
+  const int yr = (blockIdx.x * WARPS + warp) * F::LPW + line;
+  const bool active = yr < ny;
+  const int y = active ? yr : 0;
+  const size_t row = (size_t)y * NX;
+  float a1[E], a2[E];
+  if (top) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) a1[m] = a2[m] = 0.f;
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      a1[m] = part1[row + li + LANES * m];
+      a2[m] = part2[row + li + LANES * m];
+    }
+  }
+  for (int mt = m_hi - 1; mt >= m_lo; --mt) {
+    const float2* z1 = Z + (long long)((mt - m_lo) * 2 + 0) * zslot + (size_t)y * pZ;
+    const float2* z2 = Z + (long long)((mt - m_lo) * 2 + 1) * zslot + (size_t)y * pZ;
+    float2 w[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int n = li + LANES * m;
+      if (n <= H) {
+        const float2 a = z1[n], b = z2[n];
+        w[m] = (n == 0 || n == H) ? make_float2(a.x, b.x) : make_float2(a.x - b.y, a.y + b.x);
+      } else {
+        const float2 a = z1[NX - n], b = z2[NX - n];
+        w[m] = make_float2(a.x + b.y, b.x - a.y);
+      }
+    }
+    fft_line<NX, true>(w, wbuf, s_tw, li, line);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float d = delta[row + li + LANES * m];
+      a1[m] = fmaf(d, a1[m], w[m].x);
+      a2[m] = fmaf(d, a2[m], w[m].y);
+    }
+  }
+  if (!active) return;
+  if (m_lo > 0) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      part1[row + li + LANES * m] = a1[m];
+      part2[row + li + LANES * m] = a2[m];
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+      epilogue_point<float>(epi, (long long)(row + li + LANES * m), a1[m], a2[m] * inv_lambda);
+  }
+}
+
+// -------------------------------------------------------------------------
+// size dispatch
+// -------------------------------------------------------------------------
+struct Kernels {
+  void (*fwd_rows)(const float*, float2*, int, int, float, const float2*, int*, int);
+  void (*fwd_cols)(const float2*, int, float2*, int, const float2*);
+  void (*inv_cols)(const float2*, const float*, const float*, float2*, long long, int, int, int, int,
+                   const float2*);
+  void (*inv_rows)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>,
+                   float, const float2*);
+  size_t smem_x, smem_y;
+  int lpw_x, lpw_y;
+};
+
+template <int NX, int NY>
+Kernels kernels_for() {
+  Kernels k;
+  k.fwd_rows = k2d_fwd_rows<NX>;
+  k.fwd_cols = k2d_fwd_cols<NY>;
+  k.inv_cols = k2d_inv_cols<NY>;
+  k.inv_rows = k2d_inv_rows<NX>;
+  k.smem_x = dyn_smem<NX>();
+  k.smem_y = dyn_smem<NY>();
+  k.lpw_x = LineFFT<NX>::LPW;
+  k.lpw_y = LineFFT<NY>::LPW;
+  return k;
+}
+
+bool pick_kernels(int nx, int ny, Kernels* k) {
+#define VOFL_CASE(X, Y)            \
+  if (nx == X && ny == Y) {        \
+    *k = kernels_for<X, Y>();      \
+    return true;                   \
+  }
+  VOFL_CASE(64, 64)
+  VOFL_CASE(128, 128)
+  VOFL_CASE(256, 256)
+  VOFL_CASE(512, 512)
+  VOFL_CASE(1024, 1024)
+  VOFL_CASE(256, 128)
+  VOFL_CASE(128, 256)
+  VOFL_CASE(512, 64)
+  VOFL_CASE(64, 512)
+  VOFL_CASE(1024, 256)
+#undef VOFL_CASE
+  return false;
+}
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+struct Fused2D : Engine {
+  int nx = 0, ny = 0, H = 0, ncols = 0;
+  int pT = 0, pZ = 0;
+  int G = 1;  // Taylor terms per group
+  int Gcap = 1;
+  Kernels k{};
+  float2* T = nullptr;
+  float2* Uh = nullptr;
+  float2* Z = nullptr;
+  long long zslot = 0;
+  float* part = nullptr;  // 2 fields
+  float* P = nullptr;     // [2][ncols][ny]
+  float* Lg = nullptr;    // [ncols][ny]
+  float2* twx = nullptr;
+  float2* twy = nullptr;
+  size_t nbytes = 0;
+  // Operator 2's multiplier carries an exact power-of-two factor lambda so
+  // that the two operators packed into one complex row transform (A + iB)
+  // have comparable magnitude (|P1/P2| = |mu|); the row transform's
+  // round-off is relative to |A + iB|, so without it operator 2 would see
+  // round-off up to |mu|_max times its own size.  lambda ~ sqrt(|mu|_max)
+  // balances the two; it is divided out exactly in the epilogue.
+  float lambda = 1.f, inv_lambda = 1.f;
+  float ryy = 1.f;  // (h_x / h_y)^2, weight of D_yy in the transformed Laplacian
+
+  ~Fused2D() override {
+    cudaFree(T);
+    cudaFree(Uh);
+    cudaFree(Z);
+    cudaFree(part);
+    cudaFree(P);
+    cudaFree(Lg);
+    cudaFree(twx);
+    cudaFree(twy);
+  }
+
+  size_t bytes() const override { return nbytes; }
+
+  int alloc(vofl_ctx* c, void** p, size_t b) {
+    cudaError_t e = cudaMalloc(p, b);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (fused 2D scratch)");
+    nbytes += b;
+    return VOFL_OK;
+  }
+
+  int init(vofl_ctx* c) {
+    nx = (int)c->n[0];
+    ny = (int)c->n[1];
+    H = nx / 2;
+    ncols = H + 1;
+    if (!pick_kernels(nx, ny, &k)) return set_err(c, VOFL_EUNSUPPORTED, "fused 2D path: grid size not built");
+    pT = round_up(ncols, 8);
+    pZ = round_up(ncols, 8);
+    zslot = (long long)ny * pZ;
+    Gcap = 6;
+    int st;
+    if ((st = alloc(c, (void**)&T, sizeof(float2) * (size_t)ny * pT))) return st;
+    if ((st = alloc(c, (void**)&Uh, sizeof(float2) * (size_t)ncols * ny))) return st;
+    if ((st = alloc(c, (void**)&Z, sizeof(float2) * (size_t)zslot * 2 * Gcap))) return st;
+    if ((st = alloc(c, (void**)&part, sizeof(float) * 2 * (size_t)nx * ny))) return st;
+    if ((st = alloc(c, (void**)&P, sizeof(float) * 2 * (size_t)ncols * ny))) return st;
+    if ((st = alloc(c, (void**)&Lg, sizeof(float) * (size_t)ncols * ny))) return st;
+    if ((st = alloc(c, (void**)&twx, sizeof(float2) * nx))) return st;
+    if ((st = alloc(c, (void**)&twy, sizeof(float2) * ny))) return st;
+    VOFL_CUDA(c, cudaFuncSetAttribute(k.fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_x));
+    VOFL_CUDA(c, cudaFuncSetAttribute(k.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_x));
+    VOFL_CUDA(c, cudaFuncSetAttribute(k.fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_y));
+    VOFL_CUDA(c, cudaFuncSetAttribute(k.inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_y));
+    const int ex = nx >= 512 ? 32 : (nx >= 128 ? 16 : 8);
+    const int ey = ny >= 512 ? 32 : (ny >= 128 ? 16 : 8);
+    if ((st = make_line_twiddles(nx, ex, nx / ex, twx, c->stream))) return cuda_err(c, cudaGetLastError(), "twiddles");
+    if ((st = make_line_twiddles(ny, ey, ny / ey, twy, c->stream))) return cuda_err(c, cudaGetLastError(), "twiddles");
+    return VOFL_OK;
+  }
+
+  int set_model(vofl_ctx* c) override {
+    const double lx = c->hi[0] - c->lo[0], ly = c->hi[1] - c->lo[1];
+    const double mx = M_PI * nx / lx, my = M_PI * ny / ly;
+    const double mu_max = std::sqrt(mx * mx + my * my);
+    const int e2 = (int)std::lround(0.5 * std::log2(std::max(mu_max, 1.0)));
+    lambda = std::ldexp(1.0f, e2);
+    inv_lambda = std::ldexp(1.0f, -e2);
+    const double hx = lx / nx, hy = ly / ny;
+    ryy = (float)((hx * hx) / (hy * hy));
+    if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + c->gamma0, 0.5 + c->gamma0, lambda, (double)ryy, P, Lg,
+                            c->stream))
+      return cuda_err(c, cudaGetLastError(), "fused 2D tables");
+    return VOFL_OK;
+  }
+
+  int group_size(const vofl_ctx* c) const { return std::min(Gcap, c->M + 1); }
+
+  uint64_t kernels_per_step(const vofl_ctx* c) const override {
+    const int g = group_size(c);
+    const int K = (c->M + 1 + g - 1) / g;
+    return 2 + 2 * (uint64_t)K;
+  }
+
+  // forward transform of `u` into Uh
+  int forward(vofl_ctx* c, const float* u, bool inc_step) {
+    const int rows_per_cta = WARPS * k.lpw_x;  // row pairs per CTA
+    const int gx = (ny / 2 + rows_per_cta - 1) / rows_per_cta;
+    k.fwd_rows<<<gx, THREADS, k.smem_x, c->stream>>>(u, T, ny, pT, ryy, twx, c->d_step, inc_step ? 1 : 0);
+    const int cols_per_cta = WARPS * k.lpw_y;
+    const int gc = (ncols + cols_per_cta - 1) / cols_per_cta;
+    k.fwd_cols<<<gc, THREADS, k.smem_y, c->stream>>>(T, pT, Uh, ncols, twy);
+    count_launch(2);
+    return VOFL_OK;
+  }
+
+  int inverse(vofl_ctx* c, const EpiArgs<float>& epi) {
+    const int g = group_size(c);
+    const int K = (c->M + 1 + g - 1) / g;
+    const int cols_per_cta = WARPS * k.lpw_y;
+    const dim3 gic((ncols + cols_per_cta - 1) / cols_per_cta, 2);
+    const int rows_per_cta = WARPS * k.lpw_x;
+    const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
+    for (int gi = K - 1; gi >= 0; --gi) {
+      const int m_lo = gi * g, m_hi = std::min(c->M + 1, m_lo + g);
+      k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi, twy);
+      EpiArgs<float> e = epi;
+      if (gi > 0) e.mode = EPI_PARTIAL;
+      k.inv_rows<<<gir, THREADS, k.smem_x, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
+                                                        (const float*)c->delta, part, part + (size_t)nx * ny, e,
+                                                        inv_lambda, twx);
+      count_launch(2);
+    }
+    return VOFL_OK;
+  }
+
+  int apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) override {
+    EpiArgs<float> e{};
+    e.mode = EPI_APPLY;
+    e.out1 = (float*)o1;
+    e.out2 = (float*)o2;
+    e.src_flat = -1;
+    forward(c, (const float*)u, false);
+    inverse(c, e);
+    return cuda_err_if(c);
+  }
+
+  int step(vofl_ctx* c, int mode, bool count_step) override {
+    EpiArgs<float> e{};
+    e.mode = mode;
+    e.u_cur = (const float*)c->u[c->cur];
+    e.u_other = (float*)c->u[1 - c->cur];
+    e.l2p = (float*)c->l2p;
+    e.A = (const float*)c->A;
+    e.B = (const float*)c->B;
+    e.dt1 = (float)c->dt;
+    e.dt2 = (float)(c->dt * c->dt);
+    e.src_flat = c->nsrc > 0 ? c->src_flat : -1;
+    e.src = c->d_src;
+    e.nsrc = c->nsrc;
+    e.step = c->d_step;
+    double hd = 1.0;
+    for (int i = 0; i < c->ndim; ++i) hd *= (c->hi[i] - c->lo[i]) / (double)c->n[i];
+    e.src_scale = c->dt * c->dt / hd;
+    forward(c, (const float*)c->u[c->cur], count_step);
+    inverse(c, e);
+    return cuda_err_if(c);
+  }
+
+  int cuda_err_if(vofl_ctx* c) {
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_err(c, err, "fused 2D launch");
+    return VOFL_OK;
+  }
+
+  // Time every kernel of one operator-pair application in its real order
+  // (events recorded between consecutive kernels on the context stream),
+  // averaged over `reps` repetitions; each interval is the kernel's
+  // duration plus its launch gap.  The epilogue writes nothing (apply mode
+  // with null outputs), so the context state is unchanged.
+  int profile(vofl_ctx* c, int reps, std::string& names, double* ms, double* units, int cap) override {
+    if (cap < 4) return 0;
+    const int g = group_size(c);
+    const int K = (c->M + 1 + g - 1) / g;
+    const int nk = 2 + 2 * K;
+    std::vector<cudaEvent_t> ev(nk + 1);
+    for (auto& e : ev) cudaEventCreate(&e);
+    const int rows_per_cta = WARPS * k.lpw_x, cols_per_cta = WARPS * k.lpw_y;
+    const int gx = (ny / 2 + rows_per_cta - 1) / rows_per_cta;
+    const int gc = (ncols + cols_per_cta - 1) / cols_per_cta;
+    const dim3 gic(gc, 2);
+    const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
+    EpiArgs<float> ep{};
+    ep.mode = EPI_APPLY;
+    ep.src_flat = -1;
+    const float* u = (const float*)c->u[c->cur];
+    double acc[4] = {0, 0, 0, 0};
+    double terms_cols = 0, terms_rows = 0;
+    for (int r = -1; r < reps; ++r) {
+      int e = 0;
+      cudaEventRecord(ev[e++], c->stream);
+      k.fwd_rows<<<gx, THREADS, k.smem_x, c->stream>>>(u, T, ny, pT, ryy, twx, c->d_step, 0);
+      cudaEventRecord(ev[e++], c->stream);
+      k.fwd_cols<<<gc, THREADS, k.smem_y, c->stream>>>(T, pT, Uh, ncols, twy);
+      cudaEventRecord(ev[e++], c->stream);
+      for (int gi = K - 1; gi >= 0; --gi) {
+        const int m_lo = gi * g, m_hi = std::min(c->M + 1, m_lo + g);
+        k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi, twy);
+        cudaEventRecord(ev[e++], c->stream);
+        EpiArgs<float> epg = ep;
+        if (gi > 0) epg.mode = EPI_PARTIAL;
+        k.inv_rows<<<gir, THREADS, k.smem_x, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
+                                                          (const float*)c->delta, part, part + (size_t)nx * ny, epg,
+                                                          inv_lambda, twx);
+        cudaEventRecord(ev[e++], c->stream);
+        if (r == 0) {
+          terms_cols += m_hi - m_lo;
+          terms_rows += m_hi - m_lo;
+        }
+      }
+      count_launch(nk);
+      cudaEventSynchronize(ev[nk]);
+      if (r < 0) continue;  // warm-up repetition
+      float t;
+      cudaEventElapsedTime(&t, ev[0], ev[1]);
+      acc[0] += t;
+      cudaEventElapsedTime(&t, ev[1], ev[2]);
+      acc[1] += t;
+      for (int i = 0; i < K; ++i) {
+        cudaEventElapsedTime(&t, ev[2 + 2 * i], ev[3 + 2 * i]);
+        acc[2] += t;
+        cudaEventElapsedTime(&t, ev[3 + 2 * i], ev[4 + 2 * i]);
+        acc[3] += t;
+      }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    names = "k2d_fwd_rows;k2d_fwd_cols;k2d_inv_cols;k2d_inv_rows";
+    // ms = average per launch; units = complex line transforms per launch
+    ms[0] = acc[0] / reps;
+    units[0] = ny / 2.0;
+    ms[1] = acc[1] / reps;
+    units[1] = ncols;
+    ms[2] = acc[2] / reps / K;
+    units[2] = 2.0 * ncols * terms_cols / K;
+    ms[3] = acc[3] / reps / K;
+    units[3] = (double)ny * terms_rows / K;
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_err(c, err, "profile");
+    return 4;
+  }
+};
+
+}  // namespace
+
+bool fused2d_supported(int ndim, const int64_t* n, int prec) {
+  Kernels k;
+  return ndim == 2 && prec == VOFL_F32 && pick_kernels((int)n[0], (int)n[1], &k);
+}
+
+size_t fused2d_footprint(const int64_t* n, int M) {
+  const size_t nx = n[0], ny = n[1], nc = nx / 2 + 1, p = (nc + 7) / 8 * 8;
+  const size_t G = std::min(6, M + 1);
+  return sizeof(float2) * (ny * p + nc * ny + ny * p * 2 * G + nx + ny) + sizeof(float) * (2 * nx * ny + 3 * nc * ny);
+}
+
+Engine* make_fused2d(vofl_ctx* c, int* status) {
+  Fused2D* e = new Fused2D();
+  *status = e->init(c);
+  if (*status != VOFL_OK) {
+    delete e;
+    return nullptr;
+  }
+  return e;
+}
+
+}  // namespace vofl

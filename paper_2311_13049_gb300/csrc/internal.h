@@ -1,0 +1,177 @@
+// internal.h -- context state and engine interface of the vofl library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "vofl.h"
+
+namespace vofl {
+
+extern std::atomic<uint64_t> g_kernel_launches;
+inline void count_launch(uint64_t n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct Engine;
+
+// Epilogue of the last inverse pass: what to do with L1 u, L2 u at a point.
+enum EpiMode { EPI_PARTIAL = 0, EPI_APPLY = 1, EPI_STEP = 2, EPI_START = 3 };
+
+template <typename T>
+struct EpiArgs {
+  int mode;
+  T* out1;            // EPI_APPLY: L1 u (may be null)
+  T* out2;            // EPI_APPLY: L2 u (may be null)
+  const T* u_cur;     // u^n
+  T* u_other;         // in: u^{n-1} (STEP) or psi (START); out: u^{n+1}
+  T* l2p;             // in: L2 u^{n-1} (STEP) or L2 psi (START); out: L2 u^n
+  const T* A;         // c^2 eta
+  const T* B;         // c^2 tau
+  T dt1, dt2;         // dt, dt^2
+  long long src_flat; // flat index of the source node, -1 = none
+  const double* src;  // samples r_n
+  long long nsrc;
+  const int* step;    // device step counter n
+  double src_scale;   // dt^2 / h^d
+};
+
+// Pointwise update of Eq. (3.4) extended to Eq. (1.1) (see vofl.h).
+template <typename T>
+__device__ __forceinline__ void epilogue_point(const EpiArgs<T>& e, long long idx, T L1, T L2) {
+  if (e.mode == EPI_APPLY) {
+    if (e.out1) e.out1[idx] = L1;
+    if (e.out2) e.out2[idx] = L2;
+    return;
+  }
+  const T un = e.u_cur[idx];
+  const T other = e.u_other[idx];
+  const T l2o = e.l2p[idx];
+  T unew;
+  if (e.mode == EPI_STEP) {
+    // 2u^n - u^{n-1} + dt^2 A L1 u^n + dt B (L2 u^n - L2 u^{n-1})
+    unew = (T(2) * un - other) + e.dt2 * e.A[idx] * L1 + e.dt1 * e.B[idx] * (L2 - l2o);
+    if (idx == e.src_flat) {
+      const int n = *e.step;
+      if (n < e.nsrc) unew += T(e.src_scale * e.src[n]);
+    }
+  } else {  // EPI_START: u^0 + dt psi + dt^2/2 (A L1 u^0 + B L2 psi + f_0)
+    unew = un + e.dt1 * other + T(0.5) * e.dt2 * (e.A[idx] * L1 + e.B[idx] * l2o);
+    if (idx == e.src_flat && e.nsrc > 0) unew += T(0.5 * e.src_scale * e.src[0]);
+  }
+  e.u_other[idx] = unew;
+  e.l2p[idx] = L2;
+}
+
+}  // namespace vofl
+
+struct vofl_ctx {
+  int ndim = 0;
+  int64_t n[3] = {1, 1, 1};  // x, y, z
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  int64_t N = 0;             // total points
+  int prec = VOFL_F32;
+  int impl = VOFL_IMPL_FUSED;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int M = 8;
+
+  // model (after set_q / set_gamma)
+  bool model_set = false;
+  double gamma0 = 0;
+  void* delta = nullptr;  // gamma - gamma0        (prec)
+  void* A = nullptr;      // c^2 eta               (prec)
+  void* B = nullptr;      // c^2 tau               (prec)
+  double* d_gamma = nullptr;  // gamma (double), kept for re-derivation
+  double* d_scratch = nullptr;  // reduction partials
+
+  // time stepping
+  void* u[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* l2p = nullptr;
+  bool state_set = false;
+  bool psi_nonzero = false;
+  int64_t steps = 0;
+  double dt = 0;
+  int* d_step = nullptr;
+
+  // source
+  long long src_flat = -1;
+  double* d_src = nullptr;
+  int64_t nsrc = 0;
+  int64_t src_cap = 0;
+
+  vofl::Engine* eng = nullptr;
+
+  // captured one-step graphs (index = cur buffer at the start of the step)
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  uint64_t step_graph_kernels = 0;
+  bool graphs_ok = true;
+  // what the captured graphs bake in besides the context's fixed buffers
+  struct GraphKey {
+    double dt = -1;
+    int M = -1;
+    long long src_flat = -2;
+    const double* d_src = nullptr;
+    int64_t nsrc = -1;
+    bool operator==(const GraphKey& o) const {
+      return dt == o.dt && M == o.M && src_flat == o.src_flat && d_src == o.d_src && nsrc == o.nsrc;
+    }
+  } graph_key;
+
+  std::string err;
+};
+
+namespace vofl {
+
+struct Engine {
+  virtual ~Engine() {}
+  // (re)build spectral tables after the model changed (gamma0 known)
+  virtual int set_model(vofl_ctx* c) = 0;
+  // L1 u -> o1, L2 u -> o2 (either may be null)
+  virtual int apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) = 0;
+  // one step with the given epilogue (mode EPI_STEP or EPI_START); state
+  // buffers are taken from the context (cur / other / l2p)
+  virtual int step(vofl_ctx* c, int mode, bool count_step) = 0;
+  // number of kernels launched by one step(mode = EPI_STEP)
+  virtual uint64_t kernels_per_step(const vofl_ctx* c) const = 0;
+  virtual int profile(vofl_ctx* c, int reps, std::string& names, double* ms, double* units, int cap) {
+    (void)c; (void)reps; (void)names; (void)ms; (void)units; (void)cap;
+    return 0;
+  }
+  virtual size_t bytes() const = 0;
+};
+
+Engine* make_fused2d(vofl_ctx* c, int* status);
+Engine* make_plain(vofl_ctx* c, int* status);
+size_t fused2d_footprint(const int64_t* n, int M);
+size_t plain_footprint(int ndim, const int64_t* n, int prec);
+bool fused2d_supported(int ndim, const int64_t* n, int prec);
+
+// model precompute (model.cu)
+int model_from_gamma(vofl_ctx* c, const double* d_gamma, const double* d_c0field, double c0, double omega0);
+int model_gamma_from_q(vofl_ctx* c, const double* d_q, double* d_gamma);
+
+// twiddles / tables (model.cu)
+int make_line_twiddles(int N, int E, int LANES, float2* d_tw, cudaStream_t s);
+int make_fused2d_tables(int nx, int ny, double lx, double ly, double s01, double s02, double scale2, double ryy,
+                        float* P, float* Lg, cudaStream_t s);
+template <typename T>
+int make_plain_tables(int ndim, const int64_t* n, const double* lo, const double* hi, double s01, double s02,
+                      T* P1, T* P2, T* Lg, cudaStream_t s);
+
+inline int set_err(vofl_ctx* c, int code, const char* msg) {
+  if (c) c->err = msg;
+  return code;
+}
+int cuda_err(vofl_ctx* c, cudaError_t e, const char* where);
+
+}  // namespace vofl
+
+#define VOFL_CUDA(ctx, call)                                    \
+  do {                                                          \
+    cudaError_t _e = (call);                                    \
+    if (_e != cudaSuccess) return ::vofl::cuda_err(ctx, _e, #call); \
+  } while (0)

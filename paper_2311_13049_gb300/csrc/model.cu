@@ -1,0 +1,255 @@
+// model.cu -- once-per-model precompute, all in double on the GPU:
+//   gamma = arctan(1/Q)/pi and c, eta, tau (Sec. 1, coefficients of Eq. (1.1));
+//   gamma0 = grid mean of gamma (the expansion centre s0 of Eq. (2.13) is the
+//   domain average of s; s = 1 + gamma and s = 1/2 + gamma share gamma0);
+//   delta = gamma - gamma0, A = c^2 eta, B = c^2 tau (rounded to the working
+//   precision);
+//   spectral tables |mu_k|^{2 s0} / N and ln|mu_k|^2 of Eq. (2.13) (k = 0 -> 0);
+//   FFT twiddles exp(-2 pi i r k / N).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace vofl {
+
+namespace {
+
+constexpr int RED_BLOCKS = 512;
+constexpr int RED_THREADS = 256;
+
+// may run in place (q == g): each element is read before it is written
+__global__ void k_gamma_from_q(const double* q, double* g, long long n, int* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double Q = q[i];
+    if (!(Q > 0.0) || !isfinite(Q)) atomicExch(bad, 1);
+    g[i] = atan(1.0 / Q) / M_PI;
+  }
+}
+
+__global__ void k_check_gamma(const double* __restrict__ g, long long n, int* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = g[i];
+    if (!(v >= 0.0 && v < 0.5)) atomicExch(bad, 1);
+  }
+}
+
+// Deterministic two-pass sum: fixed grid, fixed tree order.
+__global__ void k_sum_pass1(const double* __restrict__ x, long long n, double* __restrict__ part) {
+  __shared__ double s[RED_THREADS];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < n; i += (long long)RED_BLOCKS * RED_THREADS)
+    acc += x[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_sum_pass2(const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double s[RED_BLOCKS];
+  for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) s[i] = part[i];
+  __syncthreads();
+  for (int w = RED_BLOCKS / 2; w > 0; w >>= 1) {
+    for (int i = threadIdx.x; i < w; i += blockDim.x) s[i] += s[i + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = s[0];
+}
+
+template <typename T>
+__global__ void k_coeffs(const double* __restrict__ g, const double* __restrict__ c0f, double c0s, double w0,
+                         double g0, long long n, T* __restrict__ delta, T* __restrict__ A, T* __restrict__ B) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double gm = g[i];
+    const double c0 = c0f ? c0f[i] : c0s;
+    const double c = c0 * cos(M_PI * gm / 2.0);
+    const double sc = pow(c0, 2.0 * gm) * pow(w0, -2.0 * gm);  // c0^{2g} w0^{-2g}
+    const double eta = -sc * cos(M_PI * gm);
+    const double tau = -(sc / c0) * sin(M_PI * gm);
+    delta[i] = T(gm - g0);
+    A[i] = T(c * c * eta);
+    B[i] = T(c * c * tau);
+  }
+}
+
+// Tables in the fused 2D layout: column-major over the half spectrum,
+// index [c][k2] for c = k1 in [0, nx/2], k2 in [0, ny).
+// P[0] = |mu|^{2 s01}/(N lambda), P[1] = scale2 |mu|^{2 s02}/(N lambda),
+// Lg = ln|mu|^2, lambda = the symbol of the transformed discrete Laplacian.
+__global__ void k_tables_fused2d(int nx, int ny, double lx, double ly, double s01, double s02, double scale2,
+                                 double ryy, float* __restrict__ P, float* __restrict__ Lg) {
+  const int H = nx / 2;
+  const long long total = (long long)(H + 1) * ny;
+  const double invN = 1.0 / ((double)nx * (double)ny);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / ny);
+    const int k2 = (int)(i % ny);
+    const int k2s = (k2 < ny / 2) ? k2 : k2 - ny;
+    const double m1 = 2.0 * M_PI * (double)c / lx;
+    const double m2 = 2.0 * M_PI * (double)k2s / ly;
+    const double mu2 = m1 * m1 + m2 * m2;
+    if (mu2 == 0.0) {
+      P[i] = 0.f;
+      P[total + i] = 0.f;
+      Lg[i] = 0.f;
+    } else {
+      // the forward transform is of the discrete Laplacian w (symbol lambda)
+      const double s1 = sinpi((double)c / nx), s2 = sinpi((double)k2 / ny);
+      const double lam = -4.0 * s1 * s1 - 4.0 * ryy * s2 * s2;
+      const double L = log(mu2);
+      P[i] = (float)(exp(s01 * L) * invN / lam);
+      P[total + i] = (float)(exp(s02 * L) * invN * scale2 / lam);
+      Lg[i] = (float)L;
+    }
+  }
+}
+
+// Tables in the cuFFT R2C layout [..][nz][ny][nx/2+1] (row-major, x halved),
+// for a forward transform of the discrete Laplacian (symbol lambda, see
+// fused2d.cu): P = |mu|^{2 s0} / (N lambda).
+template <typename T>
+__global__ void k_tables_plain(int nx, int ny, int nz, double lx, double ly, double lz, double s01, double s02,
+                               double invN, double ry, double rz, T* __restrict__ P1, T* __restrict__ P2,
+                               T* __restrict__ Lg) {
+  const int hx = nx / 2 + 1;
+  const long long total = (long long)hx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % hx);
+    const int ky = (int)((i / hx) % ny);
+    const int kz = (int)(i / ((long long)hx * ny));
+    const int kys = (ky < ny / 2) ? ky : ky - ny;
+    const int kzs = (kz < nz / 2) ? kz : kz - nz;
+    const double mx = 2.0 * M_PI * kx / lx;
+    const double my = (ny > 1) ? 2.0 * M_PI * kys / ly : 0.0;
+    const double mz = (nz > 1) ? 2.0 * M_PI * kzs / lz : 0.0;
+    const double mu2 = mx * mx + my * my + mz * mz;
+    if (mu2 == 0.0) {
+      P1[i] = T(0);
+      P2[i] = T(0);
+      Lg[i] = T(0);
+    } else {
+      const double sx = sinpi((double)kx / nx), sy = sinpi((double)ky / ny), sz = sinpi((double)kz / nz);
+      const double lam = -4.0 * (sx * sx + ry * sy * sy + rz * sz * sz);
+      const double L = log(mu2);
+      P1[i] = T(exp(s01 * L) * invN / lam);
+      P2[i] = T(exp(s02 * L) * invN / lam);
+      Lg[i] = T(L);
+    }
+  }
+}
+
+// tw[r*E + k] = exp(-2 pi i r k / N), r < LANES, k < E
+__global__ void k_twiddles(int N, int E, int LANES, float2* tw) {
+  const int total = E * LANES;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int r = i / E, k = i % E;
+    const long long t = ((long long)r * k) % N;
+    double s, c;
+    sincospi(-2.0 * (double)t / (double)N, &s, &c);
+    tw[i] = make_float2((float)c, (float)s);
+  }
+}
+
+inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 4096) b = 4096;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+std::atomic<uint64_t> g_kernel_launches{0};
+
+int cuda_err(vofl_ctx* c, cudaError_t e, const char* where) {
+  if (c) {
+    c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return e == cudaErrorMemoryAllocation ? VOFL_ENOMEM : VOFL_ECUDA;
+}
+
+int model_gamma_from_q(vofl_ctx* c, const double* d_q, double* d_gamma) {
+  int* d_bad = reinterpret_cast<int*>(c->d_scratch + RED_BLOCKS + 1);
+  VOFL_CUDA(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+  k_gamma_from_q<<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_q, d_gamma, c->N, d_bad);
+  count_launch();
+  VOFL_CUDA(c, cudaGetLastError());
+  int bad = 0;
+  VOFL_CUDA(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad) return set_err(c, VOFL_EINVAL, "Q must be positive and finite at every grid point");
+  return VOFL_OK;
+}
+
+int model_from_gamma(vofl_ctx* c, const double* d_gamma, const double* d_c0field, double c0, double omega0) {
+  int* d_bad = reinterpret_cast<int*>(c->d_scratch + RED_BLOCKS + 1);
+  VOFL_CUDA(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+  k_check_gamma<<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_gamma, c->N, d_bad);
+  k_sum_pass1<<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(d_gamma, c->N, c->d_scratch);
+  k_sum_pass2<<<1, 256, 0, c->stream>>>(c->d_scratch, c->d_scratch + RED_BLOCKS);
+  count_launch(3);
+  VOFL_CUDA(c, cudaGetLastError());
+  double sum = 0;
+  int bad = 0;
+  VOFL_CUDA(c, cudaMemcpyAsync(&sum, c->d_scratch + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad) return set_err(c, VOFL_EINVAL, "gamma must lie in [0, 1/2) at every grid point");
+  const double g0 = sum / (double)c->N;
+  c->gamma0 = g0;
+  if (c->prec == VOFL_F32) {
+    k_coeffs<float><<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_gamma, d_c0field, c0, omega0, g0, c->N,
+                                                                 (float*)c->delta, (float*)c->A, (float*)c->B);
+  } else {
+    k_coeffs<double><<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_gamma, d_c0field, c0, omega0, g0, c->N,
+                                                                  (double*)c->delta, (double*)c->A, (double*)c->B);
+  }
+  count_launch();
+  VOFL_CUDA(c, cudaGetLastError());
+  return VOFL_OK;
+}
+
+int make_line_twiddles(int N, int E, int LANES, float2* d_tw, cudaStream_t s) {
+  k_twiddles<<<grid_for((long long)E * LANES, 256), 256, 0, s>>>(N, E, LANES, d_tw);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
+}
+
+int make_fused2d_tables(int nx, int ny, double lx, double ly, double s01, double s02, double scale2, double ryy,
+                        float* P, float* Lg, cudaStream_t s) {
+  const long long total = (long long)(nx / 2 + 1) * ny;
+  k_tables_fused2d<<<grid_for(total, 256), 256, 0, s>>>(nx, ny, lx, ly, s01, s02, scale2, ryy, P, Lg);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
+}
+
+template <typename T>
+int make_plain_tables(int ndim, const int64_t* n, const double* lo, const double* hi, double s01, double s02, T* P1,
+                      T* P2, T* Lg, cudaStream_t s) {
+  const int nx = (int)n[0];
+  const int ny = ndim > 1 ? (int)n[1] : 1;
+  const int nz = ndim > 2 ? (int)n[2] : 1;
+  const double lx = hi[0] - lo[0];
+  const double ly = ndim > 1 ? hi[1] - lo[1] : 1.0;
+  const double lz = ndim > 2 ? hi[2] - lo[2] : 1.0;
+  const double invN = 1.0 / ((double)nx * ny * nz);
+  const long long total = (long long)(nx / 2 + 1) * ny * nz;
+  const double hx = lx / nx, hy = ly / ny, hz = lz / nz;
+  const double ry = ndim > 1 ? (hx * hx) / (hy * hy) : 0.0;
+  const double rz = ndim > 2 ? (hx * hx) / (hz * hz) : 0.0;
+  k_tables_plain<T><<<grid_for(total, 256), 256, 0, s>>>(nx, ny, nz, lx, ly, lz, s01, s02, invN, ry, rz, P1, P2, Lg);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
+}
+
+template int make_plain_tables<float>(int, const int64_t*, const double*, const double*, double, double, float*,
+                                      float*, float*, cudaStream_t);
+template int make_plain_tables<double>(int, const int64_t*, const double*, const double*, double, double, double*,
+                                       double*, double*, cudaStream_t);
+
+}  // namespace vofl

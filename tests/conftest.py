@@ -16,3 +16,15 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def V():
+    """The built library binding, on a machine with a CUDA device."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_13049_gb300 import build as B
+    B.build()
+    import paper_2311_13049_gb300 as vofl
+    return vofl
