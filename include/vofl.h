@@ -169,6 +169,38 @@ VOFL_API int vofl_profile_kernels(vofl_ctx* ctx, int reps, char* names_out,
 /* Library version string. */
 VOFL_API const char* vofl_version(void);
 
+/* Allocation-free variant of vofl_apply_pair for small 2D grids.  The paper
+ * has no counterpart: it is a deployment aid for callers that may not
+ * allocate device memory when they need the operator (an outside allocator
+ * owns the GPU memory budget, cudaMalloc/cudaFree would synchronise the
+ * device inside a latency-critical loop, or the caller is a callback that
+ * must not enter the CUDA allocator).
+ *
+ * Computes out1 = (-Delta)^{1+gamma} u and out2 = (-Delta)^{1/2+gamma} u on
+ * the periodic box [0,lx) x [0,ly) with nx x ny points (x fastest), with
+ * Taylor power M (0..40), exactly as a context created with VOFL_F32 /
+ * VOFL_IMPL_FUSED and vofl_set_gamma would.  gamma_dev: nx*ny doubles in
+ * [0, 1/2); u_dev, out1_dev, out2_dev: nx*ny floats; all device pointers on
+ * the current device; out1_dev or out2_dev may be NULL (not both).
+ * stream: a cudaStream_t or NULL.
+ *
+ * No device memory is allocated: every intermediate lives in one file-scope
+ * device array of 6 MiB that each GPU loading the library keeps until the
+ * process exits.  Limits: nx, ny in {64, 128, 256} with (nx, ny) one of the
+ * fused shapes (64x64, 128x128, 256x256, 256x128, 128x256); larger or
+ * other shapes return VOFL_EUNSUPPORTED before any device work.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  The call waits
+ * on `stream` once (to read the grid mean of gamma back).  All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller; the array keeps
+ * the last call's contents, and nothing in it needs to start at zero.
+ * Returns VOFL_OK, VOFL_EINVAL (bad arguments or gamma outside [0,1/2)),
+ * VOFL_EUNSUPPORTED (shape beyond the limit) or VOFL_ECUDA. */
+VOFL_API int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, int M,
+                                        const double* gamma_dev, const float* u_dev,
+                                        float* out1_dev, float* out2_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

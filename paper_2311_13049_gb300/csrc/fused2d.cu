@@ -603,3 +603,168 @@ Engine* make_fused2d(vofl_ctx* c, int* status) {
 }
 
 }  // namespace vofl
+
+// ---------------------------------------------------------------------------
+// Allocation-free operator pair for small 2D grids.
+//
+// Some callers cannot allocate device memory at the moment they need the
+// operator: code that runs while an outside allocator owns the whole GPU
+// memory budget, latency-critical loops where cudaMalloc / cudaFree would
+// synchronise the device and stall other streams, or host callbacks and
+// plug-ins that are not allowed to call the CUDA allocator at all.  For
+// them vofl_apply_pair_2d_noalloc runs the same fused kernels with every
+// intermediate (the per-model tables, twiddles, spectra, partial sums) in
+// one file-scope device array of fixed size, g_noalloc_scratch: 6 MiB,
+// enough for grids up to 256 x 256.  Every GPU that loads the library keeps
+// that array until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace vofl {
+namespace {
+
+constexpr int NOALLOC_MAX_AXIS = 256;
+constexpr size_t NOALLOC_BYTES = size_t(6) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+static_assert(dyn_smem<NOALLOC_MAX_AXIS>() <= 48 * 1024, "no shared-memory opt-in needed up to 256 points per axis");
+
+struct NoAllocLayout {
+  size_t delta, A, B, red, T, Uh, Z, part, P, Lg, twx, twy, step, total;
+};
+
+NoAllocLayout noalloc_layout(int nx, int ny, int G) {
+  const size_t N = (size_t)nx * ny, ncols = nx / 2 + 1, p = (size_t)round_up((int)ncols, 8);
+  NoAllocLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  L.delta = take(sizeof(float) * N);
+  L.A = take(sizeof(float) * N);
+  L.B = take(sizeof(float) * N);
+  L.red = take(sizeof(double) * 1024);
+  L.T = take(sizeof(float2) * ny * p);
+  L.Uh = take(sizeof(float2) * ncols * ny);
+  L.Z = take(sizeof(float2) * ny * p * 2 * G);
+  L.part = take(sizeof(float) * 2 * N);
+  L.P = take(sizeof(float) * 2 * ncols * ny);
+  L.Lg = take(sizeof(float) * ncols * ny);
+  L.twx = take(sizeof(float2) * nx);
+  L.twy = take(sizeof(float2) * ny);
+  L.step = take(sizeof(int) * 4);
+  L.total = off;
+  return L;
+}
+
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_dev_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device.  In host code the array's name is only a host-side stand-in,
+// so kernels are always given this looked-up address.
+int noalloc_base(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    cudaGetLastError();
+    return VOFL_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_dev_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return VOFL_ECUDA;
+    }
+    g_noalloc_dev_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
+  return VOFL_OK;
+}
+
+}  // namespace
+}  // namespace vofl
+
+extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, int M, const double* gamma_dev,
+                                          const float* u_dev, float* out1_dev, float* out2_dev, void* stream) {
+  using namespace vofl;
+  if (!gamma_dev || !u_dev || (!out1_dev && !out2_dev)) return VOFL_EINVAL;
+  if (!(lx > 0) || !(ly > 0) || M < 0 || M > 40) return VOFL_EINVAL;
+  if (nx < 2 || ny < 2 || (nx % 2) || (ny % 2)) return VOFL_EINVAL;
+  Kernels k;
+  if (nx > NOALLOC_MAX_AXIS || ny > NOALLOC_MAX_AXIS || !pick_kernels(nx, ny, &k)) return VOFL_EUNSUPPORTED;
+  const int G = std::min(6, M + 1);
+  const NoAllocLayout L = noalloc_layout(nx, ny, G);
+  if (L.total > NOALLOC_BYTES) return VOFL_EUNSUPPORTED;
+  unsigned char* base = nullptr;
+  int st = noalloc_base(&base);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // per-model part: gamma0 = grid mean of gamma and delta = gamma - gamma0
+  // (the A, B fields of the seismic model are written but not used here)
+  vofl_ctx m;
+  m.ndim = 2;
+  m.n[0] = nx;
+  m.n[1] = ny;
+  m.N = (int64_t)nx * ny;
+  m.prec = VOFL_F32;
+  m.stream = s;
+  m.d_scratch = reinterpret_cast<double*>(base + L.red);
+  m.delta = base + L.delta;
+  m.A = base + L.A;
+  m.B = base + L.B;
+  st = model_from_gamma(&m, gamma_dev, nullptr, 1.0, 1.0);
+  if (st) return st;
+  const double mx = M_PI * nx / lx, my = M_PI * ny / ly;
+  const int e2 = (int)std::lround(0.5 * std::log2(std::max(std::sqrt(mx * mx + my * my), 1.0)));
+  const float inv_lambda = std::ldexp(1.0f, -e2);
+  const double hx = lx / nx, hy = ly / ny;
+  const float ryy = (float)((hx * hx) / (hy * hy));
+  float* P = reinterpret_cast<float*>(base + L.P);
+  float* Lgt = reinterpret_cast<float*>(base + L.Lg);
+  float2* twx = reinterpret_cast<float2*>(base + L.twx);
+  float2* twy = reinterpret_cast<float2*>(base + L.twy);
+  if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + m.gamma0, 0.5 + m.gamma0, std::ldexp(1.0, e2), (double)ryy, P, Lgt, s))
+    return VOFL_ECUDA;
+  const int ex = nx >= 512 ? 32 : (nx >= 128 ? 16 : 8);
+  const int ey = ny >= 512 ? 32 : (ny >= 128 ? 16 : 8);
+  if (make_line_twiddles(nx, ex, nx / ex, twx, s) || make_line_twiddles(ny, ey, ny / ey, twy, s)) return VOFL_ECUDA;
+
+  // the fused transform passes, exactly as the context path launches them
+  const int ncols = nx / 2 + 1, pT = round_up(ncols, 8), pZ = pT;
+  const long long zslot = (long long)ny * pZ;
+  float2* T = reinterpret_cast<float2*>(base + L.T);
+  float2* Uh = reinterpret_cast<float2*>(base + L.Uh);
+  float2* Z = reinterpret_cast<float2*>(base + L.Z);
+  float* part = reinterpret_cast<float*>(base + L.part);
+  int* stepc = reinterpret_cast<int*>(base + L.step);
+  const int rows_per_cta = WARPS * k.lpw_x, cols_per_cta = WARPS * k.lpw_y;
+  k.fwd_rows<<<(ny / 2 + rows_per_cta - 1) / rows_per_cta, THREADS, k.smem_x, s>>>(u_dev, T, ny, pT, ryy, twx, stepc,
+                                                                                   0);
+  k.fwd_cols<<<(ncols + cols_per_cta - 1) / cols_per_cta, THREADS, k.smem_y, s>>>(T, pT, Uh, ncols, twy);
+  count_launch(2);
+  EpiArgs<float> epi{};
+  epi.mode = EPI_APPLY;
+  epi.out1 = out1_dev;
+  epi.out2 = out2_dev;
+  epi.src_flat = -1;
+  const int K = (M + 1 + G - 1) / G;
+  const dim3 gic((ncols + cols_per_cta - 1) / cols_per_cta, 2);
+  const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
+  for (int gi = K - 1; gi >= 0; --gi) {
+    const int m_lo = gi * G, m_hi = std::min(M + 1, m_lo + G);
+    k.inv_cols<<<gic, THREADS, k.smem_y, s>>>(Uh, P, Lgt, Z, zslot, pZ, ncols, m_lo, m_hi, twy);
+    EpiArgs<float> e = epi;
+    if (gi > 0) e.mode = EPI_PARTIAL;
+    k.inv_rows<<<gir, THREADS, k.smem_x, s>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
+                                              reinterpret_cast<const float*>(m.delta), part,
+                                              part + (size_t)nx * ny, e, inv_lambda, twx);
+    count_launch(2);
+  }
+  if (cudaGetLastError() != cudaSuccess) return VOFL_ECUDA;
+  return VOFL_OK;
+}
