@@ -169,6 +169,15 @@ VOFL_API int vofl_profile_kernels(vofl_ctx* ctx, int reps, char* names_out,
 /* Library version string. */
 VOFL_API const char* vofl_version(void);
 
+/* Self-test of the failure path of device waits (no counterpart in the
+ * paper).  Every wait inside the kernels (on TMA copy completion) is bounded
+ * by a clock budget: when it runs out the kernel sets an error word, drains
+ * what it issued and returns, and vofl_sync() reports VOFL_ETIMEDOUT.  This
+ * launches one kernel that waits on a barrier nothing completes, with a
+ * ~1 ms budget; *gave_up is set to 1 when the wait gave up as designed.  It
+ * faults and hangs nothing; the device stays usable.  Synchronous. */
+VOFL_API int vofl_selftest_bounded_wait(int* gave_up);
+
 /* Allocation-free variant of vofl_apply_pair for small 2D grids.  The paper
  * has no counterpart: it is a deployment aid for callers that may not
  * allocate device memory when they need the operator (an outside allocator

@@ -50,6 +50,7 @@ SIGNATURES = {
     "vofl_kernel_launches": (C.c_uint64, []),
     "vofl_profile_kernels": (C.c_int, [_vp, C.c_int, C.c_char_p, C.c_size_t, _dp, _dp, C.c_int]),
     "vofl_version": (C.c_char_p, []),
+    "vofl_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int)]),
     "vofl_apply_pair_2d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp, _vp,
                                              _vp, _vp]),
 }

@@ -370,6 +370,13 @@ int vofl_sync(vofl_ctx* c) {
   if (check_ctx(c)) return VOFL_EINVAL;
   VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
   VOFL_CUDA(c, cudaGetLastError());
+  // device error word (d_step[1]): set by a bounded wait that gave up
+  int werr = 0;
+  VOFL_CUDA(c, cudaMemcpy(&werr, c->d_step + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (werr) {
+    VOFL_CUDA(c, cudaMemset(c->d_step + 1, 0, sizeof(int)));
+    return set_err(c, VOFL_ETIMEDOUT, "a device wait gave up (asynchronous copy never completed)");
+  }
   return VOFL_OK;
 }
 

@@ -127,6 +127,36 @@ struct LineFFT {
   __device__ __forceinline__ static int pad(int a) { return a + a / E; }
 };
 
+// Stage 0 of the line transform for one lane: DFT-E over the lane's E
+// elements v[r] = x[j + LANES r] (butterfly j), Stockham write of the result
+// to the line buffer `lb` at pad(j E + r).
+template <int N, bool INV>
+__device__ __forceinline__ void stage0_to_smem(float2 (&v)[LineFFT<N>::E], float2* lb, int j) {
+  using F = LineFFT<N>;
+  constexpr int E = F::E;
+  dft<E, INV>(v);
+#pragma unroll
+  for (int r = 0; r < E; ++r) lb[F::pad(j * E + r)] = v[r];
+}
+
+// Stage 1 butterfly j (0 <= j < E) of a line whose stage-0 output is in
+// `lb`: inputs lb[pad(j + r E)], twiddles w_N^{r j}, DFT-LANES; on return
+// w[r] = X[j + r E], r < LANES.
+template <int N, bool INV>
+__device__ __forceinline__ void stage1_from_smem(float2 (&w)[LineFFT<N>::LANES], const float2* lb,
+                                                 const float2* __restrict__ tw, int j) {
+  using F = LineFFT<N>;
+  constexpr int E = F::E, LANES = F::LANES;
+#pragma unroll
+  for (int r = 0; r < LANES; ++r) w[r] = lb[F::pad(j + r * E)];
+#pragma unroll
+  for (int r = 1; r < LANES; ++r) {
+    const float2 t = tw[r * E + j];
+    w[r] = INV ? cmulc(w[r], t) : cmul(w[r], t);
+  }
+  dft<LANES, INV>(w);
+}
+
 // Transform one line in place.  v[m] = x[li + LANES*m] on entry and
 // X[li + LANES*m] on exit.  `buf` is the warp's exchange buffer
 // (LineFFT<N>::WARP_SLOTS float2), `tw` the twiddle table (shared or global),
@@ -136,32 +166,30 @@ template <int N, bool INV>
 __device__ __forceinline__ void fft_line(float2 (&v)[LineFFT<N>::E], float2* buf, const float2* __restrict__ tw,
                                          int li, int line) {
   using F = LineFFT<N>;
-  constexpr int E = F::E, LANES = F::LANES, BPL = F::BPL;
+  constexpr int LANES = F::LANES, BPL = F::BPL;
   float2* lb = buf + line * F::PAD_LINE;
-  // stage 0: one DFT-E per lane over x[li + LANES r]
-  dft<E, INV>(v);
-  // Stockham write: idxD = j*R0 + r with j = li
-#pragma unroll
-  for (int r = 0; r < E; ++r) lb[F::pad(li * E + r)] = v[r];
+  stage0_to_smem<N, INV>(v, lb, li);
   __syncwarp();
-  // stage 1: butterflies j = li + LANES q, k = j (< E), inputs j + r E
 #pragma unroll
   for (int q = 0; q < BPL; ++q) {
-    const int j = li + LANES * q;
     float2 w[LANES];
-#pragma unroll
-    for (int r = 0; r < LANES; ++r) w[r] = lb[F::pad(j + r * E)];
-#pragma unroll
-    for (int r = 1; r < LANES; ++r) {
-      const float2 t = tw[r * E + j];
-      w[r] = INV ? cmulc(w[r], t) : cmul(w[r], t);
-    }
-    dft<LANES, INV>(w);
+    stage1_from_smem<N, INV>(w, lb, tw, li + LANES * q);
     // outputs X[j + r E] = X[li + LANES (q + BPL r)]
 #pragma unroll
     for (int r = 0; r < LANES; ++r) v[q + BPL * r] = w[r];
   }
   __syncwarp();
+}
+
+// Integer power by squaring (n >= 0).
+__device__ __forceinline__ float powi(float x, int n) {
+  float r = 1.f;
+  while (n) {
+    if (n & 1) r *= x;
+    x *= x;
+    n >>= 1;
+  }
+  return r;
 }
 
 }  // namespace vofl

@@ -33,6 +33,7 @@
 
 #include "fft_warp.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace vofl {
 
@@ -114,45 +115,64 @@ __global__ void __launch_bounds__(THREADS) k2d_fwd_rows(const float* __restrict_
 }
 
 // -------------------------------------------------------------------------
-// F2: forward FFT along y of each half-spectrum column.
+// F2: forward FFT along y of each half-spectrum column.  Stage 0 is done
+// cooperatively by the CTA: thread b takes column b % CW, butterfly b / CW,
+// so each load instruction reads row segments of CW adjacent columns of T
+// (coalesced, no transposition pass); stage 1 is done by the warp owning
+// the column, whose output is a contiguous column of Uh.
 // -------------------------------------------------------------------------
 template <int NY>
 __global__ void __launch_bounds__(THREADS) k2d_fwd_cols(const float2* __restrict__ T, int pT, float2* __restrict__ Uh,
                                                         int ncols, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
-  constexpr int E = F::E, LANES = F::LANES;
+  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
+  constexpr int CW = WARPS * LPW;  // columns per CTA
   __shared__ float2 s_tw[NY];
   extern __shared__ float2 s_buf[];
   for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
+  const int c0 = blockIdx.x * CW;
+  {
+    // cooperative stage 0: one radix-E butterfly per thread
+    const int cc = threadIdx.x % CW, j = threadIdx.x / CW;
+    const int col = min(c0 + cc, ncols - 1);
+    float2 v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) v[r] = T[(size_t)(j + LANES * r) * pT + col];
+    float2* lb = s_buf + (cc / LPW) * warp_stride<NY>() + (cc % LPW) * F::PAD_LINE;
+    stage0_to_smem<NY, false>(v, lb, j);
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
-  float2* wbuf = s_buf + warp * warp_stride<NY>();
-  const int c = (blockIdx.x * WARPS + warp) * F::LPW + line;
-  const bool active = c < ncols;
-  const int cc = active ? c : 0;
-  float2 v[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = T[(size_t)(li + LANES * m) * pT + cc];
-  fft_line<NY, false>(v, wbuf, s_tw, li, line);
-  if (active) {
+  const float2* lb = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
+  const int c = c0 + warp * LPW + line;
+  if (c < ncols) {
     float2* dst = Uh + (size_t)c * NY;
 #pragma unroll
-    for (int m = 0; m < E; ++m) dst[li + LANES * m] = v[m];
+    for (int q = 0; q < BPL; ++q) {
+      float2 w[LANES];
+      stage1_from_smem<NY, false>(w, lb, s_tw, li + LANES * q);
+#pragma unroll
+      for (int r = 0; r < LANES; ++r) dst[li + LANES * (q + BPL * r)] = w[r];
+    }
   }
 }
 
 // -------------------------------------------------------------------------
 // I1: multiplier + inverse FFT along y, for terms [m_lo, m_hi) of one
 // operator (blockIdx.y).  Output Z[s][op][y][c], s = m - m_lo.
+// Each warp keeps its column's spectrum and the multiplier recurrence
+// t_m = P ln|mu|^{2m}/m! in registers and does stage 0; stage 1 is done
+// cooperatively by the CTA (thread b: column b % CW, butterfly b / CW), so
+// every store writes row segments of CW adjacent columns of Z.
 // -------------------------------------------------------------------------
 template <int NY>
 __global__ void __launch_bounds__(THREADS) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
                                                         const float* __restrict__ Lg, float2* __restrict__ Z,
                                                         long long zslot, int pZ, int ncols, int m_lo, int m_hi,
-                                                        const float2* __restrict__ twy) {
+                                                        float inv_fact_lo, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
-  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW;
+  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
   constexpr int CW = WARPS * LPW;  // columns per CTA
   __shared__ float2 s_tw[NY];
   extern __shared__ float2 s_buf[];
@@ -161,11 +181,10 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_cols(const float2* __restrict
   const int op = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
-  float2* wbuf = s_buf + warp * warp_stride<NY>();
+  float2* lb_own = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
   const int c0 = blockIdx.x * CW;
   const int c = c0 + warp * LPW + line;
-  const bool active = c < ncols;
-  const int cc = active ? c : 0;
+  const int cc = min(c, ncols - 1);
   const long long tot = (long long)ncols * NY;
   const float2* uh_col = Uh + (size_t)cc * NY;
   const float* p_col = P + op * tot + (size_t)cc * NY;
@@ -176,65 +195,96 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_cols(const float2* __restrict
   for (int m = 0; m < E; ++m) {
     const int y = li + LANES * m;
     uh[m] = uh_col[y];
-    float t = p_col[y];
-    const float l = l_col[y];
-    for (int j = 1; j <= m_lo; ++j) t = t * (l * (1.0f / (float)j));
-    tm[m] = t;
+    tm[m] = p_col[y] * powi(l_col[y], m_lo) * inv_fact_lo;
+  }
+  // cooperative stage-1 assignment of this thread
+  int sc[BPL], sj[BPL];
+#pragma unroll
+  for (int q = 0; q < BPL; ++q) {
+    const int b = threadIdx.x + THREADS * q;
+    sc[q] = b % CW;
+    sj[q] = b / CW;
   }
   for (int mt = m_lo; mt < m_hi; ++mt) {
     float2 x[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) x[m] = cscale(uh[m], tm[m]);
-    fft_line<NY, true>(x, wbuf, s_tw, li, line);
-    float2* lb = wbuf + line * F::PAD_LINE;
-#pragma unroll
-    for (int m = 0; m < E; ++m) lb[F::pad(li + LANES * m)] = x[m];
+    stage0_to_smem<NY, true>(x, lb_own, li);
     __syncthreads();
-    // cooperative, row-segment-coalesced store of the CTA's [NY][CW] tile:
-    // THREADS is a multiple of CW, so each thread keeps one column k and
-    // walks rows y = y0 + RSTEP*i with constant address increments.
-    {
-      constexpr int RSTEP = THREADS / CW;
-      const int k = threadIdx.x % CW, y0 = threadIdx.x / CW;
-      const float2* colbuf = s_buf + (k / LPW) * warp_stride<NY>() + (k % LPW) * F::PAD_LINE;
-      float2* dst = Z + (long long)((mt - m_lo) * 2 + op) * zslot + (size_t)y0 * pZ + c0 + k;
-      if (c0 + k < ncols) {
-#pragma unroll 8
-        for (int i = 0; i < NY / RSTEP; ++i) dst[(size_t)i * RSTEP * pZ] = colbuf[F::pad(y0 + RSTEP * i)];
+    float2* zb = Z + (long long)((mt - m_lo) * 2 + op) * zslot + c0;
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+      const float2* lb = s_buf + (sc[q] / LPW) * warp_stride<NY>() + (sc[q] % LPW) * F::PAD_LINE;
+      float2 w[LANES];
+      stage1_from_smem<NY, true>(w, lb, s_tw, sj[q]);
+      if (c0 + sc[q] < ncols) {
+#pragma unroll
+        for (int r = 0; r < LANES; ++r) zb[(size_t)(sj[q] + E * r) * pZ + sc[q]] = w[r];
       }
     }
-    __syncthreads();
     if (mt + 1 < m_hi) {
       const float rinv = 1.0f / (float)(mt + 1);
 #pragma unroll
       for (int m = 0; m < E; ++m) tm[m] = tm[m] * (l_col[li + LANES * m] * rinv);
     }
+    __syncthreads();  // stage-1 reads done before the next term's stage-0 writes
   }
 }
 
 // -------------------------------------------------------------------------
 // I2: inverse FFT along x of both operators (A + iB), Horner accumulation
 // over the group's terms, then partial store or epilogue.
+// The two Z rows (operator 1 and 2) of the next term are copied into shared
+// memory by TMA bulk copies while the current term is transformed (double
+// buffer per line, mbarrier completion, bounded waits).
 // -------------------------------------------------------------------------
+template <int NX>
+constexpr int rows_rb() {
+  return (NX / 2 + 2) & ~1;  // Z row copy length in float2: >= H+1, 16-byte multiple
+}
+template <int NX>
+constexpr size_t inv_rows_smem() {
+  return dyn_smem<NX>() + (size_t)WARPS * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
+}
+
 template <int NX>
 __global__ void __launch_bounds__(THREADS) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ, int ny,
                                                         int m_lo, int m_hi, int top, const float* __restrict__ delta,
                                                         float* __restrict__ part1, float* __restrict__ part2,
                                                         EpiArgs<float> epi, float inv_lambda,
-                                                        const float2* __restrict__ twx) {
+                                                        const float2* __restrict__ twx, int* err) {
   using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2;
+  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW;
+  constexpr int RB = rows_rb<NX>();
+  constexpr uint32_t RB_BYTES = RB * sizeof(float2);
   __shared__ float2 s_tw[NX];
+  __shared__ uint64_t s_bar[WARPS * LPW * 2];
   extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
+  const int lid = warp * LPW + line;  // line id inside the CTA
+  uint64_t* bar = s_bar + 2 * lid;
+  float2* zbuf = s_buf + WARPS * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
+  if (li == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
+  __syncthreads();
   float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int yr = (blockIdx.x * WARPS + warp) * F::LPW + line;
+  const int yr = (blockIdx.x * WARPS + warp) * LPW + line;
   const bool active = yr < ny;
   const int y = active ? yr : 0;
   const size_t row = (size_t)y * NX;
+  auto issue = [&](int buf, int mt) {
+    const float2* z1 = Z + (long long)((mt - m_lo) * 2 + 0) * zslot + (size_t)y * pZ;
+    const float2* z2 = Z + (long long)((mt - m_lo) * 2 + 1) * zslot + (size_t)y * pZ;
+    mbar_arrive_expect_tx(&bar[buf], 2 * RB_BYTES);
+    bulk_copy_g2s(zbuf + buf * 2 * RB, z1, RB_BYTES, &bar[buf]);
+    bulk_copy_g2s(zbuf + buf * 2 * RB + RB, z2, RB_BYTES, &bar[buf]);
+  };
+  if (li == 0) issue(0, m_hi - 1);
   float a1[E], a2[E];
   if (top) {
 #pragma unroll
@@ -246,19 +296,38 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_rows(const float2* __restrict
       a2[m] = part2[row + li + LANES * m];
     }
   }
-  for (int mt = m_hi - 1; mt >= m_lo; --mt) {
-    const float2* z1 = Z + (long long)((mt - m_lo) * 2 + 0) * zslot + (size_t)y * pZ;
-    const float2* z2 = Z + (long long)((mt - m_lo) * 2 + 1) * zslot + (size_t)y * pZ;
+  uint32_t phase = 0;  // bit b: parity to wait for on buffer b
+  int it = 0;
+  bool ok = true;
+  for (int mt = m_hi - 1; mt >= m_lo; --mt, ++it) {
+    const int b = it & 1;
+    if (mt > m_lo) {
+      __syncwarp();  // every lane finished reading buffer b^1 (two terms ago)
+      if (li == 0) {
+        fence_proxy_async_smem();
+        issue(b ^ 1, mt - 1);
+      }
+    }
+    const bool got = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, err);
+    phase ^= 1u << b;
+    if (!__all_sync(0xffffffffu, got)) {
+      // give up: drain the prefetch still in flight (bounded) and leave
+      if (mt > m_lo) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u, err);
+      ok = false;
+      break;
+    }
+    const float2* z1 = zbuf + b * 2 * RB;
+    const float2* z2 = z1 + RB;
     float2 w[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int n = li + LANES * m;
       if (n <= H) {
-        const float2 a = z1[n], b = z2[n];
-        w[m] = (n == 0 || n == H) ? make_float2(a.x, b.x) : make_float2(a.x - b.y, a.y + b.x);
+        const float2 p = z1[n], q = z2[n];
+        w[m] = (n == 0 || n == H) ? make_float2(p.x, q.x) : make_float2(p.x - q.y, p.y + q.x);
       } else {
-        const float2 a = z1[NX - n], b = z2[NX - n];
-        w[m] = make_float2(a.x + b.y, b.x - a.y);
+        const float2 p = z1[NX - n], q = z2[NX - n];
+        w[m] = make_float2(p.x + q.y, q.x - p.y);
       }
     }
     fft_line<NX, true>(w, wbuf, s_tw, li, line);
@@ -269,7 +338,7 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_rows(const float2* __restrict
       a2[m] = fmaf(d, a2[m], w[m].y);
     }
   }
-  if (!active) return;
+  if (!active || !ok) return;
   if (m_lo > 0) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -289,11 +358,11 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_rows(const float2* __restrict
 struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, float, const float2*, int*, int);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*);
-  void (*inv_cols)(const float2*, const float*, const float*, float2*, long long, int, int, int, int,
+  void (*inv_cols)(const float2*, const float*, const float*, float2*, long long, int, int, int, int, float,
                    const float2*);
   void (*inv_rows)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>,
-                   float, const float2*);
-  size_t smem_x, smem_y;
+                   float, const float2*, int*);
+  size_t smem_x, smem_y, smem_rows;
   int lpw_x, lpw_y;
 };
 
@@ -306,6 +375,7 @@ Kernels kernels_for() {
   k.inv_rows = k2d_inv_rows<NX>;
   k.smem_x = dyn_smem<NX>();
   k.smem_y = dyn_smem<NY>();
+  k.smem_rows = inv_rows_smem<NX>();
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
   return k;
@@ -332,6 +402,13 @@ bool pick_kernels(int nx, int ny, Kernels* k) {
 }
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// 1/m! in double, rounded once to float
+inline float inv_factorial(int m) {
+  double f = 1.0;
+  for (int i = 2; i <= m; ++i) f *= i;
+  return (float)(1.0 / f);
+}
 
 struct Fused2D : Engine {
   int nx = 0, ny = 0, H = 0, ncols = 0;
@@ -398,7 +475,7 @@ struct Fused2D : Engine {
     if ((st = alloc(c, (void**)&twx, sizeof(float2) * nx))) return st;
     if ((st = alloc(c, (void**)&twy, sizeof(float2) * ny))) return st;
     VOFL_CUDA(c, cudaFuncSetAttribute(k.fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_x));
-    VOFL_CUDA(c, cudaFuncSetAttribute(k.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_x));
+    VOFL_CUDA(c, cudaFuncSetAttribute(k.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_rows));
     VOFL_CUDA(c, cudaFuncSetAttribute(k.fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_y));
     VOFL_CUDA(c, cudaFuncSetAttribute(k.inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_y));
     const int ex = nx >= 512 ? 32 : (nx >= 128 ? 16 : 8);
@@ -452,12 +529,13 @@ struct Fused2D : Engine {
     const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * g, m_hi = std::min(c->M + 1, m_lo + g);
-      k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi, twy);
+      k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi,
+                                                        inv_factorial(m_lo), twy);
       EpiArgs<float> e = epi;
       if (gi > 0) e.mode = EPI_PARTIAL;
-      k.inv_rows<<<gir, THREADS, k.smem_x, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
-                                                        (const float*)c->delta, part, part + (size_t)nx * ny, e,
-                                                        inv_lambda, twx);
+      k.inv_rows<<<gir, THREADS, k.smem_rows, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
+                                                           (const float*)c->delta, part, part + (size_t)nx * ny, e,
+                                                           inv_lambda, twx, c->d_step + 1);
       count_launch(2);
     }
     return VOFL_OK;
@@ -534,13 +612,14 @@ struct Fused2D : Engine {
       cudaEventRecord(ev[e++], c->stream);
       for (int gi = K - 1; gi >= 0; --gi) {
         const int m_lo = gi * g, m_hi = std::min(c->M + 1, m_lo + g);
-        k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi, twy);
+        k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi,
+                                                          inv_factorial(m_lo), twy);
         cudaEventRecord(ev[e++], c->stream);
         EpiArgs<float> epg = ep;
         if (gi > 0) epg.mode = EPI_PARTIAL;
-        k.inv_rows<<<gir, THREADS, k.smem_x, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
-                                                          (const float*)c->delta, part, part + (size_t)nx * ny, epg,
-                                                          inv_lambda, twx);
+        k.inv_rows<<<gir, THREADS, k.smem_rows, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
+                                                             (const float*)c->delta, part, part + (size_t)nx * ny,
+                                                             epg, inv_lambda, twx, c->d_step + 1);
         cudaEventRecord(ev[e++], c->stream);
         if (r == 0) {
           terms_cols += m_hi - m_lo;
@@ -626,7 +705,7 @@ namespace {
 constexpr int NOALLOC_MAX_AXIS = 256;
 constexpr size_t NOALLOC_BYTES = size_t(6) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
-static_assert(dyn_smem<NOALLOC_MAX_AXIS>() <= 48 * 1024, "no shared-memory opt-in needed up to 256 points per axis");
+bool g_noalloc_attr_set[64] = {};
 
 struct NoAllocLayout {
   size_t delta, A, B, red, T, Uh, Z, part, P, Lg, twx, twy, step, total;
@@ -702,6 +781,26 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   unsigned char* base = nullptr;
   int st = noalloc_base(&base);
   if (st) return st;
+  {
+    // kernels with more than 48 KB of dynamic shared memory need the opt-in
+    // attribute, set once per device for every shape this entry accepts
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_attr_set[dev]) {
+      const int shapes[5][2] = {{64, 64}, {128, 128}, {256, 256}, {256, 128}, {128, 256}};
+      for (const auto& sh : shapes) {
+        Kernels kk;
+        if (!pick_kernels(sh[0], sh[1], &kk)) continue;
+        if (cudaFuncSetAttribute(kk.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kk.smem_rows) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          return VOFL_ECUDA;
+        }
+      }
+      g_noalloc_attr_set[dev] = true;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
 
   // per-model part: gamma0 = grid mean of gamma and delta = gamma - gamma0
@@ -757,12 +856,12 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
   for (int gi = K - 1; gi >= 0; --gi) {
     const int m_lo = gi * G, m_hi = std::min(M + 1, m_lo + G);
-    k.inv_cols<<<gic, THREADS, k.smem_y, s>>>(Uh, P, Lgt, Z, zslot, pZ, ncols, m_lo, m_hi, twy);
+    k.inv_cols<<<gic, THREADS, k.smem_y, s>>>(Uh, P, Lgt, Z, zslot, pZ, ncols, m_lo, m_hi, inv_factorial(m_lo), twy);
     EpiArgs<float> e = epi;
     if (gi > 0) e.mode = EPI_PARTIAL;
-    k.inv_rows<<<gir, THREADS, k.smem_x, s>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
-                                              reinterpret_cast<const float*>(m.delta), part,
-                                              part + (size_t)nx * ny, e, inv_lambda, twx);
+    k.inv_rows<<<gir, THREADS, k.smem_rows, s>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
+                                                 reinterpret_cast<const float*>(m.delta), part,
+                                                 part + (size_t)nx * ny, e, inv_lambda, twx, stepc + 1);
     count_launch(2);
   }
   if (cudaGetLastError() != cudaSuccess) return VOFL_ECUDA;
