@@ -4,15 +4,15 @@
 //
 // Data path of one step on an nx * ny grid (x fastest), H = nx/2:
 //   F1 k2d_fwd_rows   u (ny x nx f32) -> T (ny x (H+1) c64)
-//        one warp-line per PAIR of rows: the complex FFT of u[y0] + i u[y0+1]
-//        is split into the two half spectra (real-data two-for-one);
+//        one line per PAIR of rows: the complex FFT of w[y0] + i w[y0+1],
+//        w = the discrete Laplacian of u, split into the two half spectra;
 //   F2 k2d_fwd_cols   T -> Uh ((H+1) x ny c64, column-major)
-//        complex FFT along y of each of the H+1 columns; Uh = N * u_hat;
+//        complex FFT along y of each of the H+1 columns;
 //   then for Taylor groups g = K-1 .. 0 (terms [m_lo, m_hi)):
 //   I1 k2d_inv_cols   Uh -> Z[g] (per term and operator, ny x (H+1) c64)
-//        multiplier P_op(k) ln|mu_k|^{2m}/m! (P_op = |mu|^{2 s0_op}/N) applied
-//        in registers by the recurrence t_m = t_{m-1} ln|mu|^2 / m, then the
-//        inverse FFT along y; the M+1 multiplied spectra never exist in memory;
+//        multiplier P_op(k) ln|mu_k|^{2m}/m! applied in registers by the
+//        recurrence t_m = t_{m-1} ln|mu|^2 / m, then the inverse FFT along y;
+//        the M+1 multiplied spectra never exist in memory;
 //   I2 k2d_inv_rows   Z[g] -> accumulators / epilogue
 //        inverse FFT along x of BOTH operators at once: the row spectra A
 //        (operator 1) and B (operator 2) are Hermitian, so one complex
@@ -23,11 +23,17 @@
 // Only the between-group partial sums (2 fields) and one group of spectra
 // (G terms) are stored: storage O(N) in M, against O(MN) for storing every
 // term.
+//
+// Launches use programmatic dependent launch: each kernel does the work
+// that does not read its predecessor's output (twiddle and table loads,
+// barrier set-up) before griddepcontrol.wait, so it overlaps the tail of
+// the previous kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -39,8 +45,13 @@ namespace vofl {
 
 namespace {
 
-constexpr int WARPS = 8;           // warps per CTA in every fused kernel
-constexpr int THREADS = WARPS * 32;
+// CTA sizes (warps) per kernel
+constexpr int W_FROWS = 2;  // forward rows: small CTAs, 4x more CTAs than SMs at 1024^2
+constexpr int W_FCOLS = 4;  // forward columns: 4 columns -> 32-byte row segments
+constexpr int W_INV = 8;    // inverse kernels
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 template <int N>
 constexpr int warp_stride() {
@@ -49,29 +60,31 @@ constexpr int warp_stride() {
   // consecutive rows touches 16 distinct bank pairs
   return (LineFFT<N>::WARP_SLOTS + 15) / 16 * 16 + 2;
 }
-template <int N>
-constexpr size_t dyn_smem() {
-  return (size_t)WARPS * warp_stride<N>() * sizeof(float2);
+template <int N, int W>
+constexpr size_t exch_smem() {
+  return (size_t)W * warp_stride<N>() * sizeof(float2);
 }
 
 // -------------------------------------------------------------------------
 // F1: forward FFT along x of two rows at once, split into half spectra.
 // -------------------------------------------------------------------------
 template <int NX>
-__global__ void __launch_bounds__(THREADS) k2d_fwd_rows(const float* __restrict__ u, float2* __restrict__ T, int ny,
-                                                        int pT, float ryy, const float2* __restrict__ twx,
-                                                        int* step_ctr, int inc_step) {
+__global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __restrict__ u, float2* __restrict__ T,
+                                                             int ny, int pT, float ryy, const float2* __restrict__ twx,
+                                                             int* step_ctr, int inc_step) {
   using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2;
+  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, THREADS = W_FROWS * 32;
   __shared__ float2 s_tw[NX];
   extern __shared__ float2 s_buf[];
   for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
-  if (inc_step && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
   __syncthreads();
+  pdl_wait();  // u is written by the previous step's last kernel
+  pdl_trigger();
+  if (inc_step && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int pair = (blockIdx.x * WARPS + warp) * F::LPW + line;
+  const int pair = (blockIdx.x * W_FROWS + warp) * F::LPW + line;
   const bool active = pair < ny / 2;
   const int y0 = 2 * (active ? pair : 0);
   const float* r0 = u + (size_t)y0 * NX;
@@ -122,14 +135,17 @@ __global__ void __launch_bounds__(THREADS) k2d_fwd_rows(const float* __restrict_
 // the column, whose output is a contiguous column of Uh.
 // -------------------------------------------------------------------------
 template <int NY>
-__global__ void __launch_bounds__(THREADS) k2d_fwd_cols(const float2* __restrict__ T, int pT, float2* __restrict__ Uh,
-                                                        int ncols, const float2* __restrict__ twy) {
+__global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __restrict__ T, int pT,
+                                                             float2* __restrict__ Uh, int ncols,
+                                                             const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
-  constexpr int CW = WARPS * LPW;  // columns per CTA
+  constexpr int THREADS = W_FCOLS * 32, CW = W_FCOLS * LPW;  // columns per CTA
   __shared__ float2 s_tw[NY];
   extern __shared__ float2 s_buf[];
   for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
+  pdl_wait();  // T is written by k2d_fwd_rows
+  pdl_trigger();
   const int c0 = blockIdx.x * CW;
   {
     // cooperative stage 0: one radix-E butterfly per thread
@@ -162,26 +178,32 @@ __global__ void __launch_bounds__(THREADS) k2d_fwd_cols(const float2* __restrict
 // I1: multiplier + inverse FFT along y, for terms [m_lo, m_hi) of one
 // operator (blockIdx.y).  Output Z[s][op][y][c], s = m - m_lo.
 // Each warp keeps its column's spectrum and the multiplier recurrence
-// t_m = P ln|mu|^{2m}/m! in registers and does stage 0; stage 1 is done
-// cooperatively by the CTA (thread b: column b % CW, butterfly b / CW), so
-// every store writes row segments of CW adjacent columns of Z.
+// t_m = P ln|mu|^{2m}/m! in registers (ln|mu|^2 in shared memory) and does
+// stage 0; stage 1 is done cooperatively by the CTA (thread b: column
+// b % CW, butterfly b / CW), so every store writes row segments of CW
+// adjacent columns of Z.
 // -------------------------------------------------------------------------
 template <int NY>
-__global__ void __launch_bounds__(THREADS) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
-                                                        const float* __restrict__ Lg, float2* __restrict__ Z,
-                                                        long long zslot, int pZ, int ncols, int m_lo, int m_hi,
-                                                        float inv_fact_lo, const float2* __restrict__ twy) {
+constexpr size_t inv_cols_smem() {
+  return exch_smem<NY, W_INV>() + (size_t)W_INV * LineFFT<NY>::LPW * NY * sizeof(float);
+}
+
+template <int NY>
+__global__ void __launch_bounds__(W_INV * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
+                                                           const float* __restrict__ Lg, float2* __restrict__ Z,
+                                                           long long zslot, int pZ, int ncols, int m_lo, int m_hi,
+                                                           float inv_fact_lo, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
-  constexpr int CW = WARPS * LPW;  // columns per CTA
+  constexpr int THREADS = W_INV * 32, CW = W_INV * LPW;  // columns per CTA
   __shared__ float2 s_tw[NY];
   extern __shared__ float2 s_buf[];
   for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
-  __syncthreads();
   const int op = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   float2* lb_own = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
+  float* s_lg = reinterpret_cast<float*>(s_buf + W_INV * warp_stride<NY>()) + (size_t)(warp * LPW + line) * NY;
   const int c0 = blockIdx.x * CW;
   const int c = c0 + warp * LPW + line;
   const int cc = min(c, ncols - 1);
@@ -189,14 +211,21 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_cols(const float2* __restrict
   const float2* uh_col = Uh + (size_t)cc * NY;
   const float* p_col = P + op * tot + (size_t)cc * NY;
   const float* l_col = Lg + (size_t)cc * NY;
-  float2 uh[E];
   float tm[E];
+  // tables first (they do not depend on the previous kernel)
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int y = li + LANES * m;
-    uh[m] = uh_col[y];
-    tm[m] = p_col[y] * powi(l_col[y], m_lo) * inv_fact_lo;
+    const float l = l_col[y];
+    s_lg[y] = l;
+    tm[m] = p_col[y] * powi(l, m_lo) * inv_fact_lo;
   }
+  __syncthreads();
+  pdl_wait();  // Uh (k2d_fwd_cols) ready; the previous group's readers of Z are done
+  pdl_trigger();
+  float2 uh[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) uh[m] = uh_col[li + LANES * m];
   // cooperative stage-1 assignment of this thread
   int sc[BPL], sj[BPL];
 #pragma unroll
@@ -225,7 +254,7 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_cols(const float2* __restrict
     if (mt + 1 < m_hi) {
       const float rinv = 1.0f / (float)(mt + 1);
 #pragma unroll
-      for (int m = 0; m < E; ++m) tm[m] = tm[m] * (l_col[li + LANES * m] * rinv);
+      for (int m = 0; m < E; ++m) tm[m] = tm[m] * (s_lg[li + LANES * m] * rinv);
     }
     __syncthreads();  // stage-1 reads done before the next term's stage-0 writes
   }
@@ -244,27 +273,28 @@ constexpr int rows_rb() {
 }
 template <int NX>
 constexpr size_t inv_rows_smem() {
-  return dyn_smem<NX>() + (size_t)WARPS * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
+  return exch_smem<NX, W_INV>() + (size_t)W_INV * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
 }
 
 template <int NX>
-__global__ void __launch_bounds__(THREADS) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ, int ny,
-                                                        int m_lo, int m_hi, int top, const float* __restrict__ delta,
-                                                        float* __restrict__ part1, float* __restrict__ part2,
-                                                        EpiArgs<float> epi, float inv_lambda,
-                                                        const float2* __restrict__ twx, int* err) {
+__global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
+                                                           int ny, int m_lo, int m_hi, int top,
+                                                           const float* __restrict__ delta, float* __restrict__ part1,
+                                                           float* __restrict__ part2, EpiArgs<float> epi,
+                                                           float inv_lambda, const float2* __restrict__ twx,
+                                                           int* err) {
   using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW;
+  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W_INV * 32;
   constexpr int RB = rows_rb<NX>();
   constexpr uint32_t RB_BYTES = RB * sizeof(float2);
   __shared__ float2 s_tw[NX];
-  __shared__ uint64_t s_bar[WARPS * LPW * 2];
+  __shared__ uint64_t s_bar[W_INV * LPW * 2];
   extern __shared__ float2 s_buf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   const int lid = warp * LPW + line;  // line id inside the CTA
   uint64_t* bar = s_bar + 2 * lid;
-  float2* zbuf = s_buf + WARPS * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
+  float2* zbuf = s_buf + W_INV * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
   if (li == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -272,8 +302,10 @@ __global__ void __launch_bounds__(THREADS) k2d_inv_rows(const float2* __restrict
   }
   for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
   __syncthreads();
+  pdl_wait();  // Z of this group and the previous group's partial sums are ready
+  pdl_trigger();
   float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int yr = (blockIdx.x * WARPS + warp) * LPW + line;
+  const int yr = (blockIdx.x * W_INV + warp) * LPW + line;
   const bool active = yr < ny;
   const int y = active ? yr : 0;
   const size_t row = (size_t)y * NX;
@@ -362,7 +394,7 @@ struct Kernels {
                    const float2*);
   void (*inv_rows)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>,
                    float, const float2*, int*);
-  size_t smem_x, smem_y, smem_rows;
+  size_t smem_frows, smem_fcols, smem_icols, smem_irows;
   int lpw_x, lpw_y;
 };
 
@@ -373,9 +405,10 @@ Kernels kernels_for() {
   k.fwd_cols = k2d_fwd_cols<NY>;
   k.inv_cols = k2d_inv_cols<NY>;
   k.inv_rows = k2d_inv_rows<NX>;
-  k.smem_x = dyn_smem<NX>();
-  k.smem_y = dyn_smem<NY>();
-  k.smem_rows = inv_rows_smem<NX>();
+  k.smem_frows = exch_smem<NX, W_FROWS>();
+  k.smem_fcols = exch_smem<NY, W_FCOLS>();
+  k.smem_icols = inv_cols_smem<NY>();
+  k.smem_irows = inv_rows_smem<NX>();
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
   return k;
@@ -401,6 +434,17 @@ bool pick_kernels(int nx, int ny, Kernels* k) {
   return false;
 }
 
+int set_smem_attributes(const Kernels& k) {
+  if (cudaFuncSetAttribute(k.fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_frows) ||
+      cudaFuncSetAttribute(k.fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fcols) ||
+      cudaFuncSetAttribute(k.inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_icols) ||
+      cudaFuncSetAttribute(k.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_irows)) {
+    cudaGetLastError();
+    return VOFL_ECUDA;
+  }
+  return VOFL_OK;
+}
+
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // 1/m! in double, rounded once to float
@@ -410,21 +454,94 @@ inline float inv_factorial(int m) {
   return (float)(1.0 / f);
 }
 
-struct Fused2D : Engine {
-  int nx = 0, ny = 0, H = 0, ncols = 0;
-  int pT = 0, pZ = 0;
-  int G = 1;  // Taylor terms per group
-  int Gcap = 1;
+// Launch with programmatic stream serialisation: the kernel may start while
+// its predecessor finishes and synchronises itself with griddepcontrol.wait.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Every buffer and constant one fused 2D apply / step needs.
+struct Plan2D {
   Kernels k{};
-  float2* T = nullptr;
-  float2* Uh = nullptr;
-  float2* Z = nullptr;
+  int nx = 0, ny = 0, ncols = 0, pT = 0, pZ = 0, G = 6;
   long long zslot = 0;
+  float2 *T = nullptr, *Uh = nullptr, *Z = nullptr;
   float* part = nullptr;  // 2 fields
   float* P = nullptr;     // [2][ncols][ny]
   float* Lg = nullptr;    // [ncols][ny]
-  float2* twx = nullptr;
-  float2* twy = nullptr;
+  float2 *twx = nullptr, *twy = nullptr;
+  const float* delta = nullptr;
+  int* step_ctr = nullptr;
+  int* err = nullptr;
+  float ryy = 1.f, inv_lambda = 1.f;
+
+  int groups(int M) const { return (M + 1 + G - 1) / G; }
+
+  // optional events: ev[1] after F1, ev[2] after F2 (ev[0] recorded by the caller)
+  cudaError_t forward(cudaStream_t s, const float* u, bool inc_step, cudaEvent_t* ev = nullptr) const {
+    const int rpc = W_FROWS * k.lpw_x;  // row pairs per CTA
+    cudaError_t e = launch_pdl(k.fwd_rows, dim3((ny / 2 + rpc - 1) / rpc), dim3(W_FROWS * 32), k.smem_frows, s, u,
+                               T, ny, pT, ryy, (const float2*)twx, step_ctr, inc_step ? 1 : 0);
+    if (e) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+    const int cpc = W_FCOLS * k.lpw_y;
+    e = launch_pdl(k.fwd_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_FCOLS * 32), k.smem_fcols, s, (const float2*)T,
+                   pT, Uh, ncols, (const float2*)twy);
+    if (ev) cudaEventRecord(ev[2], s);
+    return e;
+  }
+
+  // optional events: one after every inverse kernel, from ev[3] on
+  cudaError_t inverse(cudaStream_t s, int M, const EpiArgs<float>& epi, cudaEvent_t* ev = nullptr) const {
+    const int K = groups(M);
+    const int cpc = W_INV * k.lpw_y;
+    const dim3 gic((ncols + cpc - 1) / cpc, 2);
+    const int rpc = W_INV * k.lpw_x;
+    const dim3 gir((ny + rpc - 1) / rpc);
+    int e_i = 3;
+    for (int gi = K - 1; gi >= 0; --gi) {
+      const int m_lo = gi * G, m_hi = std::min(M + 1, m_lo + G);
+      cudaError_t e = launch_pdl(k.inv_cols, gic, dim3(W_INV * 32), k.smem_icols, s, (const float2*)Uh,
+                                 (const float*)P, (const float*)Lg, Z, zslot, pZ, ncols, m_lo, m_hi,
+                                 inv_factorial(m_lo), (const float2*)twy);
+      if (e) return e;
+      if (ev) cudaEventRecord(ev[e_i++], s);
+      EpiArgs<float> ep = epi;
+      if (gi > 0) ep.mode = EPI_PARTIAL;
+      e = launch_pdl(k.inv_rows, gir, dim3(W_INV * 32), k.smem_irows, s, (const float2*)Z, zslot, pZ, ny, m_lo, m_hi,
+                     gi == K - 1 ? 1 : 0, delta, part, part + (size_t)nx * ny, ep, inv_lambda, (const float2*)twx,
+                     err);
+      if (e) return e;
+      if (ev) cudaEventRecord(ev[e_i++], s);
+    }
+    return cudaSuccess;
+  }
+};
+
+// constants of a model on an nx * ny box of size lx * ly
+void plan_constants(int nx, int ny, double lx, double ly, int* e2, float* ryy) {
+  const double mx = M_PI * nx / lx, my = M_PI * ny / ly;
+  *e2 = (int)std::lround(0.5 * std::log2(std::max(std::sqrt(mx * mx + my * my), 1.0)));
+  const double hx = lx / nx, hy = ly / ny;
+  *ryy = (float)((hx * hx) / (hy * hy));
+}
+
+int line_e(int n) { return n >= 512 ? 32 : (n >= 128 ? 16 : 8); }
+
+struct Fused2D : Engine {
+  Plan2D p;
   size_t nbytes = 0;
   // Operator 2's multiplier carries an exact power-of-two factor lambda so
   // that the two operators packed into one complex row transform (A + iB)
@@ -432,114 +549,70 @@ struct Fused2D : Engine {
   // round-off is relative to |A + iB|, so without it operator 2 would see
   // round-off up to |mu|_max times its own size.  lambda ~ sqrt(|mu|_max)
   // balances the two; it is divided out exactly in the epilogue.
-  float lambda = 1.f, inv_lambda = 1.f;
-  float ryy = 1.f;  // (h_x / h_y)^2, weight of D_yy in the transformed Laplacian
+  double lambda = 1.0;
 
   ~Fused2D() override {
-    cudaFree(T);
-    cudaFree(Uh);
-    cudaFree(Z);
-    cudaFree(part);
-    cudaFree(P);
-    cudaFree(Lg);
-    cudaFree(twx);
-    cudaFree(twy);
+    cudaFree(p.T);
+    cudaFree(p.Uh);
+    cudaFree(p.Z);
+    cudaFree(p.part);
+    cudaFree(p.P);
+    cudaFree(p.Lg);
+    cudaFree(p.twx);
+    cudaFree(p.twy);
   }
 
   size_t bytes() const override { return nbytes; }
 
-  int alloc(vofl_ctx* c, void** p, size_t b) {
-    cudaError_t e = cudaMalloc(p, b);
+  int alloc(vofl_ctx* c, void** ptr, size_t b) {
+    cudaError_t e = cudaMalloc(ptr, b);
     if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (fused 2D scratch)");
     nbytes += b;
     return VOFL_OK;
   }
 
   int init(vofl_ctx* c) {
-    nx = (int)c->n[0];
-    ny = (int)c->n[1];
-    H = nx / 2;
-    ncols = H + 1;
-    if (!pick_kernels(nx, ny, &k)) return set_err(c, VOFL_EUNSUPPORTED, "fused 2D path: grid size not built");
-    pT = round_up(ncols, 8);
-    pZ = round_up(ncols, 8);
-    zslot = (long long)ny * pZ;
-    Gcap = 6;
+    p.nx = (int)c->n[0];
+    p.ny = (int)c->n[1];
+    p.ncols = p.nx / 2 + 1;
+    if (!pick_kernels(p.nx, p.ny, &p.k)) return set_err(c, VOFL_EUNSUPPORTED, "fused 2D path: grid size not built");
+    p.pT = round_up(p.ncols, 8);
+    p.pZ = p.pT;
+    p.zslot = (long long)p.ny * p.pZ;
+    p.G = 6;
     int st;
-    if ((st = alloc(c, (void**)&T, sizeof(float2) * (size_t)ny * pT))) return st;
-    if ((st = alloc(c, (void**)&Uh, sizeof(float2) * (size_t)ncols * ny))) return st;
-    if ((st = alloc(c, (void**)&Z, sizeof(float2) * (size_t)zslot * 2 * Gcap))) return st;
-    if ((st = alloc(c, (void**)&part, sizeof(float) * 2 * (size_t)nx * ny))) return st;
-    if ((st = alloc(c, (void**)&P, sizeof(float) * 2 * (size_t)ncols * ny))) return st;
-    if ((st = alloc(c, (void**)&Lg, sizeof(float) * (size_t)ncols * ny))) return st;
-    if ((st = alloc(c, (void**)&twx, sizeof(float2) * nx))) return st;
-    if ((st = alloc(c, (void**)&twy, sizeof(float2) * ny))) return st;
-    VOFL_CUDA(c, cudaFuncSetAttribute(k.fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_x));
-    VOFL_CUDA(c, cudaFuncSetAttribute(k.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_rows));
-    VOFL_CUDA(c, cudaFuncSetAttribute(k.fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_y));
-    VOFL_CUDA(c, cudaFuncSetAttribute(k.inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_y));
-    const int ex = nx >= 512 ? 32 : (nx >= 128 ? 16 : 8);
-    const int ey = ny >= 512 ? 32 : (ny >= 128 ? 16 : 8);
-    if ((st = make_line_twiddles(nx, ex, nx / ex, twx, c->stream))) return cuda_err(c, cudaGetLastError(), "twiddles");
-    if ((st = make_line_twiddles(ny, ey, ny / ey, twy, c->stream))) return cuda_err(c, cudaGetLastError(), "twiddles");
+    const size_t nx = p.nx, ny = p.ny, nc = p.ncols;
+    if ((st = alloc(c, (void**)&p.T, sizeof(float2) * ny * p.pT))) return st;
+    if ((st = alloc(c, (void**)&p.Uh, sizeof(float2) * nc * ny))) return st;
+    if ((st = alloc(c, (void**)&p.Z, sizeof(float2) * (size_t)p.zslot * 2 * p.G))) return st;
+    if ((st = alloc(c, (void**)&p.part, sizeof(float) * 2 * nx * ny))) return st;
+    if ((st = alloc(c, (void**)&p.P, sizeof(float) * 2 * nc * ny))) return st;
+    if ((st = alloc(c, (void**)&p.Lg, sizeof(float) * nc * ny))) return st;
+    if ((st = alloc(c, (void**)&p.twx, sizeof(float2) * nx))) return st;
+    if ((st = alloc(c, (void**)&p.twy, sizeof(float2) * ny))) return st;
+    if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
+    if (make_line_twiddles(p.nx, line_e(p.nx), p.nx / line_e(p.nx), p.twx, c->stream) ||
+        make_line_twiddles(p.ny, line_e(p.ny), p.ny / line_e(p.ny), p.twy, c->stream))
+      return cuda_err(c, cudaGetLastError(), "twiddles");
+    p.delta = (const float*)c->delta;
+    p.step_ctr = c->d_step;
+    p.err = c->d_step + 1;
     return VOFL_OK;
   }
 
   int set_model(vofl_ctx* c) override {
     const double lx = c->hi[0] - c->lo[0], ly = c->hi[1] - c->lo[1];
-    const double mx = M_PI * nx / lx, my = M_PI * ny / ly;
-    const double mu_max = std::sqrt(mx * mx + my * my);
-    const int e2 = (int)std::lround(0.5 * std::log2(std::max(mu_max, 1.0)));
-    lambda = std::ldexp(1.0f, e2);
-    inv_lambda = std::ldexp(1.0f, -e2);
-    const double hx = lx / nx, hy = ly / ny;
-    ryy = (float)((hx * hx) / (hy * hy));
-    if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + c->gamma0, 0.5 + c->gamma0, lambda, (double)ryy, P, Lg,
+    int e2;
+    plan_constants(p.nx, p.ny, lx, ly, &e2, &p.ryy);
+    lambda = std::ldexp(1.0, e2);
+    p.inv_lambda = std::ldexp(1.0f, -e2);
+    if (make_fused2d_tables(p.nx, p.ny, lx, ly, 1.0 + c->gamma0, 0.5 + c->gamma0, lambda, (double)p.ryy, p.P, p.Lg,
                             c->stream))
       return cuda_err(c, cudaGetLastError(), "fused 2D tables");
     return VOFL_OK;
   }
 
-  int group_size(const vofl_ctx* c) const { return std::min(Gcap, c->M + 1); }
-
-  uint64_t kernels_per_step(const vofl_ctx* c) const override {
-    const int g = group_size(c);
-    const int K = (c->M + 1 + g - 1) / g;
-    return 2 + 2 * (uint64_t)K;
-  }
-
-  // forward transform of `u` into Uh
-  int forward(vofl_ctx* c, const float* u, bool inc_step) {
-    const int rows_per_cta = WARPS * k.lpw_x;  // row pairs per CTA
-    const int gx = (ny / 2 + rows_per_cta - 1) / rows_per_cta;
-    k.fwd_rows<<<gx, THREADS, k.smem_x, c->stream>>>(u, T, ny, pT, ryy, twx, c->d_step, inc_step ? 1 : 0);
-    const int cols_per_cta = WARPS * k.lpw_y;
-    const int gc = (ncols + cols_per_cta - 1) / cols_per_cta;
-    k.fwd_cols<<<gc, THREADS, k.smem_y, c->stream>>>(T, pT, Uh, ncols, twy);
-    count_launch(2);
-    return VOFL_OK;
-  }
-
-  int inverse(vofl_ctx* c, const EpiArgs<float>& epi) {
-    const int g = group_size(c);
-    const int K = (c->M + 1 + g - 1) / g;
-    const int cols_per_cta = WARPS * k.lpw_y;
-    const dim3 gic((ncols + cols_per_cta - 1) / cols_per_cta, 2);
-    const int rows_per_cta = WARPS * k.lpw_x;
-    const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
-    for (int gi = K - 1; gi >= 0; --gi) {
-      const int m_lo = gi * g, m_hi = std::min(c->M + 1, m_lo + g);
-      k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi,
-                                                        inv_factorial(m_lo), twy);
-      EpiArgs<float> e = epi;
-      if (gi > 0) e.mode = EPI_PARTIAL;
-      k.inv_rows<<<gir, THREADS, k.smem_rows, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
-                                                           (const float*)c->delta, part, part + (size_t)nx * ny, e,
-                                                           inv_lambda, twx, c->d_step + 1);
-      count_launch(2);
-    }
-    return VOFL_OK;
-  }
+  uint64_t kernels_per_step(const vofl_ctx* c) const override { return 2 + 2 * (uint64_t)p.groups(c->M); }
 
   int apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) override {
     EpiArgs<float> e{};
@@ -547,9 +620,10 @@ struct Fused2D : Engine {
     e.out1 = (float*)o1;
     e.out2 = (float*)o2;
     e.src_flat = -1;
-    forward(c, (const float*)u, false);
-    inverse(c, e);
-    return cuda_err_if(c);
+    cudaError_t err = p.forward(c->stream, (const float*)u, false);
+    if (!err) err = p.inverse(c->stream, c->M, e);
+    if (err) return cuda_err(c, err, "fused 2D launch");
+    return VOFL_OK;
   }
 
   int step(vofl_ctx* c, int mode, bool count_step) override {
@@ -569,14 +643,9 @@ struct Fused2D : Engine {
     double hd = 1.0;
     for (int i = 0; i < c->ndim; ++i) hd *= (c->hi[i] - c->lo[i]) / (double)c->n[i];
     e.src_scale = c->dt * c->dt / hd;
-    forward(c, (const float*)c->u[c->cur], count_step);
-    inverse(c, e);
-    return cuda_err_if(c);
-  }
-
-  int cuda_err_if(vofl_ctx* c) {
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return cuda_err(c, err, "fused 2D launch");
+    cudaError_t err = p.forward(c->stream, (const float*)c->u[c->cur], count_step);
+    if (!err) err = p.inverse(c->stream, c->M, e);
+    if (err) return cuda_err(c, err, "fused 2D launch");
     return VOFL_OK;
   }
 
@@ -587,57 +656,43 @@ struct Fused2D : Engine {
   // with null outputs), so the context state is unchanged.
   int profile(vofl_ctx* c, int reps, std::string& names, double* ms, double* units, int cap) override {
     if (cap < 4) return 0;
-    const int g = group_size(c);
-    const int K = (c->M + 1 + g - 1) / g;
+    const int K = p.groups(c->M);
     const int nk = 2 + 2 * K;
-    std::vector<cudaEvent_t> ev(nk + 1);
+    // one event set per repetition; all repetitions are queued back to back
+    // (one warm-up first) and read after a single synchronisation, so the
+    // host launch latency never shows up in the intervals
+    const int R = reps + 1;
+    std::vector<cudaEvent_t> ev((size_t)R * (nk + 1));
     for (auto& e : ev) cudaEventCreate(&e);
-    const int rows_per_cta = WARPS * k.lpw_x, cols_per_cta = WARPS * k.lpw_y;
-    const int gx = (ny / 2 + rows_per_cta - 1) / rows_per_cta;
-    const int gc = (ncols + cols_per_cta - 1) / cols_per_cta;
-    const dim3 gic(gc, 2);
-    const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
     EpiArgs<float> ep{};
     ep.mode = EPI_APPLY;
     ep.src_flat = -1;
     const float* u = (const float*)c->u[c->cur];
     double acc[4] = {0, 0, 0, 0};
-    double terms_cols = 0, terms_rows = 0;
-    for (int r = -1; r < reps; ++r) {
-      int e = 0;
-      cudaEventRecord(ev[e++], c->stream);
-      k.fwd_rows<<<gx, THREADS, k.smem_x, c->stream>>>(u, T, ny, pT, ryy, twx, c->d_step, 0);
-      cudaEventRecord(ev[e++], c->stream);
-      k.fwd_cols<<<gc, THREADS, k.smem_y, c->stream>>>(T, pT, Uh, ncols, twy);
-      cudaEventRecord(ev[e++], c->stream);
-      for (int gi = K - 1; gi >= 0; --gi) {
-        const int m_lo = gi * g, m_hi = std::min(c->M + 1, m_lo + g);
-        k.inv_cols<<<gic, THREADS, k.smem_y, c->stream>>>(Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi,
-                                                          inv_factorial(m_lo), twy);
-        cudaEventRecord(ev[e++], c->stream);
-        EpiArgs<float> epg = ep;
-        if (gi > 0) epg.mode = EPI_PARTIAL;
-        k.inv_rows<<<gir, THREADS, k.smem_rows, c->stream>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
-                                                             (const float*)c->delta, part, part + (size_t)nx * ny,
-                                                             epg, inv_lambda, twx, c->d_step + 1);
-        cudaEventRecord(ev[e++], c->stream);
-        if (r == 0) {
-          terms_cols += m_hi - m_lo;
-          terms_rows += m_hi - m_lo;
-        }
+    double terms = 0;
+    for (int g = 0; g < K; ++g) terms += std::min(c->M + 1, (g + 1) * p.G) - g * p.G;
+    for (int r = 0; r < R; ++r) {
+      cudaEvent_t* er = ev.data() + (size_t)r * (nk + 1);
+      cudaEventRecord(er[0], c->stream);
+      cudaError_t err = p.forward(c->stream, u, false, er);
+      if (!err) err = p.inverse(c->stream, c->M, ep, er);
+      if (err) {
+        for (auto& e : ev) cudaEventDestroy(e);
+        return cuda_err(c, err, "profile");
       }
-      count_launch(nk);
-      cudaEventSynchronize(ev[nk]);
-      if (r < 0) continue;  // warm-up repetition
+    }
+    cudaEventSynchronize(ev.back());
+    for (int r = 1; r < R; ++r) {
+      const cudaEvent_t* er = ev.data() + (size_t)r * (nk + 1);
       float t;
-      cudaEventElapsedTime(&t, ev[0], ev[1]);
+      cudaEventElapsedTime(&t, er[0], er[1]);
       acc[0] += t;
-      cudaEventElapsedTime(&t, ev[1], ev[2]);
+      cudaEventElapsedTime(&t, er[1], er[2]);
       acc[1] += t;
       for (int i = 0; i < K; ++i) {
-        cudaEventElapsedTime(&t, ev[2 + 2 * i], ev[3 + 2 * i]);
+        cudaEventElapsedTime(&t, er[2 + 2 * i], er[3 + 2 * i]);
         acc[2] += t;
-        cudaEventElapsedTime(&t, ev[3 + 2 * i], ev[4 + 2 * i]);
+        cudaEventElapsedTime(&t, er[3 + 2 * i], er[4 + 2 * i]);
         acc[3] += t;
       }
     }
@@ -645,13 +700,13 @@ struct Fused2D : Engine {
     names = "k2d_fwd_rows;k2d_fwd_cols;k2d_inv_cols;k2d_inv_rows";
     // ms = average per launch; units = complex line transforms per launch
     ms[0] = acc[0] / reps;
-    units[0] = ny / 2.0;
+    units[0] = p.ny / 2.0;
     ms[1] = acc[1] / reps;
-    units[1] = ncols;
+    units[1] = p.ncols;
     ms[2] = acc[2] / reps / K;
-    units[2] = 2.0 * ncols * terms_cols / K;
+    units[2] = 2.0 * p.ncols * terms / K;
     ms[3] = acc[3] / reps / K;
-    units[3] = (double)ny * terms_rows / K;
+    units[3] = (double)p.ny * terms / K;
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_err(c, err, "profile");
     return 4;
@@ -697,15 +752,12 @@ Engine* make_fused2d(vofl_ctx* c, int* status) {
 // enough for grids up to 256 x 256.  Every GPU that loads the library keeps
 // that array until the process exits.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace vofl {
 namespace {
 
 constexpr int NOALLOC_MAX_AXIS = 256;
 constexpr size_t NOALLOC_BYTES = size_t(6) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
-bool g_noalloc_attr_set[64] = {};
 
 struct NoAllocLayout {
   size_t delta, A, B, red, T, Uh, Z, part, P, Lg, twx, twy, step, total;
@@ -740,10 +792,12 @@ NoAllocLayout noalloc_layout(int nx, int ny, int G) {
 std::mutex g_noalloc_mu;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 void* g_noalloc_dev_ptr[NOALLOC_MAX_DEVICES] = {};
+bool g_noalloc_attr_set[NOALLOC_MAX_DEVICES] = {};
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device.  In host code the array's name is only a host-side stand-in,
-// so kernels are always given this looked-up address.
+// per device (together with the kernels' shared-memory attributes).  In
+// host code the array's name is only a host-side stand-in, so kernels are
+// always given this looked-up address.
 int noalloc_base(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
@@ -760,6 +814,14 @@ int noalloc_base(unsigned char** out) {
     }
     g_noalloc_dev_ptr[dev] = p;
   }
+  if (!g_noalloc_attr_set[dev]) {
+    const int shapes[5][2] = {{64, 64}, {128, 128}, {256, 256}, {256, 128}, {128, 256}};
+    for (const auto& sh : shapes) {
+      Kernels kk;
+      if (pick_kernels(sh[0], sh[1], &kk) && set_smem_attributes(kk)) return VOFL_ECUDA;
+    }
+    g_noalloc_attr_set[dev] = true;
+  }
   *out = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
   return VOFL_OK;
 }
@@ -773,34 +835,14 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   if (!gamma_dev || !u_dev || (!out1_dev && !out2_dev)) return VOFL_EINVAL;
   if (!(lx > 0) || !(ly > 0) || M < 0 || M > 40) return VOFL_EINVAL;
   if (nx < 2 || ny < 2 || (nx % 2) || (ny % 2)) return VOFL_EINVAL;
-  Kernels k;
-  if (nx > NOALLOC_MAX_AXIS || ny > NOALLOC_MAX_AXIS || !pick_kernels(nx, ny, &k)) return VOFL_EUNSUPPORTED;
-  const int G = std::min(6, M + 1);
-  const NoAllocLayout L = noalloc_layout(nx, ny, G);
+  Plan2D p;
+  if (nx > NOALLOC_MAX_AXIS || ny > NOALLOC_MAX_AXIS || !pick_kernels(nx, ny, &p.k)) return VOFL_EUNSUPPORTED;
+  p.G = std::min(6, M + 1);
+  const NoAllocLayout L = noalloc_layout(nx, ny, p.G);
   if (L.total > NOALLOC_BYTES) return VOFL_EUNSUPPORTED;
   unsigned char* base = nullptr;
   int st = noalloc_base(&base);
   if (st) return st;
-  {
-    // kernels with more than 48 KB of dynamic shared memory need the opt-in
-    // attribute, set once per device for every shape this entry accepts
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_attr_set[dev]) {
-      const int shapes[5][2] = {{64, 64}, {128, 128}, {256, 256}, {256, 128}, {128, 256}};
-      for (const auto& sh : shapes) {
-        Kernels kk;
-        if (!pick_kernels(sh[0], sh[1], &kk)) continue;
-        if (cudaFuncSetAttribute(kk.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kk.smem_rows) !=
-            cudaSuccess) {
-          cudaGetLastError();
-          return VOFL_ECUDA;
-        }
-      }
-      g_noalloc_attr_set[dev] = true;
-    }
-  }
   cudaStream_t s = (cudaStream_t)stream;
 
   // per-model part: gamma0 = grid mean of gamma and delta = gamma - gamma0
@@ -818,52 +860,40 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   m.B = base + L.B;
   st = model_from_gamma(&m, gamma_dev, nullptr, 1.0, 1.0);
   if (st) return st;
-  const double mx = M_PI * nx / lx, my = M_PI * ny / ly;
-  const int e2 = (int)std::lround(0.5 * std::log2(std::max(std::sqrt(mx * mx + my * my), 1.0)));
-  const float inv_lambda = std::ldexp(1.0f, -e2);
-  const double hx = lx / nx, hy = ly / ny;
-  const float ryy = (float)((hx * hx) / (hy * hy));
-  float* P = reinterpret_cast<float*>(base + L.P);
-  float* Lgt = reinterpret_cast<float*>(base + L.Lg);
-  float2* twx = reinterpret_cast<float2*>(base + L.twx);
-  float2* twy = reinterpret_cast<float2*>(base + L.twy);
-  if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + m.gamma0, 0.5 + m.gamma0, std::ldexp(1.0, e2), (double)ryy, P, Lgt, s))
+  int e2;
+  plan_constants(nx, ny, lx, ly, &e2, &p.ryy);
+  p.inv_lambda = std::ldexp(1.0f, -e2);
+  p.nx = nx;
+  p.ny = ny;
+  p.ncols = nx / 2 + 1;
+  p.pT = round_up(p.ncols, 8);
+  p.pZ = p.pT;
+  p.zslot = (long long)ny * p.pZ;
+  p.T = reinterpret_cast<float2*>(base + L.T);
+  p.Uh = reinterpret_cast<float2*>(base + L.Uh);
+  p.Z = reinterpret_cast<float2*>(base + L.Z);
+  p.part = reinterpret_cast<float*>(base + L.part);
+  p.P = reinterpret_cast<float*>(base + L.P);
+  p.Lg = reinterpret_cast<float*>(base + L.Lg);
+  p.twx = reinterpret_cast<float2*>(base + L.twx);
+  p.twy = reinterpret_cast<float2*>(base + L.twy);
+  p.delta = reinterpret_cast<const float*>(m.delta);
+  p.step_ctr = reinterpret_cast<int*>(base + L.step);
+  p.err = p.step_ctr + 1;
+  if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + m.gamma0, 0.5 + m.gamma0, std::ldexp(1.0, e2), (double)p.ryy, p.P,
+                          p.Lg, s))
     return VOFL_ECUDA;
-  const int ex = nx >= 512 ? 32 : (nx >= 128 ? 16 : 8);
-  const int ey = ny >= 512 ? 32 : (ny >= 128 ? 16 : 8);
-  if (make_line_twiddles(nx, ex, nx / ex, twx, s) || make_line_twiddles(ny, ey, ny / ey, twy, s)) return VOFL_ECUDA;
-
-  // the fused transform passes, exactly as the context path launches them
-  const int ncols = nx / 2 + 1, pT = round_up(ncols, 8), pZ = pT;
-  const long long zslot = (long long)ny * pZ;
-  float2* T = reinterpret_cast<float2*>(base + L.T);
-  float2* Uh = reinterpret_cast<float2*>(base + L.Uh);
-  float2* Z = reinterpret_cast<float2*>(base + L.Z);
-  float* part = reinterpret_cast<float*>(base + L.part);
-  int* stepc = reinterpret_cast<int*>(base + L.step);
-  const int rows_per_cta = WARPS * k.lpw_x, cols_per_cta = WARPS * k.lpw_y;
-  k.fwd_rows<<<(ny / 2 + rows_per_cta - 1) / rows_per_cta, THREADS, k.smem_x, s>>>(u_dev, T, ny, pT, ryy, twx, stepc,
-                                                                                   0);
-  k.fwd_cols<<<(ncols + cols_per_cta - 1) / cols_per_cta, THREADS, k.smem_y, s>>>(T, pT, Uh, ncols, twy);
-  count_launch(2);
+  if (make_line_twiddles(nx, line_e(nx), nx / line_e(nx), p.twx, s) ||
+      make_line_twiddles(ny, line_e(ny), ny / line_e(ny), p.twy, s))
+    return VOFL_ECUDA;
   EpiArgs<float> epi{};
   epi.mode = EPI_APPLY;
   epi.out1 = out1_dev;
   epi.out2 = out2_dev;
   epi.src_flat = -1;
-  const int K = (M + 1 + G - 1) / G;
-  const dim3 gic((ncols + cols_per_cta - 1) / cols_per_cta, 2);
-  const int gir = (ny + rows_per_cta - 1) / rows_per_cta;
-  for (int gi = K - 1; gi >= 0; --gi) {
-    const int m_lo = gi * G, m_hi = std::min(M + 1, m_lo + G);
-    k.inv_cols<<<gic, THREADS, k.smem_y, s>>>(Uh, P, Lgt, Z, zslot, pZ, ncols, m_lo, m_hi, inv_factorial(m_lo), twy);
-    EpiArgs<float> e = epi;
-    if (gi > 0) e.mode = EPI_PARTIAL;
-    k.inv_rows<<<gir, THREADS, k.smem_rows, s>>>(Z, zslot, pZ, ny, m_lo, m_hi, gi == K - 1 ? 1 : 0,
-                                                 reinterpret_cast<const float*>(m.delta), part,
-                                                 part + (size_t)nx * ny, e, inv_lambda, twx, stepc + 1);
-    count_launch(2);
+  if (p.forward(s, u_dev, false) || p.inverse(s, M, epi)) {
+    cudaGetLastError();
+    return VOFL_ECUDA;
   }
-  if (cudaGetLastError() != cudaSuccess) return VOFL_ECUDA;
   return VOFL_OK;
 }
