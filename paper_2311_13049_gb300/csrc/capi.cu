@@ -114,6 +114,8 @@ size_t vofl_footprint_bytes(int ndim, const int64_t* n, int prec, int impl, int 
   size_t b = r * (size_t)N * 6 + sizeof(double) * (size_t)N + 8192;  // delta A B u0 u1 l2p, gamma
   if (impl == VOFL_IMPL_FUSED && fused2d_supported(ndim, n, prec))
     b += fused2d_footprint(n, M);
+  else if (impl == VOFL_IMPL_FUSED && fused1d_supported(ndim, n, prec))
+    b += (size_t)N * (prec == VOFL_F64 ? 8 : 4) * 4;
   else
     b += plain_footprint(ndim, n, prec);
   return b;
@@ -133,7 +135,8 @@ int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, co
     N *= n[i];
   }
   if (N > (1LL << 34)) return VOFL_EINVAL;
-  if (impl == VOFL_IMPL_FUSED && !fused2d_supported(ndim, n, prec)) return VOFL_EUNSUPPORTED;
+  if (impl == VOFL_IMPL_FUSED && !fused2d_supported(ndim, n, prec) && !fused1d_supported(ndim, n, prec))
+    return VOFL_EUNSUPPORTED;
 
   vofl_ctx* c = new vofl_ctx();
   c->ndim = ndim;
@@ -176,7 +179,7 @@ int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, co
   cudaMemsetAsync(c->d_step, 0, sizeof(int) * 4, c->stream);
   int st = VOFL_OK;
   if (impl == VOFL_IMPL_FUSED)
-    c->eng = make_fused2d(c, &st);
+    c->eng = ndim == 1 ? make_fused1d(c, &st) : make_fused2d(c, &st);
   else
     c->eng = make_plain(c, &st);
   if (!c->eng) {
@@ -341,6 +344,16 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
       int st = c->eng->apply_pair(c, c->u[1], nullptr, c->l2p);
       if (st) return st;
     }
+  }
+  if (c->eng->can_run()) {
+    // the whole request in one launch
+    const int st = c->eng->run(c, nsteps, c->steps == 0 ? EPI_START : EPI_STEP);
+    if (st) return st;
+    c->cur = (int)((c->cur + nsteps) & 1);
+    c->steps += nsteps;
+    return VOFL_OK;
+  }
+  if (c->steps == 0) {
     int st = c->eng->step(c, EPI_START, false);
     if (st) return st;
     c->cur ^= 1;

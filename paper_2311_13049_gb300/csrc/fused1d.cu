@@ -1,0 +1,400 @@
+// fused1d.cu -- fused 1D path (float or double): the whole leap-frog run of
+// Eq. (1.1) with both operators by the matrix-free scheme of Eq. (2.10) of
+// arXiv 2311.13049, one CTA per simulation, every transform in shared
+// memory, every requested step inside one kernel launch.
+//
+// Per step (N points, M+1 Taylor terms):
+//   w = D_xx u (periodic second difference) -> complex FFT -> S = DFT(w),
+//       S_k = lambda_k * N * u_hat_k with lambda_k = -4 sin^2(pi k/N);
+//   for m = M..0: W_k = S_k (c1_m(k) + i c2_m(k)), c_op,m = P_op L^m/m!
+//       (P_op = |mu|^{2 s0_op}/(N lambda_k), op 2 scaled by an exact power of
+//       two lambda2), one complex inverse FFT gives L1-term + i L2-term
+//       (both multiplied spectra are Hermitian), and Horner's rule
+//       acc = Y_m + delta * acc accumulates the delta^m weights;
+//   pointwise leap-frog update (Eq. (3.4) extended to Eq. (1.1)).
+// The FFT is a radix-2 Stockham autosort over the CTA (Govindaraju et al.,
+// SC 2008), ping-ponging between two shared buffers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace vofl {
+
+namespace {
+
+constexpr int T1D = 256;  // threads per CTA
+constexpr int MAX_PTS_PER_THREAD = 16;
+
+template <typename R>
+struct C2;
+template <>
+struct C2<float> {
+  using T = float2;
+};
+template <>
+struct C2<double> {
+  using T = double2;
+};
+
+template <typename C>
+__device__ __forceinline__ C cm(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// radix-2 Stockham over the CTA; `a` holds the input, the returned pointer
+// (a or b) holds the output; tw[t] = exp(-2 pi i t / N), t < N/2
+template <typename C>
+__device__ C* block_fft(C* a, C* b, const C* tw, int N, bool inv) {
+  const int H = N / 2;
+  for (int Ns = 1; Ns < N; Ns <<= 1) {
+    const int step = H / Ns;  // N / (2 Ns)
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+      const int k = j & (Ns - 1);
+      C w = tw[k * step];
+      if (inv) w.y = -w.y;
+      const C x0 = a[j];
+      const C x1 = cm(a[j + H], w);
+      const int o = ((j - k) << 1) + k;
+      C s, d;
+      s.x = x0.x + x1.x;
+      s.y = x0.y + x1.y;
+      d.x = x0.x - x1.x;
+      d.y = x0.y - x1.y;
+      b[o] = s;
+      b[o + Ns] = d;
+    }
+    __syncthreads();
+    C* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+template <typename R>
+struct Sim1D {
+  int N, M;
+  int mode_first;         // EPI_START for the first step of a run, EPI_STEP otherwise, EPI_APPLY for apply
+  int nsteps;             // steps to run in this launch
+  int step0;              // index n of the first step (source sample index)
+  R* u[2];                // u buffers
+  int cur;                // buffer holding u^n at launch start
+  R* l2p;                 // L2 u^{n-1} (or L2 psi before the start step)
+  const R* delta;
+  const R* A;
+  const R* B;
+  const R* P1;            // [N] |mu|^{2 s01} / (N lambda)
+  const R* P2;            // [N] lambda2 |mu|^{2 s02} / (N lambda)
+  const R* Lg;            // [N] ln |mu|^2 (0 at k = 0)
+  const typename C2<R>::T* tw;  // [N/2]
+  R inv_lambda2;
+  R dt1, dt2;
+  long long src_flat;
+  const double* src;
+  long long nsrc;
+  double src_scale;
+  const R* apply_in;      // EPI_APPLY: input field
+  R* out1;
+  R* out2;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(T1D) k1d_run(const Sim1D<R>* sims) {
+  using C = typename C2<R>::T;
+  const Sim1D<R> sp = sims[blockIdx.x];
+  const int N = sp.N, H = N / 2;
+  const int PPT = N / T1D > 0 ? N / T1D : 1;  // points per thread (N >= T1D) or 1
+  extern __shared__ unsigned char smem_raw[];
+  C* S = reinterpret_cast<C*>(smem_raw);
+  C* B0 = S + N;
+  C* B1 = B0 + N;
+  C* tws = B1 + N;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) tws[i] = sp.tw[i];
+  // per-thread owned points j = t + T1D*i (i < PPT), only if j < N
+  R dl[MAX_PTS_PER_THREAD], a1[MAX_PTS_PER_THREAD], a2[MAX_PTS_PER_THREAD];
+  for (int i = 0; i < PPT; ++i) {
+    const int j = threadIdx.x + T1D * i;
+    dl[i] = j < N ? sp.delta[j] : R(0);
+  }
+  __syncthreads();
+  R* ucur = sp.u[sp.cur];
+  R* uoth = sp.u[1 - sp.cur];
+  for (int s = 0; s < sp.nsteps; ++s) {
+    const int mode = (s == 0) ? sp.mode_first : EPI_STEP;
+    const R* uin = (mode == EPI_APPLY) ? sp.apply_in : ucur;
+    // w = D_xx u into B0 (complex, zero imaginary part)
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const R c = uin[j];
+      const R d = (uin[j + 1 == N ? 0 : j + 1] - c) - (c - uin[j == 0 ? N - 1 : j - 1]);
+      C v;
+      v.x = d;
+      v.y = R(0);
+      B0[j] = v;
+    }
+    __syncthreads();
+    C* f = block_fft<C>(B0, B1, tws, N, false);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) S[k] = f[k];
+    __syncthreads();
+    for (int i = 0; i < PPT; ++i) a1[i] = a2[i] = R(0);
+    double fact = 1.0;  // m! in double (40! overflows float)
+    for (int m = 1; m <= sp.M; ++m) fact *= m;
+    for (int m = sp.M; m >= 0; --m) {
+      const R invf = R(1.0 / fact);
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        // L^m by squaring
+        R l = sp.Lg[k], p = R(1);
+        int e = m;
+        while (e) {
+          if (e & 1) p *= l;
+          l *= l;
+          e >>= 1;
+        }
+        const R t = p * invf;
+        const R c1 = sp.P1[k] * t, c2 = sp.P2[k] * t;
+        const C sk = S[k];
+        C w;  // (c1 + i c2) * S_k
+        w.x = c1 * sk.x - c2 * sk.y;
+        w.y = c1 * sk.y + c2 * sk.x;
+        B0[k] = w;
+      }
+      __syncthreads();
+      C* y = block_fft<C>(B0, B1, tws, N, true);
+      for (int i = 0; i < PPT; ++i) {
+        const int j = threadIdx.x + T1D * i;
+        if (j < N) {
+          const C v = y[j];
+          a1[i] = v.x + dl[i] * a1[i];
+          a2[i] = v.y + dl[i] * a2[i];
+        }
+      }
+      __syncthreads();
+      if (m > 0) fact /= m;
+    }
+    // epilogue
+    EpiArgs<R> e{};
+    e.mode = mode;
+    e.out1 = sp.out1;
+    e.out2 = sp.out2;
+    e.u_cur = ucur;
+    e.u_other = uoth;
+    e.l2p = sp.l2p;
+    e.A = sp.A;
+    e.B = sp.B;
+    e.dt1 = sp.dt1;
+    e.dt2 = sp.dt2;
+    e.src_flat = sp.src_flat;
+    e.src = sp.src;
+    e.nsrc = sp.nsrc;
+    const int n_step = sp.step0 + s;
+    e.step = &n_step;
+    e.src_scale = sp.src_scale;
+    for (int i = 0; i < PPT; ++i) {
+      const int j = threadIdx.x + T1D * i;
+      if (j < N) epilogue_point<R>(e, j, a1[i], a2[i] * sp.inv_lambda2);
+    }
+    __syncthreads();  // the next step reads the new u everywhere
+    if (mode == EPI_APPLY) break;
+    R* t = ucur;
+    ucur = uoth;
+    uoth = t;
+  }
+}
+
+template <typename R>
+__global__ void k1d_tables(int N, double L, double s01, double s02, double lambda2, R* P1, R* P2, R* Lg) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const int ks = k < N / 2 ? k : k - N;
+    const double mu = 2.0 * M_PI * ks / L;
+    const double m2 = mu * mu;
+    if (m2 == 0.0) {
+      P1[k] = R(0);
+      P2[k] = R(0);
+      Lg[k] = R(0);
+    } else {
+      const double s = sinpi((double)k / N);
+      const double lam = -4.0 * s * s;
+      const double lg = log(m2);
+      P1[k] = R(exp(s01 * lg) / (N * lam));
+      P2[k] = R(lambda2 * exp(s02 * lg) / (N * lam));
+      Lg[k] = R(lg);
+    }
+  }
+}
+
+template <typename C>
+__global__ void k1d_twiddles(int N, C* tw) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N / 2; t += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)t / (double)N, &s, &c);
+    C v;
+    v.x = (decltype(v.x))c;
+    v.y = (decltype(v.y))s;
+    tw[t] = v;
+  }
+}
+
+template <typename R>
+size_t smem_1d(int N) {
+  using C = typename C2<R>::T;
+  return sizeof(C) * (3 * (size_t)N + N / 2);
+}
+
+template <typename R>
+struct Fused1D : Engine {
+  using C = typename C2<R>::T;
+  int N = 0;
+  R *P1 = nullptr, *P2 = nullptr, *Lg = nullptr;
+  C* tw = nullptr;
+  Sim1D<R>* d_sim = nullptr;
+  double lambda2 = 1.0;
+  size_t nbytes = 0;
+
+  ~Fused1D() override {
+    cudaFree(P1);
+    cudaFree(P2);
+    cudaFree(Lg);
+    cudaFree(tw);
+    cudaFree(d_sim);
+  }
+  size_t bytes() const override { return nbytes; }
+
+  int init(vofl_ctx* c) {
+    N = (int)c->n[0];
+    const size_t b = sizeof(R) * N;
+    bool ok = cudaMalloc(&P1, b) == cudaSuccess && cudaMalloc(&P2, b) == cudaSuccess &&
+              cudaMalloc(&Lg, b) == cudaSuccess && cudaMalloc(&tw, sizeof(C) * (N / 2)) == cudaSuccess &&
+              cudaMalloc(&d_sim, sizeof(Sim1D<R>)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return set_err(c, VOFL_ENOMEM, "cudaMalloc (fused 1D tables)");
+    }
+    nbytes = 3 * b + sizeof(C) * (N / 2) + sizeof(Sim1D<R>);
+    if (cudaFuncSetAttribute(k1d_run<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_1d<R>(N)) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, VOFL_EUNSUPPORTED, "fused 1D path: line too long for shared memory");
+    }
+    k1d_twiddles<C><<<std::max(1, N / 512), 256, 0, c->stream>>>(N, tw);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 1D twiddles");
+    return VOFL_OK;
+  }
+
+  int set_model(vofl_ctx* c) override {
+    const double L = c->hi[0] - c->lo[0];
+    const double mu_max = M_PI * N / L;
+    lambda2 = std::ldexp(1.0, (int)std::lround(0.5 * std::log2(std::max(mu_max, 1.0))));
+    k1d_tables<R><<<std::max(1, N / 256), 256, 0, c->stream>>>(N, L, 1.0 + c->gamma0, 0.5 + c->gamma0, lambda2, P1,
+                                                               P2, Lg);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 1D tables");
+    return VOFL_OK;
+  }
+
+  Sim1D<R> base(vofl_ctx* c) const {
+    Sim1D<R> s{};
+    s.N = N;
+    s.M = c->M;
+    s.u[0] = (R*)c->u[0];
+    s.u[1] = (R*)c->u[1];
+    s.cur = c->cur;
+    s.l2p = (R*)c->l2p;
+    s.delta = (const R*)c->delta;
+    s.A = (const R*)c->A;
+    s.B = (const R*)c->B;
+    s.P1 = P1;
+    s.P2 = P2;
+    s.Lg = Lg;
+    s.tw = tw;
+    s.inv_lambda2 = R(1.0 / lambda2);
+    s.dt1 = R(c->dt);
+    s.dt2 = R(c->dt * c->dt);
+    s.src_flat = c->nsrc > 0 ? c->src_flat : -1;
+    s.src = c->d_src;
+    s.nsrc = c->nsrc;
+    s.src_scale = c->dt * c->dt / ((c->hi[0] - c->lo[0]) / N);
+    return s;
+  }
+
+  int launch(vofl_ctx* c, const Sim1D<R>& s) {
+    // the parameter block goes to the device on the context stream; a copy
+    // from pageable host memory is staged before the call returns, so `s`
+    // may go out of scope, and the stream orders it after earlier launches
+    if (cudaMemcpyAsync(d_sim, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, VOFL_ECUDA, "fused 1D parameters");
+    }
+    k1d_run<R><<<1, T1D, smem_1d<R>(N), c->stream>>>(d_sim);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 1D launch");
+    return VOFL_OK;
+  }
+
+  uint64_t kernels_per_step(const vofl_ctx*) const override { return 1; }
+
+  int apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) override {
+    Sim1D<R> s = base(c);
+    s.mode_first = EPI_APPLY;
+    s.nsteps = 1;
+    s.step0 = 0;
+    s.apply_in = (const R*)u;
+    s.out1 = (R*)o1;
+    s.out2 = (R*)o2;
+    return launch(c, s);
+  }
+
+  int step(vofl_ctx* c, int mode, bool count_step) override {
+    (void)count_step;
+    Sim1D<R> s = base(c);
+    s.mode_first = mode;
+    s.nsteps = 1;
+    s.step0 = (int)c->steps;
+    return launch(c, s);
+  }
+
+  bool can_run() const override { return true; }
+
+  int run(vofl_ctx* c, int64_t nsteps, int first_mode) override {
+    Sim1D<R> s = base(c);
+    s.mode_first = first_mode;
+    s.nsteps = (int)nsteps;
+    s.step0 = (int)c->steps;
+    return launch(c, s);
+  }
+};
+
+}  // namespace
+
+bool fused1d_supported(int ndim, const int64_t* n, int prec) {
+  if (ndim != 1) return false;
+  const int64_t N = n[0];
+  if (N < 16 || N > T1D * MAX_PTS_PER_THREAD || (N & (N - 1))) return false;
+  const size_t sm = prec == VOFL_F64 ? smem_1d<double>((int)N) : smem_1d<float>((int)N);
+  return sm <= 200 * 1024;
+}
+
+Engine* make_fused1d(vofl_ctx* c, int* status) {
+  Engine* e = nullptr;
+  if (c->prec == VOFL_F64) {
+    auto* p = new Fused1D<double>();
+    *status = p->init(c);
+    e = p;
+  } else {
+    auto* p = new Fused1D<float>();
+    *status = p->init(c);
+    e = p;
+  }
+  if (*status != VOFL_OK) {
+    delete e;
+    return nullptr;
+  }
+  return e;
+}
+
+}  // namespace vofl

@@ -142,9 +142,21 @@ struct Engine {
     return 0;
   }
   virtual size_t bytes() const = 0;
+  // engines that advance many steps in one launch (the first step with
+  // first_mode: EPI_START or EPI_STEP); the context's cur/steps are updated
+  // by the caller
+  virtual bool can_run() const { return false; }
+  virtual int run(vofl_ctx* c, int64_t nsteps, int first_mode) {
+    (void)c;
+    (void)nsteps;
+    (void)first_mode;
+    return VOFL_EUNSUPPORTED;
+  }
 };
 
 Engine* make_fused2d(vofl_ctx* c, int* status);
+Engine* make_fused1d(vofl_ctx* c, int* status);
+bool fused1d_supported(int ndim, const int64_t* n, int prec);
 Engine* make_plain(vofl_ctx* c, int* status);
 size_t fused2d_footprint(const int64_t* n, int M);
 size_t plain_footprint(int ndim, const int64_t* n, int prec);

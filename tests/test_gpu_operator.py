@@ -148,3 +148,15 @@ def test_smooth_inputs_keep_fp32_accuracy(V, impl):
         r1, r2 = O.seismic_operators(uin, gamma_of(Q), 8)
         assert rel_l2(g1, r1) <= 2e-6, (shape, rel_l2(g1, r1))
         assert rel_l2(g2, r2) <= 2e-6, (shape, rel_l2(g2, r2))
+
+
+@pytest.mark.parametrize("shape,prec", [((64,), "f32"), ((256,), "f32"), ((4096,), "f32"),
+                                        ((256,), "f64"), ((2048,), "f64")])
+def test_fused_1d_apply_matches_oracle(V, shape, prec):
+    pr = V.F32 if prec == "f32" else V.F64
+    tol = TOL32 if prec == "f32" else TOL64
+    for M in (0, 8, 16):
+        Q, u = _case(shape, 23 + M)
+        g1, g2, uin = gpu_apply_pair(V, shape, Q, u, M, V.IMPL_FUSED, pr)
+        r1, r2 = O.seismic_operators(uin, gamma_of(Q), M)
+        assert rel_l2(g1, r1) <= tol and rel_l2(g2, r2) <= tol, (M, rel_l2(g1, r1), rel_l2(g2, r2))

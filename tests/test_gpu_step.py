@@ -58,17 +58,34 @@ def test_run_split_calls_equal_one_call(V):
     assert np.array_equal(a, b)
 
 
-def test_run_fp64_1d_against_dense_operator(V):
+@pytest.mark.parametrize("impl", ["fused", "plain"])
+def test_run_fp64_1d_against_dense_operator(V, impl):
     """1D N = 256, FP64, M = 8, 200 steps of dt = 1e-3 (Q = 20 + 15 sin x,
     u0 = exp(-20 x^2)): the GPU run against the oracle stepping with the
     dense O(N^2) operator of Eq. (2.3), and with the matrix-free one."""
     w = S.workload_1d_256()
-    g = gpu_run(V, w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], V.IMPL_PLAIN, V.F64)
+    im = V.IMPL_FUSED if impl == "fused" else V.IMPL_PLAIN
+    g = gpu_run(V, w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], im, V.F64)
     r_mf = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"])
     r_dense = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], method="dense")
     assert rel_l2(g, r_mf) <= 1e-11, rel_l2(g, r_mf)
     # truncation of Eq. (2.9) at M = 8 on this model is far below 1e-6
     assert rel_l2(g, r_dense) <= 1e-6, rel_l2(g, r_dense)
+
+
+def test_run_fused_1d_fp32_source_and_velocity(V):
+    """1D N = 4096 FP32 with a Ricker source and a non-zero psi, in chunks."""
+    n = 4096
+    Q = S.q_lowpass((n,), 9)
+    x = S.axis(n)
+    v0 = 0.3 * np.sin(3 * (x + np.pi))
+    nsteps, dt = 150, 2e-4
+    src = S.ricker_samples(nsteps, dt, 40.0)
+    u0 = np.zeros(n)
+    g = gpu_run(V, (n,), Q, u0, v0.astype(np.float32), 12, dt, nsteps, V.IMPL_FUSED, V.F32, (n // 3,), src,
+                chunks=[1, 60, 89])
+    r = _oracle_run((n,), Q, u0, v0.astype(np.float32).astype(np.float64), 12, dt, nsteps, (n // 3,), src)
+    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
 
 
 def test_run_fp64_3d_plain(V):
