@@ -21,8 +21,10 @@
  *     on a context.
  *   - Arrays are dense, C order, indexed [z][y][x] (x fastest); grid sizes
  *     n[] and box bounds lo[], hi[] are given in (x, y, z) order.
- *   - Grid sizes must be even (Sec. 2: "J even").  The fused kernels accept
- *     powers of two 64..1024 per axis in 2D; other sizes and dimensions run on
+ *   - Grid sizes must be even (Sec. 2: "J even").  The fused kernels
+ *     (VOFL_IMPL_FUSED) cover 1D lines of 16..4096 points (float; double up
+ *     to 2048), 2D grids with power-of-two axes 64..1024 in float, and 3D
+ *     grids 64^3, 128^3, 256^3 and 128x64x256 in float; other shapes run on
  *     the plain cuFFT path (VOFL_IMPL_PLAIN) or return VOFL_EUNSUPPORTED.
  *   - "_dev" pointers are device pointers on the GPU current when the context
  *     was created; others are host pointers unless an `on_device` flag says so.

@@ -114,6 +114,8 @@ size_t vofl_footprint_bytes(int ndim, const int64_t* n, int prec, int impl, int 
   size_t b = r * (size_t)N * 6 + sizeof(double) * (size_t)N + 8192;  // delta A B u0 u1 l2p, gamma
   if (impl == VOFL_IMPL_FUSED && fused2d_supported(ndim, n, prec))
     b += fused2d_footprint(n, M);
+  else if (impl == VOFL_IMPL_FUSED && fused3d_supported(ndim, n, prec))
+    b += fused3d_footprint(n, M);
   else if (impl == VOFL_IMPL_FUSED && fused1d_supported(ndim, n, prec))
     b += (size_t)N * (prec == VOFL_F64 ? 8 : 4) * 4;
   else
@@ -135,7 +137,8 @@ int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, co
     N *= n[i];
   }
   if (N > (1LL << 34)) return VOFL_EINVAL;
-  if (impl == VOFL_IMPL_FUSED && !fused2d_supported(ndim, n, prec) && !fused1d_supported(ndim, n, prec))
+  if (impl == VOFL_IMPL_FUSED && !fused2d_supported(ndim, n, prec) && !fused1d_supported(ndim, n, prec) &&
+      !fused3d_supported(ndim, n, prec))
     return VOFL_EUNSUPPORTED;
 
   vofl_ctx* c = new vofl_ctx();
@@ -179,7 +182,7 @@ int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, co
   cudaMemsetAsync(c->d_step, 0, sizeof(int) * 4, c->stream);
   int st = VOFL_OK;
   if (impl == VOFL_IMPL_FUSED)
-    c->eng = ndim == 1 ? make_fused1d(c, &st) : make_fused2d(c, &st);
+    c->eng = ndim == 1 ? make_fused1d(c, &st) : (ndim == 2 ? make_fused2d(c, &st) : make_fused3d(c, &st));
   else
     c->eng = make_plain(c, &st);
   if (!c->eng) {

@@ -37,359 +37,18 @@
 #include <string>
 #include <vector>
 
-#include "fft_warp.cuh"
-#include "internal.h"
-#include "tma.cuh"
+#include "kernels.cuh"
 
 namespace vofl {
 
 namespace {
 
-// CTA sizes (warps) per kernel
-constexpr int W_FROWS = 2;  // forward rows: small CTAs, 4x more CTAs than SMs at 1024^2
-constexpr int W_FCOLS = 4;  // forward columns: 4 columns -> 32-byte row segments
-constexpr int W_INV = 8;    // inverse kernels
-
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
-
-template <int N>
-constexpr int warp_stride() {
-  // consecutive warp buffers start 2 (mod 16) float2 slots apart, so a
-  // half-warp reading one element from each of 8 warp buffers for 2
-  // consecutive rows touches 16 distinct bank pairs
-  return (LineFFT<N>::WARP_SLOTS + 15) / 16 * 16 + 2;
-}
-template <int N, int W>
-constexpr size_t exch_smem() {
-  return (size_t)W * warp_stride<N>() * sizeof(float2);
-}
-
-// -------------------------------------------------------------------------
-// F1: forward FFT along x of two rows at once, split into half spectra.
-// -------------------------------------------------------------------------
-template <int NX>
-__global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __restrict__ u, float2* __restrict__ T,
-                                                             int ny, int pT, float ryy, const float2* __restrict__ twx,
-                                                             int* step_ctr, int inc_step) {
-  using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, THREADS = W_FROWS * 32;
-  __shared__ float2 s_tw[NX];
-  extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
-  __syncthreads();
-  pdl_wait();  // u is written by the previous step's last kernel
-  pdl_trigger();
-  if (inc_step && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int li = lane % LANES, line = lane / LANES;
-  float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int pair = (blockIdx.x * W_FROWS + warp) * F::LPW + line;
-  const bool active = pair < ny / 2;
-  const int y0 = 2 * (active ? pair : 0);
-  const float* r0 = u + (size_t)y0 * NX;
-  const float* r1 = r0 + NX;
-  const float* rm = u + (size_t)(y0 == 0 ? ny - 1 : y0 - 1) * NX;
-  const float* rp = u + (size_t)(y0 + 2 == ny ? 0 : y0 + 2) * NX;
-  // w = D_xx u + (h_x/h_y)^2 D_yy u (second differences, no 1/h^2): its DFT is
-  // lambda_k u_hat_k exactly, with lambda_k = -4 sin^2(pi k1/nx) - 4 (h_x/h_y)^2
-  // sin^2(pi k2/ny); 1/lambda_k is folded into the multiplier table.  On FP32
-  // data the neighbour differences are exact or carry a rounding relative to
-  // themselves, so w's transform keeps the high-wavenumber content that an
-  // FP32 transform of u would bury under round-off of size eps*|u|.
-  float2 v[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int x = li + LANES * m;
-    const int xm = (x - 1) & (NX - 1), xp = (x + 1) & (NX - 1);
-    const float a = __ldg(r0 + x), b = __ldg(r1 + x);
-    const float dxa = (__ldg(r0 + xp) - a) - (a - __ldg(r0 + xm));
-    const float dxb = (__ldg(r1 + xp) - b) - (b - __ldg(r1 + xm));
-    const float dya = (b - a) - (a - __ldg(rm + x));
-    const float dyb = (__ldg(rp + x) - b) - (b - a);
-    v[m] = make_float2(dxa + ryy * dya, dxb + ryy * dyb);
-  }
-  fft_line<NX, false>(v, wbuf, s_tw, li, line);
-  float2* lb = wbuf + line * F::PAD_LINE;
-#pragma unroll
-  for (int m = 0; m < E; ++m) lb[F::pad(li + LANES * m)] = v[m];
-  __syncwarp();
-  float2* t0 = T + (size_t)y0 * pT;
-  float2* t1 = t0 + pT;
-  for (int k = li; k <= H; k += LANES) {
-    const float2 a = lb[F::pad(k)];
-    const float2 b = lb[F::pad((NX - k) & (NX - 1))];
-    // A = (X_k + conj X_{-k})/2 (row y0), B = (X_k - conj X_{-k})/(2i) (row y0+1)
-    if (active) {
-      t0[k] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-      t1[k] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
-    }
-  }
-}
-
-// -------------------------------------------------------------------------
-// F2: forward FFT along y of each half-spectrum column.  Stage 0 is done
-// cooperatively by the CTA: thread b takes column b % CW, butterfly b / CW,
-// so each load instruction reads row segments of CW adjacent columns of T
-// (coalesced, no transposition pass); stage 1 is done by the warp owning
-// the column, whose output is a contiguous column of Uh.
-// -------------------------------------------------------------------------
-template <int NY>
-__global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __restrict__ T, int pT,
-                                                             float2* __restrict__ Uh, int ncols,
-                                                             const float2* __restrict__ twy) {
-  using F = LineFFT<NY>;
-  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
-  constexpr int THREADS = W_FCOLS * 32, CW = W_FCOLS * LPW;  // columns per CTA
-  __shared__ float2 s_tw[NY];
-  extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
-  pdl_wait();  // T is written by k2d_fwd_rows
-  pdl_trigger();
-  const int c0 = blockIdx.x * CW;
-  {
-    // cooperative stage 0: one radix-E butterfly per thread
-    const int cc = threadIdx.x % CW, j = threadIdx.x / CW;
-    const int col = min(c0 + cc, ncols - 1);
-    float2 v[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = T[(size_t)(j + LANES * r) * pT + col];
-    float2* lb = s_buf + (cc / LPW) * warp_stride<NY>() + (cc % LPW) * F::PAD_LINE;
-    stage0_to_smem<NY, false>(v, lb, j);
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int li = lane % LANES, line = lane / LANES;
-  const float2* lb = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
-  const int c = c0 + warp * LPW + line;
-  if (c < ncols) {
-    float2* dst = Uh + (size_t)c * NY;
-#pragma unroll
-    for (int q = 0; q < BPL; ++q) {
-      float2 w[LANES];
-      stage1_from_smem<NY, false>(w, lb, s_tw, li + LANES * q);
-#pragma unroll
-      for (int r = 0; r < LANES; ++r) dst[li + LANES * (q + BPL * r)] = w[r];
-    }
-  }
-}
-
-// -------------------------------------------------------------------------
-// I1: multiplier + inverse FFT along y, for terms [m_lo, m_hi) of one
-// operator (blockIdx.y).  Output Z[s][op][y][c], s = m - m_lo.
-// Each warp keeps its column's spectrum and the multiplier recurrence
-// t_m = P ln|mu|^{2m}/m! in registers (ln|mu|^2 in shared memory) and does
-// stage 0; stage 1 is done cooperatively by the CTA (thread b: column
-// b % CW, butterfly b / CW), so every store writes row segments of CW
-// adjacent columns of Z.
-// -------------------------------------------------------------------------
-template <int NY>
-constexpr size_t inv_cols_smem() {
-  return exch_smem<NY, W_INV>() + (size_t)W_INV * LineFFT<NY>::LPW * NY * sizeof(float);
-}
-
-template <int NY>
-__global__ void __launch_bounds__(W_INV * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
-                                                           const float* __restrict__ Lg, float2* __restrict__ Z,
-                                                           long long zslot, int pZ, int ncols, int m_lo, int m_hi,
-                                                           float inv_fact_lo, const float2* __restrict__ twy) {
-  using F = LineFFT<NY>;
-  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
-  constexpr int THREADS = W_INV * 32, CW = W_INV * LPW;  // columns per CTA
-  __shared__ float2 s_tw[NY];
-  extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
-  const int op = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int li = lane % LANES, line = lane / LANES;
-  float2* lb_own = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
-  float* s_lg = reinterpret_cast<float*>(s_buf + W_INV * warp_stride<NY>()) + (size_t)(warp * LPW + line) * NY;
-  const int c0 = blockIdx.x * CW;
-  const int c = c0 + warp * LPW + line;
-  const int cc = min(c, ncols - 1);
-  const long long tot = (long long)ncols * NY;
-  const float2* uh_col = Uh + (size_t)cc * NY;
-  const float* p_col = P + op * tot + (size_t)cc * NY;
-  const float* l_col = Lg + (size_t)cc * NY;
-  float tm[E];
-  // tables first (they do not depend on the previous kernel)
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int y = li + LANES * m;
-    const float l = l_col[y];
-    s_lg[y] = l;
-    tm[m] = p_col[y] * powi(l, m_lo) * inv_fact_lo;
-  }
-  __syncthreads();
-  pdl_wait();  // Uh (k2d_fwd_cols) ready; the previous group's readers of Z are done
-  pdl_trigger();
-  float2 uh[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) uh[m] = uh_col[li + LANES * m];
-  // cooperative stage-1 assignment of this thread
-  int sc[BPL], sj[BPL];
-#pragma unroll
-  for (int q = 0; q < BPL; ++q) {
-    const int b = threadIdx.x + THREADS * q;
-    sc[q] = b % CW;
-    sj[q] = b / CW;
-  }
-  for (int mt = m_lo; mt < m_hi; ++mt) {
-    float2 x[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) x[m] = cscale(uh[m], tm[m]);
-    stage0_to_smem<NY, true>(x, lb_own, li);
-    __syncthreads();
-    float2* zb = Z + (long long)((mt - m_lo) * 2 + op) * zslot + c0;
-#pragma unroll
-    for (int q = 0; q < BPL; ++q) {
-      const float2* lb = s_buf + (sc[q] / LPW) * warp_stride<NY>() + (sc[q] % LPW) * F::PAD_LINE;
-      float2 w[LANES];
-      stage1_from_smem<NY, true>(w, lb, s_tw, sj[q]);
-      if (c0 + sc[q] < ncols) {
-#pragma unroll
-        for (int r = 0; r < LANES; ++r) zb[(size_t)(sj[q] + E * r) * pZ + sc[q]] = w[r];
-      }
-    }
-    if (mt + 1 < m_hi) {
-      const float rinv = 1.0f / (float)(mt + 1);
-#pragma unroll
-      for (int m = 0; m < E; ++m) tm[m] = tm[m] * (s_lg[li + LANES * m] * rinv);
-    }
-    __syncthreads();  // stage-1 reads done before the next term's stage-0 writes
-  }
-}
-
-// -------------------------------------------------------------------------
-// I2: inverse FFT along x of both operators (A + iB), Horner accumulation
-// over the group's terms, then partial store or epilogue.
-// The two Z rows (operator 1 and 2) of the next term are copied into shared
-// memory by TMA bulk copies while the current term is transformed (double
-// buffer per line, mbarrier completion, bounded waits).
-// -------------------------------------------------------------------------
-template <int NX>
-constexpr int rows_rb() {
-  return (NX / 2 + 2) & ~1;  // Z row copy length in float2: >= H+1, 16-byte multiple
-}
-template <int NX>
-constexpr size_t inv_rows_smem() {
-  return exch_smem<NX, W_INV>() + (size_t)W_INV * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
-}
-
-template <int NX>
-__global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
-                                                           int ny, int m_lo, int m_hi, int top,
-                                                           const float* __restrict__ delta, float* __restrict__ part1,
-                                                           float* __restrict__ part2, EpiArgs<float> epi,
-                                                           float inv_lambda, const float2* __restrict__ twx,
-                                                           int* err) {
-  using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W_INV * 32;
-  constexpr int RB = rows_rb<NX>();
-  constexpr uint32_t RB_BYTES = RB * sizeof(float2);
-  __shared__ float2 s_tw[NX];
-  __shared__ uint64_t s_bar[W_INV * LPW * 2];
-  extern __shared__ float2 s_buf[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int li = lane % LANES, line = lane / LANES;
-  const int lid = warp * LPW + line;  // line id inside the CTA
-  uint64_t* bar = s_bar + 2 * lid;
-  float2* zbuf = s_buf + W_INV * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
-  if (li == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
-  __syncthreads();
-  pdl_wait();  // Z of this group and the previous group's partial sums are ready
-  pdl_trigger();
-  float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int yr = (blockIdx.x * W_INV + warp) * LPW + line;
-  const bool active = yr < ny;
-  const int y = active ? yr : 0;
-  const size_t row = (size_t)y * NX;
-  auto issue = [&](int buf, int mt) {
-    const float2* z1 = Z + (long long)((mt - m_lo) * 2 + 0) * zslot + (size_t)y * pZ;
-    const float2* z2 = Z + (long long)((mt - m_lo) * 2 + 1) * zslot + (size_t)y * pZ;
-    mbar_arrive_expect_tx(&bar[buf], 2 * RB_BYTES);
-    bulk_copy_g2s(zbuf + buf * 2 * RB, z1, RB_BYTES, &bar[buf]);
-    bulk_copy_g2s(zbuf + buf * 2 * RB + RB, z2, RB_BYTES, &bar[buf]);
-  };
-  if (li == 0) issue(0, m_hi - 1);
-  float a1[E], a2[E];
-  if (top) {
-#pragma unroll
-    for (int m = 0; m < E; ++m) a1[m] = a2[m] = 0.f;
-  } else {
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      a1[m] = part1[row + li + LANES * m];
-      a2[m] = part2[row + li + LANES * m];
-    }
-  }
-  uint32_t phase = 0;  // bit b: parity to wait for on buffer b
-  int it = 0;
-  bool ok = true;
-  for (int mt = m_hi - 1; mt >= m_lo; --mt, ++it) {
-    const int b = it & 1;
-    if (mt > m_lo) {
-      __syncwarp();  // every lane finished reading buffer b^1 (two terms ago)
-      if (li == 0) {
-        fence_proxy_async_smem();
-        issue(b ^ 1, mt - 1);
-      }
-    }
-    const bool got = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, err);
-    phase ^= 1u << b;
-    if (!__all_sync(0xffffffffu, got)) {
-      // give up: drain the prefetch still in flight (bounded) and leave
-      if (mt > m_lo) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u, err);
-      ok = false;
-      break;
-    }
-    const float2* z1 = zbuf + b * 2 * RB;
-    const float2* z2 = z1 + RB;
-    float2 w[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int n = li + LANES * m;
-      if (n <= H) {
-        const float2 p = z1[n], q = z2[n];
-        w[m] = (n == 0 || n == H) ? make_float2(p.x, q.x) : make_float2(p.x - q.y, p.y + q.x);
-      } else {
-        const float2 p = z1[NX - n], q = z2[NX - n];
-        w[m] = make_float2(p.x + q.y, q.x - p.y);
-      }
-    }
-    fft_line<NX, true>(w, wbuf, s_tw, li, line);
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const float d = delta[row + li + LANES * m];
-      a1[m] = fmaf(d, a1[m], w[m].x);
-      a2[m] = fmaf(d, a2[m], w[m].y);
-    }
-  }
-  if (!active || !ok) return;
-  if (m_lo > 0) {
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      part1[row + li + LANES * m] = a1[m];
-      part2[row + li + LANES * m] = a2[m];
-    }
-  } else {
-#pragma unroll
-    for (int m = 0; m < E; ++m)
-      epilogue_point<float>(epi, (long long)(row + li + LANES * m), a1[m], a2[m] * inv_lambda);
-  }
-}
-
 // -------------------------------------------------------------------------
 // size dispatch
 // -------------------------------------------------------------------------
 struct Kernels {
-  void (*fwd_rows)(const float*, float2*, int, int, float, const float2*, int*, int);
-  void (*fwd_cols)(const float2*, int, float2*, int, const float2*);
+  void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int);
+  void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*inv_cols)(const float2*, const float*, const float*, float2*, long long, int, int, int, int, float,
                    const float2*);
   void (*inv_rows)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>,
@@ -445,33 +104,6 @@ int set_smem_attributes(const Kernels& k) {
   return VOFL_OK;
 }
 
-inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
-
-// 1/m! in double, rounded once to float
-inline float inv_factorial(int m) {
-  double f = 1.0;
-  for (int i = 2; i <= m; ++i) f *= i;
-  return (float)(1.0 / f);
-}
-
-// Launch with programmatic stream serialisation: the kernel may start while
-// its predecessor finishes and synchronises itself with griddepcontrol.wait.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  count_launch();
-  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
-
 // Every buffer and constant one fused 2D apply / step needs.
 struct Plan2D {
   Kernels k{};
@@ -493,12 +125,12 @@ struct Plan2D {
   cudaError_t forward(cudaStream_t s, const float* u, bool inc_step, cudaEvent_t* ev = nullptr) const {
     const int rpc = W_FROWS * k.lpw_x;  // row pairs per CTA
     cudaError_t e = launch_pdl(k.fwd_rows, dim3((ny / 2 + rpc - 1) / rpc), dim3(W_FROWS * 32), k.smem_frows, s, u,
-                               T, ny, pT, ryy, (const float2*)twx, step_ctr, inc_step ? 1 : 0);
+                               T, ny, 1, pT, ryy, 0.0f, (const float2*)twx, step_ctr, inc_step ? 1 : 0);
     if (e) return e;
     if (ev) cudaEventRecord(ev[1], s);
     const int cpc = W_FCOLS * k.lpw_y;
     e = launch_pdl(k.fwd_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_FCOLS * 32), k.smem_fcols, s, (const float2*)T,
-                   pT, Uh, ncols, (const float2*)twy);
+                   pT, Uh, ncols, (const float2*)twy, 0LL, 0LL);
     if (ev) cudaEventRecord(ev[2], s);
     return e;
   }
@@ -537,8 +169,6 @@ void plan_constants(int nx, int ny, double lx, double ly, int* e2, float* ryy) {
   const double hx = lx / nx, hy = ly / ny;
   *ryy = (float)((hx * hx) / (hy * hy));
 }
-
-int line_e(int n) { return n >= 512 ? 32 : (n >= 128 ? 16 : 8); }
 
 struct Fused2D : Engine {
   Plan2D p;

@@ -157,6 +157,9 @@ struct Engine {
 Engine* make_fused2d(vofl_ctx* c, int* status);
 Engine* make_fused1d(vofl_ctx* c, int* status);
 bool fused1d_supported(int ndim, const int64_t* n, int prec);
+Engine* make_fused3d(vofl_ctx* c, int* status);
+bool fused3d_supported(int ndim, const int64_t* n, int prec);
+size_t fused3d_footprint(const int64_t* n, int M);
 Engine* make_plain(vofl_ctx* c, int* status);
 size_t fused2d_footprint(const int64_t* n, int M);
 size_t plain_footprint(int ndim, const int64_t* n, int prec);

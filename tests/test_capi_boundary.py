@@ -62,7 +62,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work(vofl):
     assert lib.vofl_create(C.byref(h), 4, n, lo, hi, 0, 1, None) == -1
     bad_hi = (C.c_double * 3)(0, 1, 1)
     assert lib.vofl_create(C.byref(h), 2, n, lo, bad_hi, 0, 1, None) == -1
-    # fused path only for the built 2D FP32 sizes
+    # fused path only for the built shapes (16^3 is not one of them)
     n3 = (C.c_int64 * 3)(16, 16, 16)
     assert lib.vofl_create(C.byref(h), 3, n3, lo, hi, 0, 0, None) == -6
     assert lib.vofl_create(C.byref(h), 2, n, lo, hi, 1, 0, None) == -6

@@ -160,3 +160,21 @@ def test_fused_1d_apply_matches_oracle(V, shape, prec):
         g1, g2, uin = gpu_apply_pair(V, shape, Q, u, M, V.IMPL_FUSED, pr)
         r1, r2 = O.seismic_operators(uin, gamma_of(Q), M)
         assert rel_l2(g1, r1) <= tol and rel_l2(g2, r2) <= tol, (M, rel_l2(g1, r1), rel_l2(g2, r2))
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (128, 128, 128), (256, 64, 128)])
+def test_fused_3d_apply_matches_oracle(V, shape):
+    for M in (0, 3, 8):
+        Q = S.q_lowpass(shape, 31 + M)
+        u = S.q_lowpass(shape, 41 + M, qmin=-1.0, qmax=1.0, sigma_k=max(shape) / 8)
+        g1, g2, uin = gpu_apply_pair(V, shape, Q, u, M, V.IMPL_FUSED, V.F32)
+        r1, r2 = O.seismic_operators(uin, gamma_of(Q), M)
+        assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32, (M, rel_l2(g1, r1), rel_l2(g2, r2))
+
+
+def test_fused_3d_config_size_apply(V):
+    """3D 256^3, M = 8, two-layer Q and a 4-cell Gaussian (the 3D workload)."""
+    w = S.workload_3d_256(nsteps=1)
+    g1, g2, uin = gpu_apply_pair(V, w["shape"], w["Q"], w["u0"], w["M"], V.IMPL_FUSED, V.F32)
+    r1, r2 = O.seismic_operators(uin, gamma_of(w["Q"]), w["M"])
+    assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32, (rel_l2(g1, r1), rel_l2(g2, r2))

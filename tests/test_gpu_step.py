@@ -88,6 +88,16 @@ def test_run_fused_1d_fp32_source_and_velocity(V):
     assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
 
 
+def test_run_fused_3d_matches_oracle(V):
+    """3D 64^3, two-layer Q, Gaussian pulse, 30 steps (fused FP32)."""
+    shape = (64, 64, 64)
+    Q = S.q_two_layer_3d(64)
+    u0 = S.gaussian_pulse(shape, 3.0)
+    g = gpu_run(V, shape, Q, u0, None, 8, 8e-3, 30, V.IMPL_FUSED, V.F32)
+    r = _oracle_run(shape, Q, u0.astype(np.float32).astype(np.float64), None, 8, 8e-3, 30)
+    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+
+
 def test_run_fp64_3d_plain(V):
     shape = (32, 32, 32)
     Q = S.q_two_layer_3d(32)
