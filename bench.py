@@ -13,7 +13,11 @@ is Mpoint-steps/s = 1024^2 * 1000 * runs / time.
   e2e    the same run through the C ABI with host buffers: the H2D copies of
          Q, u0 and the samples and the D2H copy of the final wavefield are
          inside the timed region;
-  plain  the cuFFT + elementwise baseline on the same run.
+  plain  the cuFFT + elementwise baseline on the same run;
+  batch  64 independent 2D simulations of uneven sizes {256, 512, 768,
+         1024}^2 (M = 12, 300 steps each, dt a quarter of the leap-frog bound
+         of each model) advanced together by one batch (vofl_batch_*),
+         autotuned, timed over the whole 300-step run.
 
 L2 is flushed (256 MiB write) before every timed run.  Times are CUDA events
 on the context stream.  `--impl reference` times the FP64 CPU oracle on a
@@ -171,6 +175,65 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------------------
+# batched workload: 64 uneven 2D simulations
+# ---------------------------------------------------------------------------
+def batch_bench(V, torch, stream, flush):
+    import synthetic as S
+    sims = S.workload_batch()
+    nsteps = sims[0]["nsteps"]
+    solvers = []
+    t_setup = time.perf_counter()
+    b = V.Batch(stream=stream.cuda_stream)
+    pts = 0
+    for sp in sims:
+        s = V.Solver(sp["shape"], stream=stream.cuda_stream)
+        s.set_q(sp["Q"], sp["c0"], sp["omega0"])
+        s.set_M(sp["M"])
+        dt = s.suggest_dt(0.25)
+        s.set_state(np.zeros(sp["shape"], np.float32))
+        s.set_source(sp["src_idx"], S.ricker_samples(nsteps, dt, sp["f0"]))
+        b.add(s, dt)
+        solvers.append(s)
+        pts += sp["shape"][0] * sp["shape"][1]
+    t_setup = time.perf_counter() - t_setup
+    ms_default = b.time(reps=2)
+    sizes = sorted({sp["shape"][0] for sp in sims})
+    b.set_schedule(False, {n: 1 for n in sizes})
+    ms_serial = b.time(reps=2)
+    b.set_schedule(True, {})
+    ms_tuned = b.tune(reps=2)
+    par, chunks = b.schedule()
+    kps = b.kernels_per_step()
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        stream.synchronize()
+        l0 = V.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(nsteps)
+        e1.record(stream)
+        e1.synchronize()
+        launches = V.kernel_launches() - l0
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    b.close()
+    for s in solvers:
+        s.close()
+    counts = {}
+    for sp in sims:
+        counts[sp["shape"][0]] = counts.get(sp["shape"][0], 0) + 1
+    return {"value": pts * nsteps / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_run": ms,
+            "workload": f"64 independent 2D runs, edges drawn from {sizes} (seed 4): "
+                        + ", ".join(f"{counts[n]}x{n}^2" for n in sizes)
+                        + f"; M=12, {nsteps} steps each, dt = 0.25 * 2/omega_max per model",
+            "points": pts, "steps": nsteps, "kernels_per_step": kps, "gpu_launches": launches,
+            "ms_per_batch_step": {"tuned": ms_tuned, "default_all_per_launch": ms_default,
+                                  "one_sim_per_launch_serial": ms_serial},
+            "schedule": {"parallel_branches": par, "sims_per_launch": {str(k): v for k, v in chunks.items()}},
+            "setup_s": t_setup}
 
 
 # ---------------------------------------------------------------------------
@@ -335,6 +398,7 @@ def run_gpu(args):
         acc = {f"{nm}_apply_rel_l2": [O.rel_l2(res[nm][0], r1), O.rel_l2(res[nm][1], r2)] for nm in res}
         acc["input"] = "final wavefield of the timed run (FP32), oracle FP64 on the same input"
 
+    batch = None if args.skip_batch else batch_bench(V, torch, stream, flush)
     cpu = cpu_baseline() if (rank == 0 and not args.skip_cpu) else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -349,7 +413,7 @@ def run_gpu(args):
                 "ms_per_lffp_step": lffp_fused,
                 "fused_over_plain": value / plain_value,
                 "accuracy": acc, "gpu_launches": gpu_launches, "roofline": roof,
-                "cpu_baseline": cpu, "clocks": clk, "serve": None}
+                "cpu_baseline": cpu, "clocks": clk, "batch": batch, "serve": None}
         print(json.dumps(line))
     fused.close()
     plain.close()
@@ -366,6 +430,7 @@ def main():
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true", help="omit the 64-simulation batch measurement")
     ap.add_argument("--ncu-steps", type=int, default=0,
                     help="profiling mode: set up the workload, run this many leap-frog steps, print nothing")
     args = ap.parse_args()

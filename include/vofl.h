@@ -23,7 +23,8 @@
  *     n[] and box bounds lo[], hi[] are given in (x, y, z) order.
  *   - Grid sizes must be even (Sec. 2: "J even").  The fused kernels
  *     (VOFL_IMPL_FUSED) cover 1D lines of 16..4096 points (float; double up
- *     to 2048), 2D grids with power-of-two axes 64..1024 in float, and 3D
+ *     to 2048), the 2D grids 64^2, 128^2, 256^2, 512^2, 768^2, 1024^2,
+ *     256x128, 128x256, 512x64, 64x512 and 1024x256 in float, and the 3D
  *     grids 64^3, 128^3, 256^3 and 128x64x256 in float; other shapes run on
  *     the plain cuFFT path (VOFL_IMPL_PLAIN) or return VOFL_EUNSUPPORTED.
  *   - "_dev" pointers are device pointers on the GPU current when the context
@@ -142,6 +143,15 @@ VOFL_API int vofl_step(vofl_ctx* ctx, int64_t nsteps, double dt);
  * memory. */
 VOFL_API int vofl_get_state(vofl_ctx* ctx, void* u_out, int on_device);
 
+/* Time step for a run of the current model: dt = courant * 2 / omega_max,
+ * omega_max = max_x |c^2 eta|^{1/2} |mu_max|^{1+gamma(x)} with |mu_max| the
+ * largest grid wavenumber (sqrt of the sum of (pi n_i / L_i)^2): the
+ * highest angular frequency of the undamped part of Eq. (1.1) on the grid,
+ * against which explicit leap-frog needs dt < 2 / omega.  courant = 0.25 is
+ * the rule the built-in workloads use.  Blocks until done.  Returns VOFL_OK,
+ * VOFL_EINVAL, VOFL_ESTATE (no model) or VOFL_ECUDA. */
+VOFL_API int vofl_suggest_dt(vofl_ctx* ctx, double courant, double* dt);
+
 /* Number of steps taken in the current run. */
 VOFL_API int64_t vofl_steps_taken(const vofl_ctx* ctx);
 
@@ -179,6 +189,90 @@ VOFL_API const char* vofl_version(void);
  * ~1 ms budget; *gave_up is set to 1 when the wait gave up as designed.  It
  * faults and hangs nothing; the device stays usable.  Synchronous. */
 VOFL_API int vofl_selftest_bounded_wait(int* gave_up);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent 2D simulations advanced together.
+ *
+ * Each simulation is an ordinary context (VOFL_F32, VOFL_IMPL_FUSED, square
+ * 2D grid of 64, 128, 256, 512, 768 or 1024 points per side) with its model
+ * and state (and optionally a source) set; a batch borrows it and advances
+ * it by the leap-frog step of Eq. (1.1) (Eq. (3.4), with the Taylor start
+ * for a context that has not stepped yet) with the operators of Eq. (2.13),
+ * exactly as vofl_step on the context alone would, bit for bit.  Contexts
+ * of a batch may differ in grid size, model, M, dt, source and in how far
+ * they have run.  The batch queues its work on its own stream (the one
+ * given, or one it creates); every kernel of a step runs once per grid size
+ * (or per chunk of simulations of that size, see vofl_batch_tune), so small
+ * grids that cannot fill the GPU alone fill it together.  The paper
+ * steps one simulation at a time; batching is a throughput layer on top.
+ * ------------------------------------------------------------------------ */
+typedef struct vofl_batch vofl_batch;
+
+/* New empty batch on the current GPU.  cuda_stream: a cudaStream_t or NULL
+ * (the batch creates its own non-blocking stream).  Returns VOFL_OK,
+ * VOFL_EINVAL (out is NULL) or VOFL_ECUDA. */
+VOFL_API int vofl_batch_create(vofl_batch** out, void* cuda_stream);
+
+/* Wait for the batch's queued work, hand every context back (they stay
+ * valid, at the state reached) and free the batch. */
+VOFL_API void vofl_batch_destroy(vofl_batch* b);
+
+/* Message of the last error on the batch. */
+VOFL_API const char* vofl_batch_last_error(const vofl_batch* b);
+
+/* Add a context; it steps with time step dt (> 0; a context that has
+ * already stepped must keep its dt).  Until it is removed, every other
+ * entry point on the context returns VOFL_ESTATE (vofl_destroy removes it
+ * first).  *slot (may be NULL) receives an id for vofl_batch_remove.
+ * Returns VOFL_OK, VOFL_EINVAL, VOFL_ESTATE (model or state not set, or
+ * already in a batch), VOFL_EUNSUPPORTED (not a fused FP32 square 2D
+ * context of a batched size) or VOFL_ECUDA. */
+VOFL_API int vofl_batch_add(vofl_batch* b, vofl_ctx* ctx, double dt, int* slot);
+
+/* Remove the context of `slot`; its own stream waits for the batch's
+ * queued work, so vofl_get_state on it then sees every step taken.
+ * Returns VOFL_OK or VOFL_EINVAL (unknown slot). */
+VOFL_API int vofl_batch_remove(vofl_batch* b, int slot);
+
+/* Number of contexts in the batch. */
+VOFL_API int vofl_batch_size(const vofl_batch* b);
+
+/* Advance every context of the batch by nsteps >= 0 steps (asynchronous,
+ * replayed from CUDA graphs captured on first use and after each change of
+ * membership or schedule).  Returns VOFL_OK, VOFL_EINVAL or VOFL_ECUDA. */
+VOFL_API int vofl_batch_step(vofl_batch* b, int64_t nsteps);
+
+/* Kernels one batch step launches under the current membership and
+ * schedule (>= 0), or a negative status. */
+VOFL_API int64_t vofl_batch_kernels_per_step(vofl_batch* b);
+
+/* Wait for the batch's stream; VOFL_ETIMEDOUT if a bounded device wait of
+ * any member gave up (as vofl_sync), VOFL_ECUDA on a CUDA error. */
+VOFL_API int vofl_batch_sync(vofl_batch* b);
+
+/* Autotune the schedule on the live batch: per grid size, the number of
+ * simulations per launch (1, 2, 4, 8, 16 or all), then whether sizes run on
+ * parallel graph branches, each candidate timed over `reps` two-step graph
+ * replays (CUDA events) by coordinate search.  The members' states (both
+ * wavefield buffers, L2 u^{n-1} and the step counter) are saved first and
+ * put back afterwards, so tuning leaves every simulation where it was.
+ * Allocates a temporary copy of those states.  *ms_per_step (may be NULL)
+ * receives the best time of one batch step.  Blocks until done. */
+VOFL_API int vofl_batch_tune(vofl_batch* b, int reps, double* ms_per_step);
+
+/* Time one batch step of the current schedule (CUDA events over `reps`
+ * two-step graph replays after one warm-up), from a saved copy of the
+ * members' states that is put back afterwards (as vofl_batch_tune).
+ * Blocks until done. */
+VOFL_API int vofl_batch_time(vofl_batch* b, int reps, double* ms_per_step);
+
+/* The schedule in use: *parallel = 1 if sizes run on parallel branches;
+ * up to cap (size, simulations per launch) pairs (0 = all of that size).
+ * Returns the number of pairs. */
+VOFL_API int vofl_batch_get_schedule(const vofl_batch* b, int* parallel, int* sizes, int* chunks, int cap);
+
+/* Set the schedule directly (as vofl_batch_get_schedule reports it). */
+VOFL_API int vofl_batch_set_schedule(vofl_batch* b, int parallel, const int* sizes, const int* chunks, int n);
 
 /* Allocation-free variant of vofl_apply_pair for small 2D grids.  The paper
  * has no counterpart: it is a deployment aid for callers that may not

@@ -18,6 +18,9 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                                    unpinned" beyond those reductions.
   general_lffp          (O4)       pinned: the paper's printed LFFP temporal
                                    errors (Table 3, Sec. 3.2) are reproduced (P7).
+  suggested_dt                     pinned: gamma = 0 closed form and the
+                                   stability of the single-mode recurrence of
+                                   the step on both sides of the bound.
 
 Conventions (the readings of the paper are listed in the design doc):
   * arrays are indexed [z][y][x] (x fastest); `lo`, `hi` are (x, y, z) ordered;
@@ -37,7 +40,7 @@ __all__ = [
     "seismic_coefficients", "seismic_coefficients_from_gamma",
     "dense_operator", "matrix_free_operator", "matrix_free_terms",
     "seismic_operators", "seismic_lffp", "general_lffp",
-    "l2_error", "rel_l2", "taylor_remainder_bound",
+    "l2_error", "rel_l2", "taylor_remainder_bound", "suggested_dt",
 ]
 
 
@@ -317,6 +320,24 @@ def seismic_lffp(gamma, c0, omega0, u0, v0, dt, nsteps, M, lo=None, hi=None,
         if return_all:
             history.append(u.copy())
     return (u, history) if return_all else u
+
+
+def suggested_dt(gamma, c0, omega0, shape, lo=None, hi=None, courant=0.25):
+    """Time step of the built-in workloads: courant * 2 / omega_max with
+    omega_max = max_x c |eta|^{1/2} |mu_max|^{1 + gamma(x)}, |mu_max|^2 the
+    sum over axes of the squared Nyquist wavenumbers (pi J / (b - a))^2.
+
+    Reading: the undamped part of the step (Eq. (3.4) applied to Eq. (1.1))
+    maps a Fourier mode of frequency omega by the recurrence
+    u^{n+1} = (2 - (dt omega)^2) u^n - u^{n-1}, stable for dt omega < 2; the
+    paper gives no time-step rule for the seismic runs, so the workloads take
+    a quarter of the largest stable step at the fastest point and mode."""
+    d, a, b = _dims(shape, lo, hi)
+    mu_max2 = sum((math.pi * shape[d - 1 - i] / (b[i] - a[i])) ** 2 for i in range(d))
+    coef = seismic_coefficients_from_gamma(np.broadcast_to(gamma, shape), c0, omega0)
+    g = coef["gamma"]
+    w = coef["c"] * np.sqrt(np.abs(coef["eta"])) * mu_max2 ** ((1.0 + g) / 2.0)
+    return courant * 2.0 / float(np.max(w))
 
 
 # ----------------------------------------------------------------------------

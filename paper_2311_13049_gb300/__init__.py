@@ -44,6 +44,7 @@ SIGNATURES = {
     "vofl_step": (C.c_int, [_vp, C.c_int64, C.c_double]),
     "vofl_get_state": (C.c_int, [_vp, _vp, C.c_int]),
     "vofl_steps_taken": (C.c_int64, [_vp]),
+    "vofl_suggest_dt": (C.c_int, [_vp, C.c_double, _dp]),
     "vofl_sync": (C.c_int, [_vp]),
     "vofl_last_error": (C.c_char_p, [_vp]),
     "vofl_footprint_bytes": (C.c_size_t, [C.c_int, _i64p, C.c_int, C.c_int, C.c_int]),
@@ -53,6 +54,20 @@ SIGNATURES = {
     "vofl_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int)]),
     "vofl_apply_pair_2d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp, _vp,
                                              _vp, _vp]),
+    "vofl_batch_create": (C.c_int, [C.POINTER(C.c_void_p), _vp]),
+    "vofl_batch_destroy": (None, [_vp]),
+    "vofl_batch_last_error": (C.c_char_p, [_vp]),
+    "vofl_batch_add": (C.c_int, [_vp, _vp, C.c_double, C.POINTER(C.c_int)]),
+    "vofl_batch_remove": (C.c_int, [_vp, C.c_int]),
+    "vofl_batch_size": (C.c_int, [_vp]),
+    "vofl_batch_step": (C.c_int, [_vp, C.c_int64]),
+    "vofl_batch_kernels_per_step": (C.c_int64, [_vp]),
+    "vofl_batch_sync": (C.c_int, [_vp]),
+    "vofl_batch_tune": (C.c_int, [_vp, C.c_int, _dp]),
+    "vofl_batch_time": (C.c_int, [_vp, C.c_int, _dp]),
+    "vofl_batch_get_schedule": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.c_int]),
+    "vofl_batch_set_schedule": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
 }
 
 
@@ -208,6 +223,12 @@ class Solver:
     def step(self, nsteps, dt):
         self._check(lib().vofl_step(self._h, int(nsteps), float(dt)))
 
+    def suggest_dt(self, courant=0.25):
+        """courant * 2 / omega_max of the current model (see vofl.h)."""
+        dt = C.c_double()
+        self._check(lib().vofl_suggest_dt(self._h, float(courant), C.byref(dt)))
+        return dt.value
+
     def steps_taken(self):
         return int(lib().vofl_steps_taken(self._h))
 
@@ -232,3 +253,86 @@ class Solver:
             self._check(k)
         nm = names.value.decode().split(";") if k > 0 else []
         return [(nm[i], ms[i], units[i]) for i in range(k)]
+
+
+class Batch:
+    """Many 2D simulations (Solver objects: FP32, fused, square grids)
+    advanced together (vofl_batch).  While a Solver is in a batch its own
+    methods raise VoflError (ESTATE); remove it (or close the batch) first."""
+
+    def __init__(self, stream=None):
+        h = C.c_void_p()
+        rc = lib().vofl_batch_create(C.byref(h), C.c_void_p(stream) if stream else None)
+        if rc != 0:
+            raise VoflError(rc, "vofl_batch_create failed")
+        self._h = h
+        self._members = {}
+
+    def _check(self, rc):
+        if rc < 0:
+            raise VoflError(rc, lib().vofl_batch_last_error(self._h).decode())
+        return rc
+
+    def add(self, solver, dt):
+        slot = C.c_int()
+        self._check(lib().vofl_batch_add(self._h, solver._h, float(dt), C.byref(slot)))
+        self._members[slot.value] = solver
+        return slot.value
+
+    def remove(self, slot):
+        self._check(lib().vofl_batch_remove(self._h, int(slot)))
+        return self._members.pop(slot)
+
+    def __len__(self):
+        return int(lib().vofl_batch_size(self._h))
+
+    def step(self, nsteps):
+        self._check(lib().vofl_batch_step(self._h, int(nsteps)))
+
+    def kernels_per_step(self):
+        return int(self._check(lib().vofl_batch_kernels_per_step(self._h)))
+
+    def sync(self):
+        self._check(lib().vofl_batch_sync(self._h))
+
+    def tune(self, reps=2):
+        ms = C.c_double()
+        self._check(lib().vofl_batch_tune(self._h, int(reps), C.byref(ms)))
+        return ms.value
+
+    def time(self, reps=2):
+        """ms per batch step of the current schedule (state left unchanged)."""
+        ms = C.c_double()
+        self._check(lib().vofl_batch_time(self._h, int(reps), C.byref(ms)))
+        return ms.value
+
+    def schedule(self):
+        par = C.c_int()
+        sizes = (C.c_int * 16)()
+        chunks = (C.c_int * 16)()
+        k = self._check(lib().vofl_batch_get_schedule(self._h, C.byref(par), sizes, chunks, 16))
+        return bool(par.value), {sizes[i]: chunks[i] for i in range(min(k, 16))}
+
+    def set_schedule(self, parallel, chunks):
+        n = len(chunks)
+        sz = (C.c_int * max(n, 1))(*[int(k) for k in chunks])
+        ch = (C.c_int * max(n, 1))(*[int(v) for v in chunks.values()])
+        self._check(lib().vofl_batch_set_schedule(self._h, 1 if parallel else 0, sz, ch, n))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vofl_batch_destroy(self._h)
+            self._h = None
+            self._members = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -39,7 +39,32 @@ vofl_ctx::GraphKey current_key(const vofl_ctx* c) {
   return k;
 }
 
-int check_ctx(vofl_ctx* c) { return c ? VOFL_OK : VOFL_EINVAL; }
+int check_ctx(vofl_ctx* c) {
+  if (!c) return VOFL_EINVAL;
+  if (c->batch) return set_err(c, VOFL_ESTATE, "the context is stepped by a batch; remove it from the batch first");
+  return VOFL_OK;
+}
+
+}  // namespace
+
+// Checks before stepping and, before the first step, the run set-up: the
+// step counter starts at 0 and L2 psi (Taylor start) goes into l2p.
+int vofl::prepare_run(vofl_ctx* c, double dt) {
+  if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
+  if (!(dt > 0) || !std::isfinite(dt)) return set_err(c, VOFL_EINVAL, "bad dt");
+  if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");
+  if (c->steps == 0) {
+    c->dt = dt;
+    VOFL_CUDA(c, cudaMemsetAsync(c->d_step, 0, sizeof(int), c->stream));
+    if (c->psi_nonzero) {
+      int st = c->eng->apply_pair(c, c->u[1], nullptr, c->l2p);
+      if (st) return st;
+    }
+  }
+  return VOFL_OK;
+}
+
+namespace {
 
 int upload(vofl_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
   VOFL_CUDA(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -200,6 +225,7 @@ int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, co
 
 void vofl_destroy(vofl_ctx* c) {
   if (!c) return;
+  if (c->batch) batch_detach(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   delete c->eng;
@@ -230,7 +256,7 @@ static int finish_model(vofl_ctx* c, const double* d_c0field, double c0, double 
 }
 
 int vofl_set_q(vofl_ctx* c, const double* Q, int on_device, double c0, double omega0) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (!Q) return set_err(c, VOFL_EINVAL, "Q is null");
   if (!(c0 > 0) || !(omega0 > 0)) return set_err(c, VOFL_EINVAL, "c0 and omega0 must be positive");
   int st = upload(c, c->d_gamma, Q, sizeof(double) * c->N, on_device);
@@ -242,7 +268,7 @@ int vofl_set_q(vofl_ctx* c, const double* Q, int on_device, double c0, double om
 
 int vofl_set_gamma(vofl_ctx* c, const double* gamma, const double* c0_field, int on_device, double c0,
                    double omega0) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (!gamma) return set_err(c, VOFL_EINVAL, "gamma is null");
   if (!(omega0 > 0) || (!c0_field && !(c0 > 0))) return set_err(c, VOFL_EINVAL, "c0 and omega0 must be positive");
   int st = upload(c, c->d_gamma, gamma, sizeof(double) * c->N, on_device);
@@ -265,27 +291,27 @@ int vofl_set_gamma(vofl_ctx* c, const double* gamma, const double* c0_field, int
 }
 
 int vofl_set_M(vofl_ctx* c, int M) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (M < 0 || M > 40) return set_err(c, VOFL_EINVAL, "M must be in [0, 40]");
   c->M = M;  // captured graphs are re-keyed on the next step
   return VOFL_OK;
 }
 
 int vofl_apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (!c->model_set) return set_err(c, VOFL_ESTATE, "set_q / set_gamma first");
   if (!u || (!o1 && !o2)) return set_err(c, VOFL_EINVAL, "null array");
   return c->eng->apply_pair(c, u, o1, o2);
 }
 
 int vofl_apply(vofl_ctx* c, int op, const void* u, void* out) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (op != VOFL_OP_1PG && op != VOFL_OP_HPG) return set_err(c, VOFL_EINVAL, "unknown operator");
   return vofl_apply_pair(c, u, op == VOFL_OP_1PG ? out : nullptr, op == VOFL_OP_HPG ? out : nullptr);
 }
 
 int vofl_set_state(vofl_ctx* c, const void* u0, const void* v0, int on_device) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (!u0) return set_err(c, VOFL_EINVAL, "u0 is null");
   const size_t b = elem_size(c) * c->N;
   reset_run(c);
@@ -305,7 +331,7 @@ int vofl_set_state(vofl_ctx* c, const void* u0, const void* v0, int on_device) {
 }
 
 int vofl_set_source(vofl_ctx* c, const int64_t* idx, const double* samples, int64_t nsamples, int on_device) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (nsamples <= 0) {
     c->nsrc = 0;
     c->src_flat = -1;
@@ -334,20 +360,10 @@ int vofl_set_source(vofl_ctx* c, const int64_t* idx, const double* samples, int6
 }
 
 int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
-  if (check_ctx(c)) return VOFL_EINVAL;
-  if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
-  if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return set_err(c, VOFL_EINVAL, "bad nsteps or dt");
+  if (int st = check_ctx(c)) return st;
+  if (nsteps < 0) return set_err(c, VOFL_EINVAL, "bad nsteps");
+  if (int st = prepare_run(c, dt)) return st;
   if (nsteps == 0) return VOFL_OK;
-  if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");
-  if (c->steps == 0) {
-    c->dt = dt;
-    VOFL_CUDA(c, cudaMemsetAsync(c->d_step, 0, sizeof(int), c->stream));
-    if (c->psi_nonzero) {
-      // L2 psi for the Taylor start, into the l2p buffer
-      int st = c->eng->apply_pair(c, c->u[1], nullptr, c->l2p);
-      if (st) return st;
-    }
-  }
   if (c->eng->can_run()) {
     // the whole request in one launch
     const int st = c->eng->run(c, nsteps, c->steps == 0 ? EPI_START : EPI_STEP);
@@ -370,10 +386,17 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
   return VOFL_OK;
 }
 
+int vofl_suggest_dt(vofl_ctx* c, double courant, double* dt) {
+  if (int st = check_ctx(c)) return st;
+  if (!dt || !(courant > 0) || !std::isfinite(courant)) return set_err(c, VOFL_EINVAL, "bad courant or dt pointer");
+  if (!c->model_set) return set_err(c, VOFL_ESTATE, "set the model first");
+  return model_suggest_dt(c, courant, dt);
+}
+
 int64_t vofl_steps_taken(const vofl_ctx* c) { return c ? c->steps : -1; }
 
 int vofl_get_state(vofl_ctx* c, void* u_out, int on_device) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (!u_out) return set_err(c, VOFL_EINVAL, "null output");
   const size_t b = elem_size(c) * c->N;
   VOFL_CUDA(c, cudaMemcpyAsync(u_out, c->u[c->cur], b, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -383,7 +406,7 @@ int vofl_get_state(vofl_ctx* c, void* u_out, int on_device) {
 }
 
 int vofl_sync(vofl_ctx* c) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
   VOFL_CUDA(c, cudaGetLastError());
   // device error word (d_step[1]): set by a bounded wait that gave up
@@ -398,7 +421,7 @@ int vofl_sync(vofl_ctx* c) {
 
 int vofl_profile_kernels(vofl_ctx* c, int reps, char* names_out, size_t names_cap, double* ms_out, double* units_out,
                          int cap) {
-  if (check_ctx(c)) return VOFL_EINVAL;
+  if (int st = check_ctx(c)) return st;
   if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
   if (reps < 1 || !names_out || !ms_out || !units_out) return set_err(c, VOFL_EINVAL, "bad profile arguments");
   std::string names;

@@ -3,29 +3,44 @@
 // (Eq. (2.13) of arXiv 2311.13049: one forward transform of u, then one
 // inverse transform per Taylor term).
 //
-// Algorithm: Stockham autosort, two radix stages N = R0 * R1 (Govindaraju et
-// al., "High performance discrete Fourier transforms on graphics processors",
-// SC 2008, restated here for a register/warp mapping):
-//   stage 0 (Ns = 1, radix R0 = E): every lane holds E elements in registers
-//     and does one DFT-E; no twiddles;
+// Algorithm: Stockham autosort (Govindaraju et al., "High performance
+// discrete Fourier transforms on graphics processors", SC 2008, restated
+// here for a register/warp mapping).  A stage of radix R at span Ns takes
+// butterfly j (0 <= j < N/R) from x[j + r N/R], r < R, multiplies input r by
+// w_{Ns R}^{r (j mod Ns)}, does a DFT-R and writes output r to
+// (j / Ns) Ns R + (j mod Ns) + r Ns.
+//
+// Power-of-two N (64..1024), two stages N = E * LANES:
+//   stage 0 (Ns = 1, radix E): every lane holds E elements in registers and
+//     does one DFT-E; no twiddles;
 //   exchange through shared memory (one write, one read per element);
-//   stage 1 (Ns = E, radix R1 = LANES): E/LANES butterflies per lane, each
-//     with twiddles w_N^{r k}, k = j mod E, then a DFT-R1.
+//   last stage (Ns = E, radix RL = LANES): NBL = E butterflies per line,
+//     E/LANES per lane, twiddles w_N^{r j}.
+// N = 768 = 24 * 8 * 4 (for grids with a factor 3), three stages, E = 24,
+// LANES = 32:
+//   stage 0 (Ns = 1, radix 24 = 3 * 8 in registers);
+//   middle stage (Ns = 24, radix 8) in place in the warp's shared line
+//     buffer, 3 butterflies per lane, twiddles w_192^{r (j mod 24)};
+//   last stage (Ns = 192, radix RL = 4): NBL = 192 butterflies per line,
+//     6 per lane, twiddles w_768^{r j}.
+// In both cases the last stage's butterfly j returns X[j + NBL r], r < RL.
 // A line of N complex values is owned by LANES = N/E consecutive lanes; lane
 // li of the line holds element m at line index li + LANES*m, on input AND on
 // output (natural order, no bit reversal).  Global loads/stores of that
 // pattern are coalesced (LANES consecutive elements per instruction).
 //
 // Shared-memory layout of the exchange: element a of a line sits at
-// a + a/E (one pad slot per E elements), which makes both the stage-0 writes
-// (stride E between lanes) and the stage-1 reads (consecutive) conflict-free
-// for E in {8, 16, 32}.
+// a + a/E (one pad slot per E elements), which makes the stage-0 writes
+// (stride E between lanes) and the later reads (consecutive) conflict-free
+// for E in {8, 16, 32} and nearly so for E = 24.
 //
-// Twiddles come from a per-size table tw[r][k] = exp(-2 pi i r k / N),
-// r < R1, k < E, generated in double and rounded to float; the inverse uses
-// the conjugate.  The in-register DFT-R is a compile-time radix-2
-// decimation-in-time recursion whose trivial twiddles (1, -i, -1, i) are
-// folded away.
+// Twiddles come from a per-size table: tw[r NBL + j] = exp(-2 pi i r j / N)
+// (r < RL, j < NBL), followed for N = 768 by exp(-2 pi i t / 192), t < 192;
+// generated in double and rounded to float; the inverse uses the conjugate.
+// The in-register DFT-R is a compile-time decimation-in-time recursion
+// (radix 2, and one radix-3 split for R = 3 * 2^k) whose constant twiddles
+// are evaluated at compile time; the trivial ones (1, -i, -1, i) are folded
+// away.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -43,35 +58,56 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
-// cos(2 pi a / 32), a = 0..31 (double literals rounded to float at compile time)
-struct Cos32 {
-  static constexpr double v[32] = {
-      1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
-      0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173, 0.19509032201612826785,
-      0.0, -0.19509032201612826785, -0.38268343236508977173, -0.55557023301960222474,
-      -0.70710678118654752440, -0.83146961230254523708, -0.92387953251128675613, -0.98078528040323044913,
-      -1.0, -0.98078528040323044913, -0.92387953251128675613, -0.83146961230254523708,
-      -0.70710678118654752440, -0.55557023301960222474, -0.38268343236508977173, -0.19509032201612826785,
-      0.0, 0.19509032201612826785, 0.38268343236508977173, 0.55557023301960222474,
-      0.70710678118654752440, 0.83146961230254523708, 0.92387953251128675613, 0.98078528040323044913};
-};
+// cos and sin of 2 pi a / R at compile time: Taylor series about the
+// nearest multiple of pi/2 (|x| <= pi/4 there; 20 terms are far below double
+// round-off), then rounded once to float by the caller.
+constexpr double kHalfPi = 1.5707963267948966192313216916398;
+constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int i = 1; i < 20; ++i) {
+    t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    s += t;
+  }
+  return s;
+}
+constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int i = 1; i < 20; ++i) {
+    t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    s += t;
+  }
+  return s;
+}
+// 2 pi a / R = q pi/2 + x, q the nearest integer to 4a/R (0 <= a < R)
+constexpr int turn_quarter(int a, int R) { return (8 * a + R) / (2 * R); }
+constexpr double turn_rest(int a, int R) { return kHalfPi * (double)(4 * a - turn_quarter(a, R) * R) / (double)R; }
+constexpr double cos_turn(int a, int R) {
+  const int q = turn_quarter(a, R) & 3;
+  const double x = turn_rest(a, R);
+  return q == 0 ? taylor_cos(x) : q == 1 ? -taylor_sin(x) : q == 2 ? -taylor_cos(x) : taylor_sin(x);
+}
+constexpr double sin_turn(int a, int R) {
+  const int q = turn_quarter(a, R) & 3;
+  const double x = turn_rest(a, R);
+  return q == 0 ? taylor_sin(x) : q == 1 ? taylor_cos(x) : q == 2 ? -taylor_sin(x) : -taylor_cos(x);
+}
 
 // v * exp(-/+ 2 pi i K / R) (forward: minus, INV: plus), K, R compile-time.
 template <int R, int K, bool INV>
 __device__ __forceinline__ float2 twiddle_const(float2 v) {
-  constexpr int a = ((K * (32 / R)) % 32 + 32) % 32;  // angle in units of 2 pi / 32
+  constexpr int a = ((K % R) + R) % R;
   if constexpr (a == 0) {
     return v;
-  } else if constexpr (a == 16) {
+  } else if constexpr (2 * a == R) {
     return make_float2(-v.x, -v.y);
-  } else if constexpr (a == 8) {
+  } else if constexpr (4 * a == R) {
     // forward: * (-i); inverse: * (+i)
     return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
-  } else if constexpr (a == 24) {
+  } else if constexpr (4 * a == 3 * R) {
     return INV ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
   } else {
-    constexpr float c = (float)Cos32::v[a];
-    constexpr float s = (float)Cos32::v[(a + 24) % 32];  // sin(2 pi a/32) = cos(2 pi (a-8)/32)
+    constexpr float c = (float)cos_turn(a, R);
+    constexpr float s = (float)sin_turn(a, R);
     // forward: (c - i s); inverse: (c + i s)
     if constexpr (INV) {
       return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
@@ -91,7 +127,31 @@ __device__ __forceinline__ void butterflies(float2* v, const float2* e, const fl
   }
 }
 
-// In-register DFT of length R (power of two <= 32), natural order in and out.
+// DFT-3 of (a, b, c): x0 = a + b + c, x1 = a + w b + w^2 c,
+// x2 = a + w^2 b + w c, w = exp(-/+ 2 pi i / 3).
+template <bool INV>
+__device__ __forceinline__ void bfly3(float2 a, float2 b, float2 c, float2& x0, float2& x1, float2& x2) {
+  constexpr float h = 0.86602540378443864676f;  // sqrt(3) / 2
+  const float2 s = cadd(b, c);
+  const float2 t = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
+  const float2 d = make_float2(h * (b.x - c.x), h * (b.y - c.y));
+  x0 = cadd(a, s);
+  // forward: x1 = t - i d, x2 = t + i d; inverse: the other way round
+  const float2 m = make_float2(t.x + d.y, t.y - d.x), p = make_float2(t.x - d.y, t.y + d.x);
+  x1 = INV ? p : m;
+  x2 = INV ? m : p;
+}
+
+template <int R, int K, bool INV>
+__device__ __forceinline__ void radix3_combine(float2* v, const float2* s0, const float2* s1, const float2* s2) {
+  if constexpr (K < R / 3) {
+    bfly3<INV>(s0[K], twiddle_const<R, K, INV>(s1[K]), twiddle_const<R, 2 * K, INV>(s2[K]), v[K], v[K + R / 3],
+               v[K + 2 * R / 3]);
+    radix3_combine<R, K + 1, INV>(v, s0, s1, s2);
+  }
+}
+
+// In-register DFT of length R (2^k <= 32 or 3 * 2^k), natural order in and out.
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 1) {
@@ -100,6 +160,20 @@ __device__ __forceinline__ void dft(float2* v) {
     const float2 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
+  } else if constexpr (R == 3) {
+    bfly3<INV>(v[0], v[1], v[2], v[0], v[1], v[2]);
+  } else if constexpr (R % 3 == 0) {
+    float2 s0[R / 3], s1[R / 3], s2[R / 3];
+#pragma unroll
+    for (int i = 0; i < R / 3; ++i) {
+      s0[i] = v[3 * i];
+      s1[i] = v[3 * i + 1];
+      s2[i] = v[3 * i + 2];
+    }
+    dft<R / 3, INV>(s0);
+    dft<R / 3, INV>(s1);
+    dft<R / 3, INV>(s2);
+    radix3_combine<R, 0, INV>(v, s0, s1, s2);
   } else {
     float2 e[R / 2], o[R / 2];
 #pragma unroll
@@ -113,17 +187,25 @@ __device__ __forceinline__ void dft(float2* v) {
   }
 }
 
-// Static description of the two-stage line FFT of length N.
+// Static description of the line FFT of length N.
 template <int N>
 struct LineFFT {
-  static_assert(N >= 64 && N <= 1024 && (N & (N - 1)) == 0, "line length must be a power of two in [64, 1024]");
-  static constexpr int E = (N >= 512) ? 32 : (N >= 128 ? 16 : 8);  // elements per lane (radix of stage 0)
-  static constexpr int LANES = N / E;                               // lanes per line (radix of stage 1)
-  static constexpr int LPW = 32 / LANES;                            // lines per warp
-  static constexpr int BPL = E / LANES;                             // stage-1 butterflies per lane
-  static constexpr int PAD_LINE = N + N / E;                        // padded shared slots per line
-  static constexpr int WARP_SLOTS = LPW * PAD_LINE;                 // shared float2 per warp
-  static constexpr int TW = LANES * E;                              // twiddle table entries (= N)
+  static constexpr bool MIXED = (N == 768);
+  static_assert(MIXED || (N >= 64 && N <= 1024 && (N & (N - 1)) == 0),
+                "line length must be a power of two in [64, 1024] or 768");
+  static constexpr int E = MIXED ? 24 : (N >= 512) ? 32 : (N >= 128 ? 16 : 8);  // elements per lane (stage-0 radix)
+  static constexpr int LANES = N / E;                                            // lanes per line
+  static constexpr int LPW = 32 / LANES;                                         // lines per warp
+  static constexpr int RL = MIXED ? 4 : LANES;                                   // radix of the last stage
+  static constexpr int NBL = N / RL;                                             // last-stage butterflies per line
+  static constexpr int BPL = NBL / LANES;                                        // ... per lane
+  static constexpr int RM = MIXED ? 8 : 1;                                       // radix of the middle stage
+  static constexpr int BPM = MIXED ? N / (RM * LANES) : 0;                       // middle butterflies per lane
+  static constexpr int TW_MID = MIXED ? E * RM : 0;                              // middle twiddle entries
+  static constexpr int TW = N + TW_MID;                                          // twiddle table entries
+  static constexpr int PAD_LINE = N + N / E;                                     // padded shared slots per line
+  static constexpr int WARP_SLOTS = LPW * PAD_LINE;                              // shared float2 per warp
+  static_assert(LANES * LPW == 32 && NBL % LANES == 0 && E * RM * RL == N, "line layout");
   __device__ __forceinline__ static int pad(int a) { return a + a / E; }
 };
 
@@ -135,26 +217,68 @@ __device__ __forceinline__ void stage0_to_smem(float2 (&v)[LineFFT<N>::E], float
   using F = LineFFT<N>;
   constexpr int E = F::E;
   dft<E, INV>(v);
+  float2* o = lb + j * (E + 1);  // pad(j E + r) = j (E + 1) + r
 #pragma unroll
-  for (int r = 0; r < E; ++r) lb[F::pad(j * E + r)] = v[r];
+  for (int r = 0; r < E; ++r) o[r] = v[r];
 }
 
-// Stage 1 butterfly j (0 <= j < E) of a line whose stage-0 output is in
-// `lb`: inputs lb[pad(j + r E)], twiddles w_N^{r j}, DFT-LANES; on return
-// w[r] = X[j + r E], r < LANES.
+// Middle stage (N = 768 only; no-op otherwise), in place in the line buffer
+// `lb` of the calling lanes' line, li the lane index inside the line; the
+// middle twiddles start at tw + N.  Contains __syncwarp(); all 32 lanes must
+// call it together, after stage 0 of their line is in `lb`.
 template <int N, bool INV>
-__device__ __forceinline__ void stage1_from_smem(float2 (&w)[LineFFT<N>::LANES], const float2* lb,
+__device__ __forceinline__ void mid_stage(float2* lb, const float2* __restrict__ tw, int li) {
+  using F = LineFFT<N>;
+  if constexpr (F::MIXED) {
+    constexpr int E = F::E, RM = F::RM, BPM = F::BPM, LANES = F::LANES, S = N / RM;
+    static_assert(S % E == 0, "middle-stage stride");
+    constexpr int SP = S + S / E;  // pad(a + r S) = pad(a) + r SP
+    const float2* twm = tw + N;
+    __syncwarp();
+    float2 x[BPM][RM];
+#pragma unroll
+    for (int q = 0; q < BPM; ++q) {
+      const int j = li + LANES * q, k = j % E;
+      const float2* in = lb + F::pad(j);
+#pragma unroll
+      for (int r = 0; r < RM; ++r) x[q][r] = in[r * SP];
+#pragma unroll
+      for (int r = 1; r < RM; ++r) {
+        const float2 t = twm[r * k];
+        x[q][r] = INV ? cmulc(x[q][r], t) : cmul(x[q][r], t);
+      }
+      dft<RM, INV>(x[q]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < BPM; ++q) {
+      const int j = li + LANES * q, k = j % E;
+      float2* out = lb + (j / E) * (E + 1) * RM + k;  // pad((j/E) E RM + k + r E)
+#pragma unroll
+      for (int r = 0; r < RM; ++r) out[r * (E + 1)] = x[q][r];
+    }
+  }
+}
+
+// Last-stage butterfly j (0 <= j < NBL) of a line whose previous stages are
+// in `lb`: inputs lb[pad(j + r NBL)], twiddles w_N^{r j}, DFT-RL; on return
+// w[r] = X[j + r NBL], r < RL.
+template <int N, bool INV>
+__device__ __forceinline__ void stage1_from_smem(float2 (&w)[LineFFT<N>::RL], const float2* lb,
                                                  const float2* __restrict__ tw, int j) {
   using F = LineFFT<N>;
-  constexpr int E = F::E, LANES = F::LANES;
+  constexpr int NBL = F::NBL, RL = F::RL;
+  static_assert(NBL % F::E == 0, "last-stage stride");
+  constexpr int SP = NBL + NBL / F::E;  // pad(j + r NBL) = pad(j) + r SP
+  const float2* in = lb + F::pad(j);
 #pragma unroll
-  for (int r = 0; r < LANES; ++r) w[r] = lb[F::pad(j + r * E)];
+  for (int r = 0; r < RL; ++r) w[r] = in[r * SP];
 #pragma unroll
-  for (int r = 1; r < LANES; ++r) {
-    const float2 t = tw[r * E + j];
+  for (int r = 1; r < RL; ++r) {
+    const float2 t = tw[r * NBL + j];
     w[r] = INV ? cmulc(w[r], t) : cmul(w[r], t);
   }
-  dft<LANES, INV>(w);
+  dft<RL, INV>(w);
 }
 
 // Transform one line in place.  v[m] = x[li + LANES*m] on entry and
@@ -166,17 +290,18 @@ template <int N, bool INV>
 __device__ __forceinline__ void fft_line(float2 (&v)[LineFFT<N>::E], float2* buf, const float2* __restrict__ tw,
                                          int li, int line) {
   using F = LineFFT<N>;
-  constexpr int LANES = F::LANES, BPL = F::BPL;
+  constexpr int LANES = F::LANES, BPL = F::BPL, RL = F::RL;
   float2* lb = buf + line * F::PAD_LINE;
   stage0_to_smem<N, INV>(v, lb, li);
+  mid_stage<N, INV>(lb, tw, li);
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < BPL; ++q) {
-    float2 w[LANES];
+    float2 w[RL];
     stage1_from_smem<N, INV>(w, lb, tw, li + LANES * q);
-    // outputs X[j + r E] = X[li + LANES (q + BPL r)]
+    // outputs X[j + r NBL] = X[li + LANES (q + BPL r)]
 #pragma unroll
-    for (int r = 0; r < LANES; ++r) v[q + BPL * r] = w[r];
+    for (int r = 0; r < RL; ++r) v[q + BPL * r] = w[r];
   }
   __syncwarp();
 }

@@ -83,6 +83,7 @@ bool pick_kernels(int nx, int ny, Kernels* k) {
   VOFL_CASE(128, 128)
   VOFL_CASE(256, 256)
   VOFL_CASE(512, 512)
+  VOFL_CASE(768, 768)
   VOFL_CASE(1024, 1024)
   VOFL_CASE(256, 128)
   VOFL_CASE(128, 256)
@@ -194,6 +195,25 @@ struct Fused2D : Engine {
 
   size_t bytes() const override { return nbytes; }
 
+  bool batch_desc(const vofl_ctx* c, BatchSim* d) const override {
+    (void)c;
+    if (p.G != 6) return false;  // the batched launches use 6 terms per group
+    d->T = p.T;
+    d->Uh = p.Uh;
+    d->Z = p.Z;
+    d->part = p.part;
+    d->P = p.P;
+    d->Lg = p.Lg;
+    d->twx = p.twx;
+    d->twy = p.twy;
+    d->ryy = p.ryy;
+    d->inv_lambda = p.inv_lambda;
+    d->zslot = p.zslot;
+    d->pT = p.pT;
+    d->pZ = p.pZ;
+    return true;
+  }
+
   int alloc(vofl_ctx* c, void** ptr, size_t b) {
     cudaError_t e = cudaMalloc(ptr, b);
     if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (fused 2D scratch)");
@@ -218,11 +238,11 @@ struct Fused2D : Engine {
     if ((st = alloc(c, (void**)&p.part, sizeof(float) * 2 * nx * ny))) return st;
     if ((st = alloc(c, (void**)&p.P, sizeof(float) * 2 * nc * ny))) return st;
     if ((st = alloc(c, (void**)&p.Lg, sizeof(float) * nc * ny))) return st;
-    if ((st = alloc(c, (void**)&p.twx, sizeof(float2) * nx))) return st;
-    if ((st = alloc(c, (void**)&p.twy, sizeof(float2) * ny))) return st;
+    if ((st = alloc(c, (void**)&p.twx, sizeof(float2) * line_twiddle_entries(p.nx)))) return st;
+    if ((st = alloc(c, (void**)&p.twy, sizeof(float2) * line_twiddle_entries(p.ny)))) return st;
     if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
-    if (make_line_twiddles(p.nx, line_e(p.nx), p.nx / line_e(p.nx), p.twx, c->stream) ||
-        make_line_twiddles(p.ny, line_e(p.ny), p.ny / line_e(p.ny), p.twy, c->stream))
+    if (make_line_twiddles(p.nx, p.twx, c->stream) ||
+        make_line_twiddles(p.ny, p.twy, c->stream))
       return cuda_err(c, cudaGetLastError(), "twiddles");
     p.delta = (const float*)c->delta;
     p.step_ctr = c->d_step;
@@ -353,7 +373,7 @@ bool fused2d_supported(int ndim, const int64_t* n, int prec) {
 size_t fused2d_footprint(const int64_t* n, int M) {
   const size_t nx = n[0], ny = n[1], nc = nx / 2 + 1, p = (nc + 7) / 8 * 8;
   const size_t G = std::min(6, M + 1);
-  return sizeof(float2) * (ny * p + nc * ny + ny * p * 2 * G + nx + ny) + sizeof(float) * (2 * nx * ny + 3 * nc * ny);
+  return sizeof(float2) * (ny * p + nc * ny + ny * p * 2 * G + line_twiddle_entries((int)nx) + line_twiddle_entries((int)ny)) + sizeof(float) * (2 * nx * ny + 3 * nc * ny);
 }
 
 Engine* make_fused2d(vofl_ctx* c, int* status) {
@@ -412,8 +432,8 @@ NoAllocLayout noalloc_layout(int nx, int ny, int G) {
   L.part = take(sizeof(float) * 2 * N);
   L.P = take(sizeof(float) * 2 * ncols * ny);
   L.Lg = take(sizeof(float) * ncols * ny);
-  L.twx = take(sizeof(float2) * nx);
-  L.twy = take(sizeof(float2) * ny);
+  L.twx = take(sizeof(float2) * line_twiddle_entries(nx));
+  L.twy = take(sizeof(float2) * line_twiddle_entries(ny));
   L.step = take(sizeof(int) * 4);
   L.total = off;
   return L;
@@ -513,8 +533,8 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + m.gamma0, 0.5 + m.gamma0, std::ldexp(1.0, e2), (double)p.ryy, p.P,
                           p.Lg, s))
     return VOFL_ECUDA;
-  if (make_line_twiddles(nx, line_e(nx), nx / line_e(nx), p.twx, s) ||
-      make_line_twiddles(ny, line_e(ny), ny / line_e(ny), p.twy, s))
+  if (make_line_twiddles(nx, p.twx, s) ||
+      make_line_twiddles(ny, p.twy, s))
     return VOFL_ECUDA;
   EpiArgs<float> epi{};
   epi.mode = EPI_APPLY;

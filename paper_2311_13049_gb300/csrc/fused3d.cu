@@ -167,13 +167,13 @@ struct Fused3D : Engine {
     if ((st = alloc(c, (void**)&part, sizeof(float) * 2 * N))) return st;
     if ((st = alloc(c, (void**)&P, sizeof(float) * 2 * (size_t)c3 * nz))) return st;
     if ((st = alloc(c, (void**)&Lg, sizeof(float) * (size_t)c3 * nz))) return st;
-    if ((st = alloc(c, (void**)&twx, sizeof(float2) * nx))) return st;
-    if ((st = alloc(c, (void**)&twy, sizeof(float2) * ny))) return st;
-    if ((st = alloc(c, (void**)&twz, sizeof(float2) * nz))) return st;
+    if ((st = alloc(c, (void**)&twx, sizeof(float2) * line_twiddle_entries(nx)))) return st;
+    if ((st = alloc(c, (void**)&twy, sizeof(float2) * line_twiddle_entries(ny)))) return st;
+    if ((st = alloc(c, (void**)&twz, sizeof(float2) * line_twiddle_entries(nz)))) return st;
     if (set_smem3(k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused 3D kernels");
-    if (make_line_twiddles(nx, line_e(nx), nx / line_e(nx), twx, c->stream) ||
-        make_line_twiddles(ny, line_e(ny), ny / line_e(ny), twy, c->stream) ||
-        make_line_twiddles(nz, line_e(nz), nz / line_e(nz), twz, c->stream))
+    if (make_line_twiddles(nx, twx, c->stream) ||
+        make_line_twiddles(ny, twy, c->stream) ||
+        make_line_twiddles(nz, twz, c->stream))
       return cuda_err(c, cudaGetLastError(), "twiddles");
     return VOFL_OK;
   }

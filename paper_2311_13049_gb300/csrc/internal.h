@@ -16,6 +16,7 @@ inline void count_launch(uint64_t n = 1) { g_kernel_launches.fetch_add(n, std::m
 
 struct Engine;
 
+
 // Epilogue of the last inverse pass: what to do with L1 u, L2 u at a point.
 enum EpiMode { EPI_PARTIAL = 0, EPI_APPLY = 1, EPI_STEP = 2, EPI_START = 3 };
 
@@ -64,6 +65,28 @@ __device__ __forceinline__ void epilogue_point(const EpiArgs<T>& e, long long id
   e.l2p[idx] = L2;
 }
 
+// One simulation of a batch, as the batched 2D kernels see it (device copy):
+// every buffer belongs to the simulation's own context.
+struct BatchSim {
+  EpiArgs<float> epi;   // state buffers, coefficients, dt, source, step counter, mode
+  const float* delta;   // gamma - gamma0
+  float2* T;            // row half spectra
+  float2* Uh;           // column spectra
+  float2* Z;            // one group of per-term transforms
+  float* part;          // two partial-sum fields
+  const float* P;       // multipliers of both operators
+  const float* Lg;      // ln |mu|^2
+  const float2* twx;    // line twiddles along x
+  const float2* twy;    // ... along y
+  int* err;             // device error word
+  float ryy;            // (h_x / h_y)^2
+  float inv_lambda;     // 1 / (operator-2 balance factor)
+  long long zslot;      // Z slot stride (float2)
+  int pT, pZ;           // row pitches of T and Z (float2)
+  int M;                // top Taylor power
+  int inc_step;         // 1: advance the step counter in this step
+};
+
 }  // namespace vofl
 
 struct vofl_ctx {
@@ -104,6 +127,7 @@ struct vofl_ctx {
   int64_t src_cap = 0;
 
   vofl::Engine* eng = nullptr;
+  struct vofl_batch* batch = nullptr;  // set while a batch steps this context
 
   // captured one-step graphs (index = cur buffer at the start of the step)
   cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
@@ -142,6 +166,13 @@ struct Engine {
     return 0;
   }
   virtual size_t bytes() const = 0;
+  // Fill the engine-owned part of a batch descriptor (buffers, tables,
+  // pitches); false if this engine cannot take part in a 2D batch.
+  virtual bool batch_desc(const vofl_ctx* c, BatchSim* d) const {
+    (void)c;
+    (void)d;
+    return false;
+  }
   // engines that advance many steps in one launch (the first step with
   // first_mode: EPI_START or EPI_STEP); the context's cur/steps are updated
   // by the caller
@@ -165,12 +196,39 @@ size_t fused2d_footprint(const int64_t* n, int M);
 size_t plain_footprint(int ndim, const int64_t* n, int prec);
 bool fused2d_supported(int ndim, const int64_t* n, int prec);
 
+// run set-up shared by vofl_step and batches (capi.cu)
+int prepare_run(vofl_ctx* c, double dt);
+// take a context out of the batch that steps it (waits for the batch's
+// queued work); used when the context is destroyed (batch2d.cu)
+void batch_detach(vofl_ctx* c);
+
 // model precompute (model.cu)
 int model_from_gamma(vofl_ctx* c, const double* d_gamma, const double* d_c0field, double c0, double omega0);
 int model_gamma_from_q(vofl_ctx* c, const double* d_q, double* d_gamma);
+int model_suggest_dt(vofl_ctx* c, double courant, double* dt);
 
 // twiddles / tables (model.cu)
-int make_line_twiddles(int N, int E, int LANES, float2* d_tw, cudaStream_t s);
+// Twiddle layout of the warp line FFT of length N (fft_warp.cuh): the last
+// stage has radix R over NB butterflies (table of NB * R = N entries), and
+// N = 768 adds a middle stage whose NM = 192 twiddles follow.
+inline void line_twiddle_layout(int N, int* NB, int* R, int* NM) {
+  if (N == 768) {
+    *NB = 192;
+    *R = 4;
+    *NM = 192;
+  } else {
+    const int e = N >= 512 ? 32 : (N >= 128 ? 16 : 8);
+    *NB = e;
+    *R = N / e;
+    *NM = 0;
+  }
+}
+inline int line_twiddle_entries(int N) {
+  int nb, r, nm;
+  line_twiddle_layout(N, &nb, &r, &nm);
+  return nb * r + nm;
+}
+int make_line_twiddles(int N, float2* d_tw, cudaStream_t s);
 int make_fused2d_tables(int nx, int ny, double lx, double ly, double s01, double s02, double scale2, double ryy,
                         float* P, float* Lg, cudaStream_t s);
 template <typename T>

@@ -39,25 +39,24 @@ constexpr size_t exch_smem() {
 // F1: forward FFT along x of two rows at once, split into half spectra.
 // -------------------------------------------------------------------------
 template <int NX>
-__global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __restrict__ u, float2* __restrict__ T,
-                                                             int ny, int nz, int pT, float ryy, float rzz,
-                                                             const float2* __restrict__ twx, int* step_ctr,
-                                                             int inc_step) {
+__device__ __forceinline__ void fwd_rows_body(int bx, const float* __restrict__ u, float2* __restrict__ T, int ny,
+                                              int nz, int pT, float ryy, float rzz, const float2* __restrict__ twx,
+                                              int* step_ctr, int inc_step) {
   using F = LineFFT<NX>;
   constexpr int E = F::E, LANES = F::LANES, H = NX / 2, THREADS = W_FROWS * 32;
-  __shared__ float2 s_tw[NX];
+  __shared__ float2 s_tw[F::TW];
   extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
   __syncthreads();
   pdl_wait();  // u is written by the previous step's last kernel
   pdl_trigger();
-  if (inc_step && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
+  if (inc_step && bx == 0 && threadIdx.x == 0) *step_ctr += 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   float2* wbuf = s_buf + warp * warp_stride<NX>();
   // rows are flattened over planes: row = z * ny + y (nz = 1 in 2D); a
   // pair of rows never straddles two planes (ny is even)
-  const int pair = (blockIdx.x * W_FROWS + warp) * F::LPW + line;
+  const int pair = (bx * W_FROWS + warp) * F::LPW + line;
   const bool active = pair < (ny / 2) * nz;
   const int r0i = 2 * (active ? pair : 0);
   const int yy = r0i % ny, zz = r0i / ny;
@@ -80,7 +79,7 @@ __global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __rest
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int x = li + LANES * m;
-    const int xm = (x - 1) & (NX - 1), xp = (x + 1) & (NX - 1);
+    const int xm = x == 0 ? NX - 1 : x - 1, xp = x + 1 == NX ? 0 : x + 1;
     const float a = __ldg(r0 + x), b = __ldg(r1 + x);
     const float dxa = (__ldg(r0 + xp) - a) - (a - __ldg(r0 + xm));
     const float dxb = (__ldg(r1 + xp) - b) - (b - __ldg(r1 + xm));
@@ -104,13 +103,21 @@ __global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __rest
   float2* t1 = t0 + pT;
   for (int k = li; k <= H; k += LANES) {
     const float2 a = lb[F::pad(k)];
-    const float2 b = lb[F::pad((NX - k) & (NX - 1))];
+    const float2 b = lb[F::pad(k == 0 ? 0 : NX - k)];
     // A = (X_k + conj X_{-k})/2 (row y0), B = (X_k - conj X_{-k})/(2i) (row y0+1)
     if (active) {
       t0[k] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
       t1[k] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
     }
   }
+}
+
+template <int NX>
+__global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __restrict__ u, float2* __restrict__ T,
+                                                             int ny, int nz, int pT, float ryy, float rzz,
+                                                             const float2* __restrict__ twx, int* step_ctr,
+                                                             int inc_step) {
+  fwd_rows_body<NX>(blockIdx.x, u, T, ny, nz, pT, ryy, rzz, twx, step_ctr, inc_step);
 }
 
 // -------------------------------------------------------------------------
@@ -122,21 +129,17 @@ __global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __rest
 // over independent planes (strides in_plane, out_plane).
 // -------------------------------------------------------------------------
 template <int NY>
-__global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __restrict__ T, int pT,
-                                                             float2* __restrict__ Uh, int ncols,
-                                                             const float2* __restrict__ twy, long long in_plane,
-                                                             long long out_plane) {
+__device__ __forceinline__ void fwd_cols_body(int bx, const float2* __restrict__ T, int pT, float2* __restrict__ Uh,
+                                              int ncols, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
   constexpr int THREADS = W_FCOLS * 32, CW = W_FCOLS * LPW;  // columns per CTA
-  __shared__ float2 s_tw[NY];
+  __shared__ float2 s_tw[F::TW];
   extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   pdl_wait();  // T is written by k2d_fwd_rows
   pdl_trigger();
-  T += blockIdx.y * in_plane;  // independent planes of a batch (3D: one per z)
-  Uh += blockIdx.y * out_plane;
-  const int c0 = blockIdx.x * CW;
+  const int c0 = bx * CW;
   {
     // cooperative stage 0: one radix-E butterfly per thread
     const int cc = threadIdx.x % CW, j = threadIdx.x / CW;
@@ -150,18 +153,29 @@ __global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __res
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
-  const float2* lb = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
+  float2* lb = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
+  mid_stage<NY, false>(lb, s_tw, li);
+  __syncwarp();
   const int c = c0 + warp * LPW + line;
   if (c < ncols) {
     float2* dst = Uh + (size_t)c * NY;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
-      float2 w[LANES];
+      float2 w[F::RL];
       stage1_from_smem<NY, false>(w, lb, s_tw, li + LANES * q);
 #pragma unroll
-      for (int r = 0; r < LANES; ++r) dst[li + LANES * (q + BPL * r)] = w[r];
+      for (int r = 0; r < F::RL; ++r) dst[li + LANES * (q + BPL * r)] = w[r];
     }
   }
+}
+
+template <int NY>
+__global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __restrict__ T, int pT,
+                                                             float2* __restrict__ Uh, int ncols,
+                                                             const float2* __restrict__ twy, long long in_plane,
+                                                             long long out_plane) {
+  // blockIdx.y: independent planes (3D: one per z)
+  fwd_cols_body<NY>(blockIdx.x, T + blockIdx.y * in_plane, pT, Uh + blockIdx.y * out_plane, ncols, twy);
 }
 
 // -------------------------------------------------------------------------
@@ -179,22 +193,21 @@ constexpr size_t inv_cols_smem() {
 }
 
 template <int NY>
-__global__ void __launch_bounds__(W_INV * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
-                                                           const float* __restrict__ Lg, float2* __restrict__ Z,
-                                                           long long zslot, int pZ, int ncols, int m_lo, int m_hi,
-                                                           float inv_fact_lo, const float2* __restrict__ twy) {
+__device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __restrict__ Uh,
+                                              const float* __restrict__ P, const float* __restrict__ Lg,
+                                              float2* __restrict__ Z, long long zslot, int pZ, int ncols, int m_lo,
+                                              int m_hi, float inv_fact_lo, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
   constexpr int THREADS = W_INV * 32, CW = W_INV * LPW;  // columns per CTA
-  __shared__ float2 s_tw[NY];
+  __shared__ float2 s_tw[F::TW];
   extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
-  const int op = blockIdx.y;
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   float2* lb_own = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
   float* s_lg = reinterpret_cast<float*>(s_buf + W_INV * warp_stride<NY>()) + (size_t)(warp * LPW + line) * NY;
-  const int c0 = blockIdx.x * CW;
+  const int c0 = bx * CW;
   const int c = c0 + warp * LPW + line;
   const int cc = min(c, ncols - 1);
   const long long tot = (long long)ncols * NY;
@@ -216,29 +229,25 @@ __global__ void __launch_bounds__(W_INV * 32) k2d_inv_cols(const float2* __restr
   float2 uh[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) uh[m] = uh_col[li + LANES * m];
-  // cooperative stage-1 assignment of this thread
-  int sc[BPL], sj[BPL];
-#pragma unroll
-  for (int q = 0; q < BPL; ++q) {
-    const int b = threadIdx.x + THREADS * q;
-    sc[q] = b % CW;
-    sj[q] = b / CW;
-  }
   for (int mt = m_lo; mt < m_hi; ++mt) {
     float2 x[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) x[m] = cscale(uh[m], tm[m]);
     stage0_to_smem<NY, true>(x, lb_own, li);
+    mid_stage<NY, true>(lb_own, s_tw, li);
     __syncthreads();
     float2* zb = Z + (long long)((mt - m_lo) * 2 + op) * zslot + c0;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
-      const float2* lb = s_buf + (sc[q] / LPW) * warp_stride<NY>() + (sc[q] % LPW) * F::PAD_LINE;
-      float2 w[LANES];
-      stage1_from_smem<NY, true>(w, lb, s_tw, sj[q]);
-      if (c0 + sc[q] < ncols) {
+      // cooperative last stage: thread b takes column b % CW, butterfly b / CW
+      const int b = threadIdx.x + THREADS * q;
+      const int sc = b % CW, sj = b / CW;
+      const float2* lb = s_buf + (sc / LPW) * warp_stride<NY>() + (sc % LPW) * F::PAD_LINE;
+      float2 w[F::RL];
+      stage1_from_smem<NY, true>(w, lb, s_tw, sj);
+      if (c0 + sc < ncols) {
 #pragma unroll
-        for (int r = 0; r < LANES; ++r) zb[(size_t)(sj[q] + E * r) * pZ + sc[q]] = w[r];
+        for (int r = 0; r < F::RL; ++r) zb[(size_t)(sj + F::NBL * r) * pZ + sc] = w[r];
       }
     }
     if (mt + 1 < m_hi) {
@@ -248,6 +257,14 @@ __global__ void __launch_bounds__(W_INV * 32) k2d_inv_cols(const float2* __restr
     }
     __syncthreads();  // stage-1 reads done before the next term's stage-0 writes
   }
+}
+
+template <int NY>
+__global__ void __launch_bounds__(W_INV * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
+                                                           const float* __restrict__ Lg, float2* __restrict__ Z,
+                                                           long long zslot, int pZ, int ncols, int m_lo, int m_hi,
+                                                           float inv_fact_lo, const float2* __restrict__ twy) {
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi, inv_fact_lo, twy);
 }
 
 // -------------------------------------------------------------------------
@@ -267,17 +284,16 @@ constexpr size_t inv_rows_smem() {
 }
 
 template <int NX>
-__global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
-                                                           int ny, int m_lo, int m_hi, int top,
-                                                           const float* __restrict__ delta, float* __restrict__ part1,
-                                                           float* __restrict__ part2, EpiArgs<float> epi,
-                                                           float inv_lambda, const float2* __restrict__ twx,
-                                                           int* err) {
+__device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__ Z, long long zslot, int pZ, int ny,
+                                              int m_lo, int m_hi, int top, const float* __restrict__ delta,
+                                              float* __restrict__ part1, float* __restrict__ part2,
+                                              const EpiArgs<float>& epi, float inv_lambda,
+                                              const float2* __restrict__ twx, int* err) {
   using F = LineFFT<NX>;
   constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W_INV * 32;
   constexpr int RB = rows_rb<NX>();
   constexpr uint32_t RB_BYTES = RB * sizeof(float2);
-  __shared__ float2 s_tw[NX];
+  __shared__ float2 s_tw[F::TW];
   __shared__ uint64_t s_bar[W_INV * LPW * 2];
   extern __shared__ float2 s_buf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -290,12 +306,12 @@ __global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restr
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < NX; i += THREADS) s_tw[i] = twx[i];
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
   __syncthreads();
   pdl_wait();  // Z of this group and the previous group's partial sums are ready
   pdl_trigger();
   float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int yr = (blockIdx.x * W_INV + warp) * LPW + line;
+  const int yr = (bx * W_INV + warp) * LPW + line;
   const bool active = yr < ny;
   const int y = active ? yr : 0;
   const size_t row = (size_t)y * NX;
@@ -374,6 +390,16 @@ __global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restr
   }
 }
 
+template <int NX>
+__global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
+                                                           int ny, int m_lo, int m_hi, int top,
+                                                           const float* __restrict__ delta, float* __restrict__ part1,
+                                                           float* __restrict__ part2, EpiArgs<float> epi,
+                                                           float inv_lambda, const float2* __restrict__ twx,
+                                                           int* err) {
+  inv_rows_body<NX>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, delta, part1, part2, epi, inv_lambda, twx, err);
+}
+
 // -------------------------------------------------------------------------
 // 3D y pass: inverse FFT along y of the columns of independent planes
 // (blockIdx.y = plane), no multiplier.  Input plane [H+1][ny] (column-major,
@@ -387,9 +413,9 @@ __global__ void __launch_bounds__(W_INV * 32) k3d_inv_ycols(const float2* __rest
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
   constexpr int THREADS = W_INV * 32, CW = W_INV * LPW;
-  __shared__ float2 s_tw[NY];
+  __shared__ float2 s_tw[F::TW];
   extern __shared__ float2 s_buf[];
-  for (int i = threadIdx.x; i < NY; i += THREADS) s_tw[i] = twy[i];
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   __syncthreads();
   pdl_wait();
   pdl_trigger();
@@ -404,17 +430,18 @@ __global__ void __launch_bounds__(W_INV * 32) k3d_inv_ycols(const float2* __rest
 #pragma unroll
   for (int m = 0; m < E; ++m) x[m] = in[(size_t)cc * NY + li + LANES * m];
   stage0_to_smem<NY, true>(x, lb_own, li);
+  mid_stage<NY, true>(lb_own, s_tw, li);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < BPL; ++q) {
     const int b = threadIdx.x + THREADS * q;
     const int sc = b % CW, sj = b / CW;
     const float2* lb = s_buf + (sc / LPW) * warp_stride<NY>() + (sc % LPW) * F::PAD_LINE;
-    float2 w[LANES];
+    float2 w[F::RL];
     stage1_from_smem<NY, true>(w, lb, s_tw, sj);
     if (c0 + sc < ncols) {
 #pragma unroll
-      for (int r = 0; r < LANES; ++r) out[(size_t)(sj + E * r) * pZ + c0 + sc] = w[r];
+      for (int r = 0; r < F::RL; ++r) out[(size_t)(sj + F::NBL * r) * pZ + c0 + sc] = w[r];
     }
   }
 }
@@ -427,8 +454,6 @@ inline float inv_factorial(int m) {
   for (int i = 2; i <= m; ++i) f *= i;
   return (float)(1.0 / f);
 }
-
-inline int line_e(int n) { return n >= 512 ? 32 : (n >= 128 ? 16 : 8); }
 
 // Launch with programmatic stream serialisation: the kernel may start while
 // its predecessor finishes and synchronises itself with griddepcontrol.wait.

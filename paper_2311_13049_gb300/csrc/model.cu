@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "internal.h"
 
@@ -109,6 +110,20 @@ __global__ void k_tables_fused2d(int nx, int ny, double lx, double ly, double s0
   }
 }
 
+// omega(x) = sqrt|c^2 eta| |mu_max|^{1 + gamma}: the largest angular
+// frequency of the undamped part of Eq. (1.1) at x (the highest Fourier mode
+// |mu_max| of the grid).  Max over the grid as an atomic max of the bit
+// pattern (non-negative doubles order like their bits): order-independent.
+template <typename T>
+__global__ void k_omega_max(const T* __restrict__ A, const double* __restrict__ g, long long n, double lmu,
+                            unsigned long long* out) {
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, sqrt(fabs((double)A[i])) * exp((1.0 + g[i]) * lmu));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 // Tables in the cuFFT R2C layout [..][nz][ny][nx/2+1] (row-major, x halved),
 // for a forward transform of the discrete Laplacian (symbol lambda, see
 // fused2d.cu): P = |mu|^{2 s0} / (N lambda).
@@ -143,14 +158,23 @@ __global__ void k_tables_plain(int nx, int ny, int nz, double lx, double ly, dou
   }
 }
 
-// tw[r*E + k] = exp(-2 pi i r k / N), r < LANES, k < E
-__global__ void k_twiddles(int N, int E, int LANES, float2* tw) {
-  const int total = E * LANES;
+// tw[r*NB + k] = exp(-2 pi i r k / N), r < R, k < NB; then, for N with a
+// middle stage, tw[N + t] = exp(-2 pi i t / NM), t < NM
+__global__ void k_twiddles(int N, int NB, int R, int NM, float2* tw) {
+  const int total = NB * R + NM;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int r = i / E, k = i % E;
-    const long long t = ((long long)r * k) % N;
+    long long t;
+    int n;
+    if (i < NB * R) {
+      const int r = i / NB, k = i % NB;
+      t = ((long long)r * k) % N;
+      n = N;
+    } else {
+      t = i - NB * R;
+      n = NM;
+    }
     double s, c;
-    sincospi(-2.0 * (double)t / (double)N, &s, &c);
+    sincospi(-2.0 * (double)t / (double)n, &s, &c);
     tw[i] = make_float2((float)c, (float)s);
   }
 }
@@ -171,6 +195,34 @@ int cuda_err(vofl_ctx* c, cudaError_t e, const char* where) {
     c->err = std::string(where) + ": " + cudaGetErrorString(e);
   }
   return e == cudaErrorMemoryAllocation ? VOFL_ENOMEM : VOFL_ECUDA;
+}
+
+// dt = courant * 2 / omega_max (the explicit leap-frog bound 2/omega of the
+// undamped part, scaled by a safety factor).
+int model_suggest_dt(vofl_ctx* c, double courant, double* dt) {
+  double mu2 = 0.0;
+  for (int i = 0; i < c->ndim; ++i) {
+    const double m = M_PI * (double)c->n[i] / (c->hi[i] - c->lo[i]);  // Nyquist |mu| along axis i
+    mu2 += m * m;
+  }
+  unsigned long long* d_out = reinterpret_cast<unsigned long long*>(c->d_scratch + RED_BLOCKS + 2);
+  VOFL_CUDA(c, cudaMemsetAsync(d_out, 0, sizeof(unsigned long long), c->stream));
+  const double lmu = 0.5 * std::log(mu2);
+  if (c->prec == VOFL_F32)
+    k_omega_max<float><<<grid_for(c->N, 256), 256, 0, c->stream>>>((const float*)c->A, c->d_gamma, c->N, lmu, d_out);
+  else
+    k_omega_max<double><<<grid_for(c->N, 256), 256, 0, c->stream>>>((const double*)c->A, c->d_gamma, c->N, lmu,
+                                                                     d_out);
+  count_launch();
+  VOFL_CUDA(c, cudaGetLastError());
+  unsigned long long bits = 0;
+  VOFL_CUDA(c, cudaMemcpyAsync(&bits, d_out, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  double wmax;
+  std::memcpy(&wmax, &bits, sizeof(wmax));
+  if (!(wmax > 0.0)) return set_err(c, VOFL_EINVAL, "the model has no positive frequency");
+  *dt = courant * 2.0 / wmax;
+  return VOFL_OK;
 }
 
 int model_gamma_from_q(vofl_ctx* c, const double* d_q, double* d_gamma) {
@@ -214,8 +266,10 @@ int model_from_gamma(vofl_ctx* c, const double* d_gamma, const double* d_c0field
   return VOFL_OK;
 }
 
-int make_line_twiddles(int N, int E, int LANES, float2* d_tw, cudaStream_t s) {
-  k_twiddles<<<grid_for((long long)E * LANES, 256), 256, 0, s>>>(N, E, LANES, d_tw);
+int make_line_twiddles(int N, float2* d_tw, cudaStream_t s) {
+  int nb, r, nm;
+  line_twiddle_layout(N, &nb, &r, &nm);
+  k_twiddles<<<grid_for((long long)nb * r + nm, 256), 256, 0, s>>>(N, nb, r, nm, d_tw);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
 }

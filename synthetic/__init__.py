@@ -188,3 +188,22 @@ def workload_3d_256(nsteps: int = 500, n: int = 256, M: int = 8):
     return dict(shape=shape, Q=q_two_layer_3d(n), c0=1.0, omega0=TWO_PI, M=M,
                 u0=gaussian_pulse(shape, 4.0), v0=np.zeros(shape),
                 nsteps=nsteps, dt=2e-3, src_idx=None, src=None)
+
+
+def workload_batch(n_sims: int = 64, seed: int = 4, nsteps: int = 300, M: int = 12,
+                   sizes=(256, 512, 768, 1024)):
+    """Independent 2D simulations on [-pi,pi)^2: edge lengths drawn uniformly
+    from `sizes` (PCG64(seed)), Q low-passed noise in [5,100] (seeds
+    1000*seed + i), a Ricker source f0 = 10 at a seeded random node (seeds
+    1000*seed + 500 + i), u0 = u_t = 0, M = 12, 300 steps.  The time step is
+    not part of the input: each consumer derives it from the model (a quarter
+    of the leap-frog bound at the fastest point and mode).  Source samples
+    are generated by the consumer once dt is known (ricker_samples)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    edges = rng.choice(np.asarray(sizes), size=n_sims)
+    sims = []
+    for i, n in enumerate(edges):
+        shape = (int(n), int(n))
+        sims.append(dict(shape=shape, Q=q_lowpass(shape, 1000 * seed + i), c0=1.0, omega0=TWO_PI, M=M,
+                         nsteps=nsteps, f0=10.0, src_idx=random_index(shape, 1000 * seed + 500 + i)))
+    return sims

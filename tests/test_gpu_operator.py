@@ -24,7 +24,7 @@ def _case(shape, seed):
     return Q, u
 
 
-@pytest.mark.parametrize("shape", [(64, 64), (128, 128), (256, 256), (512, 512), (1024, 1024),
+@pytest.mark.parametrize("shape", [(64, 64), (128, 128), (256, 256), (512, 512), (768, 768), (1024, 1024),
                                    (128, 256), (256, 128), (64, 512), (512, 64), (256, 1024)])
 def test_fused_apply_matches_oracle_sizes(V, shape):
     Q, u = _case(shape, 7)
@@ -57,6 +57,21 @@ def test_fused_apply_white_noise_and_nyquist(V):
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 8, V.IMPL_FUSED, V.F32)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), 8)
     assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32
+
+
+@pytest.mark.parametrize("impl", ["fused", "plain"])
+def test_radix3_grid_white_noise(V, impl):
+    """768^2 (a factor 3 in every line length): a white field with both
+    Nyquist lines loads every twiddle of the mixed-radix transforms."""
+    shape = (768, 768)
+    Q = S.q_lowpass(shape, 6)
+    u = S.random_field(shape, 10)
+    u += np.cos(np.pi * np.arange(768))[None, :] + 0.5 * np.cos(np.pi * np.arange(768))[:, None]
+    im = V.IMPL_FUSED if impl == "fused" else V.IMPL_PLAIN
+    g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 12, im, V.F32)
+    r1, r2 = O.seismic_operators(uin, gamma_of(Q), 12)
+    assert rel_l2(g1, r1) <= TOL32, rel_l2(g1, r1)
+    assert rel_l2(g2, r2) <= TOL32, rel_l2(g2, r2)
 
 
 def test_fused_apply_non_square_box(V):

@@ -321,3 +321,28 @@ def test_paper_table3_lffp_constant_order_column(golden_dir):
     u = O.general_lffp(s, 1.0, cube, phi, None, 2.0 ** -8, 2 ** 8, 0, lo, hi)
     err = O.l2_error(u, ref, [1.0 / 64])
     assert abs(err - rows[8][0]) <= 0.0006 * rows[8][0], err
+
+
+def test_suggested_dt_gamma_zero_closed_form():
+    """gamma = 0: eta = -1, c = c0, so omega_max = c0 |mu_max| and
+    dt = courant * 2 / (c0 sqrt(sum_i (pi J_i / L_i)^2)); non-square box."""
+    shape = (32, 48)  # (y, x)
+    lo, hi = [0.0, -1.0], [3.0, 2.0]  # x: L = 3, y: L = 3
+    mu = np.sqrt((np.pi * 48 / 3.0) ** 2 + (np.pi * 32 / 3.0) ** 2)
+    dt = O.suggested_dt(np.zeros(shape), 1.7, 2 * np.pi, shape, lo, hi, courant=0.3)
+    assert dt == pytest.approx(0.3 * 2 / (1.7 * mu), rel=1e-14)
+
+
+@pytest.mark.parametrize("courant,stable", [(0.25, True), (0.9, True), (1.1, False)])
+def test_suggested_dt_separates_stable_from_unstable(courant, stable):
+    """The oracle's own stepper on the fastest mode (the Nyquist checkerboard)
+    of a uniform-Q model: bounded at a fraction of the suggested bound,
+    growing beyond it."""
+    shape = (16, 16)
+    gamma = np.full(shape, np.arctan(1 / 20.0) / np.pi)
+    dt = O.suggested_dt(gamma, 1.0, 2 * np.pi, shape, courant=courant)
+    y, x = np.indices(shape)
+    u0 = np.cos(np.pi * x) * np.cos(np.pi * y)
+    u = O.seismic_lffp(gamma, 1.0, 2 * np.pi, u0, None, dt, 400, 0)
+    grew = np.max(np.abs(u)) > 10.0
+    assert grew != stable
