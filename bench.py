@@ -17,7 +17,14 @@ is Mpoint-steps/s = 1024^2 * 1000 * runs / time.
   batch  64 independent 2D simulations of uneven sizes {256, 512, 768,
          1024}^2 (M = 12, 300 steps each, dt a quarter of the leap-frog bound
          of each model) advanced together by one batch (vofl_batch_*),
-         autotuned, timed over the whole 300-step run.
+         autotuned, timed over the whole 300-step run;
+  serve  continuous batching of a Poisson request stream (mean 200 per
+         second, seed 5; 1D 4096 / 2D 512^2 / 2D 1024^2 / 3D 128^3 with equal
+         probability, 100..2000 steps, M 8..16) served in real time:
+         p50/p99 latency from arrival to the answer on the host, and
+         point-steps/s; a bounded prefix of the 600-request stream by
+         default (--serve-requests), with a few answers re-run alone and
+         compared bit for bit.
 
 L2 is flushed (256 MiB write) before every timed run.  Times are CUDA events
 on the context stream.  `--impl reference` times the FP64 CPU oracle on a
@@ -237,6 +244,46 @@ def batch_bench(V, torch, stream, flush):
 
 
 # ---------------------------------------------------------------------------
+# serving: a Poisson request stream through the continuous-batching server
+# ---------------------------------------------------------------------------
+def serve_bench(nreq, check=3):
+    import synthetic as S
+    from paper_2311_13049_gb300 import serve as SV
+
+    def source(sp, dt):
+        return S.ricker_samples(sp["nsteps"], dt, sp["f0"])
+
+    reqs = S.serve_requests(600)[:nreq]
+    per_kind = min(12, nreq)  # contexts allocated at server start-up, per request kind
+    srv = SV.Server(budget_bytes=64 << 30, max_active=48, quantum=50, realtime=True,
+                    prewarm={k: per_kind for k in S.SERVE_KINDS})
+    try:
+        recs, span = srv.run(reqs, S.serve_inputs, source)
+    finally:
+        srv.close()
+    out = SV.summarize(recs, span)
+    # a few answers against the same request run alone (first of each kind)
+    seen, same = set(), []
+    for r, sp in zip(recs, sorted(reqs, key=lambda d: d["arrival"])):
+        if sp["shape"] in seen or len(same) >= check:
+            continue
+        seen.add(sp["shape"])
+        Q, idx = S.serve_inputs(sp)
+        same.append(bool(np.array_equal(r["result"], SV.solo(sp, Q, idx, source))))
+    kinds = {}
+    for sp in reqs:
+        k = "x".join(str(v) for v in sp["shape"])
+        kinds[k] = kinds.get(k, 0) + 1
+    out.update({"sample": f"first {nreq} of the 600-request stream (arrivals over "
+                          f"{reqs[-1]['arrival']:.2f} s)", "mix": kinds,
+                "point_steps": int(sum(r["point_steps"] for r in recs)),
+                "solo_equal": same, "policy": "FIFO admission by free slot (48) and footprint (64 GiB); "
+                                              "square 2D requests batched, 50-step quanta; "
+                                              f"{per_kind} contexts per kind allocated at start-up"})
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -331,6 +378,11 @@ def run_gpu(args):
             ms = float(t.item())
         return ms
 
+    if args.serve_only:
+        res = serve_bench(args.serve_requests)
+        if rank == 0:
+            print(json.dumps({"metric": "serve p50/p99 latency and Mpoint-steps/s", "serve": res}))
+        return 0
     fused = make(V.IMPL_FUSED)
     if args.ncu_steps:
         # short run for profilers: set-up, then ncu_steps leap-frog steps
@@ -399,6 +451,7 @@ def run_gpu(args):
         acc["input"] = "final wavefield of the timed run (FP32), oracle FP64 on the same input"
 
     batch = None if args.skip_batch else batch_bench(V, torch, stream, flush)
+    serve_res = None if args.serve_requests <= 0 else serve_bench(args.serve_requests)
     cpu = cpu_baseline() if (rank == 0 and not args.skip_cpu) else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -413,7 +466,7 @@ def run_gpu(args):
                 "ms_per_lffp_step": lffp_fused,
                 "fused_over_plain": value / plain_value,
                 "accuracy": acc, "gpu_launches": gpu_launches, "roofline": roof,
-                "cpu_baseline": cpu, "clocks": clk, "batch": batch, "serve": None}
+                "cpu_baseline": cpu, "clocks": clk, "batch": batch, "serve": serve_res}
         print(json.dumps(line))
     fused.close()
     plain.close()
@@ -431,6 +484,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-batch", action="store_true", help="omit the 64-simulation batch measurement")
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests of the 600-request serving stream to serve (0: skip)")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--ncu-steps", type=int, default=0,
                     help="profiling mode: set up the workload, run this many leap-frog steps, print nothing")
     args = ap.parse_args()

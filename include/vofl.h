@@ -143,6 +143,12 @@ VOFL_API int vofl_step(vofl_ctx* ctx, int64_t nsteps, double dt);
  * memory. */
 VOFL_API int vofl_get_state(vofl_ctx* ctx, void* u_out, int on_device);
 
+/* Non-blocking completion check: 1 if every piece of work queued on the
+ * context's stream has finished, 0 if some is still running, < 0 on a CUDA
+ * error.  Works on a context held by a batch (its stream then also waits
+ * for the batch's work queued before vofl_batch_remove). */
+VOFL_API int vofl_query(vofl_ctx* ctx);
+
 /* Time step for a run of the current model: dt = courant * 2 / omega_max,
  * omega_max = max_x |c^2 eta|^{1/2} |mu_max|^{1+gamma(x)} with |mu_max| the
  * largest grid wavenumber (sqrt of the sum of (pi n_i / L_i)^2): the
@@ -241,6 +247,10 @@ VOFL_API int vofl_batch_size(const vofl_batch* b);
  * replayed from CUDA graphs captured on first use and after each change of
  * membership or schedule).  Returns VOFL_OK, VOFL_EINVAL or VOFL_ECUDA. */
 VOFL_API int vofl_batch_step(vofl_batch* b, int64_t nsteps);
+
+/* Non-blocking: 1 if the batch's queued steps have finished, 0 if not,
+ * < 0 on a CUDA error. */
+VOFL_API int vofl_batch_query(vofl_batch* b);
 
 /* Kernels one batch step launches under the current membership and
  * schedule (>= 0), or a negative status. */

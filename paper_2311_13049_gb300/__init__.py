@@ -45,6 +45,7 @@ SIGNATURES = {
     "vofl_get_state": (C.c_int, [_vp, _vp, C.c_int]),
     "vofl_steps_taken": (C.c_int64, [_vp]),
     "vofl_suggest_dt": (C.c_int, [_vp, C.c_double, _dp]),
+    "vofl_query": (C.c_int, [_vp]),
     "vofl_sync": (C.c_int, [_vp]),
     "vofl_last_error": (C.c_char_p, [_vp]),
     "vofl_footprint_bytes": (C.c_size_t, [C.c_int, _i64p, C.c_int, C.c_int, C.c_int]),
@@ -62,6 +63,7 @@ SIGNATURES = {
     "vofl_batch_size": (C.c_int, [_vp]),
     "vofl_batch_step": (C.c_int, [_vp, C.c_int64]),
     "vofl_batch_kernels_per_step": (C.c_int64, [_vp]),
+    "vofl_batch_query": (C.c_int, [_vp]),
     "vofl_batch_sync": (C.c_int, [_vp]),
     "vofl_batch_tune": (C.c_int, [_vp, C.c_int, _dp]),
     "vofl_batch_time": (C.c_int, [_vp, C.c_int, _dp]),
@@ -244,6 +246,13 @@ class Solver:
     def sync(self):
         self._check(lib().vofl_sync(self._h))
 
+    def query(self):
+        """True when all queued work of this context has finished (non-blocking)."""
+        rc = lib().vofl_query(self._h)
+        if rc < 0:
+            self._check(rc)
+        return rc == 1
+
     def profile_kernels(self, reps=20):
         names = C.create_string_buffer(1024)
         ms = (C.c_double * 16)()
@@ -291,6 +300,10 @@ class Batch:
 
     def kernels_per_step(self):
         return int(self._check(lib().vofl_batch_kernels_per_step(self._h)))
+
+    def query(self):
+        """True when the batch's queued steps have finished (non-blocking)."""
+        return self._check(lib().vofl_batch_query(self._h)) == 1
 
     def sync(self):
         self._check(lib().vofl_batch_sync(self._h))

@@ -593,6 +593,17 @@ int vofl_batch_step(vofl_batch* b, int64_t nsteps) {
   return run_steps(b, nsteps, false);
 }
 
+int vofl_batch_query(vofl_batch* b) {
+  if (!b) return VOFL_EINVAL;
+  const cudaError_t e = cudaStreamQuery(b->stream);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    return 0;
+  }
+  return bcuda(b, e, "cudaStreamQuery");
+}
+
 int64_t vofl_batch_kernels_per_step(vofl_batch* b) {
   if (!b) return VOFL_EINVAL;
   if (b->mem.empty()) return 0;

@@ -386,6 +386,17 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
   return VOFL_OK;
 }
 
+int vofl_query(vofl_ctx* c) {
+  if (!c) return VOFL_EINVAL;
+  const cudaError_t e = cudaStreamQuery(c->stream);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    return 0;
+  }
+  return cuda_err(c, e, "cudaStreamQuery");
+}
+
 int vofl_suggest_dt(vofl_ctx* c, double courant, double* dt) {
   if (int st = check_ctx(c)) return st;
   if (!dt || !(courant > 0) || !std::isfinite(courant)) return set_err(c, VOFL_EINVAL, "bad courant or dt pointer");

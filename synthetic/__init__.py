@@ -207,3 +207,31 @@ def workload_batch(n_sims: int = 64, seed: int = 4, nsteps: int = 300, M: int = 
         sims.append(dict(shape=shape, Q=q_lowpass(shape, 1000 * seed + i), c0=1.0, omega0=TWO_PI, M=M,
                          nsteps=nsteps, f0=10.0, src_idx=random_index(shape, 1000 * seed + 500 + i)))
     return sims
+
+
+SERVE_KINDS = ((4096,), (512, 512), (1024, 1024), (128, 128, 128))
+
+
+def serve_requests(n_requests: int = 600, seed: int = 5, rate: float = 200.0, kinds=SERVE_KINDS,
+                   steps=(100, 2000), M=(8, 16)):
+    """A request stream: Poisson arrivals (mean `rate` per second, PCG64
+    (seed)), grid shape drawn uniformly from `kinds`, step count uniform in
+    [steps[0], steps[1]], M uniform in [M[0], M[1]].  Each request's model
+    and source node are seeded by its index (Q: low-passed noise in
+    [5, 100], seed 1000*seed + i; Ricker f0 = 10 at a random node, seed
+    1000*seed + 500 + i); generate them with serve_inputs().  Domain
+    [-pi,pi)^d, c0 = 1, omega0 = 2 pi, u0 = u_t = 0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    kind = rng.integers(0, len(kinds), size=n_requests)
+    nst = rng.integers(steps[0], steps[1] + 1, size=n_requests)
+    ms = rng.integers(M[0], M[1] + 1, size=n_requests)
+    t = np.cumsum(gaps) - gaps[0]
+    return [dict(id=i, arrival=float(t[i]), shape=tuple(kinds[kind[i]]), nsteps=int(nst[i]), M=int(ms[i]),
+                 c0=1.0, omega0=TWO_PI, f0=10.0, seed=seed) for i in range(n_requests)]
+
+
+def serve_inputs(req):
+    """Q field and source node of one request of serve_requests()."""
+    i, seed, shape = req["id"], req["seed"], req["shape"]
+    return q_lowpass(shape, 1000 * seed + i), random_index(shape, 1000 * seed + 500 + i)
