@@ -18,6 +18,8 @@ is Mpoint-steps/s = 1024^2 * 1000 * runs / time.
          1024}^2 (M = 12, 300 steps each, dt a quarter of the leap-frog bound
          of each model) advanced together by one batch (vofl_batch_*),
          autotuned, timed over the whole 300-step run;
+  configs  the 1D 256 FP64 (M = 8, 200 steps) and 3D 256^3 FP32 (M = 8,
+         500 steps) runs, fused and plain;
   serve  continuous batching of a Poisson request stream (mean 200 per
          second, seed 5; 1D 4096 / 2D 512^2 / 2D 1024^2 / 3D 128^3 with equal
          probability, 100..2000 steps, M 8..16) served in real time:
@@ -244,6 +246,51 @@ def batch_bench(V, torch, stream, flush):
 
 
 # ---------------------------------------------------------------------------
+# the other two single-run workloads: 1D 256 FP64 and 3D 256^3 FP32
+# ---------------------------------------------------------------------------
+def configs_bench(V, torch, stream, flush, reps=3):
+    import synthetic as S
+
+    def run(w, prec, impl):
+        ty = torch.float32 if prec == V.F32 else torch.float64
+        Q = torch.from_numpy(w["Q"]).cuda()
+        u0 = torch.from_numpy(w["u0"]).to(ty).cuda()
+        s = V.Solver(w["shape"], prec=prec, impl=impl, stream=stream.cuda_stream)
+        s.set_M(w["M"])
+        times = []
+        with torch.cuda.stream(stream):
+            for i in range(reps + 1):  # the first run warms up (tables, graphs)
+                flush.zero_()
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.set_q(Q, w["c0"], w["omega0"])
+                s.set_state(u0)
+                s.step(w["nsteps"], w["dt"])
+                e1.record(stream)
+                e1.synchronize()
+                if i:
+                    times.append(e0.elapsed_time(e1))
+        s.close()
+        ms = statistics.median(times)
+        pts = int(np.prod(w["shape"])) * w["nsteps"]
+        return {"value": pts / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_run": ms}
+
+    out = {}
+    w1 = S.workload_1d_256()
+    f, p = run(w1, V.F64, V.IMPL_FUSED), run(w1, V.F64, V.IMPL_PLAIN)
+    out["1d_256_f64"] = {"workload": "1D 256, FP64, M=8, Q = 20 + 15 sin x, u0 = exp(-20 x^2), dt = 1e-3, "
+                                     "200 steps (one run incl. model set-up)",
+                         "fused": f, "plain": p, "fused_over_plain": f["value"] / p["value"]}
+    w3 = S.workload_3d_256()
+    f, p = run(w3, V.F32, V.IMPL_FUSED), run(w3, V.F32, V.IMPL_PLAIN)
+    out["3d_256_f32"] = {"workload": "3D 256^3, FP32, M=8, two-layer Q (10/80), Gaussian pulse sigma = 4 cells, "
+                                     "dt = 2e-3, 500 steps (one run incl. model set-up)",
+                         "fused": f, "plain": p, "fused_over_plain": f["value"] / p["value"]}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # serving: a Poisson request stream through the continuous-batching server
 # ---------------------------------------------------------------------------
 def serve_bench(nreq, check=3):
@@ -451,6 +498,7 @@ def run_gpu(args):
         acc["input"] = "final wavefield of the timed run (FP32), oracle FP64 on the same input"
 
     batch = None if args.skip_batch else batch_bench(V, torch, stream, flush)
+    configs = None if args.skip_configs else configs_bench(V, torch, stream, flush)
     serve_res = None if args.serve_requests <= 0 else serve_bench(args.serve_requests)
     cpu = cpu_baseline() if (rank == 0 and not args.skip_cpu) else None
     if rank == 0:
@@ -466,7 +514,7 @@ def run_gpu(args):
                 "ms_per_lffp_step": lffp_fused,
                 "fused_over_plain": value / plain_value,
                 "accuracy": acc, "gpu_launches": gpu_launches, "roofline": roof,
-                "cpu_baseline": cpu, "clocks": clk, "batch": batch, "serve": serve_res}
+                "cpu_baseline": cpu, "clocks": clk, "batch": batch, "configs": configs, "serve": serve_res}
         print(json.dumps(line))
     fused.close()
     plain.close()
@@ -484,6 +532,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-batch", action="store_true", help="omit the 64-simulation batch measurement")
+    ap.add_argument("--skip-configs", action="store_true", help="omit the 1D 256 and 3D 256^3 runs")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the 600-request serving stream to serve (0: skip)")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving measurement")

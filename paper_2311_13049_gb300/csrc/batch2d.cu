@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(W_FCOLS * 32) kb_fwd_cols(const BatchSim* __re
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(W_INV * 32) kb_inv_cols(const BatchSim* __restrict__ sims, int g) {
+__global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const BatchSim* __restrict__ sims, int g) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;  // this simulation has fewer groups
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(W_INV * 32) kb_inv_cols(const BatchSim* __rest
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(W_INV * 32) kb_inv_rows(const BatchSim* __restrict__ sims, int g) {
+__global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __restrict__ sims, int g) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;
@@ -100,6 +100,7 @@ struct BKernels {
   void (*ir)(const BatchSim*, int);
   size_t smem_fr, smem_fc, smem_ic, smem_ir;
   int lpw_x, lpw_y;
+  int wic;  // warps per CTA of kb_inv_cols
 };
 
 template <int NX, int NY>
@@ -115,6 +116,7 @@ BKernels bkernels_for() {
   k.smem_ir = inv_rows_smem<NX>();
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
+  k.wic = icols_warps<NY>();
   return k;
 }
 
@@ -332,11 +334,11 @@ cudaError_t enqueue_step(vofl_batch* b, int p) {
       const int cpf = W_FCOLS * cl.k.lpw_y;
       e = launch_pdl(cl.k.fc, dim3((ncols + cpf - 1) / cpf, 1, nz), dim3(W_FCOLS * 32), cl.k.smem_fc, s, dc);
       if (e) return e;
-      const int cpc = W_INV * cl.k.lpw_y, rpi = W_INV * cl.k.lpw_x;
+      const int cpc = cl.k.wic * cl.k.lpw_y, rpi = W_IROWS * cl.k.lpw_x;
       for (int g = Mmax / BG; g >= 0; --g) {
-        e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2, nz), dim3(W_INV * 32), cl.k.smem_ic, s, dc, g);
+        e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2, nz), dim3(cl.k.wic * 32), cl.k.smem_ic, s, dc, g);
         if (e) return e;
-        e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(W_INV * 32), cl.k.smem_ir, s, dc, g);
+        e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(W_IROWS * 32), cl.k.smem_ir, s, dc, g);
         if (e) return e;
       }
     }

@@ -55,6 +55,7 @@ struct Kernels {
                    float, const float2*, int*);
   size_t smem_frows, smem_fcols, smem_icols, smem_irows;
   int lpw_x, lpw_y;
+  int wic;  // warps per CTA of inv_cols
 };
 
 template <int NX, int NY>
@@ -70,6 +71,7 @@ Kernels kernels_for() {
   k.smem_irows = inv_rows_smem<NX>();
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
+  k.wic = icols_warps<NY>();
   return k;
 }
 
@@ -139,21 +141,21 @@ struct Plan2D {
   // optional events: one after every inverse kernel, from ev[3] on
   cudaError_t inverse(cudaStream_t s, int M, const EpiArgs<float>& epi, cudaEvent_t* ev = nullptr) const {
     const int K = groups(M);
-    const int cpc = W_INV * k.lpw_y;
+    const int cpc = k.wic * k.lpw_y;
     const dim3 gic((ncols + cpc - 1) / cpc, 2);
-    const int rpc = W_INV * k.lpw_x;
+    const int rpc = W_IROWS * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
     int e_i = 3;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(M + 1, m_lo + G);
-      cudaError_t e = launch_pdl(k.inv_cols, gic, dim3(W_INV * 32), k.smem_icols, s, (const float2*)Uh,
+      cudaError_t e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, (const float2*)Uh,
                                  (const float*)P, (const float*)Lg, Z, zslot, pZ, ncols, m_lo, m_hi,
                                  inv_factorial(m_lo), (const float2*)twy);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
       EpiArgs<float> ep = epi;
       if (gi > 0) ep.mode = EPI_PARTIAL;
-      e = launch_pdl(k.inv_rows, gir, dim3(W_INV * 32), k.smem_irows, s, (const float2*)Z, zslot, pZ, ny, m_lo, m_hi,
+      e = launch_pdl(k.inv_rows, gir, dim3(W_IROWS * 32), k.smem_irows, s, (const float2*)Z, zslot, pZ, ny, m_lo, m_hi,
                      gi == K - 1 ? 1 : 0, delta, part, part + (size_t)nx * ny, ep, inv_lambda, (const float2*)twx,
                      err);
       if (e) return e;

@@ -39,6 +39,7 @@ struct Kernels3 {
                 const float2*, int*);
   size_t sm_frows, sm_fy, sm_fz, sm_iz, sm_iy, sm_ix;
   int lpw_x, lpw_y, lpw_z;
+  int wiz;  // warps per CTA of inv_z
 };
 
 template <int NX, int NY, int NZ>
@@ -54,11 +55,12 @@ Kernels3 kernels3_for() {
   k.sm_fy = exch_smem<NY, W_FCOLS>();
   k.sm_fz = exch_smem<NZ, W_FCOLS>();
   k.sm_iz = inv_cols_smem<NZ>();
-  k.sm_iy = exch_smem<NY, W_INV>();
+  k.sm_iy = exch_smem<NY, W_YCOLS>();
   k.sm_ix = inv_rows_smem<NX>();
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
   k.lpw_z = LineFFT<NZ>::LPW;
+  k.wiz = icols_warps<NZ>();
   return k;
 }
 
@@ -222,19 +224,19 @@ struct Fused3D : Engine {
     const int rows = ny * nz;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(c->M + 1, m_lo + G);
-      const int cz = W_INV * k.lpw_z;
-      cudaError_t e = launch_pdl(k.inv_z, dim3((c3 + cz - 1) / cz, 2), dim3(W_INV * 32), k.sm_iz, s, (const float2*)U3,
+      const int cz = k.wiz * k.lpw_z;
+      cudaError_t e = launch_pdl(k.inv_z, dim3((c3 + cz - 1) / cz, 2), dim3(k.wiz * 32), k.sm_iz, s, (const float2*)U3,
                                  (const float*)P, (const float*)Lg, Zz, zslot_z, p3, c3, m_lo, m_hi,
                                  inv_factorial(m_lo), (const float2*)twz);
       if (e) return e;
-      const int cy = W_INV * k.lpw_y;
-      e = launch_pdl(k.inv_y, dim3((c2 + cy - 1) / cy, 2 * (m_hi - m_lo) * nz), dim3(W_INV * 32), k.sm_iy, s,
+      const int cy = W_YCOLS * k.lpw_y;
+      e = launch_pdl(k.inv_y, dim3((c2 + cy - 1) / cy, 2 * (m_hi - m_lo) * nz), dim3(W_YCOLS * 32), k.sm_iy, s,
                      (const float2*)Zz, (long long)p3, Zy, (long long)ny * pZ, pZ, c2, (const float2*)twy);
       if (e) return e;
       EpiArgs<float> ep = epi;
       if (gi > 0) ep.mode = EPI_PARTIAL;
-      const int rpc = W_INV * k.lpw_x;
-      e = launch_pdl(k.inv_x, dim3((rows + rpc - 1) / rpc), dim3(W_INV * 32), k.sm_ix, s, (const float2*)Zy, zslot_y,
+      const int rpc = W_IROWS * k.lpw_x;
+      e = launch_pdl(k.inv_x, dim3((rows + rpc - 1) / rpc), dim3(W_IROWS * 32), k.sm_ix, s, (const float2*)Zy, zslot_y,
                      pZ, rows, m_lo, m_hi, gi == K - 1 ? 1 : 0, (const float*)c->delta, part,
                      part + (size_t)nx * ny * nz, ep, inv_lambda, (const float2*)twx, c->d_step + 1);
       if (e) return e;

@@ -18,7 +18,8 @@ namespace {
 // CTA sizes (warps) per kernel
 constexpr int W_FROWS = 2;  // forward rows: small CTAs, 4x more CTAs than SMs at 1024^2
 constexpr int W_FCOLS = 4;  // forward columns: 4 columns -> 32-byte row segments
-constexpr int W_INV = 8;    // inverse kernels
+constexpr int W_YCOLS = 4;  // 3D y-inverse kernel
+constexpr int W_IROWS = 8;  // inverse row kernel
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
@@ -33,6 +34,19 @@ constexpr int warp_stride() {
 template <int N, int W>
 constexpr size_t exch_smem() {
   return (size_t)W * warp_stride<N>() * sizeof(float2);
+}
+
+// The multiplier/inverse column kernel: long lines (E >= 24 elements per
+// lane: one CTA per SM whatever its size) transform two Taylor terms at a
+// time in CTAs of 8 warps; short lines one term at a time in CTAs of 4
+// warps, so that several CTAs share an SM.
+template <int N>
+constexpr bool icols_pair() {
+  return LineFFT<N>::E >= 24;
+}
+template <int N>
+constexpr int icols_warps() {
+  return icols_pair<N>() ? 8 : 4;
 }
 
 // -------------------------------------------------------------------------
@@ -181,15 +195,20 @@ __global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __res
 // -------------------------------------------------------------------------
 // I1: multiplier + inverse FFT along y, for terms [m_lo, m_hi) of one
 // operator (blockIdx.y).  Output Z[s][op][y][c], s = m - m_lo.
-// Each warp keeps its column's spectrum and the multiplier recurrence
-// t_m = P ln|mu|^{2m}/m! in registers (ln|mu|^2 in shared memory) and does
-// stage 0; stage 1 is done cooperatively by the CTA (thread b: column
-// b % CW, butterfly b / CW), so every store writes row segments of CW
-// adjacent columns of Z.
+// Each warp keeps its column's multiplied spectrum
+// v_m = u_hat P ln|mu|^{2m}/m! in registers, advanced term to term by
+// v_{m+1} = v_m ln|mu|^2/(m+1) (ln|mu|^2 in shared memory), and does
+// stage 0 of two terms at a time (two independent register transforms,
+// two exchange-buffer sets, one pair of barriers per two terms); the last
+// stage is done cooperatively by the CTA (thread b: column b % CW,
+// butterfly b / CW), so every store writes row segments of CW adjacent
+// columns of Z.
 // -------------------------------------------------------------------------
 template <int NY>
 constexpr size_t inv_cols_smem() {
-  return exch_smem<NY, W_INV>() + (size_t)W_INV * LineFFT<NY>::LPW * NY * sizeof(float);
+  // two exchange-buffer sets (two terms in flight) + ln|mu|^2 per column
+  constexpr int W = icols_warps<NY>();
+  return (icols_pair<NY>() ? 2 : 1) * exch_smem<NY, W>() + (size_t)W * LineFFT<NY>::LPW * NY * sizeof(float);
 }
 
 template <int NY>
@@ -199,14 +218,16 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
                                               int m_hi, float inv_fact_lo, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
-  constexpr int THREADS = W_INV * 32, CW = W_INV * LPW;  // columns per CTA
+  constexpr int W = icols_warps<NY>(), THREADS = W * 32, CW = W * LPW;  // columns per CTA
+  constexpr bool PAIR = icols_pair<NY>();
+  constexpr int SET = W * warp_stride<NY>();  // float2 slots of one exchange set
   __shared__ float2 s_tw[F::TW];
   extern __shared__ float2 s_buf[];
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
-  float2* lb_own = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
-  float* s_lg = reinterpret_cast<float*>(s_buf + W_INV * warp_stride<NY>()) + (size_t)(warp * LPW + line) * NY;
+  float2* lb_own = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;  // set 0; set 1 at + SET
+  float* s_lg = reinterpret_cast<float*>(s_buf + (PAIR ? 2 : 1) * SET) + (size_t)(warp * LPW + line) * NY;
   const int c0 = bx * CW;
   const int c = c0 + warp * LPW + line;
   const int cc = min(c, ncols - 1);
@@ -226,23 +247,25 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   __syncthreads();
   pdl_wait();  // Uh (k2d_fwd_cols) ready; the previous group's readers of Z are done
   pdl_trigger();
-  float2 uh[E];
+  // v = the multiplied spectrum of the current term: u_hat P ln|mu|^{2m}/m!
+  float2 v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) uh[m] = uh_col[li + LANES * m];
-  for (int mt = m_lo; mt < m_hi; ++mt) {
-    float2 x[E];
+  for (int m = 0; m < E; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
+  // v <- v ln|mu|^2 / (m + 1): the next term
+  auto advance = [&](int mt) {
+    const float rinv = 1.0f / (float)(mt + 1);
 #pragma unroll
-    for (int m = 0; m < E; ++m) x[m] = cscale(uh[m], tm[m]);
-    stage0_to_smem<NY, true>(x, lb_own, li);
-    mid_stage<NY, true>(lb_own, s_tw, li);
-    __syncthreads();
+    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], s_lg[li + LANES * m] * rinv);
+  };
+  // cooperative last stage of exchange set `set` into Z slot (mt - m_lo):
+  // thread b takes column b % CW, butterfly b / CW (row segments of CW columns)
+  auto finish = [&](int set, int mt) {
     float2* zb = Z + (long long)((mt - m_lo) * 2 + op) * zslot + c0;
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
-      // cooperative last stage: thread b takes column b % CW, butterfly b / CW
       const int b = threadIdx.x + THREADS * q;
       const int sc = b % CW, sj = b / CW;
-      const float2* lb = s_buf + (sc / LPW) * warp_stride<NY>() + (sc % LPW) * F::PAD_LINE;
+      const float2* lb = s_buf + set * SET + (sc / LPW) * warp_stride<NY>() + (sc % LPW) * F::PAD_LINE;
       float2 w[F::RL];
       stage1_from_smem<NY, true>(w, lb, s_tw, sj);
       if (c0 + sc < ncols) {
@@ -250,17 +273,55 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
         for (int r = 0; r < F::RL; ++r) zb[(size_t)(sj + F::NBL * r) * pZ + sc] = w[r];
       }
     }
-    if (mt + 1 < m_hi) {
-      const float rinv = 1.0f / (float)(mt + 1);
+  };
+  int mt = m_lo;
+  // two terms per iteration: two independent register transforms in flight
+  for (; PAIR && mt + 1 < m_hi; mt += 2) {
+    float2 xa[E], xb[E];
 #pragma unroll
-      for (int m = 0; m < E; ++m) tm[m] = tm[m] * (s_lg[li + LANES * m] * rinv);
+    for (int m = 0; m < E; ++m) xa[m] = v[m];
+    advance(mt);
+#pragma unroll
+    for (int m = 0; m < E; ++m) xb[m] = v[m];
+    stage0_to_smem<NY, true>(xa, lb_own, li);
+    stage0_to_smem<NY, true>(xb, lb_own + SET, li);
+    mid_stage<NY, true>(lb_own, s_tw, li);
+    mid_stage<NY, true>(lb_own + SET, s_tw, li);
+    __syncthreads();
+    finish(0, mt);
+    finish(1, mt + 1);
+    if (mt + 2 < m_hi) advance(mt + 1);
+    __syncthreads();  // last-stage reads done before the next stage-0 writes
+  }
+  if (PAIR) {
+    if (mt < m_hi) {  // an odd last term
+      float2 x[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) x[m] = v[m];
+      stage0_to_smem<NY, true>(x, lb_own, li);
+      mid_stage<NY, true>(lb_own, s_tw, li);
+      __syncthreads();
+      finish(0, mt);
     }
-    __syncthreads();  // stage-1 reads done before the next term's stage-0 writes
+  } else {
+    // short lines: one term per iteration (a separate loop: sharing it with
+    // the odd last term above made the paired form markedly slower)
+    for (; mt < m_hi; ++mt) {
+      float2 x[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) x[m] = v[m];
+      stage0_to_smem<NY, true>(x, lb_own, li);
+      mid_stage<NY, true>(lb_own, s_tw, li);
+      __syncthreads();
+      finish(0, mt);
+      if (mt + 1 < m_hi) advance(mt);
+      __syncthreads();
+    }
   }
 }
 
 template <int NY>
-__global__ void __launch_bounds__(W_INV * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
+__global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
                                                            const float* __restrict__ Lg, float2* __restrict__ Z,
                                                            long long zslot, int pZ, int ncols, int m_lo, int m_hi,
                                                            float inv_fact_lo, const float2* __restrict__ twy) {
@@ -280,7 +341,7 @@ constexpr int rows_rb() {
 }
 template <int NX>
 constexpr size_t inv_rows_smem() {
-  return exch_smem<NX, W_INV>() + (size_t)W_INV * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
+  return exch_smem<NX, W_IROWS>() + (size_t)W_IROWS * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
 }
 
 template <int NX>
@@ -290,17 +351,17 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
                                               const EpiArgs<float>& epi, float inv_lambda,
                                               const float2* __restrict__ twx, int* err) {
   using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W_INV * 32;
+  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W_IROWS * 32;
   constexpr int RB = rows_rb<NX>();
   constexpr uint32_t RB_BYTES = RB * sizeof(float2);
   __shared__ float2 s_tw[F::TW];
-  __shared__ uint64_t s_bar[W_INV * LPW * 2];
+  __shared__ uint64_t s_bar[W_IROWS * LPW * 2];
   extern __shared__ float2 s_buf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   const int lid = warp * LPW + line;  // line id inside the CTA
   uint64_t* bar = s_bar + 2 * lid;
-  float2* zbuf = s_buf + W_INV * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
+  float2* zbuf = s_buf + W_IROWS * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
   if (li == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -311,7 +372,7 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   pdl_wait();  // Z of this group and the previous group's partial sums are ready
   pdl_trigger();
   float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int yr = (bx * W_INV + warp) * LPW + line;
+  const int yr = (bx * W_IROWS + warp) * LPW + line;
   const bool active = yr < ny;
   const int y = active ? yr : 0;
   const size_t row = (size_t)y * NX;
@@ -391,7 +452,7 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
 }
 
 template <int NX>
-__global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
+__global__ void __launch_bounds__(W_IROWS * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
                                                            int ny, int m_lo, int m_hi, int top,
                                                            const float* __restrict__ delta, float* __restrict__ part1,
                                                            float* __restrict__ part2, EpiArgs<float> epi,
@@ -407,12 +468,12 @@ __global__ void __launch_bounds__(W_INV * 32) k2d_inv_rows(const float2* __restr
 // cooperative as in k2d_inv_cols, so stores are row segments.
 // -------------------------------------------------------------------------
 template <int NY>
-__global__ void __launch_bounds__(W_INV * 32) k3d_inv_ycols(const float2* __restrict__ in, long long in_plane,
+__global__ void __launch_bounds__(W_YCOLS * 32) k3d_inv_ycols(const float2* __restrict__ in, long long in_plane,
                                                             float2* __restrict__ out, long long out_plane, int pZ,
                                                             int ncols, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
-  constexpr int THREADS = W_INV * 32, CW = W_INV * LPW;
+  constexpr int THREADS = W_YCOLS * 32, CW = W_YCOLS * LPW;
   __shared__ float2 s_tw[F::TW];
   extern __shared__ float2 s_buf[];
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
