@@ -52,6 +52,11 @@ NX = NY = 1024
 NSTEPS = 1000
 M = 16
 DT = 5e-4
+# DRAM bytes (read + write) per launch of the fused kernels, from one ncu
+# capture of the headline step (profiles/ncu_k2d_kernels_2d_1024_M16.md:
+# mean over the step's three k2d_inv_cols launches, L2 not flushed between
+# kernels); to be re-taken whenever the kernel changes.
+NCU_TRAFFIC_BYTES = {"k2d_inv_cols": 24.65e6}
 METRIC = "Mpoint-steps/s (2D 1024², M=16) fused vs plain at ≤1e-5 rel L2; serve p50/p99"
 UNIT = "Mpoint-steps/s"
 WORKLOAD = "2D periodic 1024x1024, FP32, M=16, Q low-passed noise in [5,100] (seed 2), Ricker f0=10 at centre, dt=5e-4, 1000 steps"
@@ -330,13 +335,43 @@ def serve_bench(nreq, check=3):
     return out
 
 
+def profile_run(V, S, stream, args):
+    """Short runs for profilers (print nothing): set-up, then ncu_steps steps
+    of the 3D 256^3 workload or of the 64-simulation batch."""
+    if args.ncu_workload == "3d":
+        w = S.workload_3d_256()
+        with V.Solver(w["shape"], stream=stream.cuda_stream) as s:
+            s.set_M(w["M"])
+            s.set_q(w["Q"], w["c0"], w["omega0"])
+            s.set_state(w["u0"].astype(np.float32))
+            s.step(args.ncu_steps, w["dt"])
+            s.sync()
+        return 0
+    sims = S.workload_batch()
+    solvers = []
+    with V.Batch(stream=stream.cuda_stream) as b:
+        for sp in sims:
+            s = V.Solver(sp["shape"], stream=stream.cuda_stream)
+            s.set_q(sp["Q"], sp["c0"], sp["omega0"])
+            s.set_M(sp["M"])
+            dt = s.suggest_dt(0.25)
+            s.set_state(np.zeros(sp["shape"], np.float32))
+            s.set_source(sp["src_idx"], S.ricker_samples(sp["nsteps"], dt, sp["f0"]))
+            b.add(s, dt)
+            solvers.append(s)
+        b.step(args.ncu_steps)
+        b.sync()
+    for s in solvers:
+        s.close()
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
     import torch
 
-    import oracle as O
     import paper_2311_13049_gb300 as V
     import synthetic as S
     from paper_2311_13049_gb300 import build as B
@@ -430,6 +465,8 @@ def run_gpu(args):
         if rank == 0:
             print(json.dumps({"metric": "serve p50/p99 latency and Mpoint-steps/s", "serve": res}))
         return 0
+    if args.ncu_steps and args.ncu_workload != "2d":
+        return profile_run(V, S, stream, args)
     fused = make(V.IMPL_FUSED)
     if args.ncu_steps:
         # short run for profilers: set-up, then ncu_steps leap-frog steps
@@ -475,27 +512,35 @@ def run_gpu(args):
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     achieved = flops / (dom_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
+            "frac": achieved / fp32_peak, "traffic": NCU_TRAFFIC_BYTES.get(dom),
             "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x sm_max_mhz",
             "flops_per_launch": flops, "ms_per_launch": dom_ms,
             "kernels": {nm: {"ms": ms, "units": u, "launches_per_step": launches_per_step.get(nm, 1)}
                         for nm, ms, u in prof}}
 
-    # --- accuracy of one operator apply on the final wavefield (outside the timed region)
+    # --- precision (outside the timed region): one operator-pair apply on the
+    # final wavefield by the fused FP32 path and the plain FP32 path, against
+    # the plain FP64 path (cuFFT in double) on the same input
     acc = None
     if rank == 0 and not args.skip_accuracy:
-        gamma = O.seismic_coefficients(w["Q"], w["c0"], w["omega0"])["gamma"]
         ut = torch.from_numpy(final).cuda()
-        res = {}
-        for nm, s in (("fused", fused), ("plain", plain)):
-            o1 = torch.empty_like(ut)
-            o2 = torch.empty_like(ut)
+        ref = V.Solver((NY, NX), prec=V.F64, impl=V.IMPL_PLAIN, stream=stream.cuda_stream)
+        ref.set_M(M)
+        ref.set_q(Q_dev, w["c0"], w["omega0"])
+        u64 = ut.double()
+        r1, r2 = torch.empty_like(u64), torch.empty_like(u64)
+        ref.apply_pair(u64, r1, r2)
+        ref.sync()
+        ref.close()
+        acc = {}
+        for nm, s in (("fused_f32", fused), ("plain_f32", plain)):
+            o1, o2 = torch.empty_like(ut), torch.empty_like(ut)
             s.apply_pair(ut, o1, o2)
             s.sync()
-            res[nm] = (o1.cpu().numpy().astype(np.float64), o2.cpu().numpy().astype(np.float64))
-        r1, r2 = O.seismic_operators(final.astype(np.float64), gamma, M)
-        acc = {f"{nm}_apply_rel_l2": [O.rel_l2(res[nm][0], r1), O.rel_l2(res[nm][1], r2)] for nm in res}
-        acc["input"] = "final wavefield of the timed run (FP32), oracle FP64 on the same input"
+            acc[nm + "_rel_l2_vs_f64"] = [float(torch.linalg.norm(o.double() - r) / torch.linalg.norm(r))
+                                          for o, r in ((o1, r1), (o2, r2))]
+        acc["input"] = ("final wavefield of the timed run (FP32); reference: the plain path in FP64 on the GPU "
+                        "(same operators, cuFFT in double)")
 
     batch = None if args.skip_batch else batch_bench(V, torch, stream, flush)
     configs = None if args.skip_configs else configs_bench(V, torch, stream, flush)
@@ -536,6 +581,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the 600-request serving stream to serve (0: skip)")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving measurement")
+    ap.add_argument("--ncu-workload", default="2d", choices=["2d", "3d", "batch"],
+                    help="workload of the --ncu-steps profiling mode")
     ap.add_argument("--ncu-steps", type=int, default=0,
                     help="profiling mode: set up the workload, run this many leap-frog steps, print nothing")
     args = ap.parse_args()

@@ -19,7 +19,7 @@ namespace {
 constexpr int W_FROWS = 2;  // forward rows: small CTAs, 4x more CTAs than SMs at 1024^2
 constexpr int W_FCOLS = 4;  // forward columns: 4 columns -> 32-byte row segments
 constexpr int W_YCOLS = 4;  // 3D y-inverse kernel
-constexpr int W_IROWS = 8;  // inverse row kernel
+constexpr int W_IROWS = 4;  // inverse row kernel
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
@@ -368,14 +368,36 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
     fence_mbar_init();
   }
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
-  __syncthreads();
-  pdl_wait();  // Z of this group and the previous group's partial sums are ready
-  pdl_trigger();
   float2* wbuf = s_buf + warp * warp_stride<NX>();
   const int yr = (bx * W_IROWS + warp) * LPW + line;
   const bool active = yr < ny;
   const int y = active ? yr : 0;
   const size_t row = (size_t)y * NX;
+  // rows this line reads later, produced two or more kernels ago: into L2
+  // now (the last group's epilogue reads five fields that the step's
+  // spectrum traffic has usually evicted)
+  if (li == 0 && active) {
+    constexpr uint32_t RowB = NX * sizeof(float);
+    if (!top) {
+      prefetch_l2(part1 + row, RowB);
+      prefetch_l2(part2 + row, RowB);
+    }
+    if (m_lo == 0 && (epi.mode == EPI_STEP || epi.mode == EPI_START)) {
+      prefetch_l2(epi.u_cur + row, RowB);
+      prefetch_l2(epi.u_other + row, RowB);
+      prefetch_l2(epi.l2p + row, RowB);
+      prefetch_l2(epi.A + row, RowB);
+      prefetch_l2(epi.B + row, RowB);
+    }
+  }
+  // delta = gamma - gamma0 does not depend on earlier kernels: into
+  // registers before the programmatic wait
+  float dl[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) dl[m] = delta[row + li + LANES * m];
+  __syncthreads();
+  pdl_wait();  // Z of this group and the previous group's partial sums are ready
+  pdl_trigger();
   auto issue = [&](int buf, int mt) {
     const float2* z1 = Z + (long long)((mt - m_lo) * 2 + 0) * zslot + (size_t)y * pZ;
     const float2* z2 = Z + (long long)((mt - m_lo) * 2 + 1) * zslot + (size_t)y * pZ;
@@ -432,9 +454,8 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
     fft_line<NX, true>(w, wbuf, s_tw, li, line);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const float d = delta[row + li + LANES * m];
-      a1[m] = fmaf(d, a1[m], w[m].x);
-      a2[m] = fmaf(d, a2[m], w[m].y);
+      a1[m] = fmaf(dl[m], a1[m], w[m].x);
+      a2[m] = fmaf(dl[m], a2[m], w[m].y);
     }
   }
   if (!active || !ok) return;

@@ -76,4 +76,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
   return true;
 }
 
+// Hint: bring `bytes` (a multiple of 16) at the 16-byte aligned global
+// address p into L2 (no completion to wait for; data may change later).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 }  // namespace vofl
