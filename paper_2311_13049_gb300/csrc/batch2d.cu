@@ -62,7 +62,8 @@ __constant__ double c_inv_fact[41] = {
 template <int NX, int NY>
 __global__ void __launch_bounds__(W_FROWS * 32) kb_fwd_rows(const BatchSim* __restrict__ sims) {
   const BatchSim* s = sims + blockIdx.z;
-  fwd_rows_body<NX>(blockIdx.x, s->epi.u_cur, s->T, NY, 1, s->pT, s->ryy, 0.0f, s->twx, const_cast<int*>(s->epi.step), s->inc_step);
+  fwd_rows_body<NX, false>(blockIdx.x, s->epi.u_cur, s->T, NY, 1, s->pT, s->ryy, 0.0f, s->twx,
+                           const_cast<int*>(s->epi.step), s->inc_step, s->err);
 }
 
 template <int NX, int NY>
@@ -110,7 +111,7 @@ BKernels bkernels_for() {
   k.fc = kb_fwd_cols<NX, NY>;
   k.ic = kb_inv_cols<NX, NY>;
   k.ir = kb_inv_rows<NX, NY>;
-  k.smem_fr = exch_smem<NX, W_FROWS>();
+  k.smem_fr = frows_smem<NX, false>();
   k.smem_fc = exch_smem<NY, W_FCOLS>();
   k.smem_ic = inv_cols_smem<NY>();
   k.smem_ir = inv_rows_smem<NX>();
@@ -134,10 +135,10 @@ bool pick_bkernels(int nx, int ny, BKernels* k) {
 }
 
 bool set_bsmem(const BKernels& k) {
-  return cudaFuncSetAttribute(k.fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fr) == cudaSuccess &&
-         cudaFuncSetAttribute(k.fc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fc) == cudaSuccess &&
-         cudaFuncSetAttribute(k.ic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_ic) == cudaSuccess &&
-         cudaFuncSetAttribute(k.ir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_ir) == cudaSuccess;
+  return set_kernel_smem(k.fr, k.smem_fr) == cudaSuccess &&
+         set_kernel_smem(k.fc, k.smem_fc) == cudaSuccess &&
+         set_kernel_smem(k.ic, k.smem_ic) == cudaSuccess &&
+         set_kernel_smem(k.ir, k.smem_ir) == cudaSuccess;
 }
 
 // plain (non-programmatic) launch, for the first kernel of a graph branch

@@ -47,7 +47,7 @@ namespace {
 // size dispatch
 // -------------------------------------------------------------------------
 struct Kernels {
-  void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int);
+  void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*inv_cols)(const float2*, const float*, const float*, float2*, long long, int, int, int, int, float,
                    const float2*);
@@ -61,11 +61,11 @@ struct Kernels {
 template <int NX, int NY>
 Kernels kernels_for() {
   Kernels k;
-  k.fwd_rows = k2d_fwd_rows<NX>;
+  k.fwd_rows = k2d_fwd_rows<NX, false>;
   k.fwd_cols = k2d_fwd_cols<NY>;
   k.inv_cols = k2d_inv_cols<NY>;
   k.inv_rows = k2d_inv_rows<NX>;
-  k.smem_frows = exch_smem<NX, W_FROWS>();
+  k.smem_frows = frows_smem<NX, false>();
   k.smem_fcols = exch_smem<NY, W_FCOLS>();
   k.smem_icols = inv_cols_smem<NY>();
   k.smem_irows = inv_rows_smem<NX>();
@@ -97,10 +97,10 @@ bool pick_kernels(int nx, int ny, Kernels* k) {
 }
 
 int set_smem_attributes(const Kernels& k) {
-  if (cudaFuncSetAttribute(k.fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_frows) ||
-      cudaFuncSetAttribute(k.fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fcols) ||
-      cudaFuncSetAttribute(k.inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_icols) ||
-      cudaFuncSetAttribute(k.inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_irows)) {
+  if (set_kernel_smem(k.fwd_rows, k.smem_frows) ||
+      set_kernel_smem(k.fwd_cols, k.smem_fcols) ||
+      set_kernel_smem(k.inv_cols, k.smem_icols) ||
+      set_kernel_smem(k.inv_rows, k.smem_irows)) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
@@ -128,7 +128,7 @@ struct Plan2D {
   cudaError_t forward(cudaStream_t s, const float* u, bool inc_step, cudaEvent_t* ev = nullptr) const {
     const int rpc = W_FROWS * k.lpw_x;  // row pairs per CTA
     cudaError_t e = launch_pdl(k.fwd_rows, dim3((ny / 2 + rpc - 1) / rpc), dim3(W_FROWS * 32), k.smem_frows, s, u,
-                               T, ny, 1, pT, ryy, 0.0f, (const float2*)twx, step_ctr, inc_step ? 1 : 0);
+                               T, ny, 1, pT, ryy, 0.0f, (const float2*)twx, step_ctr, inc_step ? 1 : 0, err);
     if (e) return e;
     if (ev) cudaEventRecord(ev[1], s);
     const int cpc = W_FCOLS * k.lpw_y;

@@ -29,7 +29,7 @@ namespace vofl {
 namespace {
 
 struct Kernels3 {
-  void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int);
+  void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_ycols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*fwd_zcols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*inv_z)(const float2*, const float*, const float*, float2*, long long, int, int, int, int, float,
@@ -45,13 +45,13 @@ struct Kernels3 {
 template <int NX, int NY, int NZ>
 Kernels3 kernels3_for() {
   Kernels3 k;
-  k.fwd_rows = k2d_fwd_rows<NX>;
+  k.fwd_rows = k2d_fwd_rows<NX, true>;
   k.fwd_ycols = k2d_fwd_cols<NY>;
   k.fwd_zcols = k2d_fwd_cols<NZ>;
   k.inv_z = k2d_inv_cols<NZ>;
   k.inv_y = k3d_inv_ycols<NY>;
   k.inv_x = k2d_inv_rows<NX>;
-  k.sm_frows = exch_smem<NX, W_FROWS>();
+  k.sm_frows = frows_smem<NX, true>();
   k.sm_fy = exch_smem<NY, W_FCOLS>();
   k.sm_fz = exch_smem<NZ, W_FCOLS>();
   k.sm_iz = inv_cols_smem<NZ>();
@@ -79,12 +79,12 @@ bool pick_kernels3(int nx, int ny, int nz, Kernels3* k) {
 }
 
 int set_smem3(const Kernels3& k) {
-  if (cudaFuncSetAttribute(k.fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.sm_frows) ||
-      cudaFuncSetAttribute(k.fwd_ycols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.sm_fy) ||
-      cudaFuncSetAttribute(k.fwd_zcols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.sm_fz) ||
-      cudaFuncSetAttribute(k.inv_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.sm_iz) ||
-      cudaFuncSetAttribute(k.inv_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.sm_iy) ||
-      cudaFuncSetAttribute(k.inv_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.sm_ix)) {
+  if (set_kernel_smem(k.fwd_rows, k.sm_frows) ||
+      set_kernel_smem(k.fwd_ycols, k.sm_fy) ||
+      set_kernel_smem(k.fwd_zcols, k.sm_fz) ||
+      set_kernel_smem(k.inv_z, k.sm_iz) ||
+      set_kernel_smem(k.inv_y, k.sm_iy) ||
+      set_kernel_smem(k.inv_x, k.sm_ix)) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
@@ -205,7 +205,8 @@ struct Fused3D : Engine {
     const int rpc = W_FROWS * k.lpw_x;
     const int pairs = (ny / 2) * nz;
     cudaError_t e = launch_pdl(k.fwd_rows, dim3((pairs + rpc - 1) / rpc), dim3(W_FROWS * 32), k.sm_frows, s, u, T,
-                               ny, nz, pT, ryy, rzz, (const float2*)twx, c->d_step, inc_step ? 1 : 0);
+                               ny, nz, pT, ryy, rzz, (const float2*)twx, c->d_step, inc_step ? 1 : 0,
+                               c->d_step + 1);
     if (e) return e;
     const int cy = W_FCOLS * k.lpw_y;
     e = launch_pdl(k.fwd_ycols, dim3((c2 + cy - 1) / cy, nz), dim3(W_FCOLS * 32), k.sm_fy, s, (const float2*)T, pT, U2,

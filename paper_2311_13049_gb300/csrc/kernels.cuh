@@ -51,37 +51,77 @@ constexpr int icols_warps() {
 
 // -------------------------------------------------------------------------
 // F1: forward FFT along x of two rows at once, split into half spectra.
+// The rows the stencil needs (the pair, its y neighbours and, in 3D, the
+// pair in the z-neighbour planes) are copied into shared memory by TMA bulk
+// copies (one mbarrier per line, bounded wait) right after the
+// programmatic wait: one round trip instead of dependent global loads.
 // -------------------------------------------------------------------------
-template <int NX>
+template <bool Z3>
+constexpr int frows_nrows() {
+  return Z3 ? 8 : 4;
+}
+template <int NX, bool Z3>
+constexpr size_t frows_smem() {
+  return exch_smem<NX, W_FROWS>() + (size_t)W_FROWS * LineFFT<NX>::LPW * frows_nrows<Z3>() * NX * sizeof(float);
+}
+
+template <int NX, bool Z3>
 __device__ __forceinline__ void fwd_rows_body(int bx, const float* __restrict__ u, float2* __restrict__ T, int ny,
                                               int nz, int pT, float ryy, float rzz, const float2* __restrict__ twx,
-                                              int* step_ctr, int inc_step) {
+                                              int* step_ctr, int inc_step, int* err) {
   using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, THREADS = W_FROWS * 32;
+  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, H = NX / 2, THREADS = W_FROWS * 32;
+  constexpr int NR = frows_nrows<Z3>();
+  constexpr uint32_t ROWB = NX * sizeof(float);
   __shared__ float2 s_tw[F::TW];
+  __shared__ uint64_t s_rbar[W_FROWS * LPW];
   extern __shared__ float2 s_buf[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = lane % LANES, line = lane / LANES;
+  const int lid = warp * LPW + line;
+  uint64_t* bar = &s_rbar[lid];
+  // rows of this line: 0 y-1, 1 y0, 2 y0+1, 3 y0+2 [, 4-5 the pair at z-1, 6-7 at z+1]
+  float* srow = reinterpret_cast<float*>(s_buf + W_FROWS * warp_stride<NX>()) + (size_t)lid * NR * NX;
+  if (li == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
   __syncthreads();
   pdl_wait();  // u is written by the previous step's last kernel
   pdl_trigger();
   if (inc_step && bx == 0 && threadIdx.x == 0) *step_ctr += 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int li = lane % LANES, line = lane / LANES;
   float2* wbuf = s_buf + warp * warp_stride<NX>();
   // rows are flattened over planes: row = z * ny + y (nz = 1 in 2D); a
   // pair of rows never straddles two planes (ny is even)
-  const int pair = (bx * W_FROWS + warp) * F::LPW + line;
+  const int pair = (bx * W_FROWS + warp) * LPW + line;
   const bool active = pair < (ny / 2) * nz;
   const int r0i = 2 * (active ? pair : 0);
   const int yy = r0i % ny, zz = r0i / ny;
-  const float* plane = u + (size_t)zz * ny * NX;
-  const float* r0 = plane + (size_t)yy * NX;
-  const float* r1 = r0 + NX;
-  const float* rm = plane + (size_t)(yy == 0 ? ny - 1 : yy - 1) * NX;
-  const float* rp = plane + (size_t)(yy + 2 == ny ? 0 : yy + 2) * NX;
-  const size_t pl = (size_t)ny * NX;  // plane stride
-  const float* zm = nz > 1 ? r0 - (size_t)zz * pl + (size_t)(zz == 0 ? nz - 1 : zz - 1) * pl : r0;
-  const float* zp = nz > 1 ? r0 - (size_t)zz * pl + (size_t)(zz + 1 == nz ? 0 : zz + 1) * pl : r0;
+  if (li == 0 && active) {
+    const float* plane = u + (size_t)zz * ny * NX;
+    const float* r0 = plane + (size_t)yy * NX;
+    mbar_arrive_expect_tx(bar, NR * ROWB);
+    bulk_copy_g2s(srow + 0 * NX, plane + (size_t)(yy == 0 ? ny - 1 : yy - 1) * NX, ROWB, bar);
+    bulk_copy_g2s(srow + 1 * NX, r0, ROWB, bar);
+    bulk_copy_g2s(srow + 2 * NX, r0 + NX, ROWB, bar);
+    bulk_copy_g2s(srow + 3 * NX, plane + (size_t)(yy + 2 == ny ? 0 : yy + 2) * NX, ROWB, bar);
+    if constexpr (Z3) {
+      const size_t pl = (size_t)ny * NX;  // plane stride
+      const float* zm = r0 - (size_t)zz * pl + (size_t)(zz == 0 ? nz - 1 : zz - 1) * pl;
+      const float* zp = r0 - (size_t)zz * pl + (size_t)(zz + 1 == nz ? 0 : zz + 1) * pl;
+      bulk_copy_g2s(srow + 4 * NX, zm, ROWB, bar);
+      bulk_copy_g2s(srow + 5 * NX, zm + NX, ROWB, bar);
+      bulk_copy_g2s(srow + 6 * NX, zp, ROWB, bar);
+      bulk_copy_g2s(srow + 7 * NX, zp + NX, ROWB, bar);
+    }
+  }
+  const bool got = active ? mbar_wait_bounded(bar, 0, err) : true;
+  if (!__all_sync(0xffffffffu, got)) {
+    // give up (error word set): drain this line's copies (bounded), leave
+    if (active && !got) mbar_wait_bounded(bar, 0, err);
+    return;
+  }
   // w = D_xx u + (h_x/h_y)^2 D_yy u [+ (h_x/h_z)^2 D_zz u] (second
   // differences, no 1/h^2): its DFT is lambda_k u_hat_k exactly, with
   // lambda_k = -4 sin^2(pi k1/nx) - 4 (h_x/h_y)^2 sin^2(pi k2/ny) [- ...];
@@ -89,20 +129,24 @@ __device__ __forceinline__ void fwd_rows_body(int bx, const float* __restrict__ 
   // neighbour differences are exact or carry a rounding relative to
   // themselves, so w's transform keeps the high-wavenumber content that an
   // FP32 transform of u would bury under round-off of size eps*|u|.
+  const float* rm = srow;
+  const float* r0 = srow + NX;
+  const float* r1 = srow + 2 * NX;
+  const float* rp = srow + 3 * NX;
   float2 v[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int x = li + LANES * m;
     const int xm = x == 0 ? NX - 1 : x - 1, xp = x + 1 == NX ? 0 : x + 1;
-    const float a = __ldg(r0 + x), b = __ldg(r1 + x);
-    const float dxa = (__ldg(r0 + xp) - a) - (a - __ldg(r0 + xm));
-    const float dxb = (__ldg(r1 + xp) - b) - (b - __ldg(r1 + xm));
-    const float dya = (b - a) - (a - __ldg(rm + x));
-    const float dyb = (__ldg(rp + x) - b) - (b - a);
+    const float a = r0[x], b = r1[x];
+    const float dxa = (r0[xp] - a) - (a - r0[xm]);
+    const float dxb = (r1[xp] - b) - (b - r1[xm]);
+    const float dya = (b - a) - (a - rm[x]);
+    const float dyb = (rp[x] - b) - (b - a);
     float wa = dxa + ryy * dya, wb = dxb + ryy * dyb;
-    if (nz > 1) {
-      const float dza = (__ldg(zp + x) - a) - (a - __ldg(zm + x));
-      const float dzb = (__ldg(zp + NX + x) - b) - (b - __ldg(zm + NX + x));
+    if constexpr (Z3) {
+      const float dza = (srow[6 * NX + x] - a) - (a - srow[4 * NX + x]);
+      const float dzb = (srow[7 * NX + x] - b) - (b - srow[5 * NX + x]);
       wa = wa + rzz * dza;
       wb = wb + rzz * dzb;
     }
@@ -126,12 +170,12 @@ __device__ __forceinline__ void fwd_rows_body(int bx, const float* __restrict__ 
   }
 }
 
-template <int NX>
+template <int NX, bool Z3>
 __global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __restrict__ u, float2* __restrict__ T,
                                                              int ny, int nz, int pT, float ryy, float rzz,
                                                              const float2* __restrict__ twx, int* step_ctr,
-                                                             int inc_step) {
-  fwd_rows_body<NX>(blockIdx.x, u, T, ny, nz, pT, ryy, rzz, twx, step_ctr, inc_step);
+                                                             int inc_step, int* err) {
+  fwd_rows_body<NX, Z3>(blockIdx.x, u, T, ny, nz, pT, ryy, rzz, twx, step_ctr, inc_step, err);
 }
 
 // -------------------------------------------------------------------------
@@ -526,6 +570,18 @@ __global__ void __launch_bounds__(W_YCOLS * 32) k3d_inv_ycols(const float2* __re
       for (int r = 0; r < F::RL; ++r) out[(size_t)(sj + F::NBL * r) * pZ + c0 + sc] = w[r];
     }
   }
+}
+
+// Dynamic shared memory of a fused kernel, and the whole shared-memory
+// carveout for all of them: consecutive kernels of a step (overlapped by
+// programmatic dependent launch) then never need the SM's L1/shared split
+// changed between them.
+template <typename... KArgs>
+cudaError_t set_kernel_smem(void (*kern)(KArgs...), size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
