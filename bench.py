@@ -68,6 +68,24 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(ms, dist=None, device="cuda"):
+    """The slowest rank's time: every rank's timed region ends when the
+    last one does (the job's wall time)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, points_per_run, runs, ms_max):
+    """Whole-job throughput in Mpoint-steps/s: every rank runs its own
+    replica of the workload, so the job does world_size times the work in
+    the slowest rank's time."""
+    return world_size * points_per_run * runs / (ms_max * 1e-3) / 1e6
+
+
 def _config(extra=None):
     c = {"workload": WORKLOAD, "grid": [NY, NX], "M": M, "steps_per_run": NSTEPS, "dt": DT,
          "parallelism": "replicas (one independent run per GPU)",
@@ -453,12 +471,7 @@ def run_gpu(args):
                 e1.synchronize()
                 tot += e0.elapsed_time(e1)
             torch.cuda.synchronize()
-        ms = tot
-        if dist:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(tot, dist)
 
     if args.serve_only:
         res = serve_bench(args.serve_requests)
@@ -494,9 +507,9 @@ def run_gpu(args):
     lffp_plain = steady_step_ms(plain, 50)
 
     pts = NX * NY * NSTEPS
-    value = ws * pts * args.steps / (ms_dev * 1e-3) / 1e6
-    e2e = ws * pts * args.steps / (ms_e2e * 1e-3) / 1e6
-    plain_value = ws * pts * kp / (ms_plain * 1e-3) / 1e6
+    value = job_value(ws, pts, args.steps, ms_dev)
+    e2e = job_value(ws, pts, args.steps, ms_e2e)
+    plain_value = job_value(ws, pts, kp, ms_plain)
 
     # --- roofline of the dominant kernel (isolated launches, CUDA events on the context stream)
     prof = fused.profile_kernels(reps=20)
