@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const Batc
   const int m_lo = g * BG;
   if (m_lo > s->M) return;  // this simulation has fewer groups
   const int m_hi = min(s->M + 1, m_lo + BG);
-  inv_cols_body<NY>(blockIdx.x, blockIdx.y, s->Uh, s->P, s->Lg, s->Z, s->zslot, s->pZ, NX / 2 + 1, m_lo, m_hi,
+  // the descriptor (with its tensor map) was written by a host copy
+  if (threadIdx.x == 0) tmap_acquire(&s->zmap);
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, s->Uh, s->P, s->Lg, &s->zmap, NX / 2 + 1, m_lo, m_hi,
                     (float)c_inv_fact[m_lo], s->twy);
 }
 

@@ -209,17 +209,22 @@ struct LineFFT {
   __device__ __forceinline__ static int pad(int a) { return a + a / E; }
 };
 
-// Stage 0 of the line transform for one lane: DFT-E over the lane's E
-// elements v[r] = x[j + LANES r] (butterfly j), Stockham write of the result
-// to the line buffer `lb` at pad(j E + r).
-template <int N, bool INV>
-__device__ __forceinline__ void stage0_to_smem(float2 (&v)[LineFFT<N>::E], float2* lb, int j) {
-  using F = LineFFT<N>;
-  constexpr int E = F::E;
-  dft<E, INV>(v);
+// Stockham write of stage 0's output (butterfly j) to the line buffer `lb`
+// at pad(j E + r).
+template <int N>
+__device__ __forceinline__ void stage0_write(const float2 (&v)[LineFFT<N>::E], float2* lb, int j) {
+  constexpr int E = LineFFT<N>::E;
   float2* o = lb + j * (E + 1);  // pad(j E + r) = j (E + 1) + r
 #pragma unroll
   for (int r = 0; r < E; ++r) o[r] = v[r];
+}
+
+// Stage 0 of the line transform for one lane: DFT-E over the lane's E
+// elements v[r] = x[j + LANES r] (butterfly j), then its Stockham write.
+template <int N, bool INV>
+__device__ __forceinline__ void stage0_to_smem(float2 (&v)[LineFFT<N>::E], float2* lb, int j) {
+  dft<LineFFT<N>::E, INV>(v);
+  stage0_write<N>(v, lb, j);
 }
 
 // Middle stage (N = 768 only; no-op otherwise), in place in the line buffer

@@ -49,8 +49,7 @@ namespace {
 struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
-  void (*inv_cols)(const float2*, const float*, const float*, float2*, long long, int, int, int, int, float,
-                   const float2*);
+  void (*inv_cols)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float, const float2*);
   void (*inv_rows)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>,
                    float, const float2*, int*);
   size_t smem_frows, smem_fcols, smem_icols, smem_irows;
@@ -121,8 +120,13 @@ struct Plan2D {
   int* step_ctr = nullptr;
   int* err = nullptr;
   float ryy = 1.f, inv_lambda = 1.f;
+  CUtensorMap zmap{};  // Z as [2 G ny rows][pZ] for the column kernel's tile stores
 
   int groups(int M) const { return (M + 1 + G - 1) / G; }
+
+  int make_zmap() {
+    return make_tile_map(&zmap, Z, ncols, 2LL * G * ny, pZ, k.wic * k.lpw_y, std::min(ny, 256));
+  }
 
   // optional events: ev[1] after F1, ev[2] after F2 (ev[0] recorded by the caller)
   cudaError_t forward(cudaStream_t s, const float* u, bool inc_step, cudaEvent_t* ev = nullptr) const {
@@ -149,7 +153,7 @@ struct Plan2D {
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(M + 1, m_lo + G);
       cudaError_t e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, (const float2*)Uh,
-                                 (const float*)P, (const float*)Lg, Z, zslot, pZ, ncols, m_lo, m_hi,
+                                 (const float*)P, (const float*)Lg, zmap, ncols, m_lo, m_hi,
                                  inv_factorial(m_lo), (const float2*)twy);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
@@ -211,6 +215,7 @@ struct Fused2D : Engine {
     d->ryy = p.ryy;
     d->inv_lambda = p.inv_lambda;
     d->zslot = p.zslot;
+    d->zmap = p.zmap;
     d->pT = p.pT;
     d->pZ = p.pZ;
     return true;
@@ -249,6 +254,7 @@ struct Fused2D : Engine {
     p.delta = (const float*)c->delta;
     p.step_ctr = c->d_step;
     p.err = c->d_step + 1;
+    if (p.make_zmap()) return set_err(c, VOFL_ECUDA, "tensor map of the Z buffer");
     return VOFL_OK;
   }
 
@@ -532,6 +538,7 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   p.delta = reinterpret_cast<const float*>(m.delta);
   p.step_ctr = reinterpret_cast<int*>(base + L.step);
   p.err = p.step_ctr + 1;
+  if (p.make_zmap()) return VOFL_ECUDA;
   if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + m.gamma0, 0.5 + m.gamma0, std::ldexp(1.0, e2), (double)p.ryy, p.P,
                           p.Lg, s))
     return VOFL_ECUDA;

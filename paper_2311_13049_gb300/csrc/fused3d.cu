@@ -32,7 +32,7 @@ struct Kernels3 {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_ycols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*fwd_zcols)(const float2*, int, float2*, int, const float2*, long long, long long);
-  void (*inv_z)(const float2*, const float*, const float*, float2*, long long, int, int, int, int, float,
+  void (*inv_z)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float,
                 const float2*);
   void (*inv_y)(const float2*, long long, float2*, long long, int, int, const float2*);
   void (*inv_x)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>, float,
@@ -132,6 +132,7 @@ struct Fused3D : Engine {
   float ryy = 1.f, rzz = 1.f, inv_lambda = 1.f;
   double lambda = 1.0;
   size_t nbytes = 0;
+  CUtensorMap zmap{};  // Zz as [2 G nz rows][p3] for the z-inverse kernel's tile stores
 
   ~Fused3D() override {
     for (void* q : {(void*)T, (void*)U2, (void*)U3, (void*)Zz, (void*)Zy, (void*)part, (void*)P, (void*)Lg,
@@ -177,6 +178,8 @@ struct Fused3D : Engine {
         make_line_twiddles(ny, twy, c->stream) ||
         make_line_twiddles(nz, twz, c->stream))
       return cuda_err(c, cudaGetLastError(), "twiddles");
+    if (make_tile_map(&zmap, Zz, c3, 2LL * G * nz, p3, k.wiz * k.lpw_z, std::min(nz, 256)))
+      return set_err(c, VOFL_ECUDA, "tensor map of the Zz buffer");
     return VOFL_OK;
   }
 
@@ -220,14 +223,13 @@ struct Fused3D : Engine {
   cudaError_t inverse(vofl_ctx* c, const EpiArgs<float>& epi) {
     cudaStream_t s = c->stream;
     const int K = groups(c->M);
-    const long long zslot_z = (long long)nz * p3;
     const long long zslot_y = (long long)nz * ny * pZ;
     const int rows = ny * nz;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(c->M + 1, m_lo + G);
       const int cz = k.wiz * k.lpw_z;
       cudaError_t e = launch_pdl(k.inv_z, dim3((c3 + cz - 1) / cz, 2), dim3(k.wiz * 32), k.sm_iz, s, (const float2*)U3,
-                                 (const float*)P, (const float*)Lg, Zz, zslot_z, p3, c3, m_lo, m_hi,
+                                 (const float*)P, (const float*)Lg, zmap, c3, m_lo, m_hi,
                                  inv_factorial(m_lo), (const float2*)twz);
       if (e) return e;
       const int cy = W_YCOLS * k.lpw_y;

@@ -1,5 +1,6 @@
 // internal.h -- context state and engine interface of the vofl library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -68,6 +69,7 @@ __device__ __forceinline__ void epilogue_point(const EpiArgs<T>& e, long long id
 // One simulation of a batch, as the batched 2D kernels see it (device copy):
 // every buffer belongs to the simulation's own context.
 struct BatchSim {
+  CUtensorMap zmap;     // Z as [2 G ny rows][pZ] for the column kernel's tile stores
   EpiArgs<float> epi;   // state buffers, coefficients, dt, source, step counter, mode
   const float* delta;   // gamma - gamma0
   float2* T;            // row half spectra
@@ -229,6 +231,10 @@ inline int line_twiddle_entries(int N) {
   return nb * r + nm;
 }
 int make_line_twiddles(int N, float2* d_tw, cudaStream_t s);
+// Tensor map of a [rows][pitch] array of 8-byte elements (ncols valid per
+// row) for 2D tiled TMA copies of boxes of box_cols x box_rows (model.cu).
+int make_tile_map(CUtensorMap* map, const void* base, int ncols, long long rows, int pitch, int box_cols,
+                  int box_rows);
 int make_fused2d_tables(int nx, int ny, double lx, double ly, double s01, double s02, double scale2, double ryy,
                         float* P, float* Lg, cudaStream_t s);
 template <typename T>

@@ -75,7 +75,7 @@ __device__ __forceinline__ void fwd_rows_body(int bx, const float* __restrict__ 
   constexpr uint32_t ROWB = NX * sizeof(float);
   __shared__ float2 s_tw[F::TW];
   __shared__ uint64_t s_rbar[W_FROWS * LPW];
-  extern __shared__ float2 s_buf[];
+  extern __shared__ __align__(128) float2 s_buf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   const int lid = warp * LPW + line;
@@ -193,7 +193,7 @@ __device__ __forceinline__ void fwd_cols_body(int bx, const float2* __restrict__
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
   constexpr int THREADS = W_FCOLS * 32, CW = W_FCOLS * LPW;  // columns per CTA
   __shared__ float2 s_tw[F::TW];
-  extern __shared__ float2 s_buf[];
+  extern __shared__ __align__(128) float2 s_buf[];
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   pdl_wait();  // T is written by k2d_fwd_rows
   pdl_trigger();
@@ -242,11 +242,13 @@ __global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __res
 // Each warp keeps its column's multiplied spectrum
 // v_m = u_hat P ln|mu|^{2m}/m! in registers, advanced term to term by
 // v_{m+1} = v_m ln|mu|^2/(m+1) (ln|mu|^2 in shared memory), and does
-// stage 0 of two terms at a time (two independent register transforms,
-// two exchange-buffer sets, one pair of barriers per two terms); the last
-// stage is done cooperatively by the CTA (thread b: column b % CW,
-// butterfly b / CW), so every store writes row segments of CW adjacent
-// columns of Z.
+// stage 0 (long lines: of two terms at a time, two independent register
+// transforms into two exchange-buffer sets).  The last stage is done
+// cooperatively by the CTA (thread b: column b % CW, butterfly b / CW); its
+// results are written back into the exchange set as the CTA's output tile
+// [NY rows][CW columns], which one thread stores to Z with 2D tensor copies
+// (TMA, asynchronous: the next term's register transforms run while the
+// copy unit reads the tile).
 // -------------------------------------------------------------------------
 template <int NY>
 constexpr size_t inv_cols_smem() {
@@ -256,17 +258,27 @@ constexpr size_t inv_cols_smem() {
 }
 
 template <int NY>
+constexpr int icols_box_rows() {
+  return NY < 256 ? NY : 256;
+}
+
+template <int NY>
 __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __restrict__ Uh,
                                               const float* __restrict__ P, const float* __restrict__ Lg,
-                                              float2* __restrict__ Z, long long zslot, int pZ, int ncols, int m_lo,
-                                              int m_hi, float inv_fact_lo, const float2* __restrict__ twy) {
+                                              const void* zmap, int ncols, int m_lo, int m_hi, float inv_fact_lo,
+                                              const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
-  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
+  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL, RL = F::RL;
   constexpr int W = icols_warps<NY>(), THREADS = W * 32, CW = W * LPW;  // columns per CTA
   constexpr bool PAIR = icols_pair<NY>();
   constexpr int SET = W * warp_stride<NY>();  // float2 slots of one exchange set
+  constexpr int BOXR = icols_box_rows<NY>();
+  // the output tile fits an exchange set; the second set (paired terms)
+  // starts 128-byte aligned like the first, as the tensor copies require
+  static_assert(NY * CW <= SET, "output tile fits an exchange set");
+  static_assert(!PAIR || (SET * sizeof(float2)) % 128 == 0, "second exchange set alignment");
   __shared__ float2 s_tw[F::TW];
-  extern __shared__ float2 s_buf[];
+  extern __shared__ __align__(128) float2 s_buf[];
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
@@ -301,22 +313,37 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cscale(v[m], s_lg[li + LANES * m] * rinv);
   };
-  // cooperative last stage of exchange set `set` into Z slot (mt - m_lo):
-  // thread b takes column b % CW, butterfly b / CW (row segments of CW columns)
-  auto finish = [&](int set, int mt) {
-    float2* zb = Z + (long long)((mt - m_lo) * 2 + op) * zslot + c0;
+  // last stage of exchange set `set`, cooperatively: thread b takes column
+  // b % CW, butterfly b / CW; results in registers
+  auto last_read = [&](int set, float2 (&w)[BPL][RL]) {
 #pragma unroll
     for (int q = 0; q < BPL; ++q) {
       const int b = threadIdx.x + THREADS * q;
       const int sc = b % CW, sj = b / CW;
       const float2* lb = s_buf + set * SET + (sc / LPW) * warp_stride<NY>() + (sc % LPW) * F::PAD_LINE;
-      float2 w[F::RL];
-      stage1_from_smem<NY, true>(w, lb, s_tw, sj);
-      if (c0 + sc < ncols) {
-#pragma unroll
-        for (int r = 0; r < F::RL; ++r) zb[(size_t)(sj + F::NBL * r) * pZ + sc] = w[r];
-      }
+      stage1_from_smem<NY, true>(w[q], lb, s_tw, sj);
     }
+  };
+  // ... written back into the (fully read) set as the output tile
+  // [NY rows][CW columns], made visible to the tensor-copy unit
+  auto tile_write = [&](int set, const float2 (&w)[BPL][RL]) {
+    float2* tile = s_buf + set * SET;
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+      const int b = threadIdx.x + THREADS * q;
+      const int sc = b % CW, sj = b / CW;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) tile[(sj + F::NBL * r) * CW + sc] = w[q][r];
+    }
+    fence_proxy_async_smem();
+  };
+  // one thread stores the tile of `set` to Z slot (mt - m_lo) of operator op
+  // (rows (slot * 2 + op) * NY .. + NY, columns c0 .. c0 + CW; columns past
+  // ncols are clipped by the copy unit)
+  auto tile_store = [&](int set, int mt) {
+    const int y0 = ((mt - m_lo) * 2 + op) * NY;
+#pragma unroll
+    for (int k = 0; k < NY / BOXR; ++k) tma_store_2d(zmap, c0, y0 + k * BOXR, s_buf + set * SET + k * BOXR * CW);
   };
   int mt = m_lo;
   // two terms per iteration: two independent register transforms in flight
@@ -327,25 +354,55 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
     advance(mt);
 #pragma unroll
     for (int m = 0; m < E; ++m) xb[m] = v[m];
-    stage0_to_smem<NY, true>(xa, lb_own, li);
-    stage0_to_smem<NY, true>(xb, lb_own + SET, li);
+    dft<E, true>(xa);
+    dft<E, true>(xb);
+    if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tiles have left shared memory
+    __syncthreads();
+    stage0_write<NY>(xa, lb_own, li);
+    stage0_write<NY>(xb, lb_own + SET, li);
     mid_stage<NY, true>(lb_own, s_tw, li);
     mid_stage<NY, true>(lb_own + SET, s_tw, li);
     __syncthreads();
-    finish(0, mt);
-    finish(1, mt + 1);
+    {
+      float2 w[BPL][RL];
+      last_read(0, w);
+      __syncthreads();
+      tile_write(0, w);
+    }
+    {
+      float2 w[BPL][RL];
+      last_read(1, w);
+      __syncthreads();
+      tile_write(1, w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tile_store(0, mt);
+      tile_store(1, mt + 1);
+      bulk_commit();
+    }
     if (mt + 2 < m_hi) advance(mt + 1);
-    __syncthreads();  // last-stage reads done before the next stage-0 writes
   }
   if (PAIR) {
     if (mt < m_hi) {  // an odd last term
       float2 x[E];
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = v[m];
-      stage0_to_smem<NY, true>(x, lb_own, li);
+      dft<E, true>(x);
+      if (threadIdx.x == 0) bulk_wait_read_all();
+      __syncthreads();
+      stage0_write<NY>(x, lb_own, li);
       mid_stage<NY, true>(lb_own, s_tw, li);
       __syncthreads();
-      finish(0, mt);
+      float2 w[BPL][RL];
+      last_read(0, w);
+      __syncthreads();
+      tile_write(0, w);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tile_store(0, mt);
+        bulk_commit();
+      }
     }
   } else {
     // short lines: one term per iteration (a separate loop: sharing it with
@@ -354,22 +411,34 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
       float2 x[E];
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = v[m];
-      stage0_to_smem<NY, true>(x, lb_own, li);
+      dft<E, true>(x);
+      if (threadIdx.x == 0) bulk_wait_read_all();
+      __syncthreads();
+      stage0_write<NY>(x, lb_own, li);
       mid_stage<NY, true>(lb_own, s_tw, li);
       __syncthreads();
-      finish(0, mt);
-      if (mt + 1 < m_hi) advance(mt);
+      float2 w[BPL][RL];
+      last_read(0, w);
       __syncthreads();
+      tile_write(0, w);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tile_store(0, mt);
+        bulk_commit();
+      }
+      if (mt + 1 < m_hi) advance(mt);
     }
   }
+  if (threadIdx.x == 0) bulk_wait_all();  // stores complete before the CTA's shared memory goes
 }
 
 template <int NY>
 __global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
-                                                           const float* __restrict__ Lg, float2* __restrict__ Z,
-                                                           long long zslot, int pZ, int ncols, int m_lo, int m_hi,
-                                                           float inv_fact_lo, const float2* __restrict__ twy) {
-  inv_cols_body<NY>(blockIdx.x, blockIdx.y, Uh, P, Lg, Z, zslot, pZ, ncols, m_lo, m_hi, inv_fact_lo, twy);
+                                                           const float* __restrict__ Lg,
+                                                           const __grid_constant__ CUtensorMap zmap, int ncols,
+                                                           int m_lo, int m_hi, float inv_fact_lo,
+                                                           const float2* __restrict__ twy) {
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, twy);
 }
 
 // -------------------------------------------------------------------------
@@ -400,7 +469,7 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   constexpr uint32_t RB_BYTES = RB * sizeof(float2);
   __shared__ float2 s_tw[F::TW];
   __shared__ uint64_t s_bar[W_IROWS * LPW * 2];
-  extern __shared__ float2 s_buf[];
+  extern __shared__ __align__(128) float2 s_buf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   const int lid = warp * LPW + line;  // line id inside the CTA
@@ -540,7 +609,7 @@ __global__ void __launch_bounds__(W_YCOLS * 32) k3d_inv_ycols(const float2* __re
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
   constexpr int THREADS = W_YCOLS * 32, CW = W_YCOLS * LPW;
   __shared__ float2 s_tw[F::TW];
-  extern __shared__ float2 s_buf[];
+  extern __shared__ __align__(128) float2 s_buf[];
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   __syncthreads();
   pdl_wait();
