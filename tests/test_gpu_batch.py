@@ -188,3 +188,42 @@ def test_suggest_dt_matches_oracle(V, n):
         dt = s.suggest_dt(0.25)
     ref = O.suggested_dt(gamma_of(Q), 1.0, 2 * np.pi, shape, courant=0.25)
     assert abs(dt - ref) <= 1e-6 * ref, (dt, ref)
+
+
+def test_batch_workload_members_equal_solo(V):
+    """The 64-simulation workload itself (edges 256..1024 incl. 768, M = 12,
+    dt by the time-step rule), autotuned, 9 steps: the first member of every
+    size equals its solo run bit for bit."""
+    sims = S.workload_batch()
+    solvers, first = [], {}
+    with V.Batch() as b:
+        for i, sp in enumerate(sims):
+            s = V.Solver(sp["shape"])
+            s.set_q(sp["Q"])
+            s.set_M(sp["M"])
+            dt = s.suggest_dt(0.25)
+            s.set_state(np.zeros(sp["shape"], np.float32))
+            s.set_source(sp["src_idx"], S.ricker_samples(sp["nsteps"], dt, sp["f0"]))
+            b.add(s, dt)
+            solvers.append((s, dt))
+            first.setdefault(sp["shape"][0], i)
+        b.tune(reps=1)
+        b.step(4)
+        b.step(5)
+    assert sorted(first) == [256, 512, 768, 1024]
+    for n, i in first.items():
+        sp = sims[i]
+        s, dt = solvers[i]
+        got = s.get_state()
+        s.sync()
+        with V.Solver(sp["shape"]) as t:
+            t.set_q(sp["Q"])
+            t.set_M(sp["M"])
+            t.set_state(np.zeros(sp["shape"], np.float32))
+            t.set_source(sp["src_idx"], S.ricker_samples(sp["nsteps"], dt, sp["f0"]))
+            t.step(9, dt)
+            want = t.get_state()
+            t.sync()
+        assert np.array_equal(got, want), n
+    for s, _ in solvers:
+        s.close()

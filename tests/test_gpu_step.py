@@ -159,3 +159,13 @@ def test_state_errors(V):
             s.set_q(np.zeros(shape))  # Q must be positive
         with pytest.raises(V.VoflError):
             s.set_source((64, 0), np.ones(3))
+
+
+def test_headline_workload_100_steps(V):
+    """The headline run (1024^2, M = 16, Ricker at the centre, dt = 5e-4)
+    for its first 100 steps against the oracle, on every point."""
+    w = S.workload_2d_1024(nsteps=100)
+    g = gpu_run(V, w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], V.IMPL_FUSED, V.F32,
+                w["src_idx"], w["src"])
+    r = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], w["src_idx"], w["src"])
+    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
