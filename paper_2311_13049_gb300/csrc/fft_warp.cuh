@@ -117,12 +117,27 @@ __device__ __forceinline__ float2 twiddle_const(float2 v) {
   }
 }
 
+// Radix-2 butterflies of a DFT-R level: v[K] = e[K] + w^K o[K],
+// v[K + R/2] = e[K] - w^K o[K], w = exp(-/+ 2 pi i / R).  Trivial twiddles
+// (1, -i, -1, i) cost additions only; the others are fused into FMAs:
+// x = e + w o in four FMAs, then e - w o = 2e - x in two (six instructions
+// instead of a complex multiply and two complex additions).
 template <int R, int K, bool INV>
 __device__ __forceinline__ void butterflies(float2* v, const float2* e, const float2* o) {
   if constexpr (K < R / 2) {
-    const float2 t = twiddle_const<R, K, INV>(o[K]);
-    v[K] = cadd(e[K], t);
-    v[K + R / 2] = csub(e[K], t);
+    constexpr int a = ((K % R) + R) % R;
+    if constexpr (a == 0 || 2 * a == R || 4 * a == R || 4 * a == 3 * R) {
+      const float2 t = twiddle_const<R, K, INV>(o[K]);
+      v[K] = cadd(e[K], t);
+      v[K + R / 2] = csub(e[K], t);
+    } else {
+      constexpr float wr = (float)cos_turn(a, R);
+      constexpr float wi = INV ? (float)sin_turn(a, R) : -(float)sin_turn(a, R);
+      const float2 ek = e[K], ok = o[K];
+      const float2 x = make_float2(fmaf(wr, ok.x, fmaf(-wi, ok.y, ek.x)), fmaf(wr, ok.y, fmaf(wi, ok.x, ek.y)));
+      v[K] = x;
+      v[K + R / 2] = make_float2(fmaf(2.0f, ek.x, -x.x), fmaf(2.0f, ek.y, -x.y));
+    }
     butterflies<R, K + 1, INV>(v, e, o);
   }
 }
