@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __res
 // operator (blockIdx.y).  Output Z[s][op][y][c], s = m - m_lo.
 // Each warp keeps its column's multiplied spectrum
 // v_m = u_hat P ln|mu|^{2m}/m! in registers, advanced term to term by
-// v_{m+1} = v_m ln|mu|^2/(m+1) (ln|mu|^2 in shared memory), and does
+// v_{m+1} = v_m ln|mu|^2/(m+1), and does
 // stage 0 (long lines: of two terms at a time, two independent register
 // transforms into two exchange-buffer sets).  The last stage is done
 // cooperatively by the CTA (thread b: column b % CW, butterfly b / CW); its
@@ -252,9 +252,11 @@ __global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __res
 // -------------------------------------------------------------------------
 template <int NY>
 constexpr size_t inv_cols_smem() {
-  // two exchange-buffer sets (two terms in flight) + ln|mu|^2 per column
+  // long lines: two exchange-buffer sets (two terms in flight) and
+  // ln|mu|^2 per column; short lines: one set (ln|mu|^2 in registers)
   constexpr int W = icols_warps<NY>();
-  return (icols_pair<NY>() ? 2 : 1) * exch_smem<NY, W>() + (size_t)W * LineFFT<NY>::LPW * NY * sizeof(float);
+  return icols_pair<NY>() ? 2 * exch_smem<NY, W>() + (size_t)W * LineFFT<NY>::LPW * NY * sizeof(float)
+                          : exch_smem<NY, W>();
 }
 
 template <int NY>
@@ -283,7 +285,9 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   float2* lb_own = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;  // set 0; set 1 at + SET
-  float* s_lg = reinterpret_cast<float*>(s_buf + (PAIR ? 2 : 1) * SET) + (size_t)(warp * LPW + line) * NY;
+  // ln|mu|^2 of the column: shared memory for long lines (registers are
+  // short there), registers for short lines
+  float* s_lg = reinterpret_cast<float*>(s_buf + 2 * SET) + (size_t)(warp * LPW + line) * NY;
   const int c0 = bx * CW;
   const int c = c0 + warp * LPW + line;
   const int cc = min(c, ncols - 1);
@@ -291,13 +295,16 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   const float2* uh_col = Uh + (size_t)cc * NY;
   const float* p_col = P + op * tot + (size_t)cc * NY;
   const float* l_col = Lg + (size_t)cc * NY;
-  float tm[E];
+  float tm[E], lg[PAIR ? 1 : E];
   // tables first (they do not depend on the previous kernel)
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int y = li + LANES * m;
     const float l = l_col[y];
-    s_lg[y] = l;
+    if constexpr (PAIR)
+      s_lg[y] = l;
+    else
+      lg[m] = l;
     tm[m] = p_col[y] * powi(l, m_lo) * inv_fact_lo;
   }
   __syncthreads();
@@ -311,7 +318,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   auto advance = [&](int mt) {
     const float rinv = 1.0f / (float)(mt + 1);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], s_lg[li + LANES * m] * rinv);
+    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], (PAIR ? s_lg[li + LANES * m] : lg[m]) * rinv);
   };
   // last stage of exchange set `set`, cooperatively: thread b takes column
   // b % CW, butterfly b / CW; results in registers
