@@ -69,7 +69,8 @@ typedef enum { VOFL_F32 = 0, VOFL_F64 = 1 } vofl_prec;
 /* The two operators of Eq. (1.1). */
 typedef enum {
   VOFL_OP_1PG = 0, /* (-Delta)^{1+gamma(x)}   */
-  VOFL_OP_HPG = 1  /* (-Delta)^{1/2+gamma(x)} */
+  VOFL_OP_HPG = 1, /* (-Delta)^{1/2+gamma(x)} */
+  VOFL_OP_S = 2    /* (-Delta)^{s(x)} of the general model (vofl_set_order) */
 } vofl_op;
 
 /* Implementation of the operator/step: the fused hand-written kernels, or
@@ -97,6 +98,18 @@ VOFL_API void vofl_destroy(vofl_ctx* ctx);
 VOFL_API int vofl_set_q(vofl_ctx* ctx, const double* Q, int on_device, double c0,
                double omega0);
 
+/* General variable-order model (Sec. 1, Eq. (1.5)):
+ *   u_tt = -kappa (-Delta)^{s(x)} u + f(u),  f(u) = f1 u + f3 u^3,
+ * with the same matrix-free operator (Eq. (2.13), centre s0 = grid mean of
+ * s, delta = s - s0) and the leap-frog scheme of Eq. (3.4a-c) (start step
+ * u^1 = u^0 + dt psi + dt^2/2 (-kappa L u^0 + f(u^0))).  s: N doubles in
+ * (0, 2] (host or device by on_device); kappa > 0; a point source
+ * (vofl_set_source) is added as for the seismic model.  After this call
+ * vofl_apply takes VOFL_OP_S (and rejects the seismic operators); a later
+ * vofl_set_q / vofl_set_gamma switches back.  Resets the run.  Returns
+ * VOFL_OK, VOFL_EINVAL (bad arguments or s outside (0, 2]) or VOFL_ECUDA. */
+VOFL_API int vofl_set_order(vofl_ctx* ctx, const double* s, int on_device, double kappa, double f1, double f3);
+
 /* As vofl_set_q with gamma given directly (gamma = 0 allowed: the classical
  * acoustic wave equation, Sec. 1).  c0_field (prod(n) doubles or NULL) lets
  * c0 vary in space as in the paper's two-layer example (Sec. 4.3, Example 3);
@@ -108,9 +121,11 @@ VOFL_API int vofl_set_gamma(vofl_ctx* ctx, const double* gamma, const double* c0
  * terms m = 0..M.  0 <= M <= 40.  Default 8. */
 VOFL_API int vofl_set_M(vofl_ctx* ctx, int M);
 
-/* out_dev = (-Delta)_h^{s(x)} u_dev for op (Eq. (2.13)), s = 1+gamma or
- * 1/2+gamma.  u_dev, out_dev: device arrays of prod(n) elements of the
- * context precision; they may not alias the context's state.  Async. */
+/* out_dev = (-Delta)_h^{s(x)} u_dev for op (Eq. (2.13)): s = 1+gamma or
+ * 1/2+gamma for the seismic model, s(x) of vofl_set_order for VOFL_OP_S.
+ * u_dev, out_dev: device arrays of prod(n) elements of the context
+ * precision; they may not alias the context's state.  Async.  VOFL_EINVAL
+ * for an operator that does not belong to the model set. */
 VOFL_API int vofl_apply(vofl_ctx* ctx, int op, const void* u_dev, void* out_dev);
 
 /* Both operators on the same input (one forward transform, both sums). */

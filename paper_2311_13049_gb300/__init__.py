@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libvofl.so")
 _LIB = None
 
 F32, F64 = 0, 1
-OP_1PG, OP_HPG = 0, 1
+OP_1PG, OP_HPG, OP_S = 0, 1, 2
 IMPL_FUSED, IMPL_PLAIN = 0, 1
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ESTATE",
            -6: "EUNSUPPORTED"}
@@ -36,6 +36,7 @@ SIGNATURES = {
     "vofl_destroy": (None, [_vp]),
     "vofl_set_q": (C.c_int, [_vp, _vp, C.c_int, C.c_double, C.c_double]),
     "vofl_set_gamma": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_double]),
+    "vofl_set_order": (C.c_int, [_vp, _vp, C.c_int, C.c_double, C.c_double, C.c_double]),
     "vofl_set_M": (C.c_int, [_vp, C.c_int]),
     "vofl_apply": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "vofl_apply_pair": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -187,6 +188,11 @@ class Solver:
         if c0_field is not None and devc != dev:
             raise TypeError("gamma and c0_field must both be host or both be device arrays")
         self._check(lib().vofl_set_gamma(self._h, p, pc, dev, float(c0), float(omega0)))
+
+    def set_order(self, s, kappa=1.0, f1=0.0, f3=0.0):
+        """General model u_tt = -kappa (-Delta)^{s(x)} u + f1 u + f3 u^3."""
+        p, dev = _ptr(s, np.float64, "s")
+        self._check(lib().vofl_set_order(self._h, p, dev, float(kappa), float(f1), float(f3)))
 
     def set_M(self, M):
         self._check(lib().vofl_set_M(self._h, int(M)))

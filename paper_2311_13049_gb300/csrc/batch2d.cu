@@ -279,6 +279,7 @@ void describe(const vofl_batch::Member& m, int p, bool tune, BatchSim* d) {
   double hd = 1.0;
   for (int i = 0; i < c->ndim; ++i) hd *= (c->hi[i] - c->lo[i]) / (double)c->n[i];
   e.src_scale = m.dt * m.dt / hd;
+  epi_model(c, &e);
   e.dt1 = (float)m.dt;
   e.dt2 = (float)(m.dt * m.dt);
   d->delta = (const float*)c->delta;

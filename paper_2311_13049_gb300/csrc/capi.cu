@@ -36,6 +36,8 @@ vofl_ctx::GraphKey current_key(const vofl_ctx* c) {
   k.src_flat = c->nsrc > 0 ? c->src_flat : -1;
   k.d_src = c->d_src;
   k.nsrc = c->nsrc;
+  k.f1 = c->general ? c->f1 : 0.0;
+  k.f3 = c->general ? c->f3 : 0.0;
   return k;
 }
 
@@ -248,6 +250,7 @@ const char* vofl_last_error(const vofl_ctx* c) { return c ? c->err.c_str() : "nu
 static int finish_model(vofl_ctx* c, const double* d_c0field, double c0, double omega0) {
   int st = model_from_gamma(c, c->d_gamma, d_c0field, c0, omega0);
   if (st) return st;
+  c->f1 = c->f3 = 0.0;
   st = c->eng->set_model(c);
   if (st) return st;
   c->model_set = true;
@@ -264,6 +267,24 @@ int vofl_set_q(vofl_ctx* c, const double* Q, int on_device, double c0, double om
   st = model_gamma_from_q(c, c->d_gamma, c->d_gamma);
   if (st) return st;
   return finish_model(c, nullptr, c0, omega0);
+}
+
+int vofl_set_order(vofl_ctx* c, const double* s, int on_device, double kappa, double f1, double f3) {
+  if (int st = check_ctx(c)) return st;
+  if (!s) return set_err(c, VOFL_EINVAL, "s is null");
+  if (!(kappa > 0) || !std::isfinite(kappa) || !std::isfinite(f1) || !std::isfinite(f3))
+    return set_err(c, VOFL_EINVAL, "kappa must be positive, f1 and f3 finite");
+  int st = upload(c, c->d_gamma, s, sizeof(double) * c->N, on_device);
+  if (st) return st;
+  st = model_from_order(c, c->d_gamma, kappa);
+  if (st) return st;
+  c->f1 = f1;
+  c->f3 = f3;
+  st = c->eng->set_model(c);
+  if (st) return st;
+  c->model_set = true;
+  reset_run(c);
+  return VOFL_OK;
 }
 
 int vofl_set_gamma(vofl_ctx* c, const double* gamma, const double* c0_field, int on_device, double c0,
@@ -306,8 +327,10 @@ int vofl_apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) {
 
 int vofl_apply(vofl_ctx* c, int op, const void* u, void* out) {
   if (int st = check_ctx(c)) return st;
-  if (op != VOFL_OP_1PG && op != VOFL_OP_HPG) return set_err(c, VOFL_EINVAL, "unknown operator");
-  return vofl_apply_pair(c, u, op == VOFL_OP_1PG ? out : nullptr, op == VOFL_OP_HPG ? out : nullptr);
+  if (op != VOFL_OP_1PG && op != VOFL_OP_HPG && op != VOFL_OP_S) return set_err(c, VOFL_EINVAL, "unknown operator");
+  if (c->model_set && (op == VOFL_OP_S) != c->general)
+    return set_err(c, VOFL_EINVAL, "VOFL_OP_S goes with vofl_set_order, the two seismic operators with set_q/gamma");
+  return vofl_apply_pair(c, u, op != VOFL_OP_HPG ? out : nullptr, op == VOFL_OP_HPG ? out : nullptr);
 }
 
 int vofl_set_state(vofl_ctx* c, const void* u0, const void* v0, int on_device) {

@@ -99,6 +99,8 @@ struct Sim1D {
   const double* src;
   long long nsrc;
   double src_scale;
+  int nonlin;             // general model: f(u) = f1 u + f3 u^3
+  R f1, f3;
   const R* apply_in;      // EPI_APPLY: input field
   R* out1;
   R* out2;
@@ -194,6 +196,9 @@ __global__ void __launch_bounds__(T1D) k1d_run(const Sim1D<R>* sims) {
     const int n_step = sp.step0 + s;
     e.step = &n_step;
     e.src_scale = sp.src_scale;
+    e.nonlin = sp.nonlin;
+    e.f1 = sp.f1;
+    e.f3 = sp.f3;
     for (int i = 0; i < PPT; ++i) {
       const int j = threadIdx.x + T1D * i;
       if (j < N) epilogue_point<R>(e, j, a1[i], a2[i] * sp.inv_lambda2);
@@ -290,7 +295,7 @@ struct Fused1D : Engine {
     const double L = c->hi[0] - c->lo[0];
     const double mu_max = M_PI * N / L;
     lambda2 = std::ldexp(1.0, (int)std::lround(0.5 * std::log2(std::max(mu_max, 1.0))));
-    k1d_tables<R><<<std::max(1, N / 256), 256, 0, c->stream>>>(N, L, 1.0 + c->gamma0, 0.5 + c->gamma0, lambda2, P1,
+    k1d_tables<R><<<std::max(1, N / 256), 256, 0, c->stream>>>(N, L, c->s01, c->s02, lambda2, P1,
                                                                P2, Lg);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 1D tables");
@@ -319,6 +324,13 @@ struct Fused1D : Engine {
     s.src = c->d_src;
     s.nsrc = c->nsrc;
     s.src_scale = c->dt * c->dt / ((c->hi[0] - c->lo[0]) / N);
+    {
+      EpiArgs<R> em{};
+      epi_model(c, &em);
+      s.nonlin = em.nonlin;
+      s.f1 = em.f1;
+      s.f3 = em.f3;
+    }
     return s;
   }
 

@@ -264,7 +264,7 @@ struct Fused2D : Engine {
     plan_constants(p.nx, p.ny, lx, ly, &e2, &p.ryy);
     lambda = std::ldexp(1.0, e2);
     p.inv_lambda = std::ldexp(1.0f, -e2);
-    if (make_fused2d_tables(p.nx, p.ny, lx, ly, 1.0 + c->gamma0, 0.5 + c->gamma0, lambda, (double)p.ryy, p.P, p.Lg,
+    if (make_fused2d_tables(p.nx, p.ny, lx, ly, c->s01, c->s02, lambda, (double)p.ryy, p.P, p.Lg,
                             c->stream))
       return cuda_err(c, cudaGetLastError(), "fused 2D tables");
     return VOFL_OK;
@@ -301,6 +301,7 @@ struct Fused2D : Engine {
     double hd = 1.0;
     for (int i = 0; i < c->ndim; ++i) hd *= (c->hi[i] - c->lo[i]) / (double)c->n[i];
     e.src_scale = c->dt * c->dt / hd;
+    epi_model(c, &e);
     cudaError_t err = p.forward(c->stream, (const float*)c->u[c->cur], count_step);
     if (!err) err = p.inverse(c->stream, c->M, e);
     if (err) return cuda_err(c, err, "fused 2D launch");
@@ -539,7 +540,7 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   p.step_ctr = reinterpret_cast<int*>(base + L.step);
   p.err = p.step_ctr + 1;
   if (p.make_zmap()) return VOFL_ECUDA;
-  if (make_fused2d_tables(nx, ny, lx, ly, 1.0 + m.gamma0, 0.5 + m.gamma0, std::ldexp(1.0, e2), (double)p.ryy, p.P,
+  if (make_fused2d_tables(nx, ny, lx, ly, m.s01, m.s02, std::ldexp(1.0, e2), (double)p.ryy, p.P,
                           p.Lg, s))
     return VOFL_ECUDA;
   if (make_line_twiddles(nx, p.twx, s) ||

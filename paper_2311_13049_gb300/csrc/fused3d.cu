@@ -194,7 +194,7 @@ struct Fused3D : Engine {
     rzz = (float)((hx * hx) / (hz * hz));
     const long long total = (long long)c3 * nz;
     k_tables_fused3d<<<(int)std::min<long long>(4096, (total + 255) / 256), 256, 0, c->stream>>>(
-        nx, ny, nz, lx, ly, lz, 1.0 + c->gamma0, 0.5 + c->gamma0, lambda, (double)ryy, (double)rzz, P, Lg);
+        nx, ny, nz, lx, ly, lz, c->s01, c->s02, lambda, (double)ryy, (double)rzz, P, Lg);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 3D tables");
     return VOFL_OK;
@@ -276,6 +276,7 @@ struct Fused3D : Engine {
     double hd = 1.0;
     for (int i = 0; i < 3; ++i) hd *= (c->hi[i] - c->lo[i]) / (double)c->n[i];
     e.src_scale = c->dt * c->dt / hd;
+    epi_model(c, &e);
     cudaError_t err = forward(c, (const float*)c->u[c->cur], count_step);
     if (!err) err = inverse(c, e);
     if (err) return cuda_err(c, err, "fused 3D launch");

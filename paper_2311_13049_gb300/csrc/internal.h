@@ -37,6 +37,8 @@ struct EpiArgs {
   long long nsrc;
   const int* step;    // device step counter n
   double src_scale;   // dt^2 / h^d
+  int nonlin;         // general model with a source term f(u) = f1 u + f3 u^3
+  T f1, f3;
 };
 
 // Pointwise update of Eq. (3.4) extended to Eq. (1.1) (see vofl.h).
@@ -54,12 +56,14 @@ __device__ __forceinline__ void epilogue_point(const EpiArgs<T>& e, long long id
   if (e.mode == EPI_STEP) {
     // 2u^n - u^{n-1} + dt^2 A L1 u^n + dt B (L2 u^n - L2 u^{n-1})
     unew = (T(2) * un - other) + e.dt2 * e.A[idx] * L1 + e.dt1 * e.B[idx] * (L2 - l2o);
+    if (e.nonlin) unew += e.dt2 * (e.f1 * un + e.f3 * un * un * un);
     if (idx == e.src_flat) {
       const int n = *e.step;
       if (n < e.nsrc) unew += T(e.src_scale * e.src[n]);
     }
   } else {  // EPI_START: u^0 + dt psi + dt^2/2 (A L1 u^0 + B L2 psi + f_0)
     unew = un + e.dt1 * other + T(0.5) * e.dt2 * (e.A[idx] * L1 + e.B[idx] * l2o);
+    if (e.nonlin) unew += T(0.5) * e.dt2 * (e.f1 * un + e.f3 * un * un * un);
     if (idx == e.src_flat && e.nsrc > 0) unew += T(0.5 * e.src_scale * e.src[0]);
   }
   e.u_other[idx] = unew;
@@ -103,9 +107,12 @@ struct vofl_ctx {
   int device = 0;
   int M = 8;
 
-  // model (after set_q / set_gamma)
+  // model (after set_q / set_gamma / set_order)
   bool model_set = false;
-  double gamma0 = 0;
+  bool general = false;   // general model u_tt = -kappa (-Delta)^{s(x)} u + f(u)
+  double gamma0 = 0;      // seismic: grid mean of gamma
+  double s01 = 1, s02 = 0.5;  // expansion orders of the two operators (Eq. (2.13))
+  double kappa = 1, f1 = 0, f3 = 0;
   void* delta = nullptr;  // gamma - gamma0        (prec)
   void* A = nullptr;      // c^2 eta               (prec)
   void* B = nullptr;      // c^2 tau               (prec)
@@ -142,8 +149,10 @@ struct vofl_ctx {
     long long src_flat = -2;
     const double* d_src = nullptr;
     int64_t nsrc = -1;
+    double f1 = 0, f3 = 0;
     bool operator==(const GraphKey& o) const {
-      return dt == o.dt && M == o.M && src_flat == o.src_flat && d_src == o.d_src && nsrc == o.nsrc;
+      return dt == o.dt && M == o.M && src_flat == o.src_flat && d_src == o.d_src && nsrc == o.nsrc && f1 == o.f1 &&
+             f3 == o.f3;
     }
   } graph_key;
 
@@ -207,6 +216,14 @@ void batch_detach(vofl_ctx* c);
 // model precompute (model.cu)
 int model_from_gamma(vofl_ctx* c, const double* d_gamma, const double* d_c0field, double c0, double omega0);
 int model_gamma_from_q(vofl_ctx* c, const double* d_q, double* d_gamma);
+int model_from_order(vofl_ctx* c, const double* d_s, double kappa);
+// the general-model part of the epilogue arguments of a context
+template <typename T>
+void epi_model(const vofl_ctx* c, EpiArgs<T>* e) {
+  e->nonlin = c->general && (c->f1 != 0.0 || c->f3 != 0.0);
+  e->f1 = T(c->f1);
+  e->f3 = T(c->f3);
+}
 int model_suggest_dt(vofl_ctx* c, double courant, double* dt);
 
 // twiddles / tables (model.cu)

@@ -36,6 +36,25 @@ __global__ void k_check_gamma(const double* __restrict__ g, long long n, int* ba
   }
 }
 
+__global__ void k_check_order(const double* __restrict__ s, long long n, int* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = s[i];
+    if (!(v > 0.0 && v <= 2.0)) atomicExch(bad, 1);
+  }
+}
+
+// General model: delta = s - s0, A = -kappa, B = 0 (the seismic update with
+// these coefficients is the leap-frog scheme of the general model).
+template <typename T>
+__global__ void k_coeffs_general(const double* __restrict__ sfield, double s0, double kappa, long long n,
+                                 T* __restrict__ delta, T* __restrict__ A, T* __restrict__ B) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    delta[i] = T(sfield[i] - s0);
+    A[i] = T(-kappa);
+    B[i] = T(0);
+  }
+}
+
 // Deterministic two-pass sum: fixed grid, fixed tree order.
 __global__ void k_sum_pass1(const double* __restrict__ x, long long n, double* __restrict__ part) {
   __shared__ double s[RED_THREADS];
@@ -112,14 +131,15 @@ __global__ void k_tables_fused2d(int nx, int ny, double lx, double ly, double s0
 
 // omega(x) = sqrt|c^2 eta| |mu_max|^{1 + gamma}: the largest angular
 // frequency of the undamped part of Eq. (1.1) at x (the highest Fourier mode
-// |mu_max| of the grid).  Max over the grid as an atomic max of the bit
+// |mu_max| of the grid); for the general model sqrt(kappa) |mu_max|^{s}
+// (A = -kappa, g = s, off = 0).  Max over the grid as an atomic max of the bit
 // pattern (non-negative doubles order like their bits): order-independent.
 template <typename T>
 __global__ void k_omega_max(const T* __restrict__ A, const double* __restrict__ g, long long n, double lmu,
-                            unsigned long long* out) {
+                            double off, unsigned long long* out) {
   double m = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    m = fmax(m, sqrt(fabs((double)A[i])) * exp((1.0 + g[i]) * lmu));
+    m = fmax(m, sqrt(fabs((double)A[i])) * exp((off + g[i]) * lmu));
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
@@ -208,11 +228,13 @@ int model_suggest_dt(vofl_ctx* c, double courant, double* dt) {
   unsigned long long* d_out = reinterpret_cast<unsigned long long*>(c->d_scratch + RED_BLOCKS + 2);
   VOFL_CUDA(c, cudaMemsetAsync(d_out, 0, sizeof(unsigned long long), c->stream));
   const double lmu = 0.5 * std::log(mu2);
+  const double off = c->general ? 0.0 : 1.0;
   if (c->prec == VOFL_F32)
-    k_omega_max<float><<<grid_for(c->N, 256), 256, 0, c->stream>>>((const float*)c->A, c->d_gamma, c->N, lmu, d_out);
+    k_omega_max<float><<<grid_for(c->N, 256), 256, 0, c->stream>>>((const float*)c->A, c->d_gamma, c->N, lmu, off,
+                                                                    d_out);
   else
     k_omega_max<double><<<grid_for(c->N, 256), 256, 0, c->stream>>>((const double*)c->A, c->d_gamma, c->N, lmu,
-                                                                     d_out);
+                                                                     off, d_out);
   count_launch();
   VOFL_CUDA(c, cudaGetLastError());
   unsigned long long bits = 0;
@@ -254,6 +276,9 @@ int model_from_gamma(vofl_ctx* c, const double* d_gamma, const double* d_c0field
   if (bad) return set_err(c, VOFL_EINVAL, "gamma must lie in [0, 1/2) at every grid point");
   const double g0 = sum / (double)c->N;
   c->gamma0 = g0;
+  c->general = false;
+  c->s01 = 1.0 + g0;  // (-Delta)^{1+gamma}
+  c->s02 = 0.5 + g0;  // (-Delta)^{1/2+gamma}
   if (c->prec == VOFL_F32) {
     k_coeffs<float><<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_gamma, d_c0field, c0, omega0, g0, c->N,
                                                                  (float*)c->delta, (float*)c->A, (float*)c->B);
@@ -261,6 +286,40 @@ int model_from_gamma(vofl_ctx* c, const double* d_gamma, const double* d_c0field
     k_coeffs<double><<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_gamma, d_c0field, c0, omega0, g0, c->N,
                                                                   (double*)c->delta, (double*)c->A, (double*)c->B);
   }
+  count_launch();
+  VOFL_CUDA(c, cudaGetLastError());
+  return VOFL_OK;
+}
+
+// General model: order field s(x) in (0, 2] (kept in c->d_gamma), s0 =
+// grid mean; operator 1 is (-Delta)^{s(x)} (centre s0), operator 2 (centre
+// s0 - 1/2, same delta) is computed alongside and unused by the update.
+int model_from_order(vofl_ctx* c, const double* d_s, double kappa) {
+  int* d_bad = reinterpret_cast<int*>(c->d_scratch + RED_BLOCKS + 1);
+  VOFL_CUDA(c, cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+  k_check_order<<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_s, c->N, d_bad);
+  k_sum_pass1<<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(d_s, c->N, c->d_scratch);
+  k_sum_pass2<<<1, 256, 0, c->stream>>>(c->d_scratch, c->d_scratch + RED_BLOCKS);
+  count_launch(3);
+  VOFL_CUDA(c, cudaGetLastError());
+  double sum = 0;
+  int bad = 0;
+  VOFL_CUDA(c, cudaMemcpyAsync(&sum, c->d_scratch + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad) return set_err(c, VOFL_EINVAL, "the order s must lie in (0, 2] at every grid point");
+  const double s0 = sum / (double)c->N;
+  c->general = true;
+  c->gamma0 = s0 - 1.0;
+  c->s01 = s0;
+  c->s02 = s0 - 0.5;
+  c->kappa = kappa;
+  if (c->prec == VOFL_F32)
+    k_coeffs_general<float><<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_s, s0, kappa, c->N, (float*)c->delta,
+                                                                        (float*)c->A, (float*)c->B);
+  else
+    k_coeffs_general<double><<<grid_for(c->N, 256), 256, 0, c->stream>>>(d_s, s0, kappa, c->N, (double*)c->delta,
+                                                                         (double*)c->A, (double*)c->B);
   count_launch();
   VOFL_CUDA(c, cudaGetLastError());
   return VOFL_OK;

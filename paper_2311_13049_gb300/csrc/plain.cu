@@ -166,7 +166,7 @@ struct Plain : Engine {
   }
 
   int set_model(vofl_ctx* c) override {
-    if (make_plain_tables<T>(c->ndim, c->n, c->lo, c->hi, 1.0 + c->gamma0, 0.5 + c->gamma0, P1, P2, Lg, c->stream))
+    if (make_plain_tables<T>(c->ndim, c->n, c->lo, c->hi, c->s01, c->s02, P1, P2, Lg, c->stream))
       return cuda_err(c, cudaGetLastError(), "plain tables");
     return VOFL_OK;
   }
@@ -253,6 +253,7 @@ struct Plain : Engine {
     double hd = 1.0;
     for (int i = 0; i < c->ndim; ++i) hd *= (c->hi[i] - c->lo[i]) / (double)c->n[i];
     e.src_scale = c->dt * c->dt / hd;
+    epi_model(c, &e);
     k_update<T><<<grid_for(N), 256, 0, c->stream>>>(acc1, acc2, e, N);
     count_launch();
     cudaError_t err = cudaGetLastError();

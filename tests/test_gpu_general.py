@@ -1,0 +1,136 @@
+"""The general variable-order model on the GPU (vofl_set_order):
+u_tt = -kappa (-Delta)^{s(x)} u + f(u), stepped by leap-frog (Eq. (3.4)).
+
+- The paper's Table 3 (Sec. 3.2: LFFP temporal errors for Eq. (4.1) on
+  [-32, 32], h = 1/64, M = 15, f(u) = u^3, reference dt = 1e-4 at t = 1) is
+  reproduced by the GPU's FP64 path to the printed four digits, including
+  the "unstable" cells.
+- The generic operator (-Delta)^{s(x)} (s = 1 - 0.4 cos(pi x/4) cos(pi y/4),
+  the shape of the paper's 2D example, M = 20) matches the FP64 oracle.
+- Short general-model runs of the fused FP32 and FP64 paths match the
+  oracle's stepper."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _table3(golden_dir):
+    rows = {}
+    with open(os.path.join(golden_dir, "table3_lffp_temporal_errors.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[int(p[0])] = [None if v == "unstable" else float(v) for v in p[1:]]
+    return rows
+
+
+def _gpu_general(V, shape, s, u0, dt, nsteps, M, f3, impl, prec, lo=None, hi=None):
+    ty = np.float32 if prec == V.F32 else np.float64
+    with V.Solver(shape, lo, hi, prec, impl) as sv:
+        sv.set_order(np.ascontiguousarray(s, dtype=np.float64), kappa=1.0, f3=f3)
+        sv.set_M(M)
+        sv.set_state(np.ascontiguousarray(u0, dtype=ty))
+        sv.step(nsteps, dt)
+        out = sv.get_state()
+        sv.sync()
+        return out.astype(np.float64)
+
+
+@pytest.mark.parametrize("col,order", [(3, "s1"), (4, "s2")])
+def test_paper_table3_on_the_gpu(V, golden_dir, col, order):
+    rows = _table3(golden_dir)
+    J, lo, hi = 4096, [-32.0], [32.0]
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s = 1.0 + 0.3 * np.sin(np.pi * x / 8) if order == "s1" else 1.0 + 0.2 * np.tanh(np.cos(np.pi * x / 8))
+    run = lambda dt, n: _gpu_general(V, (J,), s, phi, dt, n, 15, 1.0, V.IMPL_PLAIN, V.F64, lo, hi)  # noqa: E731
+    ref = run(1e-4, 10000)
+    for p in range(7, 12):
+        printed = rows[p][col]
+        u = run(2.0 ** -p, 2 ** p)
+        if printed is None:
+            assert not np.all(np.isfinite(u)) or np.max(np.abs(u)) > 1e3, p
+        else:
+            err = O.l2_error(u, ref, [1.0 / 64])
+            assert abs(err - printed) <= 0.0006 * printed, (order, p, err, printed)
+
+
+def _s2d(shape, lo, hi):
+    x, y = S.mesh(shape, lo, hi)
+    return 1.0 - 0.4 * np.cos(np.pi * x / 4) * np.cos(np.pi * y / 4)
+
+
+@pytest.mark.parametrize("impl,prec,tol", [("fused", "f32", 1e-5), ("plain", "f64", 1e-11)])
+def test_generic_operator_2d(V, impl, prec, tol):
+    import torch
+    shape, lo, hi = (512, 512), [-8.0, -8.0], [8.0, 8.0]
+    s = _s2d(shape, lo, hi)
+    u = S.q_lowpass(shape, 31, qmin=-1.0, qmax=1.0, sigma_k=40.0)
+    P = V.F32 if prec == "f32" else V.F64
+    ty, tty = (np.float32, torch.float32) if P == V.F32 else (np.float64, torch.float64)
+    im = V.IMPL_FUSED if impl == "fused" else V.IMPL_PLAIN
+    uin = u.astype(ty)
+    with V.Solver(shape, lo, hi, P, im) as sv:
+        sv.set_order(s)
+        sv.set_M(20)
+        ut = torch.from_numpy(uin).cuda()
+        out = torch.empty_like(ut)
+        sv.apply(V.OP_S, ut, out)
+        sv.sync()
+        g = out.cpu().numpy().astype(np.float64)
+        with pytest.raises(V.VoflError):
+            sv.apply(V.OP_1PG, ut, out)  # not an operator of the general model
+    r = O.matrix_free_operator(uin.astype(np.float64), s, 20, lo, hi)
+    assert rel_l2(g, r) <= tol, rel_l2(g, r)
+
+
+@pytest.mark.parametrize("n,prec,tol", [(4096, "f32", 1e-4), (2048, "f64", 1e-10)])
+def test_general_run_fused_1d(V, n, prec, tol):
+    """s1 of Table 3 on [-32, 32] with f(u) = u^3, 256 steps of dt = 2^-9."""
+    lo, hi = [-32.0], [32.0]
+    x = S.axis(n, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s = 1.0 + 0.3 * np.sin(np.pi * x / 8)
+    P = V.F32 if prec == "f32" else V.F64
+    ty = np.float32 if P == V.F32 else np.float64
+    g = _gpu_general(V, (n,), s, phi, 2.0 ** -9, 256, 15, 1.0, V.IMPL_FUSED, P, lo, hi)
+    r = O.general_lffp(s, 1.0, lambda u: u ** 3, phi.astype(ty).astype(np.float64), None, 2.0 ** -9, 256, 15, lo, hi)
+    assert rel_l2(g, r) <= tol, rel_l2(g, r)
+
+
+def test_general_run_fused_2d_against_oracle(V):
+    """A 2D general-model run (linear, f = 0) on the fused FP32 path."""
+    shape, lo, hi = (128, 128), [-8.0, -8.0], [8.0, 8.0]
+    s = _s2d(shape, lo, hi)
+    u0 = S.gaussian_pulse(shape, 6.0)
+    g = _gpu_general(V, shape, s, u0, 2e-3, 60, 20, 0.0, V.IMPL_FUSED, V.F32, lo, hi)
+    r = O.general_lffp(s, 1.0, lambda u: 0.0 * u, u0.astype(np.float32).astype(np.float64), None, 2e-3, 60, 20,
+                       lo, hi)
+    assert rel_l2(g, r) <= 1e-4, rel_l2(g, r)
+
+
+def test_model_switch_and_checks(V):
+    shape = (64, 64)
+    with V.Solver(shape) as sv:
+        with pytest.raises(V.VoflError):
+            sv.set_order(np.full(shape, 2.5))  # s outside (0, 2]
+        with pytest.raises(V.VoflError):
+            sv.set_order(np.ones(shape), kappa=0.0)
+        sv.set_order(np.full(shape, 0.8), kappa=2.0)
+        dt = sv.suggest_dt(0.25)
+        # constant s: omega_max = sqrt(kappa) |mu_max|^s
+        mu = np.sqrt(2.0) * np.pi * 64 / (2 * np.pi)
+        assert dt == pytest.approx(0.5 / (np.sqrt(2.0) * mu ** 0.8), rel=1e-6)
+        sv.set_q(S.q_lowpass(shape, 1))  # back to the seismic model
+        import torch
+        ut = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        with pytest.raises(V.VoflError):
+            sv.apply(V.OP_S, ut, torch.empty_like(ut))
