@@ -19,7 +19,9 @@ is Mpoint-steps/s = 1024^2 * 1000 * runs / time.
          of each model) advanced together by one batch (vofl_batch_*),
          autotuned, timed over the whole 300-step run;
   configs  the 1D 256 FP64 (M = 8, 200 steps) and 3D 256^3 FP32 (M = 8,
-         500 steps) runs, fused and plain;
+         500 steps) runs, fused and plain; the general model of the
+         paper's Table 3 on the FP64 path (timed reference run, errors
+         beside the printed ones) and the generic 2D operator apply;
   serve  continuous batching of a Poisson request stream (mean 200 per
          second, seed 5; 1D 4096 / 2D 512^2 / 2D 1024^2 / 3D 128^3 with equal
          probability, 100..2000 steps, M 8..16) served in real time:
@@ -305,12 +307,87 @@ def configs_bench(V, torch, stream, flush, reps=3):
     out["1d_256_f64"] = {"workload": "1D 256, FP64, M=8, Q = 20 + 15 sin x, u0 = exp(-20 x^2), dt = 1e-3, "
                                      "200 steps (one run incl. model set-up)",
                          "fused": f, "plain": p, "fused_over_plain": f["value"] / p["value"]}
+    out["general_table3_s1_1d_4096_f64"] = table3_bench(V, S, stream)
+    out["generic_apply_2d_512_M20_f32"] = generic_apply_bench(V, S, torch, stream)
     w3 = S.workload_3d_256()
     f, p = run(w3, V.F32, V.IMPL_FUSED), run(w3, V.F32, V.IMPL_PLAIN)
     out["3d_256_f32"] = {"workload": "3D 256^3, FP32, M=8, two-layer Q (10/80), Gaussian pulse sigma = 4 cells, "
                                      "dt = 2e-3, 500 steps (one run incl. model set-up)",
                          "fused": f, "plain": p, "fused_over_plain": f["value"] / p["value"]}
     return out
+
+
+# Table 3 of the paper (Sec. 3.2), column s1(x) = 1 + 0.3 sin(pi x/8):
+# printed LFFP temporal errors at t = 1 for dt = 2^-p
+TABLE3_S1 = {9: 3.531e-7, 10: 8.758e-8, 11: 2.120e-8}
+
+
+def table3_bench(V, S, stream):
+    """The general model of the paper's Table 3 (Eq. (4.1): [-32, 32],
+    h = 1/64, M = 15, f(u) = u^3, u0 = exp(-x^2)) on the GPU's FP64 path:
+    the dt = 1e-4 reference run to t = 1 is timed; the errors of the
+    dt = 2^-p runs against it are reported beside the printed ones."""
+    import torch
+    J = 4096
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s1 = 1.0 + 0.3 * np.sin(np.pi * x / 8)
+
+    def run(dt, n, timed=False):
+        with V.Solver((J,), [-32.0], [32.0], V.F64, V.IMPL_PLAIN, stream=stream.cuda_stream) as sv:
+            sv.set_order(s1, kappa=1.0, f3=1.0)
+            sv.set_M(15)
+            sv.set_state(phi)
+            ms = None
+            with torch.cuda.stream(stream):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sv.step(n, dt)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+            u = sv.get_state()
+            sv.sync()
+        return u, ms
+
+    run(2.0 ** -9, 16)  # warm-up (plans, graphs)
+    ref, ms = run(1e-4, 10000, timed=True)
+    errs = {}
+    for p, printed in TABLE3_S1.items():
+        u, _ = run(2.0 ** -p, 2 ** p)
+        errs[str(p)] = {"gpu": float(np.sqrt((1.0 / 64) * np.sum((u - ref) ** 2))), "printed": printed}
+    return {"workload": "1D 4096 on [-32,32], FP64 plain path, M=15, s1 = 1 + 0.3 sin(pi x/8), f = u^3, "
+                        "reference run dt = 1e-4 to t = 1 (10000 steps, timed)",
+            "value": J * 10000 / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_run": ms, "l2_error_vs_reference": errs}
+
+
+def generic_apply_bench(V, S, torch, stream, reps=20):
+    """(-Delta)^{s(x)} u at 512^2 on [-8,8]^2, s = 1 - 0.4 cos(pi x/4)
+    cos(pi y/4), M = 20 (the shape of the paper's 2D example): one apply,
+    fused FP32 and plain FP32, CUDA events over `reps` applies."""
+    shape, lo, hi = (512, 512), [-8.0, -8.0], [8.0, 8.0]
+    xg, yg = S.mesh(shape, lo, hi)
+    so = 1.0 - 0.4 * np.cos(np.pi * xg / 4) * np.cos(np.pi * yg / 4)
+    u = torch.from_numpy(S.random_field(shape, 3).astype(np.float32)).cuda()
+    res = {}
+    for nm, im in (("fused", V.IMPL_FUSED), ("plain", V.IMPL_PLAIN)):
+        with V.Solver(shape, lo, hi, V.F32, im, stream=stream.cuda_stream) as sv:
+            sv.set_order(so)
+            sv.set_M(20)
+            out = torch.empty_like(u)
+            with torch.cuda.stream(stream):
+                sv.apply(V.OP_S, u, out)
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    sv.apply(V.OP_S, u, out)
+                e1.record(stream)
+                e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        res[nm] = {"ms_per_apply": ms, "value": 512 * 512 / (ms * 1e-3) / 1e6, "unit": "Mpoint/s"}
+    res["fused_over_plain"] = res["plain"]["ms_per_apply"] / res["fused"]["ms_per_apply"]
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -501,6 +578,23 @@ def run_gpu(args):
     final = fused.get_state()  # wavefield after the last run (host)
 
     lffp_fused = steady_step_ms(fused)
+    # adaptive M: the Taylor power the remainder rule picks for this model
+    # at 1e-8, its step time, and its apply against M = 16 (same FP32 path)
+    adaptive = None
+    if rank == 0:
+        M_ad = fused.suggest_M(1e-8)
+        fused.set_M(M_ad)
+        ms_ad = steady_step_ms(fused)
+        ut = torch.from_numpy(final).cuda()
+        o_ad = [torch.empty_like(ut), torch.empty_like(ut)]
+        fused.apply_pair(ut, *o_ad)
+        fused.set_M(M)
+        o16 = [torch.empty_like(ut), torch.empty_like(ut)]
+        fused.apply_pair(ut, *o16)
+        fused.sync()
+        adaptive = {"tol": 1e-8, "M": M_ad, "ms_per_lffp_step": ms_ad, "speedup_vs_M16": lffp_fused / ms_ad,
+                    "apply_rel_l2_vs_M16": [float(torch.linalg.norm(a.double() - b.double()) /
+                                                  torch.linalg.norm(b.double())) for a, b in zip(o_ad, o16)]}
     plain = make(V.IMPL_PLAIN)
     kp = max(1, min(args.steps, 3))
     ms_plain = timed(plain, False, kp, 1)
@@ -569,7 +663,7 @@ def run_gpu(args):
                         "d2h_bytes_per_step": int(out_host.numel() * 4)},
                 "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": ms_plain / kp, "steps": kp,
                           "ms_per_lffp_step": lffp_plain},
-                "ms_per_lffp_step": lffp_fused,
+                "ms_per_lffp_step": lffp_fused, "adaptive_M": adaptive,
                 "fused_over_plain": value / plain_value,
                 "accuracy": acc, "gpu_launches": gpu_launches, "roofline": roof,
                 "cpu_baseline": cpu, "clocks": clk, "batch": batch, "configs": configs, "serve": serve_res}

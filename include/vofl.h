@@ -173,6 +173,16 @@ VOFL_API int vofl_query(vofl_ctx* ctx);
  * VOFL_EINVAL, VOFL_ESTATE (no model) or VOFL_ECUDA. */
 VOFL_API int vofl_suggest_dt(vofl_ctx* ctx, double courant, double* dt);
 
+/* Taylor power for a truncation tolerance (Sec. 2.2, the choice of M):
+ * the smallest M in [0, 40] with a^{M+1}/(M+1)! e^{2a} <= tol, where
+ * a = max_x |s(x) - s0| * max_k |ln |mu_k|^2| (k != 0): every mode's weight
+ * |mu_k|^{2 s0} exp((s(x) - s0) ln|mu_k|^2) of Eq. (2.13) is then
+ * reproduced to relative error tol by the terms m = 0..M (Taylor
+ * remainder).  *M receives it (40 if none suffices); the context's M is not
+ * changed (vofl_set_M).  Blocks until done.  Returns VOFL_OK, VOFL_EINVAL,
+ * VOFL_ESTATE (no model) or VOFL_ECUDA. */
+VOFL_API int vofl_suggest_M(vofl_ctx* ctx, double tol, int* M);
+
 /* Number of steps taken in the current run. */
 VOFL_API int64_t vofl_steps_taken(const vofl_ctx* ctx);
 

@@ -21,6 +21,9 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   suggested_dt                     pinned: gamma = 0 closed form and the
                                    stability of the single-mode recurrence of
                                    the step on both sides of the bound.
+  suggested_M                      pinned: the truncation error of O2 at the
+                                   chosen M (against O2 at M = 40) is within
+                                   the tolerance.
 
 Conventions (the readings of the paper are listed in the design doc):
   * arrays are indexed [z][y][x] (x fastest); `lo`, `hi` are (x, y, z) ordered;
@@ -40,7 +43,7 @@ __all__ = [
     "seismic_coefficients", "seismic_coefficients_from_gamma",
     "dense_operator", "matrix_free_operator", "matrix_free_terms",
     "seismic_operators", "seismic_lffp", "general_lffp",
-    "l2_error", "rel_l2", "taylor_remainder_bound", "suggested_dt",
+    "l2_error", "rel_l2", "taylor_remainder_bound", "suggested_dt", "suggested_M",
 ]
 
 
@@ -320,6 +323,32 @@ def seismic_lffp(gamma, c0, omega0, u0, v0, dt, nsteps, M, lo=None, hi=None,
         if return_all:
             history.append(u.copy())
     return (u, history) if return_all else u
+
+
+def suggested_M(s, shape, lo=None, hi=None, tol=1e-8, M_max=40):
+    """Smallest M with max_k R_M <= tol, R_M = a^{M+1}/(M+1)! e^{2a},
+    a = max_x |s(x) - s0| * max_k |ln |mu_k|^2| (k != 0), s0 = grid mean.
+
+    Reading: in Eq. (2.13) the mode k at x carries |mu_k|^{2 s0}
+    exp(delta(x) ln|mu_k|^2); truncating the exponential series after the
+    power M leaves at most |z|^{M+1}/(M+1)! e^{|z|} (z = delta ln|mu|^2,
+    Taylor remainder), i.e. at most R_M relative to the mode's exact weight
+    |mu_k|^{2s0} e^{z} >= |mu_k|^{2s0} e^{-|z|}.  The paper's indicator
+    e(M, mu_k) (Sec. 2.2) assumes only |s - s0| < 1; this uses the model's
+    own |delta|."""
+    s = np.asarray(s, dtype=np.float64)
+    d, a_lo, b_hi = _dims(shape, lo, hi)
+    L = [b_hi[i] - a_lo[i] for i in range(d)]
+    mu_min = min(2.0 * math.pi / Li for Li in L)
+    mu_max = math.sqrt(sum((math.pi * shape[d - 1 - i] / L[i]) ** 2 for i in range(d)))
+    lmax = max(abs(math.log(mu_min ** 2)), abs(math.log(mu_max ** 2)))
+    a = float(np.max(np.abs(s - s.mean()))) * lmax
+    term = a * math.exp(2.0 * a)  # R_0
+    for M in range(M_max + 1):
+        if term <= tol:
+            return M
+        term *= a / (M + 2)
+    return M_max
 
 
 def suggested_dt(gamma, c0, omega0, shape, lo=None, hi=None, courant=0.25):

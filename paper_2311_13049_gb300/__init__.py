@@ -47,6 +47,7 @@ SIGNATURES = {
     "vofl_steps_taken": (C.c_int64, [_vp]),
     "vofl_suggest_dt": (C.c_int, [_vp, C.c_double, _dp]),
     "vofl_query": (C.c_int, [_vp]),
+    "vofl_suggest_M": (C.c_int, [_vp, C.c_double, C.POINTER(C.c_int)]),
     "vofl_sync": (C.c_int, [_vp]),
     "vofl_last_error": (C.c_char_p, [_vp]),
     "vofl_footprint_bytes": (C.c_size_t, [C.c_int, _i64p, C.c_int, C.c_int, C.c_int]),
@@ -236,6 +237,12 @@ class Solver:
         dt = C.c_double()
         self._check(lib().vofl_suggest_dt(self._h, float(courant), C.byref(dt)))
         return dt.value
+
+    def suggest_M(self, tol=1e-8):
+        """Smallest Taylor power whose remainder bound is within tol (vofl.h)."""
+        M = C.c_int()
+        self._check(lib().vofl_suggest_M(self._h, float(tol), C.byref(M)))
+        return M.value
 
     def steps_taken(self):
         return int(lib().vofl_steps_taken(self._h))

@@ -409,6 +409,13 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
   return VOFL_OK;
 }
 
+int vofl_suggest_M(vofl_ctx* c, double tol, int* M) {
+  if (int st = check_ctx(c)) return st;
+  if (!M || !(tol > 0) || !std::isfinite(tol)) return set_err(c, VOFL_EINVAL, "bad tol or M pointer");
+  if (!c->model_set) return set_err(c, VOFL_ESTATE, "set the model first");
+  return model_suggest_M(c, tol, 40, M);
+}
+
 int vofl_query(vofl_ctx* c) {
   if (!c) return VOFL_EINVAL;
   const cudaError_t e = cudaStreamQuery(c->stream);

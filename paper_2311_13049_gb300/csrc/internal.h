@@ -225,6 +225,7 @@ void epi_model(const vofl_ctx* c, EpiArgs<T>* e) {
   e->f3 = T(c->f3);
 }
 int model_suggest_dt(vofl_ctx* c, double courant, double* dt);
+int model_suggest_M(vofl_ctx* c, double tol, int M_max, int* M);
 
 // twiddles / tables (model.cu)
 // Twiddle layout of the warp line FFT of length N (fft_warp.cuh): the last

@@ -8,6 +8,7 @@
 //   FFT twiddles exp(-2 pi i r k / N).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -144,6 +145,15 @@ __global__ void k_omega_max(const T* __restrict__ A, const double* __restrict__ 
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// max_x |g(x) - centre| (non-negative doubles order like their bits)
+__global__ void k_abs_dev_max(const double* __restrict__ g, double centre, long long n, unsigned long long* out) {
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(g[i] - centre));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 // Tables in the cuFFT R2C layout [..][nz][ny][nx/2+1] (row-major, x halved),
 // for a forward transform of the discrete Laplacian (symbol lambda, see
 // fused2d.cu): P = |mu|^{2 s0} / (N lambda).
@@ -244,6 +254,43 @@ int model_suggest_dt(vofl_ctx* c, double courant, double* dt) {
   std::memcpy(&wmax, &bits, sizeof(wmax));
   if (!(wmax > 0.0)) return set_err(c, VOFL_EINVAL, "the model has no positive frequency");
   *dt = courant * 2.0 / wmax;
+  return VOFL_OK;
+}
+
+// Smallest M <= M_max whose Taylor remainder bound a^{M+1}/(M+1)! e^{2a}
+// (a = max|delta| max_k |ln|mu_k|^2|, k != 0) is at most tol: the relative
+// truncation error of every mode's weight |mu_k|^{2 s0} exp(delta ln|mu_k|^2)
+// in Eq. (2.13).
+int model_suggest_M(vofl_ctx* c, double tol, int M_max, int* M) {
+  double lmu_min = 1e300, mu2 = 0.0;
+  for (int i = 0; i < c->ndim; ++i) {
+    const double L = c->hi[i] - c->lo[i];
+    lmu_min = std::min(lmu_min, 2.0 * M_PI / L);
+    const double m = M_PI * (double)c->n[i] / L;
+    mu2 += m * m;
+  }
+  const double lmax = std::max(std::fabs(std::log(lmu_min * lmu_min)), std::fabs(std::log(mu2)));
+  unsigned long long* d_out = reinterpret_cast<unsigned long long*>(c->d_scratch + RED_BLOCKS + 3);
+  VOFL_CUDA(c, cudaMemsetAsync(d_out, 0, sizeof(unsigned long long), c->stream));
+  const double centre = c->general ? c->s01 : c->gamma0;  // the field in d_gamma is s or gamma
+  k_abs_dev_max<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->d_gamma, centre, c->N, d_out);
+  count_launch();
+  VOFL_CUDA(c, cudaGetLastError());
+  unsigned long long bits = 0;
+  VOFL_CUDA(c, cudaMemcpyAsync(&bits, d_out, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  double dmax;
+  std::memcpy(&dmax, &bits, sizeof(dmax));
+  const double a = dmax * lmax;
+  double term = a * std::exp(2.0 * a);  // the bound for M = 0
+  for (int m = 0; m <= M_max; ++m) {
+    if (term <= tol) {
+      *M = m;
+      return VOFL_OK;
+    }
+    term *= a / (m + 2);
+  }
+  *M = M_max;
   return VOFL_OK;
 }
 

@@ -134,3 +134,21 @@ def test_model_switch_and_checks(V):
         ut = torch.zeros(shape, dtype=torch.float32, device="cuda")
         with pytest.raises(V.VoflError):
             sv.apply(V.OP_S, ut, torch.empty_like(ut))
+
+
+def test_suggest_M_matches_the_oracle_rule(V):
+    """The library's Taylor-power rule gives the oracle's M (seismic model of
+    the headline kind, and a general model on a larger box)."""
+    shape = (256, 256)
+    Q = S.q_lowpass(shape, 2)
+    g = np.arctan(1.0 / Q) / np.pi
+    with V.Solver(shape) as sv:
+        sv.set_q(Q)
+        for tol in (1e-6, 1e-8, 1e-10):
+            assert sv.suggest_M(tol) == O.suggested_M(1.0 + g, shape, tol=tol)
+    lo, hi = [-8.0, -8.0], [8.0, 8.0]
+    s = _s2d(shape, lo, hi)
+    with V.Solver(shape, lo, hi) as sv:
+        sv.set_order(s)
+        for tol in (1e-6, 1e-10):
+            assert sv.suggest_M(tol) == O.suggested_M(s, shape, lo, hi, tol)

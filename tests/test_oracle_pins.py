@@ -346,3 +346,23 @@ def test_suggested_dt_separates_stable_from_unstable(courant, stable):
     u = O.seismic_lffp(gamma, 1.0, 2 * np.pi, u0, None, dt, 400, 0)
     grew = np.max(np.abs(u)) > 10.0
     assert grew != stable
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8, 1e-12])
+def test_suggested_M_bounds_the_truncation_of_every_mode(tol):
+    """At the rule's M, O2 applied to a single Fourier mode (the one with the
+    smallest and the one with the largest |ln|mu|^2| on [-8, 8], so that
+    ln|mu|^2 takes both signs) reproduces the exact variable-order weight
+    |mu|^{2 s(x)} at every point to within tol of that weight (P1's closed
+    form: (-Delta)^{s(x)} cos(mu (x - a)) = |mu|^{2 s(x)} cos(mu (x - a)))."""
+    J, lo, hi = 64, [-8.0], [8.0]
+    x = S.axis(J, -8.0, 8.0)
+    s = 1.0 + 0.3 * np.sin(np.pi * x / 8)
+    M = O.suggested_M(s, (J,), lo, hi, tol)
+    assert 0 < M < 40
+    for k in (1, J // 2 - 1):
+        mu = 2 * np.pi * k / 16.0
+        u = np.cos(mu * (x + 8.0))
+        got = O.matrix_free_operator(u, s, M, lo, hi)
+        exact = mu ** (2 * s) * u
+        assert np.all(np.abs(got - exact) <= tol * mu ** (2 * s) + 1e-13 * np.max(np.abs(exact))), (k, M)
