@@ -18,6 +18,8 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                                    unpinned" beyond those reductions.
   general_lffp          (O4)       pinned: the paper's printed LFFP temporal
                                    errors (Table 3, Sec. 3.2) are reproduced (P7).
+  general_tsfp2         (O4)       pinned: the paper's printed TSFP2 temporal
+                                   errors (Table 4, Sec. 3.3) are reproduced.
   suggested_dt                     pinned: gamma = 0 closed form and the
                                    stability of the single-mode recurrence of
                                    the step on both sides of the bound.
@@ -44,6 +46,7 @@ __all__ = [
     "dense_operator", "matrix_free_operator", "matrix_free_terms",
     "seismic_operators", "seismic_lffp", "general_lffp",
     "l2_error", "rel_l2", "taylor_remainder_bound", "suggested_dt", "suggested_M",
+    "general_tsfp2",
 ]
 
 
@@ -388,6 +391,50 @@ def general_lffp(s, kappa, f, phi, psi, dt, nsteps, M, lo=None, hi=None,
     for _ in range(1, nsteps):
         u_next = 2.0 * u - u_prev + dt * dt * (-kappa * op(u) + f(u))
         u_prev, u = u, u_next
+        if not np.all(np.isfinite(u)):
+            break
+    return u
+
+
+def general_tsfp2(s, kappa, f, phi, psi, dt, nsteps, M, lo=None, hi=None):
+    """Second-order time-splitting Fourier pseudospectral method (Sec. 3.3,
+    Strang splitting of u_t = v, v_t = -kappa (-Delta)^{s(x)} u + f(u)):
+    per step, the constant-order part u_t = v, v_t = -kappa (-Delta)^{s0} u
+    is integrated exactly in Fourier space over dt/2 (frequency
+    w_k = sqrt(kappa) |mu_k|^{s0}; k = 0 drifts: u += t v), then the rest
+    u_t = 0, v_t = -kappa [(-Delta)^{s(x)} - (-Delta)^{s0}] u + f(u) exactly
+    over dt, then the first part again over dt/2.  The difference operator
+    is the matrix-free sum of Eq. (2.13) without its m = 0 term (readings of
+    the printed typos: |mu|^{2 s0} in the constant-order symbol, one u_hat
+    factor in v_hat, no kappa inside the difference operator, the kick
+    v += dt (-kappa (...) + f(u)), and steps n = 0, 1, ...).  Returns
+    u^{nsteps}; u^0 = phi, v^0 = psi exactly."""
+    u = np.asarray(phi, dtype=np.float64).copy()
+    v = np.zeros_like(u) if psi is None else np.asarray(psi, dtype=np.float64).copy()
+    s = np.broadcast_to(np.asarray(s, dtype=np.float64), u.shape)
+    s0 = float(np.mean(s))
+    delta = s - s0
+    w = np.sqrt(kappa) * mu2(u.shape, lo, hi) ** (s0 / 2.0)
+    moving = w > 0
+    wsafe = np.where(moving, w, 1.0)
+
+    def linear(u, v, t):
+        uh, vh = np.fft.fftn(u), np.fft.fftn(v)
+        c, sn = np.cos(w * t), np.sin(w * t)
+        uh2 = np.where(moving, uh * c + vh * sn / wsafe, uh + t * vh)
+        vh2 = np.where(moving, -wsafe * uh * sn + vh * c, vh)
+        return np.fft.ifftn(uh2).real, np.fft.ifftn(vh2).real
+
+    for _ in range(nsteps):
+        u, v = linear(u, v, 0.5 * dt)
+        terms = matrix_free_terms(u, s0, M, lo, hi)
+        diff = np.zeros_like(u)
+        dpow = np.ones_like(u)
+        for m in range(1, M + 1):
+            dpow = dpow * delta
+            diff = diff + dpow * terms[m]
+        v = v + dt * (-kappa * diff + f(u))
+        u, v = linear(u, v, 0.5 * dt)
         if not np.all(np.isfinite(u)):
             break
     return u

@@ -366,3 +366,53 @@ def test_suggested_M_bounds_the_truncation_of_every_mode(tol):
         got = O.matrix_free_operator(u, s, M, lo, hi)
         exact = mu ** (2 * s) * u
         assert np.all(np.abs(got - exact) <= tol * mu ** (2 * s) + 1e-13 * np.max(np.abs(exact))), (k, M)
+
+
+def _table4(golden_dir):
+    rows = {}
+    with open(os.path.join(golden_dir, "table4_tsfp2_temporal_errors.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[int(p[0])] = [None if v == "unstable" else float(v) for v in p[1:]]
+    return rows
+
+
+def test_paper_table4_tsfp2_variable_order(golden_dir):
+    """Column s1 of Table 4 (TSFP2): errors at dt = 2^-9..2^-11 against the
+    dt = 1e-4 reference reproduce the printed four digits; dt = 2^-7, 2^-8
+    blow up ("unstable")."""
+    rows = _table4(golden_dir)
+    J, lo, hi = 4096, [-32.0], [32.0]
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s1 = 1.0 + 0.3 * np.sin(np.pi * x / 8)
+    cube = lambda u: u ** 3  # noqa: E731
+    ref = O.general_tsfp2(s1, 1.0, cube, phi, None, 1e-4, 10000, 15, lo, hi)
+    for p in (9, 10, 11):
+        u = O.general_tsfp2(s1, 1.0, cube, phi, None, 2.0 ** -p, 2 ** p, 15, lo, hi)
+        err = O.l2_error(u, ref, [1.0 / 64])
+        printed = rows[p][3]
+        assert abs(err - printed) <= 0.0006 * printed, (p, err, printed)
+    for p in (7, 8):
+        assert rows[p][3] is None
+        with np.errstate(all="ignore"):
+            u = O.general_tsfp2(s1, 1.0, cube, phi, None, 2.0 ** -p, 2 ** p, 15, lo, hi)
+        assert not np.all(np.isfinite(u)) or np.max(np.abs(u)) > 1e3
+
+
+def test_paper_table4_tsfp2_constant_order_column(golden_dir):
+    """Column s = 1 of Table 4: the splitting is stable for constant order at
+    every printed dt, with the printed errors."""
+    rows = _table4(golden_dir)
+    J, lo, hi = 4096, [-32.0], [32.0]
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    cube = lambda u: u ** 3  # noqa: E731
+    ref = O.general_tsfp2(1.0, 1.0, cube, phi, None, 1e-4, 10000, 0, lo, hi)
+    for p in range(7, 12):
+        u = O.general_tsfp2(1.0, 1.0, cube, phi, None, 2.0 ** -p, 2 ** p, 0, lo, hi)
+        err = O.l2_error(u, ref, [1.0 / 64])
+        printed = rows[p][1]
+        assert abs(err - printed) <= 0.0006 * printed, (p, err, printed)
