@@ -73,6 +73,14 @@ typedef enum {
   VOFL_OP_S = 2    /* (-Delta)^{s(x)} of the general model (vofl_set_order) */
 } vofl_op;
 
+/* Time stepping of vofl_step: the leap-frog scheme (Eq. (3.4); both
+ * models) or the second-order time splitting of Sec. 3.3 (general model
+ * only, plain path). */
+typedef enum {
+  VOFL_SCHEME_LFFP = 0,
+  VOFL_SCHEME_TSFP2 = 1
+} vofl_scheme;
+
 /* Implementation of the operator/step: the fused hand-written kernels, or
  * the plain baseline (cuFFT transforms + separate multiply / accumulate /
  * update kernels, same arithmetic). */
@@ -116,6 +124,18 @@ VOFL_API int vofl_set_order(vofl_ctx* ctx, const double* s, int on_device, doubl
  * when NULL the scalar c0 is used. */
 VOFL_API int vofl_set_gamma(vofl_ctx* ctx, const double* gamma, const double* c0_field,
                    int on_device, double c0, double omega0);
+
+/* Select the time-stepping scheme of vofl_step (vofl_scheme).  The time
+ * splitting (Sec. 3.3) integrates u_t = v, v_t = -kappa (-Delta)^{s0} u
+ * exactly in Fourier space over dt/2, kicks v by
+ * dt (-kappa [(-Delta)^{s(x)} - (-Delta)^{s0}] u + f(u)) (the terms
+ * m = 1..M of Eq. (2.13)), and repeats the half rotation; the state is
+ * (u, v) with v^0 = the v0 of vofl_set_state, and no point source is
+ * applied.  It needs the general model (vofl_set_order) and the plain
+ * path (VOFL_IMPL_PLAIN), else vofl_step returns VOFL_EUNSUPPORTED.
+ * Returns VOFL_OK, VOFL_EINVAL (unknown scheme) or VOFL_ESTATE (a run is
+ * in progress: set the state first). */
+VOFL_API int vofl_set_scheme(vofl_ctx* ctx, int scheme);
 
 /* Highest Taylor power M of Eq. (2.13): each operator apply runs the M+1
  * terms m = 0..M.  0 <= M <= 40.  Default 8. */

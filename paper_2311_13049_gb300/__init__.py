@@ -23,6 +23,7 @@ _LIB = None
 F32, F64 = 0, 1
 OP_1PG, OP_HPG, OP_S = 0, 1, 2
 IMPL_FUSED, IMPL_PLAIN = 0, 1
+SCHEME_LFFP, SCHEME_TSFP2 = 0, 1
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ESTATE",
            -6: "EUNSUPPORTED"}
 
@@ -38,6 +39,7 @@ SIGNATURES = {
     "vofl_set_gamma": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, C.c_double]),
     "vofl_set_order": (C.c_int, [_vp, _vp, C.c_int, C.c_double, C.c_double, C.c_double]),
     "vofl_set_M": (C.c_int, [_vp, C.c_int]),
+    "vofl_set_scheme": (C.c_int, [_vp, C.c_int]),
     "vofl_apply": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "vofl_apply_pair": (C.c_int, [_vp, _vp, _vp, _vp]),
     "vofl_set_state": (C.c_int, [_vp, _vp, _vp, C.c_int]),
@@ -194,6 +196,10 @@ class Solver:
         """General model u_tt = -kappa (-Delta)^{s(x)} u + f1 u + f3 u^3."""
         p, dev = _ptr(s, np.float64, "s")
         self._check(lib().vofl_set_order(self._h, p, dev, float(kappa), float(f1), float(f3)))
+
+    def set_scheme(self, scheme):
+        """SCHEME_LFFP (default) or SCHEME_TSFP2 (general model, plain path)."""
+        self._check(lib().vofl_set_scheme(self._h, int(scheme)))
 
     def set_M(self, M):
         self._check(lib().vofl_set_M(self._h, int(M)))

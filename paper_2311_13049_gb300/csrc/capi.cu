@@ -38,6 +38,8 @@ vofl_ctx::GraphKey current_key(const vofl_ctx* c) {
   k.nsrc = c->nsrc;
   k.f1 = c->general ? c->f1 : 0.0;
   k.f3 = c->general ? c->f3 : 0.0;
+  k.kappa = c->general ? c->kappa : 0.0;
+  k.scheme = c->scheme;
   return k;
 }
 
@@ -101,6 +103,57 @@ int capture_step(vofl_ctx* c) {
   }
   c->step_graph[c->cur] = ex;
   c->step_graph_kernels = c->eng->kernels_per_step(c);
+  return VOFL_OK;
+}
+
+// Capture one step of the time splitting into the graph slot of `cur`.
+int capture_split(vofl_ctx* c) {
+  const uint64_t before = g_kernel_launches.load();
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return VOFL_EUNSUPPORTED;
+  }
+  int st = c->eng->step_split(c);
+  e = cudaStreamEndCapture(c->stream, &g);
+  const uint64_t n = g_kernel_launches.load() - before;
+  g_kernel_launches.store(before);
+  if (st != VOFL_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return VOFL_EUNSUPPORTED;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return VOFL_EUNSUPPORTED;
+  }
+  c->step_graph[c->cur] = ex;
+  c->step_graph_kernels = n;
+  return VOFL_OK;
+}
+
+// one step of the time splitting (u, v in place; `cur` does not change)
+int split_step(vofl_ctx* c) {
+  const vofl_ctx::GraphKey key = current_key(c);
+  if (!(key == c->graph_key)) {
+    drop_graphs(c);
+    c->graph_key = key;
+  }
+  if (c->graphs_ok && !c->step_graph[c->cur]) {
+    if (capture_split(c) != VOFL_OK) c->graphs_ok = false;
+  }
+  if (c->graphs_ok && c->step_graph[c->cur]) {
+    VOFL_CUDA(c, cudaGraphLaunch(c->step_graph[c->cur], c->stream));
+    count_launch(c->step_graph_kernels);
+  } else {
+    int st = c->eng->step_split(c);
+    if (st) return st;
+  }
+  c->steps += 1;
   return VOFL_OK;
 }
 
@@ -382,9 +435,28 @@ int vofl_set_source(vofl_ctx* c, const int64_t* idx, const double* samples, int6
   return VOFL_OK;
 }
 
+int vofl_set_scheme(vofl_ctx* c, int scheme) {
+  if (int st = check_ctx(c)) return st;
+  if (scheme != VOFL_SCHEME_LFFP && scheme != VOFL_SCHEME_TSFP2) return set_err(c, VOFL_EINVAL, "unknown scheme");
+  if (c->steps > 0 && scheme != c->scheme) return set_err(c, VOFL_ESTATE, "a run is in progress; set the state first");
+  c->scheme = scheme;
+  return VOFL_OK;
+}
+
 int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
   if (int st = check_ctx(c)) return st;
   if (nsteps < 0) return set_err(c, VOFL_EINVAL, "bad nsteps");
+  if (c->scheme == VOFL_SCHEME_TSFP2) {
+    if (!c->general || !c->eng->can_split())
+      return set_err(c, VOFL_EUNSUPPORTED, "the time splitting needs the general model and the plain path");
+    if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
+    if (!(dt > 0) || !std::isfinite(dt)) return set_err(c, VOFL_EINVAL, "bad dt");
+    if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");
+    c->dt = dt;
+    for (int64_t i = 0; i < nsteps; ++i)
+      if (int st = split_step(c)) return st;
+    return VOFL_OK;
+  }
   if (int st = prepare_run(c, dt)) return st;
   if (nsteps == 0) return VOFL_OK;
   if (c->eng->can_run()) {

@@ -113,6 +113,7 @@ struct vofl_ctx {
   double gamma0 = 0;      // seismic: grid mean of gamma
   double s01 = 1, s02 = 0.5;  // expansion orders of the two operators (Eq. (2.13))
   double kappa = 1, f1 = 0, f3 = 0;
+  int scheme = VOFL_SCHEME_LFFP;  // time stepping of vofl_step
   void* delta = nullptr;  // gamma - gamma0        (prec)
   void* A = nullptr;      // c^2 eta               (prec)
   void* B = nullptr;      // c^2 tau               (prec)
@@ -149,10 +150,11 @@ struct vofl_ctx {
     long long src_flat = -2;
     const double* d_src = nullptr;
     int64_t nsrc = -1;
-    double f1 = 0, f3 = 0;
+    double f1 = 0, f3 = 0, kappa = 0;
+    int scheme = 0;
     bool operator==(const GraphKey& o) const {
       return dt == o.dt && M == o.M && src_flat == o.src_flat && d_src == o.d_src && nsrc == o.nsrc && f1 == o.f1 &&
-             f3 == o.f3;
+             f3 == o.f3 && kappa == o.kappa && scheme == o.scheme;
     }
   } graph_key;
 
@@ -188,6 +190,13 @@ struct Engine {
   // first_mode: EPI_START or EPI_STEP); the context's cur/steps are updated
   // by the caller
   virtual bool can_run() const { return false; }
+  // engines with the second-order time splitting (Sec. 3.3) of the general
+  // model: one step, u = u[cur] and v = u[1 - cur] updated in place
+  virtual bool can_split() const { return false; }
+  virtual int step_split(vofl_ctx* c) {
+    (void)c;
+    return VOFL_EUNSUPPORTED;
+  }
   virtual int run(vofl_ctx* c, int64_t nsteps, int first_mode) {
     (void)c;
     (void)nsteps;

@@ -10,6 +10,9 @@
 //   pointwise update                                          (kernel)
 // Works for 1D, 2D, 3D and for float or double.  It keeps every field in
 // memory between kernels; that traffic is what the fused path removes.
+// For the general model it also runs the second-order time splitting of
+// Sec. 3.3 (step_split): exact half-step rotations of (u_hat, v_hat) in
+// Fourier space, the variable-order kick (terms m >= 1), the rotations again.
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -53,12 +56,76 @@ __global__ void k_mult(const C* __restrict__ uh, const T* __restrict__ P, const 
 }
 
 template <typename T>
-__global__ void k_acc(const T* __restrict__ Y, const T* __restrict__ delta, int m, T* __restrict__ acc, long long n) {
+__global__ void k_acc(const T* __restrict__ Y, const T* __restrict__ delta, int m, int first, T* __restrict__ acc,
+                      long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     T w = T(1);
     const T d = delta[i];
     for (int j = 0; j < m; ++j) w *= d;
-    acc[i] = (m == 0 ? T(0) : acc[i]) + w * Y[i];
+    acc[i] = (first ? T(0) : acc[i]) + w * Y[i];
+  }
+}
+
+// Time splitting (Sec. 3.3): the exact flow of u_t = v, v_t = -kappa
+// (-Delta)^{s0} u over time t, mode by mode on the R2C half spectra of u
+// and v (unnormalised transforms: the 1/N goes in here); w_k = sqrt(kappa)
+// |mu_k|^{s0}, and the k = 0 mode drifts (u += t v).
+template <typename T, typename C>
+__global__ void k_rotate(C* __restrict__ uh, C* __restrict__ vh, const T* __restrict__ W, T t, T invN,
+                         long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T w = W[i];
+    const C a = uh[i], b = vh[i];
+    C a2, b2;
+    if (w > T(0)) {
+      T sn, cs;
+      if constexpr (sizeof(T) == 8)
+        sincos(w * t, &sn, &cs);
+      else
+        sincosf(w * t, &sn, &cs);
+      const T q = sn / w;
+      a2.x = a.x * cs + b.x * q;
+      a2.y = a.y * cs + b.y * q;
+      b2.x = b.x * cs - a.x * w * sn;
+      b2.y = b.y * cs - a.y * w * sn;
+    } else {
+      a2.x = a.x + t * b.x;
+      a2.y = a.y + t * b.y;
+      b2 = b;
+    }
+    a2.x *= invN;
+    a2.y *= invN;
+    b2.x *= invN;
+    b2.y *= invN;
+    uh[i] = a2;
+    vh[i] = b2;
+  }
+}
+
+// w_k = sqrt(kappa) |mu_k|^{s0} on the R2C layout [nz][ny][nx/2+1] (double, rounded once)
+template <typename T>
+__global__ void k_omega_table(int nx, int ny, int nz, double lx, double ly, double lz, double s0, double kappa,
+                              T* __restrict__ W) {
+  const int H = nx / 2 + 1;
+  const long long n = (long long)H * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % H);
+    const int ky0 = (int)((i / H) % ny), kz0 = (int)(i / ((long long)H * ny));
+    const int ky = ky0 < ny / 2 ? ky0 : ky0 - ny, kz = kz0 < nz / 2 ? kz0 : kz0 - nz;
+    const double m1 = 2.0 * M_PI * kx / lx, m2 = 2.0 * M_PI * ky / ly, m3 = 2.0 * M_PI * kz / lz;
+    const double mu2 = m1 * m1 + (ny > 1 ? m2 * m2 : 0.0) + (nz > 1 ? m3 * m3 : 0.0);
+    W[i] = T(mu2 > 0.0 ? sqrt(kappa) * pow(mu2, 0.5 * s0) : 0.0);
+  }
+}
+
+// the kick of the splitting: v += dt (-kappa D u + f1 u + f3 u^3), D u the
+// variable-order remainder sum_{m >= 1} delta^m Y_m
+template <typename T>
+__global__ void k_kick(T* __restrict__ v, const T* __restrict__ Du, const T* __restrict__ u, T dt, T kappa, T f1,
+                       T f3, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T x = u[i];
+    v[i] += dt * (-kappa * Du[i] + f1 * x + f3 * x * x * x);
   }
 }
 
@@ -113,6 +180,8 @@ struct Plain : Engine {
   T* P1 = nullptr;
   T* P2 = nullptr;
   T* Lg = nullptr;
+  T* W = nullptr;  // splitting: sqrt(kappa) |mu|^{s0} (general model)
+  C* vh = nullptr;
   size_t nbytes = 0;
 
   ~Plain() override {
@@ -126,6 +195,8 @@ struct Plain : Engine {
     cudaFree(P1);
     cudaFree(P2);
     cudaFree(Lg);
+    cudaFree(W);
+    cudaFree(vh);
   }
   size_t bytes() const override { return nbytes; }
 
@@ -162,12 +233,22 @@ struct Plain : Engine {
     if ((st = alloc(c, (void**)&P1, sizeof(T) * Nh))) return st;
     if ((st = alloc(c, (void**)&P2, sizeof(T) * Nh))) return st;
     if ((st = alloc(c, (void**)&Lg, sizeof(T) * Nh))) return st;
+    if ((st = alloc(c, (void**)&W, sizeof(T) * Nh))) return st;
+    if ((st = alloc(c, (void**)&vh, sizeof(C) * Nh))) return st;
     return VOFL_OK;
   }
 
   int set_model(vofl_ctx* c) override {
     if (make_plain_tables<T>(c->ndim, c->n, c->lo, c->hi, c->s01, c->s02, P1, P2, Lg, c->stream))
       return cuda_err(c, cudaGetLastError(), "plain tables");
+    if (c->general) {
+      const int nx = (int)c->n[0], ny = c->ndim > 1 ? (int)c->n[1] : 1, nz = c->ndim > 2 ? (int)c->n[2] : 1;
+      const double lx = c->hi[0] - c->lo[0], ly = c->ndim > 1 ? c->hi[1] - c->lo[1] : 1.0;
+      const double lz = c->ndim > 2 ? c->hi[2] - c->lo[2] : 1.0;
+      k_omega_table<T><<<grid_for(Nh), 256, 0, c->stream>>>(nx, ny, nz, lx, ly, lz, c->s01, c->kappa, W);
+      count_launch();
+      if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "splitting frequency table");
+    }
     return VOFL_OK;
   }
 
@@ -185,17 +266,30 @@ struct Plain : Engine {
     if (r != CUFFT_SUCCESS) return set_err(c, VOFL_ECUDA, "cuFFT forward");
     return VOFL_OK;
   }
-  int exec_inv(vofl_ctx* c) {
+  int exec_inv(vofl_ctx* c, C* in = nullptr, T* out = nullptr) {
     cufftResult r;
+    if (!in) in = X;
+    if (!out) out = Y;
     if constexpr (sizeof(T) == 8)
-      r = cufftExecZ2D(inv, (cufftDoubleComplex*)X, (cufftDoubleReal*)Y);
+      r = cufftExecZ2D(inv, (cufftDoubleComplex*)in, (cufftDoubleReal*)out);
     else
-      r = cufftExecC2R(inv, (cufftComplex*)X, (cufftReal*)Y);
+      r = cufftExecC2R(inv, (cufftComplex*)in, (cufftReal*)out);
     if (r != CUFFT_SUCCESS) return set_err(c, VOFL_ECUDA, "cuFFT inverse");
     return VOFL_OK;
   }
+  int exec_fwd_to(vofl_ctx* c, const T* u, C* out) {
+    cufftResult r;
+    if constexpr (sizeof(T) == 8)
+      r = cufftExecD2Z(fwd, (cufftDoubleReal*)const_cast<T*>(u), (cufftDoubleComplex*)out);
+    else
+      r = cufftExecR2C(fwd, (cufftReal*)const_cast<T*>(u), (cufftComplex*)out);
+    if (r != CUFFT_SUCCESS) return set_err(c, VOFL_ECUDA, "cuFFT forward");
+    return VOFL_OK;
+  }
 
-  int operators(vofl_ctx* c, const T* u) {
+  // sums of Eq. (2.13) for terms m0..M of the first nops operators into
+  // acc1 (, acc2)
+  int operators(vofl_ctx* c, const T* u, int m0 = 0, int nops = 2) {
     int st;
     // forward transform of the discrete Laplacian of u (into Y, free here)
     const int nx = (int)c->n[0], ny = c->ndim > 1 ? (int)c->n[1] : 1, nz = c->ndim > 2 ? (int)c->n[2] : 1;
@@ -209,14 +303,48 @@ struct Plain : Engine {
     double fact = 1.0;
     for (int m = 0; m <= c->M; ++m) {
       if (m > 0) fact *= m;
-      for (int op = 0; op < 2; ++op) {
+      if (m < m0) continue;
+      for (int op = 0; op < nops; ++op) {
         k_mult<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(uh, op == 0 ? P1 : P2, Lg, m, T(1.0 / fact), X, Nh);
         count_launch();
         if ((st = exec_inv(c))) return st;
-        k_acc<T><<<grid_for(N), 256, 0, c->stream>>>(Y, (const T*)c->delta, m, op == 0 ? acc1 : acc2, N);
+        k_acc<T><<<grid_for(N), 256, 0, c->stream>>>(Y, (const T*)c->delta, m, m == m0 ? 1 : 0,
+                                                      op == 0 ? acc1 : acc2, N);
         count_launch();
       }
     }
+    if (m0 > c->M) {
+      for (int op = 0; op < nops; ++op)
+        VOFL_CUDA(c, cudaMemsetAsync(op == 0 ? acc1 : acc2, 0, sizeof(T) * N, c->stream));
+    }
+    return VOFL_OK;
+  }
+
+  bool can_split() const override { return true; }
+
+  // one step of the second-order time splitting (Sec. 3.3) of the general
+  // model: u = u[cur], v = u[1 - cur], both updated in place
+  int step_split(vofl_ctx* c) override {
+    T* u = (T*)c->u[c->cur];
+    T* v = (T*)c->u[1 - c->cur];
+    const T half = T(0.5 * c->dt), invN = T(1.0 / (double)N);
+    auto rotate = [&]() -> int {
+      int st;
+      if ((st = exec_fwd_to(c, u, uh))) return st;
+      if ((st = exec_fwd_to(c, v, vh))) return st;
+      k_rotate<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(uh, vh, W, half, invN, Nh);
+      count_launch();
+      if ((st = exec_inv(c, uh, u))) return st;
+      return exec_inv(c, vh, v);
+    };
+    int st;
+    if ((st = rotate())) return st;
+    if ((st = operators(c, u, 1, 1))) return st;
+    k_kick<T><<<grid_for(N), 256, 0, c->stream>>>(v, acc1, u, T(c->dt), T(c->kappa), T(c->f1), T(c->f3), N);
+    count_launch();
+    if ((st = rotate())) return st;
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_err(c, err, "plain splitting step");
     return VOFL_OK;
   }
 

@@ -152,3 +152,79 @@ def test_suggest_M_matches_the_oracle_rule(V):
         sv.set_order(s)
         for tol in (1e-6, 1e-10):
             assert sv.suggest_M(tol) == O.suggested_M(s, shape, lo, hi, tol)
+
+
+def _table4(golden_dir):
+    rows = {}
+    with open(os.path.join(golden_dir, "table4_tsfp2_temporal_errors.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[int(p[0])] = [None if v == "unstable" else float(v) for v in p[1:]]
+    return rows
+
+
+def _gpu_split(V, shape, s, u0, dt, nsteps, M, f3, prec, lo=None, hi=None, v0=None):
+    ty = np.float32 if prec == V.F32 else np.float64
+    with V.Solver(shape, lo, hi, prec, V.IMPL_PLAIN) as sv:
+        sv.set_order(np.ascontiguousarray(np.broadcast_to(s, shape), dtype=np.float64), kappa=1.0, f3=f3)
+        sv.set_M(M)
+        sv.set_scheme(V.SCHEME_TSFP2)
+        sv.set_state(np.ascontiguousarray(u0, dtype=ty), None if v0 is None else np.ascontiguousarray(v0, dtype=ty))
+        sv.step(nsteps, dt)
+        out = sv.get_state()
+        sv.sync()
+        return out.astype(np.float64)
+
+
+@pytest.mark.parametrize("col,order", [(3, "s1"), (1, "one")])
+def test_paper_table4_tsfp2_on_the_gpu(V, golden_dir, col, order):
+    """Table 4 (TSFP2, Sec. 3.3) with the GPU's FP64 path: column s1 (with
+    its unstable cells) and the constant-order column s = 1."""
+    rows = _table4(golden_dir)
+    J, lo, hi = 4096, [-32.0], [32.0]
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s = 1.0 + 0.3 * np.sin(np.pi * x / 8) if order == "s1" else np.ones(J)
+    M = 15 if order == "s1" else 0
+    run = lambda dt, n: _gpu_split(V, (J,), s, phi, dt, n, M, 1.0, V.F64, lo, hi)  # noqa: E731
+    ref = run(1e-4, 10000)
+    for p in range(7, 12):
+        printed = rows[p][col]
+        u = run(2.0 ** -p, 2 ** p)
+        if printed is None:
+            assert not np.all(np.isfinite(u)) or np.max(np.abs(u)) > 1e3, p
+        else:
+            err = O.l2_error(u, ref, [1.0 / 64])
+            assert abs(err - printed) <= 0.0006 * printed, (order, p, err, printed)
+
+
+def test_tsfp2_fp32_2d_against_oracle(V):
+    """A 2D splitting run in FP32 with a non-zero initial velocity."""
+    shape, lo, hi = (128, 128), [-8.0, -8.0], [8.0, 8.0]
+    s = _s2d(shape, lo, hi)
+    u0 = S.gaussian_pulse(shape, 6.0).astype(np.float32)
+    xg, yg = S.mesh(shape, lo, hi)
+    v0 = (0.3 * np.sin(np.pi * xg / 4) * np.cos(np.pi * yg / 8)).astype(np.float32)
+    g = _gpu_split(V, shape, s, u0, 2e-3, 50, 20, 1.0, V.F32, lo, hi, v0)
+    r = O.general_tsfp2(s, 1.0, lambda u: u ** 3, u0.astype(np.float64), v0.astype(np.float64), 2e-3, 50, 20, lo, hi)
+    assert rel_l2(g, r) <= 1e-4, rel_l2(g, r)
+
+
+def test_tsfp2_needs_general_model_and_plain_path(V):
+    shape = (64, 64)
+    with V.Solver(shape) as sv:  # fused path
+        sv.set_order(np.ones(shape))
+        sv.set_scheme(V.SCHEME_TSFP2)
+        sv.set_state(np.zeros(shape, np.float32))
+        with pytest.raises(V.VoflError):
+            sv.step(1, 1e-3)
+    with V.Solver(shape, impl=V.IMPL_PLAIN) as sv:  # seismic model
+        sv.set_q(S.q_lowpass(shape, 1))
+        sv.set_scheme(V.SCHEME_TSFP2)
+        sv.set_state(np.zeros(shape, np.float32))
+        with pytest.raises(V.VoflError):
+            sv.step(1, 1e-3)
+        with pytest.raises(V.VoflError):
+            sv.set_scheme(7)
