@@ -228,3 +228,44 @@ def test_tsfp2_needs_general_model_and_plain_path(V):
             sv.step(1, 1e-3)
         with pytest.raises(V.VoflError):
             sv.set_scheme(7)
+
+
+def _table5(golden_dir):
+    rows = {}
+    with open(os.path.join(golden_dir, "table5_tsfp2_spatial_errors.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[int(p[0])] = [float(v) for v in p[1:]]
+    return rows
+
+
+@pytest.mark.parametrize("col,order", [(1, "one"), (3, "s1"), (4, "s2")])
+def test_paper_table5_spatial_errors_on_the_gpu(V, golden_dir, col, order):
+    """Table 5 (TSFP2 at dt = 1e-4, h = 1 .. 1/8 against h = 1/64) with the
+    GPU's FP64 path: the printed digits at h = 1, 1/2, 1/4; the round-off
+    floor at h = 1/8."""
+    rows = _table5(golden_dir)
+    lo, hi = [-32.0], [32.0]
+
+    def run(J):
+        x = S.axis(J, -32.0, 32.0)
+        if order == "one":
+            s, M = np.ones(J), 0
+        elif order == "s1":
+            s, M = 1.0 + 0.3 * np.sin(np.pi * x / 8), 15
+        else:
+            s, M = 1.0 + 0.2 * np.tanh(np.cos(np.pi * x / 8)), 15
+        return _gpu_split(V, (J,), s, np.exp(-x * x), 1e-4, 10000, M, 1.0, V.F64, lo, hi)
+
+    ref = run(4096)
+    for inv_h in (1, 2, 4, 8):
+        J = 64 * inv_h
+        u = run(J)
+        err = np.sqrt((1.0 / inv_h) * np.sum((u - ref[:: 4096 // J]) ** 2))
+        printed = rows[inv_h][col]
+        if inv_h < 8:
+            assert abs(err - printed) <= 1e-4 * printed, (order, inv_h, err, printed)
+        else:
+            assert err < 1e-11, (order, err)
