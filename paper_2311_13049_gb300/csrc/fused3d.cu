@@ -26,6 +26,12 @@
 
 namespace vofl {
 
+// Taylor terms per inverse group.  Each group re-reads the z spectrum and
+// reads and rewrites both partial sums in HBM, so the fewer groups the
+// better; 9 terms make M = 8 one group (Zz + Zy hold 18 transformed planes
+// per z: 2.5 GB at 256^3) and M = 16 two.
+constexpr int kTerms3D = 9;
+
 namespace {
 
 struct Kernels3 {
@@ -125,7 +131,7 @@ __global__ void k_tables_fused3d(int nx, int ny, int nz, double lx, double ly, d
 struct Fused3D : Engine {
   Kernels3 k{};
   int nx = 0, ny = 0, nz = 0, H = 0, c2 = 0, c3 = 0;  // c2 = H+1 columns per plane, c3 = (H+1)*ny z-columns
-  int pT = 0, pZ = 0, p3 = 0, G = 4;
+  int pT = 0, pZ = 0, p3 = 0, G = kTerms3D;
   float2 *T = nullptr, *U2 = nullptr, *U3 = nullptr, *Zz = nullptr, *Zy = nullptr;
   float *part = nullptr, *P = nullptr, *Lg = nullptr;
   float2 *twx = nullptr, *twy = nullptr, *twz = nullptr;
@@ -159,7 +165,7 @@ struct Fused3D : Engine {
     pT = round_up(c2, 8);
     pZ = pT;
     p3 = round_up(c3, 8);
-    G = 4;
+    G = kTerms3D;
     const size_t N = (size_t)nx * ny * nz;
     int st;
     if ((st = alloc(c, (void**)&T, sizeof(float2) * (size_t)nz * ny * pT))) return st;
@@ -293,7 +299,7 @@ bool fused3d_supported(int ndim, const int64_t* n, int prec) {
 
 size_t fused3d_footprint(const int64_t* n, int M) {
   const size_t nx = n[0], ny = n[1], nz = n[2], c2 = nx / 2 + 1, c3 = c2 * ny;
-  const size_t pT = (c2 + 7) / 8 * 8, p3 = (c3 + 7) / 8 * 8, G = std::min(4, M + 1);
+  const size_t pT = (c2 + 7) / 8 * 8, p3 = (c3 + 7) / 8 * 8, G = kTerms3D;
   return sizeof(float2) * (nz * ny * pT + 2 * nz * c3 + 2 * G * nz * p3 + 2 * G * nz * ny * pT + nx + ny + nz) +
          sizeof(float) * (2 * nx * ny * nz + 3 * c3 * nz);
 }

@@ -16,7 +16,7 @@ namespace vofl {
 namespace {
 
 // CTA sizes (warps) per kernel
-constexpr int W_FROWS = 2;  // forward rows: small CTAs, 4x more CTAs than SMs at 1024^2
+constexpr int W_FROWS = 1;  // forward rows: one-warp CTAs, 512 of them at 1024^2
 constexpr int W_FCOLS = 4;  // forward columns: 4 columns -> 32-byte row segments
 constexpr int W_YCOLS = 4;  // 3D y-inverse kernel
 constexpr int W_IROWS = 4;  // inverse row kernel
