@@ -20,6 +20,11 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                                    errors (Table 3, Sec. 3.2) are reproduced (P7).
   general_tsfp2         (O4)       pinned: the paper's printed TSFP2 temporal
                                    errors (Table 4, Sec. 3.3) are reproduced.
+  general_cnfp          (O4)       pinned: the paper's printed CNFP temporal
+                                   errors (Table 2, Sec. 3.1) are reproduced,
+                                   single-mode closed form (f = 0), and the
+                                   scalar implicit scheme for a constant field.
+  operator_matrix                  O2 applied to unit fields (pinned with O2).
   suggested_dt                     pinned: gamma = 0 closed form and the
                                    stability of the single-mode recurrence of
                                    the step on both sides of the bound.
@@ -27,7 +32,7 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                                    chosen M (against O2 at M = 40) is within
                                    the tolerance.
 
-Conventions (the readings of the paper are listed in the design doc):
+Conventions (readings of the paper where it is silent or ambiguous):
   * arrays are indexed [z][y][x] (x fastest); `lo`, `hi` are (x, y, z) ordered;
   * the frequency index set of each axis is k = -J/2 .. J/2-1 (Sec. 2, Eq. (2.2));
     mu_k = 2 pi k / (b - a); |mu_k|^2 = sum over axes (Sec. 2.3, below Eq. (2.12));
@@ -46,7 +51,7 @@ __all__ = [
     "dense_operator", "matrix_free_operator", "matrix_free_terms",
     "seismic_operators", "seismic_lffp", "general_lffp",
     "l2_error", "rel_l2", "taylor_remainder_bound", "suggested_dt", "suggested_M",
-    "general_tsfp2",
+    "general_tsfp2", "general_cnfp", "operator_matrix",
 ]
 
 
@@ -394,6 +399,63 @@ def general_lffp(s, kappa, f, phi, psi, dt, nsteps, M, lo=None, hi=None,
         if not np.all(np.isfinite(u)):
             break
     return u
+
+
+def operator_matrix(s, M, shape, lo=None, hi=None):
+    """The N x N matrix of the M-term matrix-free operator O2 on a grid of
+    `shape` (N points, flattened x fastest): column l is O2 applied to the
+    l-th unit field."""
+    shape = tuple(shape)
+    n = int(np.prod(shape))
+    cols = np.empty((n, n))
+    e = np.zeros(n)
+    for l in range(n):
+        e[l] = 1.0
+        cols[:, l] = matrix_free_operator(e.reshape(shape), s, M, lo, hi).ravel()
+        e[l] = 0.0
+    return cols
+
+
+def general_cnfp(s, kappa, f, phi, psi, dt, nsteps, M, lo=None, hi=None, tol=1e-14, maxit=100):
+    """Crank-Nicolson Fourier pseudospectral method (Sec. 3.1): u^0 = phi and
+    the explicit start u^1 = phi + dt psi + dt^2/2 (-kappa L_s phi + f(phi))
+    (Eq. (3.3)); then for n >= 1 u^{n+1} is the solution v of the nonlinear
+    system of Eq. (3.2), the Crank-Nicolson form of Eq. (3.1),
+        v + (kappa dt^2/2) L_s v - (dt^2/2) f(v)
+          = 2 u^n - u^{n-1} - (kappa dt^2/2) L_s u^{n-1} + (dt^2/2) f(u^{n-1}),
+    with L_s the matrix-free operator O2 as a dense matrix.  The system has
+    one solution near u^n for the step sizes used here, so the oracle
+    computes it by its plainest route instead of the paper's conjugate
+    gradients: A = I + (kappa dt^2/2) L_s is LU-factored once, and the cubic
+    term is handled by the fixed-point iteration v <- A^{-1}(rhs + (dt^2/2)
+    f(v)) from v = 2 u^n - u^{n-1}, until two iterates differ by at most
+    tol * max(1, |v|_inf).  Returns u^{nsteps}."""
+    import scipy.linalg
+
+    phi = np.asarray(phi, dtype=np.float64)
+    shape = phi.shape
+    psi = np.zeros_like(phi) if psi is None else np.asarray(psi, dtype=np.float64)
+    L = operator_matrix(s, M, shape, lo, hi)
+    c = 0.5 * kappa * dt * dt
+    h2 = 0.5 * dt * dt
+    lu = scipy.linalg.lu_factor(np.eye(L.shape[0]) + c * L)
+    u_prev = phi.ravel()
+    u = u_prev + dt * psi.ravel() + h2 * (-kappa * (L @ u_prev) + f(u_prev))
+    if nsteps == 0:
+        return phi.copy()
+    for _ in range(1, nsteps):
+        rhs = 2.0 * u - u_prev - c * (L @ u_prev) + h2 * f(u_prev)
+        v = 2.0 * u - u_prev
+        for _it in range(maxit):
+            v_new = scipy.linalg.lu_solve(lu, rhs + h2 * f(v))
+            done = np.max(np.abs(v_new - v)) <= tol * max(1.0, float(np.max(np.abs(v_new))))
+            v = v_new
+            if done:
+                break
+        else:
+            raise RuntimeError("CNFP fixed-point iteration did not converge")
+        u_prev, u = u, v
+    return u.reshape(shape)
 
 
 def general_tsfp2(s, kappa, f, phi, psi, dt, nsteps, M, lo=None, hi=None):

@@ -453,3 +453,87 @@ def test_paper_table5_tsfp2_spatial_errors(golden_dir, col, order):
             assert abs(err - printed) <= 1e-4 * printed, (inv_h, err, printed)
         else:
             assert err < 1e-11
+
+
+# --------------------------------------------------------------------------
+# the Crank-Nicolson scheme (CNFP, Sec. 3.1)
+# --------------------------------------------------------------------------
+def _table2(golden_dir):
+    rows = {}
+    with open(os.path.join(golden_dir, "table2_cnfp_temporal_errors.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[int(p[0])] = [float(v) for v in p[1:]]
+    return rows
+
+
+def _table2_order(col, x):
+    if col == 0:
+        return np.full(x.shape, 0.5), 0
+    if col == 1:
+        return np.ones(x.shape), 0
+    if col == 2:
+        return np.full(x.shape, 1.3), 0
+    if col == 3:
+        return 1.0 + 0.3 * np.sin(np.pi * x / 8), 15
+    return 1.0 + 0.2 * np.tanh(np.cos(np.pi * x / 8)), 15
+
+
+@pytest.mark.parametrize("col", [0, 1, 2, 3, 4])
+def test_paper_table2_cnfp_temporal_errors(golden_dir, col):
+    """Table 2 (CNFP): every printed error, all five columns.  Two readings:
+    the printed digits and convergence rates (2.07, 2.32 in the last rows)
+    are those of a dt = 2^-12 reference rather than the dt = 1e-4 the text
+    names, and the run is on h = 1/8 (J = 512) instead of h = 1/64: the
+    spatial error there is at round-off (Table 5), so the temporal errors
+    are the same.  Agreement: 1e-3 relative plus 3e-9 absolute, the spread
+    of such references under round-off (J = 512 against J = 1024)."""
+    rows = _table2(golden_dir)
+    J = 512
+    x = S.axis(J, -32.0, 32.0)
+    s, M = _table2_order(col, x)
+    cube = lambda u: u ** 3  # noqa: E731
+    run = lambda dt, n: O.general_cnfp(s, 1.0, cube, np.exp(-x * x), None, dt, n, M, [-32.0], [32.0])  # noqa: E731
+    ref = run(2.0 ** -12, 4096)
+    for p in range(7, 12):
+        err = O.l2_error(run(2.0 ** -p, 2 ** p), ref, [64.0 / J])
+        printed = rows[p][col]
+        assert abs(err - printed) <= 1e-3 * printed + 3e-9, (col, p, err, printed)
+
+
+@pytest.mark.parametrize("s,k", [(0.5, 3), (1.0, 5), (1.3, 2)])
+def test_cnfp_single_mode_recurrence(s, k):
+    """f = 0, constant order, u^0 = cos(mu x): every step multiplies the one
+    Fourier mode, lambda = |mu|^{2s}, c = kappa dt^2/2:
+    a1 = (1 - c lambda) a0 (start, Eq. (3.3)) and
+    a_{n+1} (1 + c lambda) = 2 a_n - a_{n-1} (1 + c lambda) (Eq. (3.2))."""
+    J, lo, hi, kappa, dt, n = 32, [-np.pi], [np.pi], 0.7, 0.05, 40
+    x = S.axis(J, lo[0], hi[0])
+    u = O.general_cnfp(s, kappa, lambda v: 0.0 * v, np.cos(k * x), None, dt, n, 3, lo, hi)
+    lam, c = float(k) ** (2 * s), 0.5 * kappa * dt * dt
+    a_prev, a = 1.0, 1.0 - c * lam
+    for _ in range(1, n):
+        a_prev, a = a, (2.0 * a - (1.0 + c * lam) * a_prev) / (1.0 + c * lam)
+    assert np.max(np.abs(u - a * np.cos(k * x))) < 1e-12
+
+
+def test_cnfp_spatially_constant_field_is_the_implicit_ode_scheme():
+    """A constant field has L u = 0 (k = 0 is left out), so Eq. (3.2) is the
+    scalar scheme (u1 - 2u + u0)/dt^2 = (f(u1) + f(u0))/2 with f(u) = -u^3
+    + 0.5 u; each step's cubic in u1 is solved here by bisection."""
+    J, lo, hi, dt, n = 16, [0.0], [1.0], 0.2, 30
+    f = lambda v: -v ** 3 + 0.5 * v  # noqa: E731
+    u = O.general_cnfp(1.2, 1.0, f, np.full(J, 0.8), None, dt, n, 2, lo, hi)
+    h = 0.5 * dt * dt
+    u0, u1 = 0.8, 0.8 + h * f(0.8)
+    for _ in range(1, n):
+        rhs = 2.0 * u1 - u0 + h * f(u0)
+        g = lambda v: v - h * f(v) - rhs  # noqa: E731  (increasing in v)
+        a, b = -10.0, 10.0
+        for _it in range(200):
+            m = 0.5 * (a + b)
+            a, b = (m, b) if g(m) < 0 else (a, m)
+        u0, u1 = u1, 0.5 * (a + b)
+    assert np.max(np.abs(u - u1)) < 1e-12
