@@ -20,8 +20,9 @@ is Mpoint-steps/s = 1024^2 * 1000 * runs / time.
          autotuned, timed over the whole 300-step run;
   configs  the 1D 256 FP64 (M = 8, 200 steps) and 3D 256^3 FP32 (M = 8,
          500 steps) runs, fused and plain; the general model of the
-         paper's Table 3 on the FP64 path (timed reference run, errors
-         beside the printed ones) and the generic 2D operator apply;
+         paper's Tables 3 (leap-frog) and 2 (Crank-Nicolson) on the FP64
+         path (timed reference runs, errors beside the printed ones) and
+         the generic 2D operator apply;
   serve  continuous batching of a Poisson request stream (mean 200 per
          second, seed 5; 1D 4096 / 2D 512^2 / 2D 1024^2 / 3D 128^3 with equal
          probability, 100..2000 steps, M 8..16) served in real time:
@@ -58,7 +59,7 @@ DT = 5e-4
 # capture of the headline step (profiles/ncu_k2d_kernels_2d_1024_M16.md:
 # mean over the step's three k2d_inv_cols launches, L2 not flushed between
 # kernels); to be re-taken whenever the kernel changes.
-NCU_TRAFFIC_BYTES = {"k2d_inv_cols": 25.04e6}
+NCU_TRAFFIC_BYTES = {"k2d_inv_cols": 24.93e6}
 METRIC = "Mpoint-steps/s (2D 1024², M=16) fused vs plain at ≤1e-5 rel L2; serve p50/p99"
 UNIT = "Mpoint-steps/s"
 WORKLOAD = "2D periodic 1024x1024, FP32, M=16, Q low-passed noise in [5,100] (seed 2), Ricker f0=10 at centre, dt=5e-4, 1000 steps"
@@ -308,6 +309,7 @@ def configs_bench(V, torch, stream, flush, reps=3):
                                      "200 steps (one run incl. model set-up)",
                          "fused": f, "plain": p, "fused_over_plain": f["value"] / p["value"]}
     out["general_table3_s1_1d_4096_f64"] = table3_bench(V, S, stream)
+    out["cnfp_table2_s1_1d_4096_f64"] = cnfp_bench(V, S, stream)
     out["generic_apply_2d_512_M20_f32"] = generic_apply_bench(V, S, torch, stream)
     w3 = S.workload_3d_256()
     f, p = run(w3, V.F32, V.IMPL_FUSED), run(w3, V.F32, V.IMPL_PLAIN)
@@ -359,6 +361,54 @@ def table3_bench(V, S, stream):
     return {"workload": "1D 4096 on [-32,32], FP64 plain path, M=15, s1 = 1 + 0.3 sin(pi x/8), f = u^3, "
                         "reference run dt = 1e-4 to t = 1 (10000 steps, timed)",
             "value": J * 10000 / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_run": ms, "l2_error_vs_reference": errs}
+
+
+# Table 2 of the paper (Sec. 3.1), column s1(x): printed CNFP temporal
+# errors at t = 1 for dt = 2^-p (their reference is the dt = 2^-12 run)
+TABLE2_S1 = {9: 1.739e-6, 10: 4.143e-7, 11: 8.281e-8}
+
+
+def cnfp_bench(V, S, stream):
+    """The Crank-Nicolson scheme (Sec. 3.1) on the problem of Table 2 (as in
+    Table 3, FP64 plain path, CG on the normal equations to the default
+    relative residual 1e-15): the dt = 2^-12 reference run to t = 1 is
+    timed; the errors of the dt = 2^-p runs against it are reported beside
+    the printed ones, with the solver's iteration counts."""
+    import torch
+    J = 4096
+    x = S.axis(J, -32.0, 32.0)
+    phi = np.exp(-x * x)
+    s1 = 1.0 + 0.3 * np.sin(np.pi * x / 8)
+
+    def run(dt, n):
+        with V.Solver((J,), [-32.0], [32.0], V.F64, V.IMPL_PLAIN, stream=stream.cuda_stream) as sv:
+            sv.set_order(s1, kappa=1.0, f3=1.0)
+            sv.set_M(15)
+            sv.set_scheme(V.SCHEME_CNFP)
+            sv.set_state(phi)
+            with torch.cuda.stream(stream):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sv.step(n, dt)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+            u = sv.get_state()
+            sv.sync()
+            return u, ms, sv.solver_stats()
+
+    run(2.0 ** -9, 16)  # warm-up (plans, graphs)
+    ref, ms, (iters, solves) = run(2.0 ** -12, 4096)
+    errs = {}
+    for p, printed in TABLE2_S1.items():
+        u, ms_p, (it_p, so_p) = run(2.0 ** -p, 2 ** p)
+        errs[str(p)] = {"gpu": float(np.sqrt((1.0 / 64) * np.sum((u - ref) ** 2))), "printed": printed,
+                        "cg_iterations": it_p, "ms_run": ms_p}
+    return {"workload": "1D 4096 on [-32,32], FP64 plain path, CNFP (CG on the normal equations, rel. residual "
+                        "1e-15), M=15, s1 = 1 + 0.3 sin(pi x/8), f = u^3, reference run dt = 2^-12 to t = 1 "
+                        "(4096 steps, timed)",
+            "value": J * 4096 / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_run": ms, "cg_iterations": iters,
+            "linear_solves": solves, "l2_error_vs_reference": errs}
 
 
 def generic_apply_bench(V, S, torch, stream, reps=20):

@@ -61,7 +61,8 @@ typedef enum {
   VOFL_ECUDA = -3,         /* a CUDA / cuFFT call failed */
   VOFL_ETIMEDOUT = -4,     /* a bounded device wait gave up */
   VOFL_ESTATE = -5,        /* call out of order (e.g. step before set_q) */
-  VOFL_EUNSUPPORTED = -6   /* size / dimension / precision not built */
+  VOFL_EUNSUPPORTED = -6,  /* size / dimension / precision not built */
+  VOFL_ENOCONV = -7        /* the implicit (Crank-Nicolson) solve did not converge */
 } vofl_status;
 
 typedef enum { VOFL_F32 = 0, VOFL_F64 = 1 } vofl_prec;
@@ -74,11 +75,13 @@ typedef enum {
 } vofl_op;
 
 /* Time stepping of vofl_step: the leap-frog scheme (Eq. (3.4); both
- * models) or the second-order time splitting of Sec. 3.3 (general model
- * only, plain path). */
+ * models), the second-order time splitting of Sec. 3.3 or the
+ * Crank-Nicolson scheme of Sec. 3.1 (these two: general model only, plain
+ * path). */
 typedef enum {
   VOFL_SCHEME_LFFP = 0,
-  VOFL_SCHEME_TSFP2 = 1
+  VOFL_SCHEME_TSFP2 = 1,
+  VOFL_SCHEME_CNFP = 2
 } vofl_scheme;
 
 /* Implementation of the operator/step: the fused hand-written kernels, or
@@ -133,9 +136,39 @@ VOFL_API int vofl_set_gamma(vofl_ctx* ctx, const double* gamma, const double* c0
  * (u, v) with v^0 = the v0 of vofl_set_state, and no point source is
  * applied.  It needs the general model (vofl_set_order) and the plain
  * path (VOFL_IMPL_PLAIN), else vofl_step returns VOFL_EUNSUPPORTED.
+ * The Crank-Nicolson scheme (Sec. 3.1, Eq. (3.2)) takes the explicit start
+ * step of Eq. (3.3) (that of the leap-frog scheme), then for n >= 1 solves
+ *     u^{n+1} + c L u^{n+1} - h f(u^{n+1})
+ *         = 2 u^n - u^{n-1} - c L u^{n-1} + h f(u^{n-1})  (+ source),
+ * c = kappa dt^2/2, h = dt^2/2, L the operator of Eq. (2.13), by a
+ * fixed-point iteration on f around conjugate gradients on the normal
+ * equations of A = I + c L (A is not symmetric when s varies), to the
+ * tolerance of vofl_set_solver.  It has the same requirements and takes
+ * no point source (vofl_step returns VOFL_EUNSUPPORTED while one is set).
  * Returns VOFL_OK, VOFL_EINVAL (unknown scheme) or VOFL_ESTATE (a run is
  * in progress: set the state first). */
 VOFL_API int vofl_set_scheme(vofl_ctx* ctx, int scheme);
+
+/* Stopping rule of the Crank-Nicolson solve (VOFL_SCHEME_CNFP): each step
+ * ends when the residual r = b + h f(v) - A v of its nonlinear system
+ * (notation of vofl_set_scheme) has |r|_2 <= tol |b + h f(v)|_2; every
+ * linear solve of the fixed-point iteration stops at half that residual
+ * or after max_iter conjugate-gradient iterations (then vofl_step returns
+ * VOFL_ENOCONV, as it does when a fixed-point pass no longer lowers a
+ * residual above 10 tol: tol below what the precision reaches for this
+ * step; one that stalls within 10 tol ends the step).  The k = 0 mode of
+ * the scheme accumulates each step's solve error, so long FP64 runs want
+ * tol near the rounding floor.  Defaults: tol = 1e-15 (VOFL_F64) or 1e-6
+ * (VOFL_F32),
+ * max_iter = 5000.  Returns VOFL_OK or VOFL_EINVAL (tol outside (0, 1) or
+ * max_iter < 1). */
+VOFL_API int vofl_set_solver(vofl_ctx* ctx, double tol, int max_iter);
+
+/* Totals of the Crank-Nicolson solver since the state was set: conjugate-
+ * gradient iterations and linear solves (fixed-point passes).  Either
+ * pointer may be NULL.  Read after vofl_sync for the final values.
+ * Returns VOFL_OK or VOFL_EINVAL. */
+VOFL_API int vofl_solver_stats(vofl_ctx* ctx, int64_t* iterations, int64_t* solves);
 
 /* Highest Taylor power M of Eq. (2.13): each operator apply runs the M+1
  * terms m = 0..M.  0 <= M <= 40.  Default 8. */

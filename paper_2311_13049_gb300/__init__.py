@@ -23,9 +23,9 @@ _LIB = None
 F32, F64 = 0, 1
 OP_1PG, OP_HPG, OP_S = 0, 1, 2
 IMPL_FUSED, IMPL_PLAIN = 0, 1
-SCHEME_LFFP, SCHEME_TSFP2 = 0, 1
+SCHEME_LFFP, SCHEME_TSFP2, SCHEME_CNFP = 0, 1, 2
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ESTATE",
-           -6: "EUNSUPPORTED"}
+           -6: "EUNSUPPORTED", -7: "ENOCONV"}
 
 _i64p = C.POINTER(C.c_int64)
 _dp = C.POINTER(C.c_double)
@@ -50,6 +50,8 @@ SIGNATURES = {
     "vofl_suggest_dt": (C.c_int, [_vp, C.c_double, _dp]),
     "vofl_query": (C.c_int, [_vp]),
     "vofl_suggest_M": (C.c_int, [_vp, C.c_double, C.POINTER(C.c_int)]),
+    "vofl_set_solver": (C.c_int, [_vp, C.c_double, C.c_int]),
+    "vofl_solver_stats": (C.c_int, [_vp, _i64p, _i64p]),
     "vofl_sync": (C.c_int, [_vp]),
     "vofl_last_error": (C.c_char_p, [_vp]),
     "vofl_footprint_bytes": (C.c_size_t, [C.c_int, _i64p, C.c_int, C.c_int, C.c_int]),
@@ -198,8 +200,19 @@ class Solver:
         self._check(lib().vofl_set_order(self._h, p, dev, float(kappa), float(f1), float(f3)))
 
     def set_scheme(self, scheme):
-        """SCHEME_LFFP (default) or SCHEME_TSFP2 (general model, plain path)."""
+        """SCHEME_LFFP (default), SCHEME_TSFP2 or SCHEME_CNFP (these two:
+        general model, plain path)."""
         self._check(lib().vofl_set_scheme(self._h, int(scheme)))
+
+    def set_solver(self, tol, max_iter=5000):
+        """Relative residual and CG iteration cap of the Crank-Nicolson solve."""
+        self._check(lib().vofl_set_solver(self._h, float(tol), int(max_iter)))
+
+    def solver_stats(self):
+        """(CG iterations, linear solves) of the Crank-Nicolson run so far."""
+        it, so = C.c_int64(), C.c_int64()
+        self._check(lib().vofl_solver_stats(self._h, C.byref(it), C.byref(so)))
+        return it.value, so.value
 
     def set_M(self, M):
         self._check(lib().vofl_set_M(self._h, int(M)))

@@ -27,6 +27,8 @@ void drop_graphs(vofl_ctx* c) {
 void reset_run(vofl_ctx* c) {
   c->steps = 0;
   c->cur = 0;
+  c->cn_iters = 0;
+  c->cn_solves = 0;
 }
 
 vofl_ctx::GraphKey current_key(const vofl_ctx* c) {
@@ -226,6 +228,7 @@ int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, co
   c->N = N;
   c->prec = prec;
   c->impl = impl;
+  c->cn_tol = prec == VOFL_F64 ? 1e-15 : 1e-6;
   for (int i = 0; i < ndim; ++i) {
     c->n[i] = n[i];
     c->lo[i] = lo[i];
@@ -437,7 +440,8 @@ int vofl_set_source(vofl_ctx* c, const int64_t* idx, const double* samples, int6
 
 int vofl_set_scheme(vofl_ctx* c, int scheme) {
   if (int st = check_ctx(c)) return st;
-  if (scheme != VOFL_SCHEME_LFFP && scheme != VOFL_SCHEME_TSFP2) return set_err(c, VOFL_EINVAL, "unknown scheme");
+  if (scheme != VOFL_SCHEME_LFFP && scheme != VOFL_SCHEME_TSFP2 && scheme != VOFL_SCHEME_CNFP)
+    return set_err(c, VOFL_EINVAL, "unknown scheme");
   if (c->steps > 0 && scheme != c->scheme) return set_err(c, VOFL_ESTATE, "a run is in progress; set the state first");
   c->scheme = scheme;
   return VOFL_OK;
@@ -455,6 +459,27 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
     c->dt = dt;
     for (int64_t i = 0; i < nsteps; ++i)
       if (int st = split_step(c)) return st;
+    return VOFL_OK;
+  }
+  if (c->scheme == VOFL_SCHEME_CNFP) {
+    if (!c->general || !c->eng->can_cn())
+      return set_err(c, VOFL_EUNSUPPORTED, "the Crank-Nicolson scheme needs the general model and the plain path");
+    if (c->nsrc > 0) return set_err(c, VOFL_EUNSUPPORTED, "the Crank-Nicolson scheme takes no point source");
+    if (int st = prepare_run(c, dt)) return st;
+    if (nsteps == 0) return VOFL_OK;
+    if (c->steps == 0) {  // explicit start (Eq. (3.3)), as in the leap-frog scheme
+      int st = c->eng->step(c, EPI_START, false);
+      if (st) return st;
+      c->cur ^= 1;
+      c->steps = 1;
+      --nsteps;
+    }
+    for (int64_t i = 0; i < nsteps; ++i) {
+      int st = c->eng->step_cn(c);
+      if (st) return st;
+      c->cur ^= 1;
+      c->steps += 1;
+    }
     return VOFL_OK;
   }
   if (int st = prepare_run(c, dt)) return st;
@@ -478,6 +503,21 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
     int st = one_step(c);
     if (st) return st;
   }
+  return VOFL_OK;
+}
+
+int vofl_set_solver(vofl_ctx* c, double tol, int max_iter) {
+  if (int st = check_ctx(c)) return st;
+  if (!(tol > 0) || !(tol < 1) || max_iter < 1) return set_err(c, VOFL_EINVAL, "bad solver tolerance or iteration cap");
+  c->cn_tol = tol;
+  c->cn_maxit = max_iter;
+  return VOFL_OK;
+}
+
+int vofl_solver_stats(vofl_ctx* c, int64_t* iterations, int64_t* solves) {
+  if (!c) return VOFL_EINVAL;
+  if (iterations) *iterations = c->cn_iters;
+  if (solves) *solves = c->cn_solves;
   return VOFL_OK;
 }
 

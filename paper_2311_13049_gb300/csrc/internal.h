@@ -114,6 +114,9 @@ struct vofl_ctx {
   double s01 = 1, s02 = 0.5;  // expansion orders of the two operators (Eq. (2.13))
   double kappa = 1, f1 = 0, f3 = 0;
   int scheme = VOFL_SCHEME_LFFP;  // time stepping of vofl_step
+  double cn_tol = 0;              // Crank-Nicolson: relative residual of each step's system (set by precision at creation)
+  int cn_maxit = 5000;            // ... CG iterations per linear solve
+  int64_t cn_iters = 0, cn_solves = 0;  // ... totals since the state was set
   void* delta = nullptr;  // gamma - gamma0        (prec)
   void* A = nullptr;      // c^2 eta               (prec)
   void* B = nullptr;      // c^2 tau               (prec)
@@ -194,6 +197,13 @@ struct Engine {
   // model: one step, u = u[cur] and v = u[1 - cur] updated in place
   virtual bool can_split() const { return false; }
   virtual int step_split(vofl_ctx* c) {
+    (void)c;
+    return VOFL_EUNSUPPORTED;
+  }
+  // engines with the Crank-Nicolson scheme (Sec. 3.1) of the general model:
+  // one step n >= 1, u^{n+1} written to u[1 - cur]
+  virtual bool can_cn() const { return false; }
+  virtual int step_cn(vofl_ctx* c) {
     (void)c;
     return VOFL_EUNSUPPORTED;
   }
