@@ -59,6 +59,7 @@ int vofl::prepare_run(vofl_ctx* c, double dt) {
   if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
   if (!(dt > 0) || !std::isfinite(dt)) return set_err(c, VOFL_EINVAL, "bad dt");
   if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");
+  if (int st = c->eng->prepare(c)) return st;
   if (c->steps == 0) {
     c->dt = dt;
     VOFL_CUDA(c, cudaMemsetAsync(c->d_step, 0, sizeof(int), c->stream));
@@ -201,7 +202,7 @@ size_t vofl_footprint_bytes(int ndim, const int64_t* n, int prec, int impl, int 
   else if (impl == VOFL_IMPL_FUSED && fused1d_supported(ndim, n, prec))
     b += (size_t)N * (prec == VOFL_F64 ? 8 : 4) * 4;
   else
-    b += plain_footprint(ndim, n, prec);
+    b += plain_footprint(ndim, n, prec, M);
   return b;
 }
 
@@ -378,6 +379,7 @@ int vofl_apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) {
   if (int st = check_ctx(c)) return st;
   if (!c->model_set) return set_err(c, VOFL_ESTATE, "set_q / set_gamma first");
   if (!u || (!o1 && !o2)) return set_err(c, VOFL_EINVAL, "null array");
+  if (int st = c->eng->prepare(c)) return st;
   return c->eng->apply_pair(c, u, o1, o2);
 }
 
@@ -456,6 +458,7 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
     if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
     if (!(dt > 0) || !std::isfinite(dt)) return set_err(c, VOFL_EINVAL, "bad dt");
     if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");
+    if (int st = c->eng->prepare(c)) return st;
     c->dt = dt;
     for (int64_t i = 0; i < nsteps; ++i)
       if (int st = split_step(c)) return st;

@@ -200,6 +200,12 @@ struct Engine {
     (void)c;
     return VOFL_EUNSUPPORTED;
   }
+  // size M-dependent scratch before stepping or applying (outside any graph
+  // capture: allocations and plans are not stream operations)
+  virtual int prepare(vofl_ctx* c) {
+    (void)c;
+    return VOFL_OK;
+  }
   // engines with the Crank-Nicolson scheme (Sec. 3.1) of the general model:
   // one step n >= 1, u^{n+1} written to u[1 - cur]
   virtual bool can_cn() const { return false; }
@@ -223,7 +229,7 @@ bool fused3d_supported(int ndim, const int64_t* n, int prec);
 size_t fused3d_footprint(const int64_t* n, int M);
 Engine* make_plain(vofl_ctx* c, int* status);
 size_t fused2d_footprint(const int64_t* n, int M);
-size_t plain_footprint(int ndim, const int64_t* n, int prec);
+size_t plain_footprint(int ndim, const int64_t* n, int prec, int M);
 bool fused2d_supported(int ndim, const int64_t* n, int prec);
 
 // run set-up shared by vofl_step and batches (capi.cu)

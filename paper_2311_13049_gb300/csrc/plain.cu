@@ -1,18 +1,21 @@
 // plain.cu -- the plain baseline: the same arithmetic as the fused path
 // (Eq. (2.13) of arXiv 2311.13049 for both operators of Eq. (1.1), then the
 // leap-frog update of Eq. (3.4)) with library transforms (cuFFT R2C / C2R)
-// and one separate elementwise kernel per step of the formula:
-//   forward R2C of u;
-//   for m = 0..M, op in {1, 2}:
-//     multiply: X = u_hat * P_op(k) (ln|mu_k|^2)^m / m!      (kernel)
-//     inverse C2R of X                                        (cuFFT)
-//     accumulate: acc_op += (s(x) - s0)^m * Y                 (kernel)
-//   pointwise update                                          (kernel)
-// Works for 1D, 2D, 3D and for float or double.  It keeps every field in
-// memory between kernels; that traffic is what the fused path removes.
+// and separate elementwise kernels, every intermediate field in memory:
+//   stencil: w = discrete Laplacian of u                         (kernel)
+//   forward R2C of w                                             (cuFFT)
+//   multiply: X[op][m] = w_hat * P_op(k) (ln|mu_k|^2)^m / m!,
+//             all terms of both operators                        (kernel)
+//   inverse C2R of all 2(M+1) spectra in one batched call        (cuFFT)
+//   accumulate: acc_op = sum_m (s(x) - s0)^m Y[op][m], Horner     (kernel)
+//   pointwise update                                             (kernel)
+// Works for 1D, 2D, 3D and for float or double.  It keeps all 2(M+1)
+// transformed fields in memory (O(MN) storage and traffic); that is what
+// the fused path removes.
 // For the general model it also runs the second-order time splitting of
 // Sec. 3.3 (step_split): exact half-step rotations of (u_hat, v_hat) in
-// Fourier space, the variable-order kick (terms m >= 1), the rotations again.
+// Fourier space, the variable-order kick (terms m >= 1), the rotations
+// again; and the Crank-Nicolson scheme of Sec. 3.1 (step_cn, below).
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -40,31 +43,6 @@ inline int grid_for(long long n) {
   long long b = (n + 255) / 256;
   if (b > 8192) b = 8192;
   return (int)(b < 1 ? 1 : b);
-}
-
-template <typename T, typename C>
-__global__ void k_mult(const C* __restrict__ uh, const T* __restrict__ P, const T* __restrict__ Lg, int m, T inv_fact,
-                       C* __restrict__ X, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    T c = P[i] * inv_fact;
-    const T l = Lg[i];
-    for (int j = 0; j < m; ++j) c *= l;
-    C v = uh[i];
-    v.x *= c;
-    v.y *= c;
-    X[i] = v;
-  }
-}
-
-template <typename T>
-__global__ void k_acc(const T* __restrict__ Y, const T* __restrict__ delta, int m, int first, T* __restrict__ acc,
-                      long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    T w = T(1);
-    const T d = delta[i];
-    for (int j = 0; j < m; ++j) w *= d;
-    acc[i] = (first ? T(0) : acc[i]) + w * Y[i];
-  }
 }
 
 // Time splitting (Sec. 3.3): the exact flow of u_t = v, v_t = -kappa
@@ -219,20 +197,43 @@ __device__ __forceinline__ void cn_block_sum2(double& a, double& b) {
   }
 }
 
-// all M+1 multiplied spectra: Xm[m] = u_hat P L^m / m!
+// the multiplied spectra of both operators: X[op][m] = u_hat P_op L^m / m!
 template <typename T, typename C>
-__global__ void k_mult_all(const C* __restrict__ uh, const T* __restrict__ P, const T* __restrict__ Lg, int M,
-                           C* __restrict__ Xm, long long nh) {
+__global__ void k_mult_ops(const C* __restrict__ uh, const T* __restrict__ P1, const T* __restrict__ P2,
+                           const T* __restrict__ Lg, int M, int nops, C* __restrict__ X, long long nh) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nh; i += (long long)gridDim.x * blockDim.x) {
-    T t = P[i];
     const T l = Lg[i];
     const C v = uh[i];
-    for (int m = 0; m <= M; ++m) {
-      C o;
-      o.x = v.x * t;
-      o.y = v.y * t;
-      Xm[m * nh + i] = o;
-      t = t * l / T(m + 1);
+    for (int op = 0; op < nops; ++op) {
+      T t = op == 0 ? P1[i] : P2[i];
+      C* out = X + (long long)op * (M + 1) * nh + i;
+      for (int m = 0; m <= M; ++m) {
+        C o;
+        o.x = v.x * t;
+        o.y = v.y * t;
+        out[m * nh] = o;
+        t = t * l / T(m + 1);
+      }
+    }
+  }
+}
+
+// acc_op = sum_{m = m0..M} delta^m Y[op][m] for op < nops (Horner, then
+// delta^m0); zero when m0 > M
+template <typename T>
+__global__ void k_acc_ops(const T* __restrict__ Y, const T* __restrict__ delta, int M, int m0, int nops,
+                          T* __restrict__ acc1, T* __restrict__ acc2, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T d = delta[i];
+    for (int op = 0; op < nops; ++op) {
+      const T* y = Y + (long long)op * (M + 1) * n + i;
+      T acc = T(0);
+      if (m0 <= M) {
+        acc = y[M * n];
+        for (int m = M - 1; m >= m0; --m) acc = y[m * n] + d * acc;
+        for (int m = 0; m < m0; ++m) acc *= d;
+      }
+      (op == 0 ? acc1 : acc2)[i] = acc;
     }
   }
 }
@@ -472,13 +473,21 @@ struct Plain : Engine {
   C* vh = nullptr;
   size_t nbytes = 0;
 
-  // Crank-Nicolson solver state (allocated on first use, sized by M)
-  struct Cn {
+  // all Taylor terms of both operators (sized by M in prepare(), before any
+  // graph capture: plans and allocations are not stream operations)
+  struct Terms {
     int M = -1;
-    cufftHandle fwdB = 0, invB = 0;  // M+1 transforms per call
-    bool have_plans = false;
-    C* Xm = nullptr;
-    T* Ym = nullptr;
+    int gen = 0;                              // bumped on every re-allocation
+    cufftHandle fwd1 = 0, inv1 = 0, inv2 = 0;  // M+1 R2C, M+1 C2R, 2(M+1) C2R
+    bool have = false;
+    C* X = nullptr;  // [2][M+1][Nh]
+    T* Y = nullptr;  // [2][M+1][N]
+    size_t bytes = 0;
+  } tb;
+
+  // Crank-Nicolson solver state (allocated on first use)
+  struct Cn {
+    int gen = -1;  // term-batch generation the graphs were captured with
     T *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr;
     double *pa = nullptr, *pb = nullptr, *s = nullptr;
     double* hs = nullptr;  // pinned copy of s
@@ -500,21 +509,30 @@ struct Plain : Engine {
   }
   void cn_free() {
     cn_drop_graphs();
-    if (cn.have_plans) {
-      cufftDestroy(cn.fwdB);
-      cufftDestroy(cn.invB);
-      cn.have_plans = false;
-    }
-    for (void* q : {(void*)cn.Xm, (void*)cn.Ym, (void*)cn.b, (void*)cn.x, (void*)cn.r, (void*)cn.z, (void*)cn.p,
-                    (void*)cn.w, (void*)cn.pa, (void*)cn.pb, (void*)cn.s})
+    for (void* q : {(void*)cn.b, (void*)cn.x, (void*)cn.r, (void*)cn.z, (void*)cn.p, (void*)cn.w, (void*)cn.pa,
+                    (void*)cn.pb, (void*)cn.s})
       cudaFree(q);
     if (cn.hs) cudaFreeHost(cn.hs);
     nbytes -= cn.bytes;
     cn = Cn{};
   }
+  void tb_free() {
+    if (tb.have) {
+      cufftDestroy(tb.fwd1);
+      cufftDestroy(tb.inv1);
+      cufftDestroy(tb.inv2);
+    }
+    cudaFree(tb.X);
+    cudaFree(tb.Y);
+    nbytes -= tb.bytes;
+    const int gen = tb.gen;
+    tb = Terms{};
+    tb.gen = gen + 1;
+  }
 
   ~Plain() override {
     cn_free();
+    tb_free();
     if (have_fwd) cufftDestroy(fwd);
     if (have_inv) cufftDestroy(inv);
     cudaFree(uh);
@@ -583,8 +601,46 @@ struct Plain : Engine {
   }
 
   uint64_t kernels_per_step(const vofl_ctx* c) const override {
-    // our own kernels only (cuFFT's are library launches)
-    return 2ull * 2 * (c->M + 1) + 3;  // multiply + accumulate per term, stencil, update, step counter
+    (void)c;
+    // our own kernels only (cuFFT's are library launches): step counter,
+    // stencil, multiply, accumulate, update
+    return 5;
+  }
+
+  // size the term batch for the context's M
+  int prepare(vofl_ctx* c) override {
+    if (tb.M == c->M) return VOFL_OK;
+    VOFL_CUDA(c, cudaStreamSynchronize(c->stream));  // queued work may still use the old buffers
+    tb_free();
+    const int B = c->M + 1;
+    int dims[3];
+    for (int i = 0; i < ndim; ++i) dims[i] = (int)c->n[ndim - 1 - i];
+    const bool dbl = sizeof(T) == 8;
+    if (cufftPlanMany(&tb.fwd1, ndim, dims, nullptr, 1, 0, nullptr, 1, 0, dbl ? CUFFT_D2Z : CUFFT_R2C, B) !=
+        CUFFT_SUCCESS)
+      return set_err(c, VOFL_ECUDA, "cufftPlanMany (batched forward)");
+    if (cufftPlanMany(&tb.inv1, ndim, dims, nullptr, 1, 0, nullptr, 1, 0, dbl ? CUFFT_Z2D : CUFFT_C2R, B) !=
+        CUFFT_SUCCESS) {
+      cufftDestroy(tb.fwd1);
+      return set_err(c, VOFL_ECUDA, "cufftPlanMany (batched inverse)");
+    }
+    if (cufftPlanMany(&tb.inv2, ndim, dims, nullptr, 1, 0, nullptr, 1, 0, dbl ? CUFFT_Z2D : CUFFT_C2R, 2 * B) !=
+        CUFFT_SUCCESS) {
+      cufftDestroy(tb.fwd1);
+      cufftDestroy(tb.inv1);
+      return set_err(c, VOFL_ECUDA, "cufftPlanMany (batched inverse, two operators)");
+    }
+    tb.have = true;
+    cufftSetStream(tb.fwd1, c->stream);
+    cufftSetStream(tb.inv1, c->stream);
+    cufftSetStream(tb.inv2, c->stream);
+    cudaError_t e = cudaMalloc(&tb.X, sizeof(C) * Nh * 2 * B);
+    if (e == cudaSuccess) e = cudaMalloc(&tb.Y, sizeof(T) * N * 2 * B);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (plain term batch)");
+    tb.bytes = (sizeof(C) * Nh + sizeof(T) * N) * 2 * B;
+    nbytes += tb.bytes;
+    tb.M = c->M;
+    return VOFL_OK;
   }
 
   int exec_fwd(vofl_ctx* c, const T* u) {
@@ -618,35 +674,27 @@ struct Plain : Engine {
   }
 
   // sums of Eq. (2.13) for terms m0..M of the first nops operators into
-  // acc1 (, acc2)
+  // acc1 (, acc2): one forward transform, every term's inverse transform in
+  // one batched call
   int operators(vofl_ctx* c, const T* u, int m0 = 0, int nops = 2) {
+    if (tb.M != c->M) return set_err(c, VOFL_ESTATE, "plain path: term batch not prepared for this M");
     int st;
     // forward transform of the discrete Laplacian of u (into Y, free here)
     const int nx = (int)c->n[0], ny = c->ndim > 1 ? (int)c->n[1] : 1, nz = c->ndim > 2 ? (int)c->n[2] : 1;
-    const double hx = (c->hi[0] - c->lo[0]) / nx;
-    const double hy = c->ndim > 1 ? (c->hi[1] - c->lo[1]) / ny : 1.0;
-    const double hz = c->ndim > 2 ? (c->hi[2] - c->lo[2]) / nz : 1.0;
-    k_laplacian<T><<<grid_for(N), 256, 0, c->stream>>>(u, Y, nx, ny, nz, T((hx * hx) / (hy * hy)),
-                                                        T((hx * hx) / (hz * hz)));
+    k_laplacian<T><<<grid_for(N), 256, 0, c->stream>>>(u, Y, nx, ny, nz, ryy(c), rzz(c));
     count_launch();
     if ((st = exec_fwd(c, Y))) return st;
-    double fact = 1.0;
-    for (int m = 0; m <= c->M; ++m) {
-      if (m > 0) fact *= m;
-      if (m < m0) continue;
-      for (int op = 0; op < nops; ++op) {
-        k_mult<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(uh, op == 0 ? P1 : P2, Lg, m, T(1.0 / fact), X, Nh);
-        count_launch();
-        if ((st = exec_inv(c))) return st;
-        k_acc<T><<<grid_for(N), 256, 0, c->stream>>>(Y, (const T*)c->delta, m, m == m0 ? 1 : 0,
-                                                      op == 0 ? acc1 : acc2, N);
-        count_launch();
-      }
-    }
-    if (m0 > c->M) {
-      for (int op = 0; op < nops; ++op)
-        VOFL_CUDA(c, cudaMemsetAsync(op == 0 ? acc1 : acc2, 0, sizeof(T) * N, c->stream));
-    }
+    k_mult_ops<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(uh, P1, P2, Lg, c->M, nops, tb.X, Nh);
+    count_launch();
+    cufftResult r;
+    const cufftHandle plan = nops == 2 ? tb.inv2 : tb.inv1;
+    if constexpr (sizeof(T) == 8)
+      r = cufftExecZ2D(plan, (cufftDoubleComplex*)tb.X, (cufftDoubleReal*)tb.Y);
+    else
+      r = cufftExecC2R(plan, (cufftComplex*)tb.X, (cufftReal*)tb.Y);
+    if (r != CUFFT_SUCCESS) return set_err(c, VOFL_ECUDA, "cuFFT batched inverse");
+    k_acc_ops<T><<<grid_for(N), 256, 0, c->stream>>>(tb.Y, (const T*)c->delta, c->M, m0, nops, acc1, acc2, N);
+    count_launch();
     return VOFL_OK;
   }
 
@@ -682,23 +730,12 @@ struct Plain : Engine {
   bool can_cn() const override { return true; }
 
   int cn_alloc(vofl_ctx* c) {
-    if (cn.M == c->M) return VOFL_OK;
-    cn_free();
-    const int B = c->M + 1;
-    int dims[3];
-    for (int i = 0; i < ndim; ++i) dims[i] = (int)c->n[ndim - 1 - i];
-    const bool dbl = sizeof(T) == 8;
-    if (cufftPlanMany(&cn.fwdB, ndim, dims, nullptr, 1, 0, nullptr, 1, 0, dbl ? CUFFT_D2Z : CUFFT_R2C, B) !=
-        CUFFT_SUCCESS)
-      return set_err(c, VOFL_ECUDA, "cufftPlanMany (batched forward)");
-    if (cufftPlanMany(&cn.invB, ndim, dims, nullptr, 1, 0, nullptr, 1, 0, dbl ? CUFFT_Z2D : CUFFT_C2R, B) !=
-        CUFFT_SUCCESS) {
-      cufftDestroy(cn.fwdB);
-      return set_err(c, VOFL_ECUDA, "cufftPlanMany (batched inverse)");
+    if (tb.M != c->M) return set_err(c, VOFL_ESTATE, "plain path: term batch not prepared for this M");
+    if (cn.gen != tb.gen) {  // the graphs hold term-batch pointers
+      cn_drop_graphs();
+      cn.gen = tb.gen;
     }
-    cn.have_plans = true;
-    cufftSetStream(cn.fwdB, c->stream);
-    cufftSetStream(cn.invB, c->stream);
+    if (cn.b) return VOFL_OK;
     auto get = [&](void** q, size_t b) -> int {
       cudaError_t e = cudaMalloc(q, b);
       if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (Crank-Nicolson scratch)");
@@ -706,8 +743,6 @@ struct Plain : Engine {
       return VOFL_OK;
     };
     int st;
-    if ((st = get((void**)&cn.Xm, sizeof(C) * Nh * B))) return st;
-    if ((st = get((void**)&cn.Ym, sizeof(T) * N * B))) return st;
     for (T** v : {&cn.b, &cn.x, &cn.r, &cn.z, &cn.p, &cn.w})
       if ((st = get((void**)v, sizeof(T) * N))) return st;
     if ((st = get((void**)&cn.pa, sizeof(double) * CN_MAXG))) return st;
@@ -719,7 +754,6 @@ struct Plain : Engine {
     }
     VOFL_CUDA(c, cudaMemsetAsync(cn.s, 0, sizeof(double) * S_COUNT, c->stream));
     nbytes += cn.bytes;
-    cn.M = c->M;
     return VOFL_OK;
   }
 
@@ -730,13 +764,13 @@ struct Plain : Engine {
     count_launch();
     int st;
     if ((st = exec_fwd(c, Y))) return st;
-    k_mult_all<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(uh, P1, Lg, c->M, cn.Xm, Nh);
+    k_mult_ops<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(uh, P1, P2, Lg, c->M, 1, tb.X, Nh);
     count_launch();
     cufftResult r;
     if constexpr (sizeof(T) == 8)
-      r = cufftExecZ2D(cn.invB, (cufftDoubleComplex*)cn.Xm, (cufftDoubleReal*)cn.Ym);
+      r = cufftExecZ2D(tb.inv1, (cufftDoubleComplex*)tb.X, (cufftDoubleReal*)tb.Y);
     else
-      r = cufftExecC2R(cn.invB, (cufftComplex*)cn.Xm, (cufftReal*)cn.Ym);
+      r = cufftExecC2R(tb.inv1, (cufftComplex*)tb.X, (cufftReal*)tb.Y);
     if (r != CUFFT_SUCCESS) return set_err(c, VOFL_ECUDA, "cuFFT batched inverse");
     return VOFL_OK;
   }
@@ -744,16 +778,16 @@ struct Plain : Engine {
   // r -> Y = L^T r
   int cn_transpose(vofl_ctx* c, const T* r) {
     const int nx = (int)c->n[0], ny = c->ndim > 1 ? (int)c->n[1] : 1, nz = c->ndim > 2 ? (int)c->n[2] : 1;
-    k_cn_pow_lap<T><<<grid_for(N), 256, 0, c->stream>>>(r, (const T*)c->delta, c->M, cn.Ym, nx, ny, nz, ryy(c),
+    k_cn_pow_lap<T><<<grid_for(N), 256, 0, c->stream>>>(r, (const T*)c->delta, c->M, tb.Y, nx, ny, nz, ryy(c),
                                                          rzz(c));
     count_launch();
     cufftResult res;
     if constexpr (sizeof(T) == 8)
-      res = cufftExecD2Z(cn.fwdB, (cufftDoubleReal*)cn.Ym, (cufftDoubleComplex*)cn.Xm);
+      res = cufftExecD2Z(tb.fwd1, (cufftDoubleReal*)tb.Y, (cufftDoubleComplex*)tb.X);
     else
-      res = cufftExecR2C(cn.fwdB, (cufftReal*)cn.Ym, (cufftComplex*)cn.Xm);
+      res = cufftExecR2C(tb.fwd1, (cufftReal*)tb.Y, (cufftComplex*)tb.X);
     if (res != CUFFT_SUCCESS) return set_err(c, VOFL_ECUDA, "cuFFT batched forward");
-    k_cn_tsum<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(cn.Xm, P1, Lg, c->M, X, Nh);
+    k_cn_tsum<T, C><<<grid_for(Nh), 256, 0, c->stream>>>(tb.X, P1, Lg, c->M, X, Nh);
     count_launch();
     return exec_inv(c, X, Y);
   }
@@ -776,7 +810,7 @@ struct Plain : Engine {
     int st;
     if ((st = cn_terms(c, (const T*)c->u[1 - cur]))) return st;
     const int G = cn_grid(N);
-    k_cn_horner<T><<<G, CN_THREADS, 0, c->stream>>>(cn.Ym, (const T*)c->delta, c->M, nullptr, T(0), T(1), acc1,
+    k_cn_horner<T><<<G, CN_THREADS, 0, c->stream>>>(tb.Y, (const T*)c->delta, c->M, nullptr, T(0), T(1), acc1,
                                                      nullptr, N);
     count_launch();
     const double c2 = 0.5 * c->kappa * c->dt * c->dt, h2 = 0.5 * c->dt * c->dt;
@@ -792,7 +826,7 @@ struct Plain : Engine {
     if ((st = cn_terms(c, cn.x))) return st;
     const int G = cn_grid(N);
     const double c2 = 0.5 * c->kappa * c->dt * c->dt, h2 = 0.5 * c->dt * c->dt;
-    k_cn_horner<T><<<G, CN_THREADS, 0, c->stream>>>(cn.Ym, (const T*)c->delta, c->M, cn.x, T(1), T(c2), cn.w,
+    k_cn_horner<T><<<G, CN_THREADS, 0, c->stream>>>(tb.Y, (const T*)c->delta, c->M, cn.x, T(1), T(c2), cn.w,
                                                      nullptr, N);
     count_launch();
     k_cn_resid<T><<<G, CN_THREADS, 0, c->stream>>>(cn.b, cn.x, cn.w, T(h2), T(c->f1), T(c->f3), cn.r, cn.pa, cn.pb,
@@ -823,7 +857,7 @@ struct Plain : Engine {
     for (int it = 0; it < kCnChunk; ++it) {
       int st;
       if ((st = cn_terms(c, cn.p))) return st;  // w = A p
-      k_cn_horner<T><<<G, CN_THREADS, 0, c->stream>>>(cn.Ym, (const T*)c->delta, c->M, cn.p, T(1), T(c2), cn.w,
+      k_cn_horner<T><<<G, CN_THREADS, 0, c->stream>>>(tb.Y, (const T*)c->delta, c->M, cn.p, T(1), T(c2), cn.w,
                                                        cn.pa, N);
       count_launch();
       k_cn_fin<<<1, CN_THREADS, 0, c->stream>>>(FIN_WW, cn.pa, nullptr, G, 0.0, cn.s);
@@ -979,12 +1013,14 @@ struct Plain : Engine {
 
 }  // namespace
 
-size_t plain_footprint(int ndim, const int64_t* n, int prec) {
+size_t plain_footprint(int ndim, const int64_t* n, int prec, int M) {
   long long N = 1;
   for (int i = 0; i < ndim; ++i) N *= n[i];
   const long long Nh = (n[0] / 2 + 1) * (N / n[0]);
   const size_t r = prec == VOFL_F64 ? 8 : 4;
-  return r * (2 * Nh * 2 + 3 * N + 3 * Nh) + 2 * r * N;  // + cuFFT work area (about one real field)
+  const size_t B = 2 * (size_t)(M + 1);  // the term batch: spectra and fields of both operators
+  // + cuFFT work areas (about one real field per transform of the batch)
+  return r * (2 * Nh * 2 + 3 * N + 3 * Nh) + 2 * r * N + B * r * (2 * Nh + N) + B * r * N;
 }
 
 Engine* make_plain(vofl_ctx* c, int* status) {

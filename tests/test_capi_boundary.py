@@ -48,6 +48,8 @@ def test_host_only_entry_points(vofl):
     # O(N) storage: a bounded number of fields, far below (M+1) * 2 spectra
     assert 6 * 4 * n < f_fused < 40 * 4 * n
     assert f_plain > 6 * 4 * n
+    # the plain baseline keeps every term's transformed field of both operators
+    assert f_plain > 2 * 17 * 4 * n > f_fused
     assert vofl.footprint_bytes((256, 256, 256), vofl.F32, vofl.IMPL_PLAIN, 8) > 6 * 4 * 256 ** 3
 
 
