@@ -181,7 +181,9 @@ VOFL_API int vofl_set_M(vofl_ctx* ctx, int M);
  * for an operator that does not belong to the model set. */
 VOFL_API int vofl_apply(vofl_ctx* ctx, int op, const void* u_dev, void* out_dev);
 
-/* Both operators on the same input (one forward transform, both sums). */
+/* Both operators of the seismic model on the same input (one forward
+ * transform, both sums).  VOFL_EINVAL for the general model, whose one
+ * operator is VOFL_OP_S of vofl_apply. */
 VOFL_API int vofl_apply_pair(vofl_ctx* ctx, const void* u_dev, void* out1_dev,
                     void* out2_dev);
 
@@ -310,7 +312,8 @@ VOFL_API const char* vofl_batch_last_error(const vofl_batch* b);
  * first).  *slot (may be NULL) receives an id for vofl_batch_remove.
  * Returns VOFL_OK, VOFL_EINVAL, VOFL_ESTATE (model or state not set, or
  * already in a batch), VOFL_EUNSUPPORTED (not a fused FP32 square 2D
- * context of a batched size) or VOFL_ECUDA. */
+ * context of a batched size, or a context of the general model) or
+ * VOFL_ECUDA. */
 VOFL_API int vofl_batch_add(vofl_batch* b, vofl_ctx* ctx, double dt, int* slot);
 
 /* Remove the context of `slot`; its own stream waits for the batch's

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const Batc
   // the descriptor (with its tensor map) was written by a host copy
   if (threadIdx.x == 0) tmap_acquire(&s->zmap);
   inv_cols_body<NY>(blockIdx.x, blockIdx.y, s->Uh, s->P, s->Lg, &s->zmap, NX / 2 + 1, m_lo, m_hi,
-                    (float)c_inv_fact[m_lo], s->twy);
+                    (float)c_inv_fact[m_lo], (float)c_inv_fact[m_lo], 0, s->twy);
 }
 
 template <int NX, int NY>
@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __re
   const int m_hi = min(s->M + 1, m_lo + BG);
   // groups above 0 store partial sums (the body tests m_lo), so the
   // epilogue arguments are read from the descriptor only by group 0
-  inv_rows_body<NX>(blockIdx.x, s->Z, s->zslot, s->pZ, NY, m_lo, m_hi, m_hi == s->M + 1 ? 1 : 0, s->delta, s->part,
+  inv_rows_body<NX, false>(blockIdx.x, s->Z, s->zslot, s->pZ, NY, m_lo, m_hi, m_hi == s->M + 1 ? 1 : 0, s->M + 1, 0, s->delta,
+                    s->part,
                     s->part + (size_t)NX * NY, s->epi, s->inv_lambda, s->twx, s->err);
 }
 
@@ -557,6 +558,8 @@ int vofl_batch_add(vofl_batch* b, vofl_ctx* c, double dt, int* slot) {
   if (c->batch) return berr(b, VOFL_ESTATE, "the context is already in a batch");
   if (c->ndim != 2 || c->prec != VOFL_F32 || c->impl != VOFL_IMPL_FUSED || c->n[0] != c->n[1])
     return berr(b, VOFL_EUNSUPPORTED, "batches take fused FP32 contexts of square 2D grids");
+  if (c->general)  // its solo steps split one operator's terms over both slots; batched steps do not
+    return berr(b, VOFL_EUNSUPPORTED, "batches take contexts of the seismic model");
   BatchSim probe{};
   BKernels k;
   if (!c->eng || !c->eng->batch_desc(c, &probe) || !pick_bkernels((int)c->n[0], (int)c->n[1], &k))

@@ -375,12 +375,19 @@ int vofl_set_M(vofl_ctx* c, int M) {
   return VOFL_OK;
 }
 
-int vofl_apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) {
-  if (int st = check_ctx(c)) return st;
-  if (!c->model_set) return set_err(c, VOFL_ESTATE, "set_q / set_gamma first");
+namespace {
+int apply_checked(vofl_ctx* c, const void* u, void* o1, void* o2) {
+  if (!c->model_set) return set_err(c, VOFL_ESTATE, "set the model first");
   if (!u || (!o1 && !o2)) return set_err(c, VOFL_EINVAL, "null array");
   if (int st = c->eng->prepare(c)) return st;
   return c->eng->apply_pair(c, u, o1, o2);
+}
+}  // namespace
+
+int vofl_apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) {
+  if (int st = check_ctx(c)) return st;
+  if (c->general) return set_err(c, VOFL_EINVAL, "the general model has one operator: vofl_apply(VOFL_OP_S)");
+  return apply_checked(c, u, o1, o2);
 }
 
 int vofl_apply(vofl_ctx* c, int op, const void* u, void* out) {
@@ -388,7 +395,7 @@ int vofl_apply(vofl_ctx* c, int op, const void* u, void* out) {
   if (op != VOFL_OP_1PG && op != VOFL_OP_HPG && op != VOFL_OP_S) return set_err(c, VOFL_EINVAL, "unknown operator");
   if (c->model_set && (op == VOFL_OP_S) != c->general)
     return set_err(c, VOFL_EINVAL, "VOFL_OP_S goes with vofl_set_order, the two seismic operators with set_q/gamma");
-  return vofl_apply_pair(c, u, op != VOFL_OP_HPG ? out : nullptr, op == VOFL_OP_HPG ? out : nullptr);
+  return apply_checked(c, u, op != VOFL_OP_HPG ? out : nullptr, op == VOFL_OP_HPG ? out : nullptr);
 }
 
 int vofl_set_state(vofl_ctx* c, const void* u0, const void* v0, int on_device) {

@@ -77,6 +77,16 @@ __device__ C* block_fft(C* a, C* b, const C* tw, int N, bool inv) {
   return a;
 }
 
+// the term layout of the two packed slots (as term_split in kernels.cuh)
+struct TermSplit1 {
+  int split_k, k2;
+};
+inline TermSplit1 term_split1(int M, bool one_operator) {
+  if (!one_operator) return {0, M + 1};
+  const int K = (M + 2) / 2;
+  return {K, M + 1 - K};
+}
+
 template <typename R>
 struct Sim1D {
   int N, M;
@@ -101,6 +111,8 @@ struct Sim1D {
   double src_scale;
   int nonlin;             // general model: f(u) = f1 u + f3 u^3
   R f1, f3;
+  int split_k;            // > 0: one operator, terms K.. in the imaginary slot (K = split_k)
+  int k2;                 // ... of which the first k2 exist (terms K..M)
   const R* apply_in;      // EPI_APPLY: input field
   R* out1;
   R* out2;
@@ -144,13 +156,21 @@ __global__ void __launch_bounds__(T1D) k1d_run(const Sim1D<R>* sims) {
     for (int k = threadIdx.x; k < N; k += blockDim.x) S[k] = f[k];
     __syncthreads();
     for (int i = 0; i < PPT; ++i) a1[i] = a2[i] = R(0);
-    double fact = 1.0;  // m! in double (40! overflows float)
-    for (int m = 1; m <= sp.M; ++m) fact *= m;
-    for (int m = sp.M; m >= 0; --m) {
+    // two operators: slot indices m = M..0, operator 1 real, operator 2
+    // imaginary; one operator (split_k = K): m = K-1..0, term m real and
+    // term m + K imaginary (when it exists)
+    const int K = sp.split_k;
+    const int top = K > 0 ? K - 1 : sp.M;
+    double fact = 1.0, fact2 = 1.0;  // m! and (m + K)! in double (40! overflows float)
+    for (int m = 1; m <= top; ++m) fact *= m;
+    for (int m = 1; m <= top + K; ++m) fact2 *= m;
+    for (int m = top; m >= 0; --m) {
       const R invf = R(1.0 / fact);
+      const R invf2 = K > 0 ? (m < sp.k2 ? R(1.0 / fact2) : R(0)) : invf;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        // L^m by squaring
-        R l = sp.Lg[k], p = R(1);
+        // L^m (and L^{m+K}) by squaring
+        const R l0 = sp.Lg[k];
+        R l = l0, p = R(1), q = R(1);
         int e = m;
         while (e) {
           if (e & 1) p *= l;
@@ -158,7 +178,19 @@ __global__ void __launch_bounds__(T1D) k1d_run(const Sim1D<R>* sims) {
           e >>= 1;
         }
         const R t = p * invf;
-        const R c1 = sp.P1[k] * t, c2 = sp.P2[k] * t;
+        R c1 = sp.P1[k] * t, c2;
+        if (K > 0) {
+          l = l0;
+          e = m + K;
+          while (e) {
+            if (e & 1) q *= l;
+            l *= l;
+            e >>= 1;
+          }
+          c2 = sp.P1[k] * q * invf2;
+        } else {
+          c2 = sp.P2[k] * t;
+        }
         const C sk = S[k];
         C w;  // (c1 + i c2) * S_k
         w.x = c1 * sk.x - c2 * sk.y;
@@ -177,6 +209,7 @@ __global__ void __launch_bounds__(T1D) k1d_run(const Sim1D<R>* sims) {
       }
       __syncthreads();
       if (m > 0) fact /= m;
+      if (m + K > 0) fact2 /= m + K;
     }
     // epilogue
     EpiArgs<R> e{};
@@ -201,7 +234,14 @@ __global__ void __launch_bounds__(T1D) k1d_run(const Sim1D<R>* sims) {
     e.f3 = sp.f3;
     for (int i = 0; i < PPT; ++i) {
       const int j = threadIdx.x + T1D * i;
-      if (j < N) epilogue_point<R>(e, j, a1[i], a2[i] * sp.inv_lambda2);
+      if (j >= N) continue;
+      if (K > 0) {  // sum_{m<K} + delta^K sum_{m>=K}
+        R dk = R(1);
+        for (int r = 0; r < K; ++r) dk *= dl[i];
+        epilogue_point<R>(e, j, a1[i] + dk * a2[i], R(0));
+      } else {
+        epilogue_point<R>(e, j, a1[i], a2[i] * sp.inv_lambda2);
+      }
     }
     __syncthreads();  // the next step reads the new u everywhere
     if (mode == EPI_APPLY) break;
@@ -331,6 +371,9 @@ struct Fused1D : Engine {
       s.f1 = em.f1;
       s.f3 = em.f3;
     }
+    const TermSplit1 ts = term_split1(c->M, c->general);
+    s.split_k = ts.split_k;
+    s.k2 = ts.k2;
     return s;
   }
 

@@ -49,9 +49,12 @@ namespace {
 struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
-  void (*inv_cols)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float, const float2*);
-  void (*inv_rows)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>,
-                   float, const float2*, int*);
+  void (*inv_cols)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int,
+                   const float2*);
+  using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
+                           EpiArgs<float>, float, const float2*, int*);
+  InvRows inv_rows;        // two operators
+  InvRows inv_rows_split;  // one operator, terms split over the slots
   size_t smem_frows, smem_fcols, smem_icols, smem_irows;
   int lpw_x, lpw_y;
   int wic;  // warps per CTA of inv_cols
@@ -63,7 +66,8 @@ Kernels kernels_for() {
   k.fwd_rows = k2d_fwd_rows<NX, false>;
   k.fwd_cols = k2d_fwd_cols<NY>;
   k.inv_cols = k2d_inv_cols<NY>;
-  k.inv_rows = k2d_inv_rows<NX>;
+  k.inv_rows = k2d_inv_rows<NX, false>;
+  k.inv_rows_split = k2d_inv_rows<NX, true>;
   k.smem_frows = frows_smem<NX, false>();
   k.smem_fcols = exch_smem<NY, W_FCOLS>();
   k.smem_icols = inv_cols_smem<NY>();
@@ -99,7 +103,7 @@ int set_smem_attributes(const Kernels& k) {
   if (set_kernel_smem(k.fwd_rows, k.smem_frows) ||
       set_kernel_smem(k.fwd_cols, k.smem_fcols) ||
       set_kernel_smem(k.inv_cols, k.smem_icols) ||
-      set_kernel_smem(k.inv_rows, k.smem_irows)) {
+      set_kernel_smem(k.inv_rows, k.smem_irows) || set_kernel_smem(k.inv_rows_split, k.smem_irows)) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
@@ -122,7 +126,8 @@ struct Plan2D {
   float ryy = 1.f, inv_lambda = 1.f;
   CUtensorMap zmap{};  // Z as [2 G ny rows][pZ] for the column kernel's tile stores
 
-  int groups(int M) const { return (M + 1 + G - 1) / G; }
+  // one_op: a model with one operator (its terms fill both slots)
+  int groups(int M, bool one_op = false) const { return (term_split(M, one_op).slots + G - 1) / G; }
 
   int make_zmap() {
     return make_tile_map(&zmap, Z, ncols, 2LL * G * ny, pZ, k.wic * k.lpw_y, std::min(ny, 256));
@@ -143,25 +148,29 @@ struct Plan2D {
   }
 
   // optional events: one after every inverse kernel, from ev[3] on
-  cudaError_t inverse(cudaStream_t s, int M, const EpiArgs<float>& epi, cudaEvent_t* ev = nullptr) const {
-    const int K = groups(M);
+  cudaError_t inverse(cudaStream_t s, int M, const EpiArgs<float>& epi, cudaEvent_t* ev = nullptr,
+                      bool one_op = false) const {
+    const TermSplit ts = term_split(M, one_op);
+    const int K = groups(M, one_op);
     const int cpc = k.wic * k.lpw_y;
     const dim3 gic((ncols + cpc - 1) / cpc, 2);
     const int rpc = W_IROWS * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
     int e_i = 3;
     for (int gi = K - 1; gi >= 0; --gi) {
-      const int m_lo = gi * G, m_hi = std::min(M + 1, m_lo + G);
+      const int m_lo = gi * G, m_hi = std::min(ts.slots, m_lo + G);
+      const float f0 = inv_factorial(m_lo), f1 = ts.split_k ? inv_factorial(m_lo + ts.split_k) : f0;
       cudaError_t e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, (const float2*)Uh,
-                                 (const float*)P, (const float*)Lg, zmap, ncols, m_lo, m_hi,
-                                 inv_factorial(m_lo), (const float2*)twy);
+                                 (const float*)P, (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k,
+                                 (const float2*)twy);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
       EpiArgs<float> ep = epi;
       if (gi > 0) ep.mode = EPI_PARTIAL;
-      e = launch_pdl(k.inv_rows, gir, dim3(W_IROWS * 32), k.smem_irows, s, (const float2*)Z, zslot, pZ, ny, m_lo, m_hi,
-                     gi == K - 1 ? 1 : 0, delta, part, part + (size_t)nx * ny, ep, inv_lambda, (const float2*)twx,
-                     err);
+      e = launch_pdl(one_op ? k.inv_rows_split : k.inv_rows, gir, dim3(W_IROWS * 32), k.smem_irows, s,
+                     (const float2*)Z, zslot, pZ, ny, m_lo, m_hi,
+                     gi == K - 1 ? 1 : 0, ts.k2, ts.split_k, delta, part, part + (size_t)nx * ny, ep, inv_lambda,
+                     (const float2*)twx, err);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
     }
@@ -270,7 +279,9 @@ struct Fused2D : Engine {
     return VOFL_OK;
   }
 
-  uint64_t kernels_per_step(const vofl_ctx* c) const override { return 2 + 2 * (uint64_t)p.groups(c->M); }
+  uint64_t kernels_per_step(const vofl_ctx* c) const override {
+    return 2 + 2 * (uint64_t)p.groups(c->M, c->general);
+  }
 
   int apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) override {
     EpiArgs<float> e{};
@@ -279,7 +290,7 @@ struct Fused2D : Engine {
     e.out2 = (float*)o2;
     e.src_flat = -1;
     cudaError_t err = p.forward(c->stream, (const float*)u, false);
-    if (!err) err = p.inverse(c->stream, c->M, e);
+    if (!err) err = p.inverse(c->stream, c->M, e, nullptr, c->general);
     if (err) return cuda_err(c, err, "fused 2D launch");
     return VOFL_OK;
   }
@@ -303,7 +314,7 @@ struct Fused2D : Engine {
     e.src_scale = c->dt * c->dt / hd;
     epi_model(c, &e);
     cudaError_t err = p.forward(c->stream, (const float*)c->u[c->cur], count_step);
-    if (!err) err = p.inverse(c->stream, c->M, e);
+    if (!err) err = p.inverse(c->stream, c->M, e, nullptr, c->general);
     if (err) return cuda_err(c, err, "fused 2D launch");
     return VOFL_OK;
   }
@@ -315,7 +326,8 @@ struct Fused2D : Engine {
   // with null outputs), so the context state is unchanged.
   int profile(vofl_ctx* c, int reps, std::string& names, double* ms, double* units, int cap) override {
     if (cap < 4) return 0;
-    const int K = p.groups(c->M);
+    const int K = p.groups(c->M, c->general);
+    const int slots = term_split(c->M, c->general).slots;
     const int nk = 2 + 2 * K;
     // one event set per repetition; all repetitions are queued back to back
     // (one warm-up first) and read after a single synchronisation, so the
@@ -329,12 +341,12 @@ struct Fused2D : Engine {
     const float* u = (const float*)c->u[c->cur];
     double acc[4] = {0, 0, 0, 0};
     double terms = 0;
-    for (int g = 0; g < K; ++g) terms += std::min(c->M + 1, (g + 1) * p.G) - g * p.G;
+    for (int g = 0; g < K; ++g) terms += std::min(slots, (g + 1) * p.G) - g * p.G;
     for (int r = 0; r < R; ++r) {
       cudaEvent_t* er = ev.data() + (size_t)r * (nk + 1);
       cudaEventRecord(er[0], c->stream);
       cudaError_t err = p.forward(c->stream, u, false, er);
-      if (!err) err = p.inverse(c->stream, c->M, ep, er);
+      if (!err) err = p.inverse(c->stream, c->M, ep, er, c->general);
       if (err) {
         for (auto& e : ev) cudaEventDestroy(e);
         return cuda_err(c, err, "profile");

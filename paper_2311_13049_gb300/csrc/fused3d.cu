@@ -38,11 +38,13 @@ struct Kernels3 {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_ycols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*fwd_zcols)(const float2*, int, float2*, int, const float2*, long long, long long);
-  void (*inv_z)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float,
+  void (*inv_z)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int,
                 const float2*);
   void (*inv_y)(const float2*, long long, float2*, long long, int, int, const float2*);
-  void (*inv_x)(const float2*, long long, int, int, int, int, int, const float*, float*, float*, EpiArgs<float>, float,
-                const float2*, int*);
+  using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
+                           EpiArgs<float>, float, const float2*, int*);
+  InvRows inv_x;        // two operators
+  InvRows inv_x_split;  // one operator, terms split over the slots
   size_t sm_frows, sm_fy, sm_fz, sm_iz, sm_iy, sm_ix;
   int lpw_x, lpw_y, lpw_z;
   int wiz;  // warps per CTA of inv_z
@@ -56,7 +58,8 @@ Kernels3 kernels3_for() {
   k.fwd_zcols = k2d_fwd_cols<NZ>;
   k.inv_z = k2d_inv_cols<NZ>;
   k.inv_y = k3d_inv_ycols<NY>;
-  k.inv_x = k2d_inv_rows<NX>;
+  k.inv_x = k2d_inv_rows<NX, false>;
+  k.inv_x_split = k2d_inv_rows<NX, true>;
   k.sm_frows = frows_smem<NX, true>();
   k.sm_fy = exch_smem<NY, W_FCOLS>();
   k.sm_fz = exch_smem<NZ, W_FCOLS>();
@@ -90,7 +93,7 @@ int set_smem3(const Kernels3& k) {
       set_kernel_smem(k.fwd_zcols, k.sm_fz) ||
       set_kernel_smem(k.inv_z, k.sm_iz) ||
       set_kernel_smem(k.inv_y, k.sm_iy) ||
-      set_kernel_smem(k.inv_x, k.sm_ix)) {
+      set_kernel_smem(k.inv_x, k.sm_ix) || set_kernel_smem(k.inv_x_split, k.sm_ix)) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
@@ -206,8 +209,11 @@ struct Fused3D : Engine {
     return VOFL_OK;
   }
 
-  int groups(int M) const { return (M + 1 + G - 1) / G; }
-  uint64_t kernels_per_step(const vofl_ctx* c) const override { return 3 + 3 * (uint64_t)groups(c->M); }
+  // one_op: a model with one operator (its terms fill both slots)
+  int groups(int M, bool one_op) const { return (term_split(M, one_op).slots + G - 1) / G; }
+  uint64_t kernels_per_step(const vofl_ctx* c) const override {
+    return 3 + 3 * (uint64_t)groups(c->M, c->general);
+  }
 
   cudaError_t forward(vofl_ctx* c, const float* u, bool inc_step) {
     cudaStream_t s = c->stream;
@@ -228,15 +234,17 @@ struct Fused3D : Engine {
 
   cudaError_t inverse(vofl_ctx* c, const EpiArgs<float>& epi) {
     cudaStream_t s = c->stream;
-    const int K = groups(c->M);
+    const TermSplit ts = term_split(c->M, c->general);
+    const int K = groups(c->M, c->general);
     const long long zslot_y = (long long)nz * ny * pZ;
     const int rows = ny * nz;
     for (int gi = K - 1; gi >= 0; --gi) {
-      const int m_lo = gi * G, m_hi = std::min(c->M + 1, m_lo + G);
+      const int m_lo = gi * G, m_hi = std::min(ts.slots, m_lo + G);
+      const float f0 = inv_factorial(m_lo), f1 = ts.split_k ? inv_factorial(m_lo + ts.split_k) : f0;
       const int cz = k.wiz * k.lpw_z;
       cudaError_t e = launch_pdl(k.inv_z, dim3((c3 + cz - 1) / cz, 2), dim3(k.wiz * 32), k.sm_iz, s, (const float2*)U3,
-                                 (const float*)P, (const float*)Lg, zmap, c3, m_lo, m_hi,
-                                 inv_factorial(m_lo), (const float2*)twz);
+                                 (const float*)P, (const float*)Lg, zmap, c3, m_lo, m_hi, f0, f1, ts.split_k,
+                                 (const float2*)twz);
       if (e) return e;
       const int cy = W_YCOLS * k.lpw_y;
       e = launch_pdl(k.inv_y, dim3((c2 + cy - 1) / cy, 2 * (m_hi - m_lo) * nz), dim3(W_YCOLS * 32), k.sm_iy, s,
@@ -245,8 +253,9 @@ struct Fused3D : Engine {
       EpiArgs<float> ep = epi;
       if (gi > 0) ep.mode = EPI_PARTIAL;
       const int rpc = W_IROWS * k.lpw_x;
-      e = launch_pdl(k.inv_x, dim3((rows + rpc - 1) / rpc), dim3(W_IROWS * 32), k.sm_ix, s, (const float2*)Zy, zslot_y,
-                     pZ, rows, m_lo, m_hi, gi == K - 1 ? 1 : 0, (const float*)c->delta, part,
+      e = launch_pdl(ts.split_k ? k.inv_x_split : k.inv_x, dim3((rows + rpc - 1) / rpc), dim3(W_IROWS * 32), k.sm_ix,
+                     s, (const float2*)Zy, zslot_y,
+                     pZ, rows, m_lo, m_hi, gi == K - 1 ? 1 : 0, ts.k2, ts.split_k, (const float*)c->delta, part,
                      part + (size_t)nx * ny * nz, ep, inv_lambda, (const float2*)twx, c->d_step + 1);
       if (e) return e;
     }

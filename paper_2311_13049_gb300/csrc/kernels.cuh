@@ -268,7 +268,7 @@ template <int NY>
 __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __restrict__ Uh,
                                               const float* __restrict__ P, const float* __restrict__ Lg,
                                               const void* zmap, int ncols, int m_lo, int m_hi, float inv_fact_lo,
-                                              const float2* __restrict__ twy) {
+                                              float inv_fact_lo1, int split_k, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL, RL = F::RL;
   constexpr int W = icols_warps<NY>(), THREADS = W * 32, CW = W * LPW;  // columns per CTA
@@ -293,7 +293,10 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   const int cc = min(c, ncols - 1);
   const long long tot = (long long)ncols * NY;
   const float2* uh_col = Uh + (size_t)cc * NY;
-  const float* p_col = P + op * tot + (size_t)cc * NY;
+  // split_k > 0 (one operator): slot op = 1 carries the terms m + split_k of
+  // operator 1 (multiplier P[0] ln|mu|^{2(m + split_k)} / (m + split_k)!)
+  const int off = (split_k > 0 && op) ? split_k : 0;
+  const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
   const float* l_col = Lg + (size_t)cc * NY;
   float tm[E], lg[PAIR ? 1 : E];
   // tables first (they do not depend on the previous kernel)
@@ -305,7 +308,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
       s_lg[y] = l;
     else
       lg[m] = l;
-    tm[m] = p_col[y] * powi(l, m_lo) * inv_fact_lo;
+    tm[m] = p_col[y] * powi(l, m_lo + off) * (op ? inv_fact_lo1 : inv_fact_lo);
   }
   __syncthreads();
   pdl_wait();  // Uh (k2d_fwd_cols) ready; the previous group's readers of Z are done
@@ -316,7 +319,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   for (int m = 0; m < E; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
   // v <- v ln|mu|^2 / (m + 1): the next term
   auto advance = [&](int mt) {
-    const float rinv = 1.0f / (float)(mt + 1);
+    const float rinv = 1.0f / (float)(mt + 1 + off);
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cscale(v[m], (PAIR ? s_lg[li + LANES * m] : lg[m]) * rinv);
   };
@@ -444,8 +447,10 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(const flo
                                                            const float* __restrict__ Lg,
                                                            const __grid_constant__ CUtensorMap zmap, int ncols,
                                                            int m_lo, int m_hi, float inv_fact_lo,
+                                                           float inv_fact_lo1, int split_k,
                                                            const float2* __restrict__ twy) {
-  inv_cols_body<NY>(blockIdx.x, blockIdx.y, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, twy);
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, inv_fact_lo1, split_k,
+                    twy);
 }
 
 // -------------------------------------------------------------------------
@@ -464,9 +469,12 @@ constexpr size_t inv_rows_smem() {
   return exch_smem<NX, W_IROWS>() + (size_t)W_IROWS * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
 }
 
-template <int NX>
+// SPLIT: one operator whose terms fill both slots (TermSplit); k2 and
+// split_k are read only then
+template <int NX, bool SPLIT>
 __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__ Z, long long zslot, int pZ, int ny,
-                                              int m_lo, int m_hi, int top, const float* __restrict__ delta,
+                                              int m_lo, int m_hi, int top, int k2, int split_k,
+                                              const float* __restrict__ delta,
                                               float* __restrict__ part1, float* __restrict__ part2,
                                               const EpiArgs<float>& epi, float inv_lambda,
                                               const float2* __restrict__ twx, int* err) {
@@ -572,10 +580,11 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
       }
     }
     fft_line<NX, true>(w, wbuf, s_tw, li, line);
+    const bool use2 = !SPLIT || mt < k2;  // slot 2 holds a term of the expansion
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       a1[m] = fmaf(dl[m], a1[m], w[m].x);
-      a2[m] = fmaf(dl[m], a2[m], w[m].y);
+      if (use2) a2[m] = fmaf(dl[m], a2[m], w[m].y);
     }
   }
   if (!active || !ok) return;
@@ -585,6 +594,13 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
       part1[row + li + LANES * m] = a1[m];
       part2[row + li + LANES * m] = a2[m];
     }
+  } else if constexpr (SPLIT) {  // one operator: sum_{m<K} + delta^K sum_{m>=K}
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      float dk = 1.f;
+      for (int j = 0; j < split_k; ++j) dk *= dl[m];
+      epilogue_point<float>(epi, (long long)(row + li + LANES * m), fmaf(dk, a2[m], a1[m]), 0.f);
+    }
   } else {
 #pragma unroll
     for (int m = 0; m < E; ++m)
@@ -592,14 +608,15 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   }
 }
 
-template <int NX>
+template <int NX, bool SPLIT>
 __global__ void __launch_bounds__(W_IROWS * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
-                                                           int ny, int m_lo, int m_hi, int top,
+                                                           int ny, int m_lo, int m_hi, int top, int k2, int split_k,
                                                            const float* __restrict__ delta, float* __restrict__ part1,
                                                            float* __restrict__ part2, EpiArgs<float> epi,
                                                            float inv_lambda, const float2* __restrict__ twx,
                                                            int* err) {
-  inv_rows_body<NX>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, delta, part1, part2, epi, inv_lambda, twx, err);
+  inv_rows_body<NX, SPLIT>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, k2, split_k, delta, part1, part2, epi,
+                           inv_lambda, twx, err);
 }
 
 // -------------------------------------------------------------------------
@@ -663,6 +680,21 @@ cudaError_t set_kernel_smem(void (*kern)(KArgs...), size_t bytes) {
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // 1/m! in double, rounded once to float
+// How the Taylor terms m = 0..M fill the two operator slots of the inverse
+// kernels: one term of each operator per slot index (two operators), or,
+// for a model with one operator, terms 0..K-1 in slot 0 and K..M in slot 1
+// (K = ceil((M+1)/2)), combined as sum_0 + delta^K sum_1 in the epilogue.
+struct TermSplit {
+  int slots;    // slot indices 0..slots-1
+  int k2;       // slot-1 indices below k2 hold a term
+  int split_k;  // slot-1 term offset (0: two operators)
+};
+inline TermSplit term_split(int M, bool one_operator) {
+  if (!one_operator) return {M + 1, M + 1, 0};
+  const int K = (M + 2) / 2;
+  return {K, M + 1 - K, K};
+}
+
 inline float inv_factorial(int m) {
   double f = 1.0;
   for (int i = 2; i <= m; ++i) f *= i;

@@ -269,3 +269,64 @@ def test_paper_table5_spatial_errors_on_the_gpu(V, golden_dir, col, order):
             assert abs(err - printed) <= 1e-4 * printed, (order, inv_h, err, printed)
         else:
             assert err < 1e-11, (order, err)
+
+
+def _apply_s(V, shape, s, u, M, prec, lo, hi):
+    import torch
+    P = V.F32 if prec == "f32" else V.F64
+    ty = np.float32 if P == V.F32 else np.float64
+    uin = np.ascontiguousarray(u, dtype=ty)
+    with V.Solver(shape, lo, hi, P, V.IMPL_FUSED) as sv:
+        sv.set_order(np.ascontiguousarray(s, dtype=np.float64))
+        sv.set_M(M)
+        ut = torch.from_numpy(uin).cuda()
+        out = torch.empty_like(ut)
+        sv.apply(V.OP_S, ut, out)
+        sv.sync()
+        with pytest.raises(V.VoflError):
+            sv.apply_pair(ut, out, torch.empty_like(ut))  # one operator: vofl_apply(VOFL_OP_S)
+        return out.cpu().numpy().astype(np.float64), uin.astype(np.float64)
+
+
+@pytest.mark.parametrize("M", [0, 1, 2, 7, 8, 15, 20])
+def test_one_operator_split_2d(V, M):
+    """The general model's terms fill both slots of the fused 2D kernels
+    (terms 0..K-1 and K..M, K = ceil((M+1)/2)): every M, odd and even term
+    counts, against the oracle's M-term operator."""
+    shape, lo, hi = (128, 128), [-8.0, -8.0], [8.0, 8.0]
+    s = _s2d(shape, lo, hi)
+    u = S.q_lowpass(shape, 7, qmin=-1.0, qmax=1.0, sigma_k=20.0)
+    g, uin = _apply_s(V, shape, s, u, M, "f32", lo, hi)
+    r = O.matrix_free_operator(uin, s, M, lo, hi)
+    assert rel_l2(g, r) <= 1e-5, (M, rel_l2(g, r))
+
+
+@pytest.mark.parametrize("M", [3, 8])
+def test_one_operator_split_3d(V, M):
+    shape, lo, hi = (64, 64, 64), [-4.0] * 3, [4.0] * 3
+    xg, yg, zg = S.mesh(shape, lo, hi)
+    s = 1.0 + 0.25 * np.sin(np.pi * xg / 4) * np.cos(np.pi * yg / 4) + 0.1 * np.cos(np.pi * zg / 4)
+    u = S.gaussian_pulse(shape, 5.0)
+    g, uin = _apply_s(V, shape, s, u, M, "f32", lo, hi)
+    r = O.matrix_free_operator(uin, s, M, lo, hi)
+    assert rel_l2(g, r) <= 1e-5, (M, rel_l2(g, r))
+
+
+@pytest.mark.parametrize("M,prec,tol", [(5, "f64", 1e-11), (12, "f64", 1e-11), (9, "f32", 1e-5)])
+def test_one_operator_split_1d(V, M, prec, tol):
+    n, lo, hi = 1024, [-32.0], [32.0]
+    x = S.axis(n, -32.0, 32.0)
+    s = 1.0 + 0.3 * np.sin(np.pi * x / 8)
+    u = np.exp(-x * x) * np.cos(2.0 * x)
+    g, uin = _apply_s(V, (n,), s, u, M, prec, lo, hi)
+    r = O.matrix_free_operator(uin, s, M, lo, hi)
+    assert rel_l2(g, r) <= tol, (M, rel_l2(g, r))
+
+
+def test_batches_take_seismic_contexts_only(V):
+    shape = (256, 256)
+    with V.Solver(shape) as sv, V.Batch() as b:
+        sv.set_order(np.ones(shape))
+        sv.set_state(np.zeros(shape, np.float32))
+        with pytest.raises(V.VoflError):
+            b.add(sv, 1e-3)
