@@ -14,6 +14,7 @@
 //   pointwise leap-frog update (Eq. (3.4) extended to Eq. (1.1)).
 // The FFT is a radix-2 Stockham autosort over the CTA (Govindaraju et al.,
 // SC 2008), ping-ponging between two shared buffers.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -251,6 +252,187 @@ __global__ void __launch_bounds__(T1D) k1d_run(const Sim1D<R>* sims) {
   }
 }
 
+// The same run on a thread-block cluster of CL CTAs (distributed shared
+// memory).  GB300's FP64 rate is ~8 GFLOP/s per SM, so one CTA per line is
+// FP64-bound on a single SM; the cluster spreads the M+1 (or K) inverse
+// transforms over CL SMs.  Per step:
+//   1. every CTA transforms the whole u^n (held in its shared memory U);
+//   2. CTA r takes the slot indices m = r, r+CL, ... (descending), sums
+//      Y_m delta^(m-r) by Horner in delta^CL and scales by delta^r;
+//   3. it stores its partial sums for the points of slice q (N/CL points)
+//      into CTA q's receive buffer (DSMEM);          -- cluster barrier
+//   4. CTA q adds the CL partials of its slice in rank order, runs the
+//      epilogue for its slice and stores u^{n+1} of the slice into every
+//      CTA's U (DSMEM);                               -- cluster barrier
+// Every CTA runs the same steps, so every CTA reaches every barrier.
+template <typename R>
+size_t smem_1dc(int N) {
+  using C = typename C2<R>::T;
+  return sizeof(C) * (3 * (size_t)N + N / 2) + sizeof(R) * 3 * (size_t)N;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(T1D) k1d_cluster_run(const Sim1D<R>* sims, int CL) {
+  namespace cg = cooperative_groups;
+  using C = typename C2<R>::T;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const Sim1D<R> sp = sims[blockIdx.x / CL];
+  const int N = sp.N, H = N / 2, SL = N / CL;
+  const int PPT = N / T1D > 0 ? N / T1D : 1;
+  extern __shared__ unsigned char smem_raw[];
+  C* S = reinterpret_cast<C*>(smem_raw);
+  C* B0 = S + N;
+  C* B1 = B0 + N;
+  C* tws = B1 + N;
+  R* U = reinterpret_cast<R*>(tws + H);  // u^n, whole line
+  R* RX = U + N;                         // [CL][SL][2] partial sums of this CTA's slice
+  const int K = sp.split_k;
+  const int slots = K > 0 ? K : sp.M + 1;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) tws[i] = sp.tw[i];
+  R dl[MAX_PTS_PER_THREAD], dcl[MAX_PTS_PER_THREAD], a1[MAX_PTS_PER_THREAD], a2[MAX_PTS_PER_THREAD];
+  for (int i = 0; i < PPT; ++i) {
+    const int j = threadIdx.x + T1D * i;
+    dl[i] = j < N ? sp.delta[j] : R(0);
+    R p = R(1);
+    for (int r = 0; r < CL; ++r) p *= dl[i];
+    dcl[i] = p;
+  }
+  R* ucur = sp.u[sp.cur];
+  R* uoth = sp.u[1 - sp.cur];
+  {
+    const R* u0 = sp.mode_first == EPI_APPLY ? sp.apply_in : ucur;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) U[j] = u0[j];
+  }
+  cluster.sync();  // every CTA of the cluster runs before any remote access
+  // this CTA's highest slot index m = rank + CL t
+  const int mtop = rank < slots ? rank + CL * ((slots - 1 - rank) / CL) : -1;
+  for (int s = 0; s < sp.nsteps; ++s) {
+    const int mode = (s == 0) ? sp.mode_first : EPI_STEP;
+    // 1. spectrum of D_xx u^n
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const R c = U[j];
+      C v;
+      v.x = (U[j + 1 == N ? 0 : j + 1] - c) - (c - U[j == 0 ? N - 1 : j - 1]);
+      v.y = R(0);
+      B0[j] = v;
+    }
+    __syncthreads();
+    C* f = block_fft<C>(B0, B1, tws, N, false);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) S[k] = f[k];
+    __syncthreads();
+    // 2. this CTA's slot indices, Horner in delta^CL
+    for (int i = 0; i < PPT; ++i) a1[i] = a2[i] = R(0);
+    double fact = 1.0, fact2 = 1.0;  // m! and (m + K)! of the current m
+    for (int m = 1; m <= mtop; ++m) fact *= m;
+    for (int m = 1; m <= mtop + K; ++m) fact2 *= m;
+    for (int m = mtop; m >= 0; m -= CL) {
+      const R invf = R(1.0 / fact);
+      const R invf2 = K > 0 ? (m < sp.k2 ? R(1.0 / fact2) : R(0)) : invf;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const R l0 = sp.Lg[k];
+        R l = l0, p = R(1), q = R(1);
+        int e = m;
+        while (e) {
+          if (e & 1) p *= l;
+          l *= l;
+          e >>= 1;
+        }
+        const R c1 = sp.P1[k] * p * invf;
+        R c2;
+        if (K > 0) {
+          l = l0;
+          e = m + K;
+          while (e) {
+            if (e & 1) q *= l;
+            l *= l;
+            e >>= 1;
+          }
+          c2 = sp.P1[k] * q * invf2;
+        } else {
+          c2 = sp.P2[k] * p * invf;
+        }
+        const C sk = S[k];
+        C w;
+        w.x = c1 * sk.x - c2 * sk.y;
+        w.y = c1 * sk.y + c2 * sk.x;
+        B0[k] = w;
+      }
+      __syncthreads();
+      C* y = block_fft<C>(B0, B1, tws, N, true);
+      for (int i = 0; i < PPT; ++i) {
+        const int j = threadIdx.x + T1D * i;
+        if (j < N) {
+          const C v = y[j];
+          a1[i] = v.x + dcl[i] * a1[i];
+          a2[i] = v.y + dcl[i] * a2[i];
+        }
+      }
+      __syncthreads();
+      for (int t = 0; t < CL && m - t > 0; ++t) fact /= (m - t);      // (m - CL)!
+      for (int t = 0; t < CL && m + K - t > 0; ++t) fact2 /= (m + K - t);
+    }
+    // 3. scale by delta^rank and send each slice's partials to its owner
+    for (int i = 0; i < PPT; ++i) {
+      const int j = threadIdx.x + T1D * i;
+      if (j >= N) continue;
+      R dr = R(1);
+      for (int r = 0; r < rank; ++r) dr *= dl[i];
+      const int q = j / SL, jj = j - q * SL;
+      R* dst = cluster.map_shared_rank(RX, q) + 2 * ((size_t)rank * SL + jj);
+      dst[0] = a1[i] * dr;
+      dst[1] = a2[i] * dr;
+    }
+    cluster.sync();
+    // 4. the owner of slice `rank` sums, updates and broadcasts
+    EpiArgs<R> e{};
+    e.mode = mode;
+    e.out1 = sp.out1;
+    e.out2 = sp.out2;
+    e.u_cur = ucur;
+    e.u_other = uoth;
+    e.l2p = sp.l2p;
+    e.A = sp.A;
+    e.B = sp.B;
+    e.dt1 = sp.dt1;
+    e.dt2 = sp.dt2;
+    e.src_flat = sp.src_flat;
+    e.src = sp.src;
+    e.nsrc = sp.nsrc;
+    const int n_step = sp.step0 + s;
+    e.step = &n_step;
+    e.src_scale = sp.src_scale;
+    e.nonlin = sp.nonlin;
+    e.f1 = sp.f1;
+    e.f3 = sp.f3;
+    for (int jj = threadIdx.x; jj < SL; jj += blockDim.x) {
+      const int j = rank * SL + jj;
+      R L1 = R(0), L2 = R(0);
+      for (int r = 0; r < CL; ++r) {
+        L1 += RX[2 * ((size_t)r * SL + jj)];
+        L2 += RX[2 * ((size_t)r * SL + jj) + 1];
+      }
+      if (K > 0) {  // sum_{m<K} + delta^K sum_{m>=K}
+        const R d = sp.delta[j];
+        R dk = R(1);
+        for (int r = 0; r < K; ++r) dk *= d;
+        epilogue_point<R>(e, j, L1 + dk * L2, R(0));
+      } else {
+        epilogue_point<R>(e, j, L1, L2 * sp.inv_lambda2);
+      }
+      if (mode != EPI_APPLY) {
+        const R un = uoth[j];
+        for (int q = 0; q < CL; ++q) cluster.map_shared_rank(U, q)[j] = un;
+      }
+    }
+    cluster.sync();  // U holds u^{n+1} everywhere; RX may be rewritten
+    if (mode == EPI_APPLY) break;
+    R* t = ucur;
+    ucur = uoth;
+    uoth = t;
+  }
+}
+
 template <typename R>
 __global__ void k1d_tables(int N, double L, double s01, double s02, double lambda2, R* P1, R* P2, R* Lg) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
@@ -299,6 +481,36 @@ struct Fused1D : Engine {
   Sim1D<R>* d_sim = nullptr;
   double lambda2 = 1.0;
   size_t nbytes = 0;
+  bool cluster_ok = false;
+  int cluster_fits[4] = {-1, -1, -1, -1};  // CL = 2, 4, 8: can one cluster be resident (-1 unknown)
+  static constexpr size_t kMaxSmem = 227 * 1024;
+
+  cudaLaunchConfig_t cluster_cfg(int CL, cudaLaunchAttribute* at, cudaStream_t st) const {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(T1D);
+    cfg.dynamicSmemBytes = smem_1dc<R>(N);
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+  }
+  // whether a cluster of CL CTAs with this line's shared memory can run
+  bool fits(int CL, cudaStream_t st) {
+    int& f = cluster_fits[CL == 2 ? 0 : CL == 4 ? 1 : 2];
+    if (f < 0) {
+      cudaLaunchAttribute at[1];
+      cudaLaunchConfig_t cfg = cluster_cfg(CL, at, st);
+      int n = 0;
+      f = cudaOccupancyMaxActiveClusters(&n, k1d_cluster_run<R>, &cfg) == cudaSuccess && n >= 1 ? 1 : 0;
+      cudaGetLastError();
+    }
+    return f == 1;
+  }
 
   ~Fused1D() override {
     cudaFree(P1);
@@ -325,6 +537,11 @@ struct Fused1D : Engine {
       cudaGetLastError();
       return set_err(c, VOFL_EUNSUPPORTED, "fused 1D path: line too long for shared memory");
     }
+    // the cluster form where its buffers fit one CTA's shared memory
+    cluster_ok = smem_1dc<R>(N) <= kMaxSmem &&
+                 cudaFuncSetAttribute(k1d_cluster_run<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_1dc<R>(N)) == cudaSuccess;
+    cudaGetLastError();
     k1d_twiddles<C><<<std::max(1, N / 512), 256, 0, c->stream>>>(N, tw);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 1D twiddles");
@@ -384,6 +601,20 @@ struct Fused1D : Engine {
     if (cudaMemcpyAsync(d_sim, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
       cudaGetLastError();
       return set_err(c, VOFL_ECUDA, "fused 1D parameters");
+    }
+    // CTAs per line: a power of two up to 8 (the portable cluster size), at
+    // most one per slot index
+    const int slots = s.split_k > 0 ? s.split_k : s.M + 1;
+    int CL = 1;
+    while (CL * 2 <= std::min(8, slots) && N % (CL * 2) == 0) CL *= 2;
+    while (CL > 1 && !(cluster_ok && fits(CL, c->stream))) CL /= 2;
+    if (CL > 1) {
+      cudaLaunchAttribute at[1];
+      cudaLaunchConfig_t cfg = cluster_cfg(CL, at, c->stream);
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k1d_cluster_run<R>, (const Sim1D<R>*)d_sim, CL);
+      count_launch();
+      if (e != cudaSuccess) return cuda_err(c, e, "fused 1D cluster launch");
+      return VOFL_OK;
     }
     k1d_run<R><<<1, T1D, smem_1d<R>(N), c->stream>>>(d_sim);
     count_launch();
