@@ -464,14 +464,14 @@ template <int NX>
 constexpr int rows_rb() {
   return (NX / 2 + 2) & ~1;  // Z row copy length in float2: >= H+1, 16-byte multiple
 }
-template <int NX>
+template <int NX, int W = W_IROWS>
 constexpr size_t inv_rows_smem() {
-  return exch_smem<NX, W_IROWS>() + (size_t)W_IROWS * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
+  return exch_smem<NX, W>() + (size_t)W * LineFFT<NX>::LPW * 2 * 2 * rows_rb<NX>() * sizeof(float2);
 }
 
 // SPLIT: one operator whose terms fill both slots (TermSplit); k2 and
-// split_k are read only then
-template <int NX, bool SPLIT>
+// split_k are read only then.  W: warps (rows) per CTA.
+template <int NX, bool SPLIT, int W = W_IROWS>
 __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__ Z, long long zslot, int pZ, int ny,
                                               int m_lo, int m_hi, int top, int k2, int split_k,
                                               const float* __restrict__ delta,
@@ -479,17 +479,17 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
                                               const EpiArgs<float>& epi, float inv_lambda,
                                               const float2* __restrict__ twx, int* err) {
   using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W_IROWS * 32;
+  constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W * 32;
   constexpr int RB = rows_rb<NX>();
   constexpr uint32_t RB_BYTES = RB * sizeof(float2);
   __shared__ float2 s_tw[F::TW];
-  __shared__ uint64_t s_bar[W_IROWS * LPW * 2];
+  __shared__ uint64_t s_bar[W * LPW * 2];
   extern __shared__ __align__(128) float2 s_buf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   const int lid = warp * LPW + line;  // line id inside the CTA
   uint64_t* bar = s_bar + 2 * lid;
-  float2* zbuf = s_buf + W_IROWS * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
+  float2* zbuf = s_buf + W * warp_stride<NX>() + (size_t)lid * 4 * RB;  // [buf][op][RB]
   if (li == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -497,7 +497,7 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   }
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
   float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int yr = (bx * W_IROWS + warp) * LPW + line;
+  const int yr = (bx * W + warp) * LPW + line;
   const bool active = yr < ny;
   const int y = active ? yr : 0;
   const size_t row = (size_t)y * NX;
@@ -608,15 +608,15 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   }
 }
 
-template <int NX, bool SPLIT>
-__global__ void __launch_bounds__(W_IROWS * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
+template <int NX, bool SPLIT, int W = W_IROWS>
+__global__ void __launch_bounds__(W * 32) k2d_inv_rows(const float2* __restrict__ Z, long long zslot, int pZ,
                                                            int ny, int m_lo, int m_hi, int top, int k2, int split_k,
                                                            const float* __restrict__ delta, float* __restrict__ part1,
                                                            float* __restrict__ part2, EpiArgs<float> epi,
                                                            float inv_lambda, const float2* __restrict__ twx,
                                                            int* err) {
-  inv_rows_body<NX, SPLIT>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, k2, split_k, delta, part1, part2, epi,
-                           inv_lambda, twx, err);
+  inv_rows_body<NX, SPLIT, W>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, k2, split_k, delta, part1, part2, epi,
+                              inv_lambda, twx, err);
 }
 
 // -------------------------------------------------------------------------
