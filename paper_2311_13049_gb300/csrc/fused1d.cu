@@ -114,6 +114,7 @@ struct Sim1D {
   R f1, f3;
   int split_k;            // > 0: one operator, terms K.. in the imaginary slot (K = split_k)
   int k2;                 // ... of which the first k2 exist (terms K..M)
+  const R* T;             // [2][M+1][N] multipliers P_op ln|mu|^{2m}/m! (cluster kernel)
   const R* apply_in;      // EPI_APPLY: input field
   R* out1;
   R* out2;
@@ -323,35 +324,11 @@ __global__ void __launch_bounds__(T1D) k1d_cluster_run(const Sim1D<R>* sims, int
     __syncthreads();
     // 2. this CTA's slot indices, Horner in delta^CL
     for (int i = 0; i < PPT; ++i) a1[i] = a2[i] = R(0);
-    double fact = 1.0, fact2 = 1.0;  // m! and (m + K)! of the current m
-    for (int m = 1; m <= mtop; ++m) fact *= m;
-    for (int m = 1; m <= mtop + K; ++m) fact2 *= m;
     for (int m = mtop; m >= 0; m -= CL) {
-      const R invf = R(1.0 / fact);
-      const R invf2 = K > 0 ? (m < sp.k2 ? R(1.0 / fact2) : R(0)) : invf;
+      const R* t1 = sp.T + (size_t)m * N;
+      const R* t2 = K > 0 ? (m < sp.k2 ? sp.T + (size_t)(m + K) * N : nullptr) : sp.T + (size_t)(sp.M + 1 + m) * N;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const R l0 = sp.Lg[k];
-        R l = l0, p = R(1), q = R(1);
-        int e = m;
-        while (e) {
-          if (e & 1) p *= l;
-          l *= l;
-          e >>= 1;
-        }
-        const R c1 = sp.P1[k] * p * invf;
-        R c2;
-        if (K > 0) {
-          l = l0;
-          e = m + K;
-          while (e) {
-            if (e & 1) q *= l;
-            l *= l;
-            e >>= 1;
-          }
-          c2 = sp.P1[k] * q * invf2;
-        } else {
-          c2 = sp.P2[k] * p * invf;
-        }
+        const R c1 = t1[k], c2 = t2 ? t2[k] : R(0);
         const C sk = S[k];
         C w;
         w.x = c1 * sk.x - c2 * sk.y;
@@ -369,8 +346,6 @@ __global__ void __launch_bounds__(T1D) k1d_cluster_run(const Sim1D<R>* sims, int
         }
       }
       __syncthreads();
-      for (int t = 0; t < CL && m - t > 0; ++t) fact /= (m - t);      // (m - CL)!
-      for (int t = 0; t < CL && m + K - t > 0; ++t) fact2 /= (m + K - t);
     }
     // 3. scale by delta^rank and send each slice's partials to its owner
     for (int i = 0; i < PPT; ++i) {
@@ -433,6 +408,24 @@ __global__ void __launch_bounds__(T1D) k1d_cluster_run(const Sim1D<R>* sims, int
   }
 }
 
+// T[op][m][k] = P_op[k] ln|mu_k|^{2m} / m!, m = 0..M (the multipliers of
+// Eq. (2.13) per term; the cluster kernel reads them instead of forming
+// the powers every step)
+template <typename R>
+__global__ void k1d_term_tables(int N, int M, const R* __restrict__ P1, const R* __restrict__ P2,
+                                const R* __restrict__ Lg, R* __restrict__ T) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    // in double, rounded once to R (set-up work)
+    const double l = (double)Lg[k], p1 = (double)P1[k], p2 = (double)P2[k];
+    double t = 1.0;  // ln|mu|^{2m} / m!
+    for (int m = 0; m <= M; ++m) {
+      if (m > 0) t = t * l / m;
+      T[(size_t)m * N + k] = R(p1 * t);
+      T[(size_t)(M + 1 + m) * N + k] = R(p2 * t);
+    }
+  }
+}
+
 template <typename R>
 __global__ void k1d_tables(int N, double L, double s01, double s02, double lambda2, R* P1, R* P2, R* Lg) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
@@ -482,6 +475,9 @@ struct Fused1D : Engine {
   double lambda2 = 1.0;
   size_t nbytes = 0;
   bool cluster_ok = false;
+  R* T = nullptr;  // per-term multipliers [2][M+1][N] (cluster kernel)
+  int tab_M = -1, model_gen = 0, tab_gen = -1;
+  size_t tab_bytes = 0;
   int cluster_fits[4] = {-1, -1, -1, -1};  // CL = 2, 4, 8: can one cluster be resident (-1 unknown)
   static constexpr size_t kMaxSmem = 227 * 1024;
 
@@ -518,6 +514,7 @@ struct Fused1D : Engine {
     cudaFree(Lg);
     cudaFree(tw);
     cudaFree(d_sim);
+    cudaFree(T);
   }
   size_t bytes() const override { return nbytes; }
 
@@ -556,6 +553,33 @@ struct Fused1D : Engine {
                                                                P2, Lg);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 1D tables");
+    ++model_gen;  // the term tables follow in prepare()
+    return VOFL_OK;
+  }
+
+  // per-term multiplier tables for the context's M and model
+  int prepare(vofl_ctx* c) override {
+    if (T && tab_M == c->M && tab_gen == model_gen) return VOFL_OK;
+    if (tab_M != c->M) {
+      VOFL_CUDA(c, cudaStreamSynchronize(c->stream));  // queued work may still read the old table
+      cudaFree(T);
+      T = nullptr;
+      nbytes -= tab_bytes;
+      tab_bytes = sizeof(R) * 2 * (size_t)(c->M + 1) * N;
+      const cudaError_t e = cudaMalloc(&T, tab_bytes);
+      if (e != cudaSuccess) {
+        T = nullptr;
+        tab_bytes = 0;
+        tab_M = -1;
+        return cuda_err(c, e, "cudaMalloc (fused 1D term tables)");
+      }
+      nbytes += tab_bytes;
+      tab_M = c->M;
+    }
+    k1d_term_tables<R><<<std::max(1, N / 256), 256, 0, c->stream>>>(N, c->M, P1, P2, Lg, T);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "fused 1D term tables");
+    tab_gen = model_gen;
     return VOFL_OK;
   }
 
@@ -591,6 +615,7 @@ struct Fused1D : Engine {
     const TermSplit1 ts = term_split1(c->M, c->general);
     s.split_k = ts.split_k;
     s.k2 = ts.k2;
+    s.T = (T && tab_M == c->M && tab_gen == model_gen) ? T : nullptr;
     return s;
   }
 
@@ -607,7 +632,7 @@ struct Fused1D : Engine {
     const int slots = s.split_k > 0 ? s.split_k : s.M + 1;
     int CL = 1;
     while (CL * 2 <= std::min(8, slots) && N % (CL * 2) == 0) CL *= 2;
-    while (CL > 1 && !(cluster_ok && fits(CL, c->stream))) CL /= 2;
+    while (CL > 1 && !(cluster_ok && s.T && fits(CL, c->stream))) CL /= 2;
     if (CL > 1) {
       cudaLaunchAttribute at[1];
       cudaLaunchConfig_t cfg = cluster_cfg(CL, at, c->stream);
