@@ -1,17 +1,22 @@
 // fused1d.cu -- fused 1D path (float or double): the whole leap-frog run of
 // Eq. (1.1) with both operators by the matrix-free scheme of Eq. (2.10) of
-// arXiv 2311.13049, one CTA per simulation, every transform in shared
-// memory, every requested step inside one kernel launch.
+// arXiv 2311.13049, every transform in shared memory, every requested step
+// inside one kernel launch.
 //
 // Per step (N points, M+1 Taylor terms):
 //   w = D_xx u (periodic second difference) -> complex FFT -> S = DFT(w),
 //       S_k = lambda_k * N * u_hat_k with lambda_k = -4 sin^2(pi k/N);
-//   for m = M..0: W_k = S_k (c1_m(k) + i c2_m(k)), c_op,m = P_op L^m/m!
+//   per slot index m: W_k = S_k (c1_m(k) + i c2_m(k)), c_op,m = P_op L^m/m!
 //       (P_op = |mu|^{2 s0_op}/(N lambda_k), op 2 scaled by an exact power of
 //       two lambda2), one complex inverse FFT gives L1-term + i L2-term
-//       (both multiplied spectra are Hermitian), and Horner's rule
-//       acc = Y_m + delta * acc accumulates the delta^m weights;
-//   pointwise leap-frog update (Eq. (3.4) extended to Eq. (1.1)).
+//       (both multiplied spectra are Hermitian); for the general model (one
+//       operator) the two slots carry terms m and m + K instead;
+//   the delta^m weights by Horner's rule, then the pointwise leap-frog update
+//   (Eq. (3.4) extended to Eq. (1.1)).
+// Two kernels: k1d_cluster_run spreads the slot indices of one line over a
+// thread-block cluster of up to 8 CTAs (distributed shared memory, per-term
+// multiplier tables); k1d_run keeps the whole line in one CTA (a single
+// slot index, or when no cluster can be resident).
 // The FFT is a radix-2 Stockham autosort over the CTA (Govindaraju et al.,
 // SC 2008), ping-ponging between two shared buffers.
 #include <cooperative_groups.h>
