@@ -200,7 +200,7 @@ size_t vofl_footprint_bytes(int ndim, const int64_t* n, int prec, int impl, int 
   else if (impl == VOFL_IMPL_FUSED && fused3d_supported(ndim, n, prec))
     b += fused3d_footprint(n, M);
   else if (impl == VOFL_IMPL_FUSED && fused1d_supported(ndim, n, prec))
-    b += (size_t)N * (prec == VOFL_F64 ? 8 : 4) * 4;
+    b += (size_t)N * (prec == VOFL_F64 ? 8 : 4) * (4 + 2 * (size_t)(M + 1));  // tables, twiddles, term tables
   else
     b += plain_footprint(ndim, n, prec, M);
   return b;
