@@ -73,14 +73,15 @@ __global__ void __launch_bounds__(W_FCOLS * 32) kb_fwd_cols(const BatchSim* __re
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const BatchSim* __restrict__ sims, int g) {
+__global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const BatchSim* __restrict__ sims, int g,
+                                                                      int parts) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;  // this simulation has fewer groups
   const int m_hi = min(s->M + 1, m_lo + BG);
   // the descriptor (with its tensor map) was written by a host copy
   if (threadIdx.x == 0) tmap_acquire(&s->zmap);
-  inv_cols_body<NY>(blockIdx.x, blockIdx.y, s->Uh, s->P, s->Lg, &s->zmap, NX / 2 + 1, m_lo, m_hi,
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, s->Uh, s->P, s->Lg, &s->zmap, NX / 2 + 1, m_lo, m_hi,
                     (float)c_inv_fact[m_lo], (float)c_inv_fact[m_lo], 0, s->twy);
 }
 
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __re
 struct BKernels {
   void (*fr)(const BatchSim*);
   void (*fc)(const BatchSim*);
-  void (*ic)(const BatchSim*, int);
+  void (*ic)(const BatchSim*, int, int);
   void (*ir)(const BatchSim*, int);
   size_t smem_fr, smem_fc, smem_ic, smem_ir;
   int lpw_x, lpw_y;
@@ -341,7 +342,9 @@ cudaError_t enqueue_step(vofl_batch* b, int p) {
       if (e) return e;
       const int cpc = cl.k.wic * cl.k.lpw_y, rpi = W_IROWS * cl.k.lpw_x;
       for (int g = Mmax / BG; g >= 0; --g) {
-        e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2, nz), dim3(cl.k.wic * 32), cl.k.smem_ic, s, dc, g);
+        const int parts = icols_parts_2d(ny);  // the split of the solo launches of this size
+        e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2 * parts, nz), dim3(cl.k.wic * 32), cl.k.smem_ic, s,
+                       dc, g, parts);
         if (e) return e;
         e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(W_IROWS * 32), cl.k.smem_ir, s, dc, g);
         if (e) return e;

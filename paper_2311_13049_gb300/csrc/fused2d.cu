@@ -49,7 +49,7 @@ namespace {
 struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
-  void (*inv_cols)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int,
+  void (*inv_cols)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int,
                    const float2*);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
                            EpiArgs<float>, float, const float2*, int*);
@@ -164,7 +164,8 @@ struct Plan2D {
     const TermSplit ts = term_split(M, one_op);
     const int K = groups(M, one_op);
     const int cpc = k.wic * k.lpw_y;
-    const dim3 gic((ncols + cpc - 1) / cpc, 2);
+    const int parts = icols_parts_2d(ny);
+    const dim3 gic((ncols + cpc - 1) / cpc, 2 * parts);
     const int rpc = k.wir * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
     int e_i = 3;
@@ -173,7 +174,7 @@ struct Plan2D {
       const float f0 = inv_factorial(m_lo), f1 = ts.split_k ? inv_factorial(m_lo + ts.split_k) : f0;
       cudaError_t e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, (const float2*)Uh,
                                  (const float*)P, (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k,
-                                 (const float2*)twy);
+                                 parts, (const float2*)twy);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
       EpiArgs<float> ep = epi;

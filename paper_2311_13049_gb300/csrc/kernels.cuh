@@ -265,7 +265,9 @@ constexpr int icols_box_rows() {
 }
 
 template <int NY>
-__device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __restrict__ Uh,
+// yidx = operator slot + 2 * part: the group's terms [m_lo, m_hi) are split
+// into `parts` consecutive runs, one per CTA (parts = 1: the whole group)
+__device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, const float2* __restrict__ Uh,
                                               const float* __restrict__ P, const float* __restrict__ Lg,
                                               const void* zmap, int ncols, int m_lo, int m_hi, float inv_fact_lo,
                                               float inv_fact_lo1, int split_k, const float2* __restrict__ twy) {
@@ -295,10 +297,17 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   const float2* uh_col = Uh + (size_t)cc * NY;
   // split_k > 0 (one operator): slot op = 1 carries the terms m + split_k of
   // operator 1 (multiplier P[0] ln|mu|^{2(m + split_k)} / (m + split_k)!)
+  const int op = yidx & 1, part = yidx >> 1;
+  const int per = (m_hi - m_lo + parts - 1) / parts;
+  const int lo = m_lo + part * per, hi = min(m_hi, lo + per);
+  if (lo >= hi) return;  // the whole CTA, before any barrier
   const int off = (split_k > 0 && op) ? split_k : 0;
   const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
   const float* l_col = Lg + (size_t)cc * NY;
   float tm[E], lg[PAIR ? 1 : E];
+  // 1 / (lo + off)!: the group's factor advanced to this run's first term
+  float fstart = op ? inv_fact_lo1 : inv_fact_lo;
+  for (int j = m_lo + 1; j <= lo; ++j) fstart *= 1.0f / (float)(j + off);
   // tables first (they do not depend on the previous kernel)
 #pragma unroll
   for (int m = 0; m < E; ++m) {
@@ -308,7 +317,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
       s_lg[y] = l;
     else
       lg[m] = l;
-    tm[m] = p_col[y] * powi(l, m_lo + off) * (op ? inv_fact_lo1 : inv_fact_lo);
+    tm[m] = p_col[y] * powi(l, lo + off) * fstart;
   }
   __syncthreads();
   pdl_wait();  // Uh (k2d_fwd_cols) ready; the previous group's readers of Z are done
@@ -355,9 +364,9 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
 #pragma unroll
     for (int k = 0; k < NY / BOXR; ++k) tma_store_2d(zmap, c0, y0 + k * BOXR, s_buf + set * SET + k * BOXR * CW);
   };
-  int mt = m_lo;
+  int mt = lo;
   // two terms per iteration: two independent register transforms in flight
-  for (; PAIR && mt + 1 < m_hi; mt += 2) {
+  for (; PAIR && mt + 1 < hi; mt += 2) {
     float2 xa[E], xb[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) xa[m] = v[m];
@@ -391,10 +400,10 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
       tile_store(1, mt + 1);
       bulk_commit();
     }
-    if (mt + 2 < m_hi) advance(mt + 1);
+    if (mt + 2 < hi) advance(mt + 1);
   }
   if (PAIR) {
-    if (mt < m_hi) {  // an odd last term
+    if (mt < hi) {  // an odd last term
       float2 x[E];
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = v[m];
@@ -417,7 +426,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
   } else {
     // short lines: one term per iteration (a separate loop: sharing it with
     // the odd last term above made the paired form markedly slower)
-    for (; mt < m_hi; ++mt) {
+    for (; mt < hi; ++mt) {
       float2 x[E];
 #pragma unroll
       for (int m = 0; m < E; ++m) x[m] = v[m];
@@ -436,7 +445,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int op, const float2* __re
         tile_store(0, mt);
         bulk_commit();
       }
-      if (mt + 1 < m_hi) advance(mt);
+      if (mt + 1 < hi) advance(mt);
     }
   }
   if (threadIdx.x == 0) bulk_wait_all();  // stores complete before the CTA's shared memory goes
@@ -447,10 +456,10 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(const flo
                                                            const float* __restrict__ Lg,
                                                            const __grid_constant__ CUtensorMap zmap, int ncols,
                                                            int m_lo, int m_hi, float inv_fact_lo,
-                                                           float inv_fact_lo1, int split_k,
+                                                           float inv_fact_lo1, int split_k, int parts,
                                                            const float2* __restrict__ twy) {
-  inv_cols_body<NY>(blockIdx.x, blockIdx.y, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, inv_fact_lo1, split_k,
-                    twy);
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, inv_fact_lo1,
+                    split_k, twy);
 }
 
 // -------------------------------------------------------------------------
@@ -680,6 +689,12 @@ cudaError_t set_kernel_smem(void (*kern)(KArgs...), size_t bytes) {
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // 1/m! in double, rounded once to float
+// Column passes of small 2D grids have fewer CTAs than SMs and run each
+// group's terms one after another; there the group is split into runs of
+// terms over several CTAs.  The solo and batched launches of a grid use the
+// same split (and so the same arithmetic); 3D z passes use one run.
+inline int icols_parts_2d(int ny) { return ny <= 256 ? 3 : (ny <= 512 ? 2 : 1); }
+
 // How the Taylor terms m = 0..M fill the two operator slots of the inverse
 // kernels: one term of each operator per slot index (two operators), or,
 // for a model with one operator, terms 0..K-1 in slot 0 and K..M in slot 1
