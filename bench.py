@@ -57,9 +57,10 @@ M = 16
 DT = 5e-4
 # DRAM bytes (read + write) per launch of the fused kernels, from one ncu
 # capture of the headline step (profiles/ncu_k2d_kernels_2d_1024_M16.md:
-# mean over the step's three k2d_inv_cols launches, L2 not flushed between
-# kernels); to be re-taken whenever the kernel changes.
-NCU_TRAFFIC_BYTES = {"k2d_inv_cols": 24.76e6}
+# mean over the third step's three k2d_inv_cols launches, three metrics,
+# L2 not flushed between kernels); to be re-taken whenever the kernel
+# changes.
+NCU_TRAFFIC_BYTES = {"k2d_inv_cols": 21.31e6}
 METRIC = "Mpoint-steps/s (2D 1024², M=16) fused vs plain at ≤1e-5 rel L2; serve p50/p99"
 UNIT = "Mpoint-steps/s"
 WORKLOAD = "2D periodic 1024x1024, FP32, M=16, Q low-passed noise in [5,100] (seed 2), Ricker f0=10 at centre, dt=5e-4, 1000 steps"
