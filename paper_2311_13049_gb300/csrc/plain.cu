@@ -170,9 +170,9 @@ __global__ void k_update(const T* __restrict__ L1, const T* __restrict__ L2, Epi
 // fixed-point (Picard) outer loop: r = b + h2 f(v) - A v is the residual of
 // the nonlinear system, and each outer pass solves A d = r by CGNR and sets
 // v += d, until |r| <= tol |b + h2 f(v)|.
-//   L v   = sum_m delta^m IFFT[P L^m/m! FFT(Lap v)]         (M+1 inverse
-//           transforms in one batched cuFFT call)
-//   L^T r = IFFT[P sum_m L^m/m! FFT(Lap(delta^m r))]       (M+1 forward
+//   L v   = sum_m delta^m IFFT[P l^m/m! FFT(Lap v)]         (M+1 inverse
+//           transforms in one batched cuFFT call; l = ln|mu|^2)
+//   L^T r = IFFT[P sum_m l^m/m! FFT(Lap(delta^m r))]       (M+1 forward
 //           transforms in one batched call; the circulant factors are
 //           symmetric, so the transpose only moves delta^m to the front)
 // Dot products are two-pass (fixed block partials, then one block in fixed
