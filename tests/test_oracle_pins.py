@@ -537,3 +537,20 @@ def test_cnfp_spatially_constant_field_is_the_implicit_ode_scheme():
             a, b = (m, b) if g(m) < 0 else (a, m)
         u0, u1 = u1, 0.5 * (a + b)
     assert np.max(np.abs(u - u1)) < 1e-12
+
+
+@pytest.mark.parametrize("shape,kvec", [((16, 16), (2, 3)), ((8, 8, 8), (1, 2, 1))])
+def test_cnfp_single_mode_recurrence_multid(shape, kvec):
+    """The closed form of test_cnfp_single_mode_recurrence on 2D and 3D
+    grids (box [-pi, pi)^d, so mu = k): u^0 = cos(k . x), lambda =
+    |k|^{2s} with |k|^2 summed over the axes (Sec. 2.3)."""
+    d = len(shape)
+    lo, hi, s, kappa, dt, n = [-np.pi] * d, [np.pi] * d, 0.8, 1.3, 0.1, 25
+    X = S.mesh(shape, lo, hi)  # x, y[, z]
+    phase = sum(k * xi for k, xi in zip(kvec, X))
+    u = O.general_cnfp(s, kappa, lambda v: 0.0 * v, np.cos(phase), None, dt, n, 2, lo, hi)
+    lam, c = float(sum(k * k for k in kvec)) ** s, 0.5 * kappa * dt * dt
+    a_prev, a = 1.0, 1.0 - c * lam
+    for _ in range(1, n):
+        a_prev, a = a, (2.0 * a - (1.0 + c * lam) * a_prev) / (1.0 + c * lam)
+    assert np.max(np.abs(u - a * np.cos(phase))) < 1e-12
