@@ -208,6 +208,26 @@ VOFL_API int vofl_set_source(vofl_ctx* ctx, const int64_t* idx, const double* sa
  * a captured CUDA graph when the path allows it). */
 VOFL_API int vofl_step(vofl_ctx* ctx, int64_t nsteps, double dt);
 
+/* Checkpoint of a run (host memory): the grid, M, the scheme and model
+ * scalars, the step count, dt, the state fields (u^n, u^{n-1} or v,
+ * L2 u^{n-1}), the model fields (delta, A, B and the gamma or s field) and
+ * the source samples.  With blob == NULL, *nbytes receives the size;
+ * otherwise *nbytes is the buffer size on entry and the bytes written on
+ * return.  Waits for the queued work.  Returns VOFL_OK, VOFL_EINVAL (null
+ * nbytes, buffer too small: *nbytes then holds the size), VOFL_ESTATE (no
+ * model or state) or VOFL_ECUDA. */
+VOFL_API int vofl_save_state(vofl_ctx* ctx, void* blob, size_t* nbytes);
+
+/* Resume a run from a checkpoint of vofl_save_state, into a context of the
+ * same grid, box and precision (any context: the model is restored with the
+ * run).  The engine's spectral tables are rebuilt from the restored model,
+ * so the next steps equal those of the saved run on the same path and GPU,
+ * bit for bit.  The solver counters of vofl_solver_stats restart at 0.
+ * Waits for the queued work.  Returns VOFL_OK, VOFL_EINVAL (not a
+ * checkpoint, another grid or precision, a size that does not match) or
+ * VOFL_ECUDA. */
+VOFL_API int vofl_load_state(vofl_ctx* ctx, const void* blob, size_t nbytes);
+
 /* Copy the current wavefield u^n (n = steps taken) to u_out (host or device,
  * context precision).  Synchronises the stream when the target is host
  * memory. */

@@ -51,6 +51,8 @@ SIGNATURES = {
     "vofl_query": (C.c_int, [_vp]),
     "vofl_suggest_M": (C.c_int, [_vp, C.c_double, C.POINTER(C.c_int)]),
     "vofl_set_solver": (C.c_int, [_vp, C.c_double, C.c_int]),
+    "vofl_save_state": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t)]),
+    "vofl_load_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "vofl_solver_stats": (C.c_int, [_vp, _i64p, _i64p]),
     "vofl_sync": (C.c_int, [_vp]),
     "vofl_last_error": (C.c_char_p, [_vp]),
@@ -207,6 +209,19 @@ class Solver:
     def set_solver(self, tol, max_iter=5000):
         """Relative residual and CG iteration cap of the Crank-Nicolson solve."""
         self._check(lib().vofl_set_solver(self._h, float(tol), int(max_iter)))
+
+    def save_state(self) -> bytes:
+        """Checkpoint of the run (vofl_save_state)."""
+        n = C.c_size_t(0)
+        self._check(lib().vofl_save_state(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(lib().vofl_save_state(self._h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def load_state(self, blob: bytes):
+        """Resume from a checkpoint of save_state (same grid and precision)."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        self._check(lib().vofl_load_state(self._h, buf, len(blob)))
 
     def solver_stats(self):
         """(CG iterations, linear solves) of the Crank-Nicolson run so far."""

@@ -516,6 +516,137 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
   return VOFL_OK;
 }
 
+// ---- checkpoint / resume ----
+namespace {
+// the fixed part of a checkpoint; the arrays follow it in this order:
+// u[0], u[1], l2p, delta, A, B (N elements of the context precision each),
+// the order field s or gamma (N doubles), the source samples (nsrc doubles)
+struct Checkpoint {
+  char magic[8];
+  int64_t ndim, n[3], prec, M, scheme, general, cur, psi_nonzero, steps, cn_maxit, nsrc, src_flat;
+  double lo[3], hi[3], dt, gamma0, s01, s02, kappa, f1, f3, cn_tol;
+  int32_t d_step[2];  // step counter and error word
+};
+const char kCkptMagic[8] = {'V', 'O', 'F', 'L', 'C', 'K', 'P', '1'};
+
+size_t ckpt_bytes(const vofl_ctx* c, int64_t nsrc) {
+  return sizeof(Checkpoint) + 6 * elem_size(c) * (size_t)c->N + sizeof(double) * ((size_t)c->N + (size_t)nsrc);
+}
+}  // namespace
+
+int vofl_save_state(vofl_ctx* c, void* blob, size_t* nbytes) {
+  if (int st = check_ctx(c)) return st;
+  if (!nbytes) return set_err(c, VOFL_EINVAL, "nbytes is null");
+  if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
+  const size_t need = ckpt_bytes(c, c->nsrc);
+  if (!blob) {
+    *nbytes = need;
+    return VOFL_OK;
+  }
+  if (*nbytes < need) {
+    *nbytes = need;
+    return set_err(c, VOFL_EINVAL, "checkpoint buffer too small");
+  }
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));  // the queued steps first
+  Checkpoint h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.ndim = c->ndim;
+  h.prec = c->prec;
+  for (int i = 0; i < 3; ++i) {
+    h.n[i] = c->n[i];
+    h.lo[i] = c->lo[i];
+    h.hi[i] = c->hi[i];
+  }
+  h.M = c->M;
+  h.scheme = c->scheme;
+  h.general = c->general ? 1 : 0;
+  h.cur = c->cur;
+  h.psi_nonzero = c->psi_nonzero ? 1 : 0;
+  h.steps = c->steps;
+  h.cn_maxit = c->cn_maxit;
+  h.nsrc = c->nsrc;
+  h.src_flat = c->src_flat;
+  h.dt = c->dt;
+  h.gamma0 = c->gamma0;
+  h.s01 = c->s01;
+  h.s02 = c->s02;
+  h.kappa = c->kappa;
+  h.f1 = c->f1;
+  h.f3 = c->f3;
+  h.cn_tol = c->cn_tol;
+  VOFL_CUDA(c, cudaMemcpy(h.d_step, c->d_step, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  unsigned char* p = static_cast<unsigned char*>(blob);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const size_t b = elem_size(c) * (size_t)c->N;
+  for (const void* src : {(const void*)c->u[0], (const void*)c->u[1], (const void*)c->l2p, (const void*)c->delta,
+                          (const void*)c->A, (const void*)c->B}) {
+    VOFL_CUDA(c, cudaMemcpy(p, src, b, cudaMemcpyDeviceToHost));
+    p += b;
+  }
+  VOFL_CUDA(c, cudaMemcpy(p, c->d_gamma, sizeof(double) * c->N, cudaMemcpyDeviceToHost));
+  p += sizeof(double) * c->N;
+  if (c->nsrc > 0) VOFL_CUDA(c, cudaMemcpy(p, c->d_src, sizeof(double) * c->nsrc, cudaMemcpyDeviceToHost));
+  *nbytes = need;
+  return VOFL_OK;
+}
+
+int vofl_load_state(vofl_ctx* c, const void* blob, size_t nbytes) {
+  if (int st = check_ctx(c)) return st;
+  if (!blob || nbytes < sizeof(Checkpoint)) return set_err(c, VOFL_EINVAL, "not a checkpoint");
+  Checkpoint h;
+  std::memcpy(&h, blob, sizeof(h));
+  if (std::memcmp(h.magic, kCkptMagic, 8) != 0) return set_err(c, VOFL_EINVAL, "not a checkpoint");
+  bool same = h.ndim == c->ndim && h.prec == c->prec;
+  for (int i = 0; i < 3; ++i) same = same && h.n[i] == c->n[i] && h.lo[i] == c->lo[i] && h.hi[i] == c->hi[i];
+  if (!same) return set_err(c, VOFL_EINVAL, "the checkpoint belongs to another grid or precision");
+  if (h.nsrc < 0 || h.M < 0 || h.M > 40 || nbytes != ckpt_bytes(c, h.nsrc))
+    return set_err(c, VOFL_EINVAL, "checkpoint size does not match its header");
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  const unsigned char* p = static_cast<const unsigned char*>(blob) + sizeof(h);
+  const size_t b = elem_size(c) * (size_t)c->N;
+  for (void* dst : {c->u[0], c->u[1], c->l2p, c->delta, c->A, c->B}) {
+    VOFL_CUDA(c, cudaMemcpy(dst, p, b, cudaMemcpyHostToDevice));
+    p += b;
+  }
+  VOFL_CUDA(c, cudaMemcpy(c->d_gamma, p, sizeof(double) * c->N, cudaMemcpyHostToDevice));
+  p += sizeof(double) * c->N;
+  if (h.nsrc > c->src_cap) {
+    cudaFree(c->d_src);
+    c->d_src = nullptr;
+    c->src_cap = 0;
+    VOFL_CUDA(c, cudaMalloc(&c->d_src, sizeof(double) * h.nsrc));
+    c->src_cap = h.nsrc;
+  }
+  if (h.nsrc > 0) VOFL_CUDA(c, cudaMemcpy(c->d_src, p, sizeof(double) * h.nsrc, cudaMemcpyHostToDevice));
+  VOFL_CUDA(c, cudaMemcpy(c->d_step, h.d_step, 2 * sizeof(int), cudaMemcpyHostToDevice));
+  drop_graphs(c);  // they may hold the old source pointer
+  c->M = (int)h.M;
+  c->scheme = (int)h.scheme;
+  c->general = h.general != 0;
+  c->gamma0 = h.gamma0;
+  c->s01 = h.s01;
+  c->s02 = h.s02;
+  c->kappa = h.kappa;
+  c->f1 = h.f1;
+  c->f3 = h.f3;
+  c->cn_tol = h.cn_tol;
+  c->cn_maxit = (int)h.cn_maxit;
+  c->nsrc = h.nsrc;
+  c->src_flat = h.nsrc > 0 ? h.src_flat : -1;
+  // the engine's spectral tables follow from s01, s02 (and kappa)
+  if (int st = c->eng->set_model(c)) return st;
+  c->model_set = true;
+  c->state_set = true;
+  c->cur = (int)h.cur;
+  c->psi_nonzero = h.psi_nonzero != 0;
+  c->steps = h.steps;
+  c->dt = h.dt;
+  c->cn_iters = 0;
+  c->cn_solves = 0;
+  return VOFL_OK;
+}
+
 int vofl_set_solver(vofl_ctx* c, double tol, int max_iter) {
   if (int st = check_ctx(c)) return st;
   if (!(tol > 0) || !(tol < 1) || max_iter < 1) return set_err(c, VOFL_EINVAL, "bad solver tolerance or iteration cap");
