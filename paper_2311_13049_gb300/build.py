@@ -89,7 +89,7 @@ def build(verbose_ptxas: bool = False, force: bool = False, quiet: bool = True) 
     link_dig = _digest(objs)
     stamp = LIB + ".sha"
     if not (os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == link_dig):
-        cmd = [_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcufft", "-lcudart"]
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcufft", "-lcudart", "-ldl"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"link failed:\n{p.stderr}")

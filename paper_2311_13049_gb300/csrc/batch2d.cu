@@ -600,6 +600,7 @@ int vofl_batch_remove(vofl_batch* b, int slot) {
 int vofl_batch_size(const vofl_batch* b) { return b ? (int)b->mem.size() : VOFL_EINVAL; }
 
 int vofl_batch_step(vofl_batch* b, int64_t nsteps) {
+  NvtxRange nvtx_range("vofl_batch_step");
   if (!b || nsteps < 0) return berr(b, VOFL_EINVAL, "bad batch or nsteps");
   if (nsteps == 0 || b->mem.empty()) return VOFL_OK;
   return run_steps(b, nsteps, false);

@@ -316,6 +316,7 @@ static int finish_model(vofl_ctx* c, const double* d_c0field, double c0, double 
 }
 
 int vofl_set_q(vofl_ctx* c, const double* Q, int on_device, double c0, double omega0) {
+  NvtxRange nvtx_range("vofl_set_q");
   if (int st = check_ctx(c)) return st;
   if (!Q) return set_err(c, VOFL_EINVAL, "Q is null");
   if (!(c0 > 0) || !(omega0 > 0)) return set_err(c, VOFL_EINVAL, "c0 and omega0 must be positive");
@@ -327,6 +328,7 @@ int vofl_set_q(vofl_ctx* c, const double* Q, int on_device, double c0, double om
 }
 
 int vofl_set_order(vofl_ctx* c, const double* s, int on_device, double kappa, double f1, double f3) {
+  NvtxRange nvtx_range("vofl_set_order");
   if (int st = check_ctx(c)) return st;
   if (!s) return set_err(c, VOFL_EINVAL, "s is null");
   if (!(kappa > 0) || !std::isfinite(kappa) || !std::isfinite(f1) || !std::isfinite(f3))
@@ -385,12 +387,14 @@ int apply_checked(vofl_ctx* c, const void* u, void* o1, void* o2) {
 }  // namespace
 
 int vofl_apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) {
+  NvtxRange nvtx_range("vofl_apply_pair");
   if (int st = check_ctx(c)) return st;
   if (c->general) return set_err(c, VOFL_EINVAL, "the general model has one operator: vofl_apply(VOFL_OP_S)");
   return apply_checked(c, u, o1, o2);
 }
 
 int vofl_apply(vofl_ctx* c, int op, const void* u, void* out) {
+  NvtxRange nvtx_range("vofl_apply");
   if (int st = check_ctx(c)) return st;
   if (op != VOFL_OP_1PG && op != VOFL_OP_HPG && op != VOFL_OP_S) return set_err(c, VOFL_EINVAL, "unknown operator");
   if (c->model_set && (op == VOFL_OP_S) != c->general)
@@ -457,6 +461,7 @@ int vofl_set_scheme(vofl_ctx* c, int scheme) {
 }
 
 int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
+  NvtxRange nvtx_range("vofl_step");
   if (int st = check_ctx(c)) return st;
   if (nsteps < 0) return set_err(c, VOFL_EINVAL, "bad nsteps");
   if (c->scheme == VOFL_SCHEME_TSFP2) {
@@ -535,6 +540,7 @@ size_t ckpt_bytes(const vofl_ctx* c, int64_t nsrc) {
 }  // namespace
 
 int vofl_save_state(vofl_ctx* c, void* blob, size_t* nbytes) {
+  NvtxRange nvtx_range("vofl_save_state");
   if (int st = check_ctx(c)) return st;
   if (!nbytes) return set_err(c, VOFL_EINVAL, "nbytes is null");
   if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
@@ -592,6 +598,7 @@ int vofl_save_state(vofl_ctx* c, void* blob, size_t* nbytes) {
 }
 
 int vofl_load_state(vofl_ctx* c, const void* blob, size_t nbytes) {
+  NvtxRange nvtx_range("vofl_load_state");
   if (int st = check_ctx(c)) return st;
   if (!blob || nbytes < sizeof(Checkpoint)) return set_err(c, VOFL_EINVAL, "not a checkpoint");
   Checkpoint h;

@@ -8,9 +8,20 @@
 #include <cstdio>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vofl.h"
 
 namespace vofl {
+
+// NVTX range over one C-ABI call (nsys, ncu --nvtx); without an attached
+// tool a push/pop pair costs a function-pointer test
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 extern std::atomic<uint64_t> g_kernel_launches;
 inline void count_launch(uint64_t n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }

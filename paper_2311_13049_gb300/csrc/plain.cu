@@ -934,6 +934,7 @@ struct Plain : Engine {
   // one Crank-Nicolson step n >= 1: u^{n+1} into u[1 - cur] (the caller
   // flips cur)
   int step_cn(vofl_ctx* c) override {
+    NvtxRange nvtx_range("cnfp_step");
     int st;
     if ((st = cn_alloc(c))) return st;
     if (cn.key_dt != c->dt || cn.key_kappa != c->kappa || cn.key_f1 != c->f1 || cn.key_f3 != c->f3 ||
