@@ -23,6 +23,12 @@
 // Only the between-group partial sums (2 fields) and one group of spectra
 // (G terms) are stored: storage O(N) in M, against O(MN) for storing every
 // term.
+// A model with one operator (the general model) puts its terms 0..K-1 in
+// the operator-1 slot and K..M in the operator-2 slot (K = ceil((M+1)/2)),
+// summed as sum_0 + delta^K sum_1 in the epilogue: half the line
+// transforms.  On grids of ny <= 512 the column pass splits each group's
+// terms into runs over 2-3 CTAs (icols_parts_2d); at 1024^2 the row pass
+// uses seven-row CTAs (one per SM).
 //
 // Launches use programmatic dependent launch: each kernel does the work
 // that does not read its predecessor's output (twiddle and table loads,
