@@ -554,3 +554,16 @@ def test_cnfp_single_mode_recurrence_multid(shape, kvec):
     for _ in range(1, n):
         a_prev, a = a, (2.0 * a - (1.0 + c * lam) * a_prev) / (1.0 + c * lam)
     assert np.max(np.abs(u - a * np.cos(phase))) < 1e-12
+
+
+def test_cnfp_single_mode_with_initial_velocity():
+    """psi = b cos(k x) enters only the start step (Eq. (3.3)):
+    a1 = (1 - c lambda) a0 + dt b, then the recurrence of Eq. (3.2)."""
+    J, lo, hi, s, k, kappa, dt, n, b = 32, [-np.pi], [np.pi], 1.1, 4, 0.9, 0.07, 30, 0.6
+    x = S.axis(J, lo[0], hi[0])
+    u = O.general_cnfp(s, kappa, lambda v: 0.0 * v, np.cos(k * x), b * np.cos(k * x), dt, n, 3, lo, hi)
+    lam, c = float(k) ** (2 * s), 0.5 * kappa * dt * dt
+    a_prev, a = 1.0, (1.0 - c * lam) + dt * b
+    for _ in range(1, n):
+        a_prev, a = a, (2.0 * a - (1.0 + c * lam) * a_prev) / (1.0 + c * lam)
+    assert np.max(np.abs(u - a * np.cos(k * x))) < 1e-12
