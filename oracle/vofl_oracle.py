@@ -17,9 +17,12 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                                    variable-gamma full run is "parity
                                    unpinned" beyond those reductions.
   general_lffp          (O4)       pinned: the paper's printed LFFP temporal
-                                   errors (Table 3, Sec. 3.2) are reproduced (P7).
+                                   errors (Table 3, Sec. 3.2) are reproduced (P7),
+                                   and the single-mode leap-frog recurrence.
   general_tsfp2         (O4)       pinned: the paper's printed TSFP2 temporal
-                                   errors (Table 4, Sec. 3.3) are reproduced.
+                                   and spatial errors (Tables 4, 5, Sec. 3.3) are
+                                   reproduced, and a constant-order linear mode
+                                   is integrated exactly.
   general_cnfp          (O4)       pinned: the paper's printed CNFP temporal
                                    errors (Table 2, Sec. 3.1) are reproduced,
                                    single-mode closed form (f = 0), and the

@@ -567,3 +567,29 @@ def test_cnfp_single_mode_with_initial_velocity():
     for _ in range(1, n):
         a_prev, a = a, (2.0 * a - (1.0 + c * lam) * a_prev) / (1.0 + c * lam)
     assert np.max(np.abs(u - a * np.cos(k * x))) < 1e-12
+
+
+@pytest.mark.parametrize("s,k", [(0.7, 3), (1.0, 2), (1.4, 5)])
+def test_tsfp2_constant_order_linear_mode_is_exact(s, k):
+    """Constant order and f = 0: the splitting of Sec. 3.3 integrates
+    u_tt = -kappa (-Delta)^s u exactly (the kick vanishes), so a single mode
+    is u(t) = cos(w t) u0 + sin(w t)/w v0 with w = sqrt(kappa) |k|^s."""
+    J, lo, hi, kappa, dt, n, b = 32, [-np.pi], [np.pi], 1.7, 0.13, 40, 0.4
+    x = S.axis(J, lo[0], hi[0])
+    u = O.general_tsfp2(s, kappa, lambda v: 0.0 * v, np.cos(k * x), b * np.cos(k * x), dt, n, 4, lo, hi)
+    w, t = np.sqrt(kappa) * float(k) ** s, n * dt
+    assert np.max(np.abs(u - (np.cos(w * t) + b * np.sin(w * t) / w) * np.cos(k * x))) < 1e-12
+
+
+@pytest.mark.parametrize("s,k", [(0.6, 2), (1.2, 3)])
+def test_general_lffp_single_mode_recurrence(s, k):
+    """Constant order and f = 0 (Eq. (3.4)): a1 = (1 - dt^2 kappa lambda/2)
+    a0 and a_{n+1} = (2 - dt^2 kappa lambda) a_n - a_{n-1}."""
+    J, lo, hi, kappa, dt, n = 32, [-np.pi], [np.pi], 0.8, 0.05, 60
+    x = S.axis(J, lo[0], hi[0])
+    u = O.general_lffp(s, kappa, lambda v: 0.0 * v, np.cos(k * x), None, dt, n, 3, lo, hi)
+    q = dt * dt * kappa * float(k) ** (2 * s)
+    a_prev, a = 1.0, 1.0 - 0.5 * q
+    for _ in range(1, n):
+        a_prev, a = a, (2.0 - q) * a - a_prev
+    assert np.max(np.abs(u - a * np.cos(k * x))) < 1e-12
