@@ -55,12 +55,14 @@ NX = NY = 1024
 NSTEPS = 1000
 M = 16
 DT = 5e-4
-# DRAM bytes (read + write) per launch of the fused kernels, from one ncu
-# capture of the headline step (profiles/ncu_k2d_kernels_2d_1024_M16.md:
-# mean over the third step's three k2d_inv_cols launches, three metrics,
-# L2 not flushed between kernels); to be re-taken whenever the kernel
-# changes.
-NCU_TRAFFIC_BYTES = {"k2d_inv_cols": 21.31e6}
+# DRAM bytes (read + write) per launch of the dominant kernel come from an
+# ncu capture summarised in a text file under profiles/, which also records
+# a digest of the kernel sources it was taken on; a kernel changed since then
+# reports traffic null (see _ncu_traffic).
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic_2d_1024_M16.txt")
+KERNEL_SOURCES = ["paper_2311_13049_gb300/csrc/kernels.cuh", "paper_2311_13049_gb300/csrc/fft_warp.cuh",
+                  "paper_2311_13049_gb300/csrc/fused2d.cu", "paper_2311_13049_gb300/csrc/tma.cuh",
+                  "paper_2311_13049_gb300/csrc/internal.h"]
 METRIC = "Mpoint-steps/s (2D 1024², M=16) fused vs plain at ≤1e-5 rel L2; serve p50/p99"
 UNIT = "Mpoint-steps/s"
 WORKLOAD = "2D periodic 1024x1024, FP32, M=16, Q low-passed noise in [5,100] (seed 2), Ricker f0=10 at centre, dt=5e-4, 1000 steps"
@@ -155,6 +157,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_sources_digest():
+    """sha256 over the sources of the fused 2D kernels (file name + bytes)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(rel.encode())
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _ncu_traffic(kernel):
+    """(bytes per launch, note) of `kernel` from the traffic summary, or
+    (None, why) when there is none or the kernel sources changed since the
+    capture.  File lines: 'key: value'."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            kv = dict(ln.split(":", 1) for ln in f if ":" in ln and not ln.startswith((" ", "#")))
+    except OSError:
+        return None, "no ncu traffic summary"
+    kv = {k.strip(): v.strip() for k, v in kv.items()}
+    if kv.get("kernel") != kernel:
+        return None, f"the ncu traffic summary covers {kv.get('kernel')}, not {kernel}"
+    if kv.get("sources_sha256") != kernel_sources_digest():
+        return None, "kernel sources changed since the ncu capture"
+    return float(kv["dram_bytes_per_launch"]), "ncu capture of the same kernel sources"
+
+
+def _sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -174,16 +209,47 @@ def _oracle_sample(w, gamma, nsteps):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(nsteps=3):
+def _oracle_worker(nsteps):
+    """One independent copy of the bounded oracle sample (a spawned process:
+    no CUDA in it); returns its wall time."""
     import oracle as O
     import synthetic as S
     w = S.workload_2d_1024(nsteps=NSTEPS)
     gamma = O.seismic_coefficients(w["Q"], w["c0"], w["omega0"])["gamma"]
     _oracle_sample(w, gamma, 1)  # warm the multiplier-table cache
-    t = _oracle_sample(w, gamma, nsteps)
-    return {"value": NX * NY * nsteps / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} leap-frog steps of the 1024^2 M=16 workload (FP64 NumPy, pocketfft, 1 thread), "
-                      f"{t:.1f} s"}
+    return _oracle_sample(w, gamma, nsteps)
+
+
+def cpu_baseline(nsteps=10, par_steps=4):
+    """The FP64 oracle as it stands on the host cores.  One simulation runs
+    on one core (NumPy's FFT is single-threaded), so the all-core figure is
+    the aggregate of os.cpu_count() independent copies of the same bounded
+    sample, run as spawned processes at the same time."""
+    import multiprocessing as mp
+    import oracle as O
+    import synthetic as S
+    w = S.workload_2d_1024(nsteps=NSTEPS)
+    gamma = O.seismic_coefficients(w["Q"], w["c0"], w["omega0"])["gamma"]
+    _oracle_sample(w, gamma, 1)  # warm the multiplier-table cache
+    t1 = _oracle_sample(w, gamma, nsteps)
+    one = {"value": NX * NY * nsteps / t1 / 1e6, "unit": UNIT, "cores": 1,
+           "sample": f"{nsteps} leap-frog steps of the 1024^2 M=16 workload (FP64 NumPy, pocketfft, 1 thread), "
+                     f"{t1:.1f} s"}
+    ncores = os.cpu_count() or 1
+    try:
+        with mp.get_context("spawn").Pool(ncores) as pool:
+            t0 = time.perf_counter()
+            times = pool.map(_oracle_worker, [par_steps] * ncores)
+            wall = time.perf_counter() - t0
+        # aggregate over the stepping phases (each copy's set-up is outside its timed sample)
+        agg = NX * NY * par_steps * ncores / max(times) / 1e6
+    except Exception as e:  # noqa: BLE001 - report, do not fail the bench
+        return dict(one, kind="oracle", box_cores=ncores, all_cores_error=str(e)[:200])
+    return {"value": agg, "unit": UNIT, "cores": ncores, "kind": "oracle", "box_cores": ncores,
+            "sample": f"{ncores} independent copies (spawned processes, one per host core) of {par_steps} leap-frog "
+                      f"steps of the 1024^2 M=16 workload each (FP64 NumPy, pocketfft); aggregate point-steps over the "
+                      f"slowest copy's stepping time {max(times):.1f} s (wall {wall:.1f} s with set-up)",
+            "single_thread": one}
 
 
 def run_reference(args):
@@ -701,12 +767,17 @@ def run_gpu(args):
     # algorithmic flops of a complex line FFT of length L: 5 L log2 L
     flops = dom_units * 5.0 * 1024 * 10
     peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    # the SM clock ceiling: nvidia-smi's clocks.max.sm seen during the timed
+    # region, else the measured-peaks file, else GB300's 2070 MHz
+    sm_max = float((clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    n_sm = _sm_count()
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     achieved = flops / (dom_ms * 1e-3) / 1e12
+    traffic, traffic_note = _ncu_traffic(dom)
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": NCU_TRAFFIC_BYTES.get(dom),
-            "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x sm_max_mhz",
+            "frac": achieved / fp32_peak, "traffic": traffic, "traffic_note": traffic_note,
+            "peak_note": f"derived FP32 FMA peak: {n_sm} SMs (read from the device) x 128 lanes x 2 flop x "
+                         f"sm_max_mhz {sm_max:.0f}",
             "flops_per_launch": flops, "ms_per_launch": dom_ms,
             "kernels": {nm: {"ms": ms, "units": u, "launches_per_step": launches_per_step.get(nm, 1)}
                         for nm, ms, u in prof}}

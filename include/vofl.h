@@ -406,13 +406,20 @@ VOFL_API int vofl_batch_set_schedule(vofl_batch* b, int parallel, const int* siz
  * fused shapes (64x64, 128x128, 256x256, 256x128, 128x256); larger or
  * other shapes return VOFL_EUNSUPPORTED before any device work.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  The call waits
- * on `stream` once (to read the grid mean of gamma back).  All calls share
- * the one array, so calls that overlap on the GPU (other streams, other
- * host threads) race and must be serialised by the caller; the array keeps
- * the last call's contents, and nothing in it needs to start at zero.
+ * device); make that first call before any stream capture.  The call is
+ * synchronous: it waits on `stream` twice, once to read the grid mean of
+ * gamma back and once at the end, after the outputs are written, to read
+ * the kernels' error word; when it returns VOFL_OK the outputs are
+ * complete.  All calls share the one array, so calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by
+ * the caller; the array keeps the last call's contents.  Each call clears
+ * the two words that must start at zero (the step counter and the error
+ * word) on `stream` before its kernels run; everything else in the array
+ * is written before it is read.
  * Returns VOFL_OK, VOFL_EINVAL (bad arguments or gamma outside [0,1/2)),
- * VOFL_EUNSUPPORTED (shape beyond the limit) or VOFL_ECUDA. */
+ * VOFL_EUNSUPPORTED (shape beyond the limit), VOFL_ETIMEDOUT (a bounded
+ * device wait inside the kernels gave up; the outputs are then incomplete)
+ * or VOFL_ECUDA. */
 VOFL_API int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, int M,
                                         const double* gamma_dev, const float* u_dev,
                                         float* out1_dev, float* out2_dev, void* stream);

@@ -609,6 +609,25 @@ int vofl_load_state(vofl_ctx* c, const void* blob, size_t nbytes) {
   if (!same) return set_err(c, VOFL_EINVAL, "the checkpoint belongs to another grid or precision");
   if (h.nsrc < 0 || h.M < 0 || h.M > 40 || nbytes != ckpt_bytes(c, h.nsrc))
     return set_err(c, VOFL_EINVAL, "checkpoint size does not match its header");
+  // every header field that indexes memory or selects a code path is
+  // checked before anything is copied: a damaged or foreign header must
+  // not index past the state buffers or move the source node off the grid
+  if (h.cur != 0 && h.cur != 1) return set_err(c, VOFL_EINVAL, "checkpoint: bad state buffer index");
+  if (h.nsrc > 0 && (h.src_flat < 0 || h.src_flat >= c->N))
+    return set_err(c, VOFL_EINVAL, "checkpoint: source node outside the grid");
+  if (h.scheme != VOFL_SCHEME_LFFP && h.scheme != VOFL_SCHEME_TSFP2 && h.scheme != VOFL_SCHEME_CNFP)
+    return set_err(c, VOFL_EINVAL, "checkpoint: unknown scheme");
+  if ((h.general != 0 && h.general != 1) || (h.psi_nonzero != 0 && h.psi_nonzero != 1))
+    return set_err(c, VOFL_EINVAL, "checkpoint: bad flag");
+  if (!h.general && h.scheme != VOFL_SCHEME_LFFP)
+    return set_err(c, VOFL_EINVAL, "checkpoint: the seismic model has only the leap-frog scheme");
+  if (h.cn_maxit < 1 || h.cn_maxit > INT32_MAX || !(h.cn_tol > 0) || !(h.cn_tol < 1))
+    return set_err(c, VOFL_EINVAL, "checkpoint: bad solver settings");
+  if (h.steps < 0 || !std::isfinite(h.dt) || h.dt < 0 || h.d_step[0] < 0)
+    return set_err(c, VOFL_EINVAL, "checkpoint: bad step count or time step");
+  if (!std::isfinite(h.gamma0) || !std::isfinite(h.s01) || !std::isfinite(h.s02) || !std::isfinite(h.kappa) ||
+      !std::isfinite(h.f1) || !std::isfinite(h.f3))
+    return set_err(c, VOFL_EINVAL, "checkpoint: non-finite model constant");
   VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
   const unsigned char* p = static_cast<const unsigned char*>(blob) + sizeof(h);
   const size_t b = elem_size(c) * (size_t)c->N;

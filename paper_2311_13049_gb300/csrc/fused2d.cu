@@ -581,9 +581,23 @@ extern "C" int vofl_apply_pair_2d_noalloc(int nx, int ny, double lx, double ly, 
   epi.out1 = out1_dev;
   epi.out2 = out2_dev;
   epi.src_flat = -1;
+  // the step counter and the kernels' error word start at zero on every
+  // call: a word left set by an earlier call must not be read as this one's
+  if (cudaMemsetAsync(p.step_ctr, 0, 2 * sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return VOFL_ECUDA;
+  }
   if (p.forward(s, u_dev, false) || p.inverse(s, M, epi)) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
-  return VOFL_OK;
+  // a bounded device wait that gave up leaves the outputs incomplete and
+  // sets the error word: read it back once the call's work is done
+  int word = 0;
+  if (cudaMemcpyAsync(&word, p.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return VOFL_ECUDA;
+  }
+  return word ? VOFL_ETIMEDOUT : VOFL_OK;
 }

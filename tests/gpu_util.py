@@ -51,3 +51,23 @@ def gpu_run(V, shape, Q, u0, v0, M, dt, nsteps, impl, prec, src_idx=None, src=No
         out = s.get_state()
         s.sync()
         return out.astype(np.float64)
+
+
+# Pointwise bound beside every relative-L2 bound: max|g - r| <= PW tol max|r|.
+# FP32 round-off of the transforms is spread over the grid like noise, so
+# its largest entry is a few times its RMS (PW = 10 leaves room for that);
+# an error confined to a few points (one tile column, the Nyquist column,
+# one Taylor group's slot) can hide under a relative L2 bound but not
+# under this one.
+PW = 10.0
+
+
+def check(g, r, tol, what=""):
+    """Assert rel_l2(g, r) <= tol and max|g - r| <= PW * tol * max|r|."""
+    g = np.asarray(g, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    e = rel_l2(g, r)
+    assert e <= tol, (what, "rel_l2", e, tol)
+    scale = float(np.max(np.abs(r)))
+    pw = float(np.max(np.abs(g - r))) / scale if scale > 0 else float(np.max(np.abs(g)))
+    assert pw <= PW * tol, (what, "max|g-r|/max|r|", pw, PW * tol)

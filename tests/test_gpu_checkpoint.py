@@ -101,3 +101,41 @@ def test_bad_checkpoints_are_refused(V):
         c.load_state(blob)  # the context is still usable
         c.step(1, 2e-3)
         c.sync()
+
+
+# byte offsets of the checkpoint header's int64 fields (after the 8-byte
+# magic: ndim, n[3], prec, M, scheme, general, cur, psi_nonzero, steps,
+# cn_maxit, nsrc, src_flat), then its doubles (lo[3], hi[3], dt, ...)
+_HDR = {"scheme": 56, "general": 64, "cur": 72, "psi_nonzero": 80, "steps": 88, "cn_maxit": 96,
+        "src_flat": 112}
+_HDR_DT = 168
+
+
+def test_tampered_checkpoint_headers_are_refused(V):
+    """A blob of the right grid and size whose header fields are damaged
+    (a state index past the two buffers, a source node off the grid, an
+    unknown scheme, no solver iterations, ...) is refused with EINVAL before
+    anything is copied, and the context stays usable."""
+    import struct
+    shape = (64, 64)
+    n = shape[0] * shape[1]
+    with _seismic_2d(V, shape) as a:
+        a.step(3, 2e-3)
+        blob = a.save_state()
+    bad_values = [("cur", 2), ("cur", -1), ("src_flat", n), ("src_flat", -1), ("scheme", 7),
+                  ("scheme", 1),  # TSFP2 on the seismic model
+                  ("general", 2), ("psi_nonzero", 5), ("cn_maxit", 0), ("steps", -4)]
+    with V.Solver(shape) as c:
+        for field, val in bad_values:
+            b = bytearray(blob)
+            struct.pack_into("<q", b, _HDR[field], val)
+            with pytest.raises(V.VoflError) as ei:
+                c.load_state(bytes(b))
+            assert ei.value.code == -1, (field, val, ei.value.code)
+        b = bytearray(blob)
+        struct.pack_into("<d", b, _HDR_DT, float("nan"))
+        with pytest.raises(V.VoflError):
+            c.load_state(bytes(b))
+        c.load_state(blob)  # the untouched blob still loads
+        c.step(1, 2e-3)
+        c.sync()

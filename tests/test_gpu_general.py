@@ -16,7 +16,7 @@ import pytest
 
 import oracle as O
 import synthetic as S
-from gpu_util import rel_l2
+from gpu_util import rel_l2, check
 
 pytestmark = pytest.mark.gpu
 
@@ -89,7 +89,7 @@ def test_generic_operator_2d(V, impl, prec, tol):
         with pytest.raises(V.VoflError):
             sv.apply(V.OP_1PG, ut, out)  # not an operator of the general model
     r = O.matrix_free_operator(uin.astype(np.float64), s, 20, lo, hi)
-    assert rel_l2(g, r) <= tol, rel_l2(g, r)
+    check(g, r, tol)
 
 
 @pytest.mark.parametrize("n,prec,tol", [(4096, "f32", 1e-4), (2048, "f64", 1e-10)])
@@ -103,7 +103,7 @@ def test_general_run_fused_1d(V, n, prec, tol):
     ty = np.float32 if P == V.F32 else np.float64
     g = _gpu_general(V, (n,), s, phi, 2.0 ** -9, 256, 15, 1.0, V.IMPL_FUSED, P, lo, hi)
     r = O.general_lffp(s, 1.0, lambda u: u ** 3, phi.astype(ty).astype(np.float64), None, 2.0 ** -9, 256, 15, lo, hi)
-    assert rel_l2(g, r) <= tol, rel_l2(g, r)
+    check(g, r, tol)
 
 
 def test_general_run_fused_2d_against_oracle(V):
@@ -114,7 +114,7 @@ def test_general_run_fused_2d_against_oracle(V):
     g = _gpu_general(V, shape, s, u0, 2e-3, 60, 20, 0.0, V.IMPL_FUSED, V.F32, lo, hi)
     r = O.general_lffp(s, 1.0, lambda u: 0.0 * u, u0.astype(np.float32).astype(np.float64), None, 2e-3, 60, 20,
                        lo, hi)
-    assert rel_l2(g, r) <= 1e-4, rel_l2(g, r)
+    check(g, r, 1e-4)
 
 
 def test_model_switch_and_checks(V):
@@ -209,7 +209,7 @@ def test_tsfp2_fp32_2d_against_oracle(V):
     v0 = (0.3 * np.sin(np.pi * xg / 4) * np.cos(np.pi * yg / 8)).astype(np.float32)
     g = _gpu_split(V, shape, s, u0, 2e-3, 50, 20, 1.0, V.F32, lo, hi, v0)
     r = O.general_tsfp2(s, 1.0, lambda u: u ** 3, u0.astype(np.float64), v0.astype(np.float64), 2e-3, 50, 20, lo, hi)
-    assert rel_l2(g, r) <= 1e-4, rel_l2(g, r)
+    check(g, r, 1e-4)
 
 
 def test_tsfp2_needs_general_model_and_plain_path(V):
@@ -298,7 +298,7 @@ def test_one_operator_split_2d(V, M):
     u = S.q_lowpass(shape, 7, qmin=-1.0, qmax=1.0, sigma_k=20.0)
     g, uin = _apply_s(V, shape, s, u, M, "f32", lo, hi)
     r = O.matrix_free_operator(uin, s, M, lo, hi)
-    assert rel_l2(g, r) <= 1e-5, (M, rel_l2(g, r))
+    check(g, r, 1e-5)
 
 
 @pytest.mark.parametrize("M", [3, 8])
@@ -309,7 +309,7 @@ def test_one_operator_split_3d(V, M):
     u = S.gaussian_pulse(shape, 5.0)
     g, uin = _apply_s(V, shape, s, u, M, "f32", lo, hi)
     r = O.matrix_free_operator(uin, s, M, lo, hi)
-    assert rel_l2(g, r) <= 1e-5, (M, rel_l2(g, r))
+    check(g, r, 1e-5)
 
 
 @pytest.mark.parametrize("M,prec,tol", [(5, "f64", 1e-11), (12, "f64", 1e-11), (9, "f32", 1e-5)])
@@ -320,7 +320,7 @@ def test_one_operator_split_1d(V, M, prec, tol):
     u = np.exp(-x * x) * np.cos(2.0 * x)
     g, uin = _apply_s(V, (n,), s, u, M, prec, lo, hi)
     r = O.matrix_free_operator(uin, s, M, lo, hi)
-    assert rel_l2(g, r) <= tol, (M, rel_l2(g, r))
+    check(g, r, tol)
 
 
 def test_batches_take_seismic_contexts_only(V):

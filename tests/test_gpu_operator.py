@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 import synthetic as S
-from gpu_util import gpu_apply_pair, gamma_of, rel_l2
+from gpu_util import gpu_apply_pair, gamma_of, rel_l2, check
 
 pytestmark = pytest.mark.gpu
 
@@ -31,8 +31,8 @@ def test_fused_apply_matches_oracle_sizes(V, shape):
     M = 8
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, M, V.IMPL_FUSED, V.F32)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), M)
-    assert rel_l2(g1, r1) <= TOL32, rel_l2(g1, r1)
-    assert rel_l2(g2, r2) <= TOL32, rel_l2(g2, r2)
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
 
 
 @pytest.mark.parametrize("M", [0, 1, 5, 6, 7, 11, 12, 13, 16, 20])
@@ -43,8 +43,8 @@ def test_fused_apply_taylor_groups(V, M):
     Q, u = _case(shape, 3)
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, M, V.IMPL_FUSED, V.F32)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), M)
-    assert rel_l2(g1, r1) <= TOL32
-    assert rel_l2(g2, r2) <= TOL32
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
 
 
 def test_fused_apply_white_noise_and_nyquist(V):
@@ -56,7 +56,8 @@ def test_fused_apply_white_noise_and_nyquist(V):
     u[:, :] += 0.5 * np.cos(np.pi * np.arange(256))[:, None]  # y-Nyquist mode
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 8, V.IMPL_FUSED, V.F32)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), 8)
-    assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
 
 
 @pytest.mark.parametrize("impl", ["fused", "plain"])
@@ -70,8 +71,8 @@ def test_radix3_grid_white_noise(V, impl):
     im = V.IMPL_FUSED if impl == "fused" else V.IMPL_PLAIN
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 12, im, V.F32)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), 12)
-    assert rel_l2(g1, r1) <= TOL32, rel_l2(g1, r1)
-    assert rel_l2(g2, r2) <= TOL32, rel_l2(g2, r2)
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
 
 
 def test_fused_apply_non_square_box(V):
@@ -81,7 +82,8 @@ def test_fused_apply_non_square_box(V):
     Q, u = _case(shape, 11)
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 6, V.IMPL_FUSED, V.F32, lo, hi)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), 6, lo, hi)
-    assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
 
 
 @pytest.mark.parametrize("shape", [(256,), (4096,), (128, 128), (32, 32, 32)])
@@ -89,10 +91,12 @@ def test_plain_apply_matches_oracle(V, shape):
     Q, u = _case(shape, 13)
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 8, V.IMPL_PLAIN, V.F32)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), 8)
-    assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 8, V.IMPL_PLAIN, V.F64)
     r1, r2 = O.seismic_operators(uin, gamma_of(Q), 8)
-    assert rel_l2(g1, r1) <= TOL64 and rel_l2(g2, r2) <= TOL64
+    check(g1, r1, TOL64)
+    check(g2, r2, TOL64)
 
 
 def test_constant_q_single_mode_closed_form(V):
@@ -106,8 +110,8 @@ def test_constant_q_single_mode_closed_form(V):
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 4, V.IMPL_FUSED, V.F32)
     gam = np.arctan(1 / 20.0) / np.pi
     m2 = kx * kx + ky * ky
-    assert rel_l2(g1, m2 ** (1 + gam) * uin) <= TOL32
-    assert rel_l2(g2, m2 ** (0.5 + gam) * uin) <= TOL32
+    check(g1, m2 ** (1 + gam) * uin, TOL32)
+    check(g2, m2 ** (0.5 + gam) * uin, TOL32)
 
 
 def test_headline_size_per_apply_tolerance(V):
@@ -121,11 +125,12 @@ def test_headline_size_per_apply_tolerance(V):
     u = (1 - 2 * a) * np.exp(-a) + 0.1 * S.q_lowpass(shape, 21, qmin=-1, qmax=1, sigma_k=64)
     g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 16, V.IMPL_FUSED, V.F32)
     r1, r2_ = O.seismic_operators(uin, gamma_of(Q), 16)
-    e1, e2 = rel_l2(g1, r1), rel_l2(g2, r2_)
-    assert e1 <= TOL32 and e2 <= TOL32, (e1, e2)
+    check(g1, r1, TOL32)
+    check(g2, r2_, TOL32)
     # the plain path at the same accuracy
     p1, p2, _ = gpu_apply_pair(V, shape, Q, u, 16, V.IMPL_PLAIN, V.F32)
-    assert rel_l2(p1, r1) <= TOL32 and rel_l2(p2, r2_) <= TOL32
+    check(p1, r1, TOL32)
+    check(p2, r2_, TOL32)
 
 
 def test_apply_single_operator_entry(V):
@@ -140,10 +145,10 @@ def test_apply_single_operator_entry(V):
         s.apply(V.OP_HPG, ut, o)
         s.sync()
         r1, r2 = O.seismic_operators(u.astype(np.float32).astype(np.float64), gamma_of(Q), 5)
-        assert rel_l2(o.cpu().numpy().astype(np.float64), r2) <= TOL32
+        check(o.cpu().numpy().astype(np.float64), r2, TOL32)
         s.apply(V.OP_1PG, ut, o)
         s.sync()
-        assert rel_l2(o.cpu().numpy().astype(np.float64), r1) <= TOL32
+        check(o.cpu().numpy().astype(np.float64), r1, TOL32)
 
 
 @pytest.mark.parametrize("impl", ["fused", "plain"])
@@ -161,8 +166,8 @@ def test_smooth_inputs_keep_fp32_accuracy(V, impl):
         Q = S.q_lowpass(shape, 2)
         g1, g2, uin = gpu_apply_pair(V, shape, Q, u, 8, im, V.F32)
         r1, r2 = O.seismic_operators(uin, gamma_of(Q), 8)
-        assert rel_l2(g1, r1) <= 2e-6, (shape, rel_l2(g1, r1))
-        assert rel_l2(g2, r2) <= 2e-6, (shape, rel_l2(g2, r2))
+        check(g1, r1, 2e-6)
+        check(g2, r2, 2e-6)
 
 
 @pytest.mark.parametrize("shape,prec", [((64,), "f32"), ((256,), "f32"), ((4096,), "f32"),
@@ -174,7 +179,8 @@ def test_fused_1d_apply_matches_oracle(V, shape, prec):
         Q, u = _case(shape, 23 + M)
         g1, g2, uin = gpu_apply_pair(V, shape, Q, u, M, V.IMPL_FUSED, pr)
         r1, r2 = O.seismic_operators(uin, gamma_of(Q), M)
-        assert rel_l2(g1, r1) <= tol and rel_l2(g2, r2) <= tol, (M, rel_l2(g1, r1), rel_l2(g2, r2))
+        check(g1, r1, tol)
+        check(g2, r2, tol)
 
 
 @pytest.mark.parametrize("shape", [(64, 64, 64), (128, 128, 128), (256, 64, 128)])
@@ -184,7 +190,8 @@ def test_fused_3d_apply_matches_oracle(V, shape):
         u = S.q_lowpass(shape, 41 + M, qmin=-1.0, qmax=1.0, sigma_k=max(shape) / 8)
         g1, g2, uin = gpu_apply_pair(V, shape, Q, u, M, V.IMPL_FUSED, V.F32)
         r1, r2 = O.seismic_operators(uin, gamma_of(Q), M)
-        assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32, (M, rel_l2(g1, r1), rel_l2(g2, r2))
+        check(g1, r1, TOL32)
+        check(g2, r2, TOL32)
 
 
 def test_fused_3d_config_size_apply(V):
@@ -192,4 +199,52 @@ def test_fused_3d_config_size_apply(V):
     w = S.workload_3d_256(nsteps=1)
     g1, g2, uin = gpu_apply_pair(V, w["shape"], w["Q"], w["u0"], w["M"], V.IMPL_FUSED, V.F32)
     r1, r2 = O.seismic_operators(uin, gamma_of(w["Q"]), w["M"])
-    assert rel_l2(g1, r1) <= TOL32 and rel_l2(g2, r2) <= TOL32, (rel_l2(g1, r1), rel_l2(g2, r2))
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
+
+
+def test_headline_size_nyquist_column_and_top_taylor_group(V):
+    """1024^2, M = 16: the x-Nyquist column (kx = nx/2, the last column of
+    every half-spectrum tile and of the row transforms' packing) and the top
+    Taylor group (terms 12..16, the ragged group of five) both carry weight.
+    gamma swings over most of [0, 1/2), so delta ln|mu|^2 reaches ~3 and the
+    top group's terms sit far above FP32 round-off: a wrong slot, tile edge
+    or Nyquist handling there moves single columns or rows, which the
+    pointwise bound catches."""
+    shape = (1024, 1024)
+    x, y = S.mesh(shape)
+    gamma = 0.25 + 0.245 * np.tanh(4 * np.sin(x) * np.cos(y))
+    u = (np.cos(np.pi * np.arange(1024))[None, :] * (1.0 + 0.5 * np.cos(3 * y))  # x-Nyquist column
+         + np.cos(317 * x + 211 * y) + 0.5 * np.sin(5 * x - 7 * y))
+    uin = u.astype(np.float32)
+    import torch
+    with V.Solver(shape, None, None, V.F32, V.IMPL_FUSED) as s:
+        s.set_gamma(gamma)
+        s.set_M(16)
+        ut = torch.from_numpy(uin).cuda()
+        o1, o2 = torch.empty_like(ut), torch.empty_like(ut)
+        s.apply_pair(ut, o1, o2)
+        s.sync()
+        g1, g2 = o1.cpu().numpy().astype(np.float64), o2.cpu().numpy().astype(np.float64)
+    r1, r2 = O.seismic_operators(uin.astype(np.float64), gamma, 16)
+    # the top group matters: dropping terms 12..16 moves the answer past
+    # the tolerance
+    t1, _ = O.seismic_operators(uin.astype(np.float64), gamma, 11)
+    assert rel_l2(t1, r1) > 5 * TOL32, rel_l2(t1, r1)
+    check(g1, r1, TOL32)
+    check(g2, r2, TOL32)
+    # the general model's one operator, whose order swings far more (delta
+    # up to 0.4): its terms fill both slots, so the top group lands in slot 1
+    order = 1.0 - 0.4 * np.tanh(3 * np.cos(x) * np.sin(y))
+    with V.Solver(shape, None, None, V.F32, V.IMPL_FUSED) as s:
+        s.set_order(order)
+        s.set_M(16)
+        ut = torch.from_numpy(uin).cuda()
+        o = torch.empty_like(ut)
+        s.apply(V.OP_S, ut, o)
+        s.sync()
+        g = o.cpu().numpy().astype(np.float64)
+    r = O.matrix_free_operator(uin.astype(np.float64), order, 16)
+    t = O.matrix_free_operator(uin.astype(np.float64), order, 11)
+    assert rel_l2(t, r) > 100 * TOL32, rel_l2(t, r)
+    check(g, r, TOL32)

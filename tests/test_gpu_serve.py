@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import synthetic as S
-from gpu_util import gamma_of, rel_l2
+from gpu_util import gamma_of, rel_l2, check
 
 pytestmark = pytest.mark.gpu
 
@@ -51,4 +51,4 @@ def test_served_answer_against_oracle(V):
         dt = O.suggested_dt(g, 1.0, 2 * np.pi, sp["shape"], courant=0.25)
         ref = O.seismic_lffp(g, 1.0, 2 * np.pi, np.zeros(sp["shape"]), None, dt, sp["nsteps"], sp["M"],
                              src_idx=idx, src=_source(sp, dt))
-        assert rel_l2(r["result"].astype(np.float64), ref) <= 1e-4
+        check(r["result"].astype(np.float64), ref, 1e-4)

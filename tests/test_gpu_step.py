@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import synthetic as S
-from gpu_util import gamma_of, gpu_run, rel_l2
+from gpu_util import gamma_of, gpu_run, rel_l2, check
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def test_run_2d_source_matches_oracle(V, impl):
     g = gpu_run(V, shape, Q, u0, None, 8, dt, nsteps, im, V.F32, idx, src)
     r = _oracle_run(shape, Q, u0, None, 8, dt, nsteps, idx, src)
     assert np.max(np.abs(r)) > 0
-    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+    check(g, r, TOL32_RUN)
 
 
 def test_run_2d_pulse_with_velocity_start(V):
@@ -45,7 +45,7 @@ def test_run_2d_pulse_with_velocity_start(V):
     g = gpu_run(V, shape, Q, u0.astype(np.float32), v0.astype(np.float32), 7, dt, nsteps, V.IMPL_FUSED, V.F32)
     r = _oracle_run(shape, Q, u0.astype(np.float32).astype(np.float64), v0.astype(np.float32).astype(np.float64),
                     7, dt, nsteps)
-    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+    check(g, r, TOL32_RUN)
 
 
 def test_run_split_calls_equal_one_call(V):
@@ -68,9 +68,9 @@ def test_run_fp64_1d_against_dense_operator(V, impl):
     g = gpu_run(V, w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], im, V.F64)
     r_mf = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"])
     r_dense = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], method="dense")
-    assert rel_l2(g, r_mf) <= 1e-11, rel_l2(g, r_mf)
+    check(g, r_mf, 1e-11)
     # truncation of Eq. (2.9) at M = 8 on this model is far below 1e-6
-    assert rel_l2(g, r_dense) <= 1e-6, rel_l2(g, r_dense)
+    check(g, r_dense, 1e-6)
 
 
 def test_run_fused_1d_fp32_source_and_velocity(V):
@@ -85,7 +85,7 @@ def test_run_fused_1d_fp32_source_and_velocity(V):
     g = gpu_run(V, (n,), Q, u0, v0.astype(np.float32), 12, dt, nsteps, V.IMPL_FUSED, V.F32, (n // 3,), src,
                 chunks=[1, 60, 89])
     r = _oracle_run((n,), Q, u0, v0.astype(np.float32).astype(np.float64), 12, dt, nsteps, (n // 3,), src)
-    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+    check(g, r, TOL32_RUN)
 
 
 def test_run_fused_3d_matches_oracle(V):
@@ -95,7 +95,7 @@ def test_run_fused_3d_matches_oracle(V):
     u0 = S.gaussian_pulse(shape, 3.0)
     g = gpu_run(V, shape, Q, u0, None, 8, 8e-3, 30, V.IMPL_FUSED, V.F32)
     r = _oracle_run(shape, Q, u0.astype(np.float32).astype(np.float64), None, 8, 8e-3, 30)
-    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+    check(g, r, TOL32_RUN)
 
 
 def test_run_fp64_3d_plain(V):
@@ -104,7 +104,7 @@ def test_run_fp64_3d_plain(V):
     u0 = S.gaussian_pulse(shape, 3.0)
     g = gpu_run(V, shape, Q, u0, None, 6, 1e-2, 25, V.IMPL_PLAIN, V.F64)
     r = _oracle_run(shape, Q, u0, None, 6, 1e-2, 25)
-    assert rel_l2(g, r) <= 1e-9
+    check(g, r, 1e-9)
 
 
 def test_run_gamma_zero_is_classical_wave(V):
@@ -121,7 +121,7 @@ def test_run_gamma_zero_is_classical_wave(V):
         s.step(n, dt)
         g = s.get_state().astype(np.float64)
     theta = np.arccos(1 - 0.5 * dt * dt * 13)
-    assert rel_l2(g, np.cos(n * theta) * u0.astype(np.float32)) <= TOL32_RUN
+    check(g, np.cos(n * theta) * u0.astype(np.float32), TOL32_RUN)
 
 
 def test_headline_workload_short_run(V):
@@ -131,7 +131,7 @@ def test_headline_workload_short_run(V):
     g = gpu_run(V, w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], V.IMPL_FUSED, V.F32,
                 w["src_idx"], w["src"])
     r = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], w["src_idx"], w["src"])
-    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+    check(g, r, TOL32_RUN)
 
 
 def test_headline_workload_scaled_full_length(V):
@@ -140,7 +140,7 @@ def test_headline_workload_scaled_full_length(V):
     g = gpu_run(V, w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], V.IMPL_FUSED, V.F32,
                 w["src_idx"], w["src"])
     r = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], w["src_idx"], w["src"])
-    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+    check(g, r, TOL32_RUN)
 
 
 def test_state_errors(V):
@@ -168,4 +168,4 @@ def test_headline_workload_100_steps(V):
     g = gpu_run(V, w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], V.IMPL_FUSED, V.F32,
                 w["src_idx"], w["src"])
     r = _oracle_run(w["shape"], w["Q"], w["u0"], None, w["M"], w["dt"], w["nsteps"], w["src_idx"], w["src"])
-    assert rel_l2(g, r) <= TOL32_RUN, rel_l2(g, r)
+    check(g, r, TOL32_RUN)
