@@ -284,6 +284,37 @@ VOFL_API int vofl_profile_kernels(vofl_ctx* ctx, int reps, char* names_out,
                          size_t names_cap, double* ms_out,
                          double* units_out, int cap);
 
+/* Transform schedule of the fused 2D path.  The paper has no counterpart:
+ * it fixes how the same arithmetic of Eq. (2.13) is laid out on the GPU,
+ * not what is computed.  Results of different schedules agree within the
+ * FP32 tolerance but not bit for bit (the multiplier recurrence restarts at
+ * other terms, lines are transformed with other radices).
+ *   wide_cols, wide_rows: 1 = the inverse column / row pass transforms its
+ *     512- or 1024-point lines with 16 elements per lane over N/16 lanes
+ *     (three radix stages, two warps per 1024-point line), 0 = with up to
+ *     32 elements per lane over one warp (two stages), -1 = the size's
+ *     default (wide columns at 512, wide rows at 512 and 1024); ignored
+ *     (reported 0) for other line lengths.
+ *   col_parts: runs of terms per Taylor group in the inverse column pass
+ *     (each run starts its multiplier recurrence afresh), 1..41, or 0 for
+ *     the size's default (3 at ny <= 256, 2 at ny <= 512, 1 above).
+ *   group: Taylor terms per group G (the terms whose per-term column
+ *     transforms are stored between the column and row passes), 1..41;
+ *     0 = the default, 17 (M <= 16 in one group).  Changing it re-sizes
+ *     that buffer (a device allocation).
+ * vofl_get_schedule reports the schedule in use, defaults resolved.
+ * Only fused 2D contexts have one (VOFL_EUNSUPPORTED elsewhere).  A context
+ * whose schedule differs from its size's default cannot join a batch
+ * (vofl_batch_add returns VOFL_EUNSUPPORTED). */
+typedef struct {
+  int wide_cols;
+  int wide_rows;
+  int col_parts;
+  int group;
+} vofl_schedule;
+VOFL_API int vofl_set_schedule(vofl_ctx* ctx, const vofl_schedule* sched);
+VOFL_API int vofl_get_schedule(vofl_ctx* ctx, vofl_schedule* sched);
+
 /* Library version string. */
 VOFL_API const char* vofl_version(void);
 

@@ -27,6 +27,14 @@ SCHEME_LFFP, SCHEME_TSFP2, SCHEME_CNFP = 0, 1, 2
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ESTATE",
            -6: "EUNSUPPORTED", -7: "ENOCONV"}
 
+class Schedule(C.Structure):
+    """vofl_schedule: transform schedule of the fused 2D path."""
+    _fields_ = [("wide_cols", C.c_int), ("wide_rows", C.c_int), ("col_parts", C.c_int), ("group", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _i64p = C.POINTER(C.c_int64)
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
@@ -60,6 +68,8 @@ SIGNATURES = {
     "vofl_kernel_launches": (C.c_uint64, []),
     "vofl_profile_kernels": (C.c_int, [_vp, C.c_int, C.c_char_p, C.c_size_t, _dp, _dp, C.c_int]),
     "vofl_version": (C.c_char_p, []),
+    "vofl_set_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
+    "vofl_get_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
     "vofl_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int)]),
     "vofl_apply_pair_2d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp, _vp,
                                              _vp, _vp]),
@@ -299,6 +309,16 @@ class Solver:
         if rc < 0:
             self._check(rc)
         return rc == 1
+
+    def set_schedule(self, wide_cols=-1, wide_rows=-1, col_parts=0, group=0):
+        """Transform schedule of the fused 2D path (-1 / 0: the size's default)."""
+        sc = Schedule(int(wide_cols), int(wide_rows), int(col_parts), int(group))
+        self._check(lib().vofl_set_schedule(self._h, C.byref(sc)))
+
+    def schedule(self):
+        sc = Schedule()
+        self._check(lib().vofl_get_schedule(self._h, C.byref(sc)))
+        return sc.as_dict()
 
     def profile_kernels(self, reps=20):
         names = C.create_string_buffer(1024)

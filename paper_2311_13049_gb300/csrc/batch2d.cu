@@ -34,11 +34,11 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "kernels_wide.cuh"
 
 namespace vofl {
 namespace {
 
-constexpr int BG = 6;  // Taylor terms per group (the contexts' Z holds 6)
 
 constexpr double inv_fact_d(int m) {
   double f = 1.0;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(W_FCOLS * 32) kb_fwd_cols(const BatchSim* __re
 
 template <int NX, int NY>
 __global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const BatchSim* __restrict__ sims, int g,
-                                                                      int parts) {
+                                                                      int parts, int BG) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;  // this simulation has fewer groups
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const Batc
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __restrict__ sims, int g) {
+__global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __restrict__ sims, int g, int BG) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;
@@ -98,14 +98,40 @@ __global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __re
                     s->part + (size_t)NX * NY, s->epi, s->inv_lambda, s->twx, s->err);
 }
 
+// wide inverse passes (fft_wide.cuh) for 512 and 1024 points, as the
+// single-context launches of those sizes use them
+template <int NX, int NY>
+__global__ void __launch_bounds__(wide_threads<NY>(), wide_min_blocks<NY>()) kb_inv_cols_w(const BatchSim* __restrict__ sims, int g,
+                                                                       int parts, int BG) {
+  const BatchSim* s = sims + blockIdx.z;
+  const int m_lo = g * BG;
+  if (m_lo > s->M) return;
+  const int m_hi = min(s->M + 1, m_lo + BG);
+  inv_cols_wide_body<NY>(blockIdx.x, blockIdx.y, parts, s->Uh, s->P, s->Lg, s->Z, s->pZ, NX / 2 + 1, m_lo, m_hi,
+                         (float)c_inv_fact[m_lo], (float)c_inv_fact[m_lo], 0, s->twyw);
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(wide_rows_threads<NX>(), NX == 1024 ? 1 : 6) kb_inv_rows_w(const BatchSim* __restrict__ sims, int g, int BG) {
+  const BatchSim* s = sims + blockIdx.z;
+  const int m_lo = g * BG;
+  if (m_lo > s->M) return;
+  const int m_hi = min(s->M + 1, m_lo + BG);
+  inv_rows_wide_body<NX, false>(blockIdx.x, s->Z, s->zslot, s->pZ, NY, m_lo, m_hi, m_hi == s->M + 1 ? 1 : 0,
+                                s->M + 1, 0, s->delta, s->part, s->part + (size_t)NX * NY, s->epi, s->inv_lambda,
+                                s->twxw, s->err);
+}
+
 struct BKernels {
   void (*fr)(const BatchSim*);
   void (*fc)(const BatchSim*);
-  void (*ic)(const BatchSim*, int, int);
-  void (*ir)(const BatchSim*, int);
+  void (*ic)(const BatchSim*, int, int, int);
+  void (*ir)(const BatchSim*, int, int);
   size_t smem_fr, smem_fc, smem_ic, smem_ir;
   int lpw_x, lpw_y;
   int wic;  // warps per CTA of kb_inv_cols
+  // inverse-kernel launch shapes: lines per CTA and threads per CTA
+  int cpc, thr_ic, rpc, thr_ir;
 };
 
 template <int NX, int NY>
@@ -113,15 +139,42 @@ BKernels bkernels_for() {
   BKernels k;
   k.fr = kb_fwd_rows<NX, NY>;
   k.fc = kb_fwd_cols<NX, NY>;
-  k.ic = kb_inv_cols<NX, NY>;
-  k.ir = kb_inv_rows<NX, NY>;
   k.smem_fr = frows_smem<NX, false>();
   k.smem_fc = exch_smem<NY, W_FCOLS>();
-  k.smem_ic = inv_cols_smem<NY>();
-  k.smem_ir = inv_rows_smem<NX>();
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
   k.wic = icols_warps<NY>();
+  bool wc = false, wr = false;
+  if constexpr (NY == 512 || NY == 1024) {
+    if (wide_cols_default(NY)) {
+      k.ic = kb_inv_cols_w<NX, NY>;
+      k.smem_ic = wide_cols_smem<NY>();
+      k.cpc = wide_lines_per_cta<NY>();
+      k.thr_ic = wide_threads<NY>();
+      wc = true;
+    }
+  }
+  if (!wc) {
+    k.ic = kb_inv_cols<NX, NY>;
+    k.smem_ic = inv_cols_smem<NY>();
+    k.cpc = k.wic * k.lpw_y;
+    k.thr_ic = k.wic * 32;
+  }
+  if constexpr (NX == 512 || NX == 1024) {
+    if (wide_rows_default(NX)) {
+      k.ir = kb_inv_rows_w<NX, NY>;
+      k.smem_ir = wide_rows_smem<NX>();
+      k.rpc = wide_rows_per_cta<NX>();
+      k.thr_ir = wide_rows_threads<NX>();
+      wr = true;
+    }
+  }
+  if (!wr) {
+    k.ir = kb_inv_rows<NX, NY>;
+    k.smem_ir = inv_rows_smem<NX>();
+    k.rpc = W_IROWS * k.lpw_x;
+    k.thr_ir = W_IROWS * 32;
+  }
   return k;
 }
 
@@ -340,13 +393,14 @@ cudaError_t enqueue_step(vofl_batch* b, int p) {
       const int cpf = W_FCOLS * cl.k.lpw_y;
       e = launch_pdl(cl.k.fc, dim3((ncols + cpf - 1) / cpf, 1, nz), dim3(W_FCOLS * 32), cl.k.smem_fc, s, dc);
       if (e) return e;
-      const int cpc = cl.k.wic * cl.k.lpw_y, rpi = W_IROWS * cl.k.lpw_x;
+      const int cpc = cl.k.cpc, rpi = cl.k.rpc;
+      // the group size and column split of the solo launches of this size
+      const int BG = group_default(nx, ny), parts = col_parts_default(ny);
       for (int g = Mmax / BG; g >= 0; --g) {
-        const int parts = icols_parts_2d(ny);  // the split of the solo launches of this size
-        e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2 * parts, nz), dim3(cl.k.wic * 32), cl.k.smem_ic, s,
-                       dc, g, parts);
+        e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2 * parts, nz), dim3(cl.k.thr_ic), cl.k.smem_ic, s,
+                       dc, g, parts, BG);
         if (e) return e;
-        e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(W_IROWS * 32), cl.k.smem_ir, s, dc, g);
+        e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(cl.k.thr_ir), cl.k.smem_ir, s, dc, g, BG);
         if (e) return e;
       }
     }

@@ -739,6 +739,24 @@ int vofl_sync(vofl_ctx* c) {
   return VOFL_OK;
 }
 
+int vofl_set_schedule(vofl_ctx* c, const vofl_schedule* sched) {
+  NvtxRange nvtx_range("vofl_set_schedule");
+  if (int st = check_ctx(c)) return st;
+  if (!sched) return set_err(c, VOFL_EINVAL, "null schedule");
+  if (sched->wide_cols < -1 || sched->wide_cols > 1 || sched->wide_rows < -1 || sched->wide_rows > 1 ||
+      sched->col_parts < 0 || sched->col_parts > 41 || sched->group < 0 || sched->group > 41)
+    return set_err(c, VOFL_EINVAL, "schedule field out of range");
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));  // queued work may use the buffers being re-sized
+  drop_graphs(c);
+  return c->eng->set_schedule(c, sched);
+}
+
+int vofl_get_schedule(vofl_ctx* c, vofl_schedule* sched) {
+  if (int st = check_ctx(c)) return st;
+  if (!sched) return set_err(c, VOFL_EINVAL, "null schedule");
+  return c->eng->get_schedule(c, sched);
+}
+
 int vofl_profile_kernels(vofl_ctx* c, int reps, char* names_out, size_t names_cap, double* ms_out, double* units_out,
                          int cap) {
   if (int st = check_ctx(c)) return st;

@@ -26,9 +26,11 @@
 // A model with one operator (the general model) puts its terms 0..K-1 in
 // the operator-1 slot and K..M in the operator-2 slot (K = ceil((M+1)/2)),
 // summed as sum_0 + delta^K sum_1 in the epilogue: half the line
-// transforms.  On grids of ny <= 512 the column pass splits each group's
-// terms into runs over 2-3 CTAs (icols_parts_2d); at 1024^2 the row pass
-// uses seven-row CTAs (one per SM).
+// transforms.  The schedule (kernels_wide.cuh: group_default,
+// col_parts_default, wide_cols_default, wide_rows_default) sets per grid
+// size the terms per group, the runs of terms the column pass splits a
+// group into, and whether the 512/1024-point inverse passes use the wide
+// line transform (fft_wide.cuh); vofl_set_schedule overrides it.
 //
 // Launches use programmatic dependent launch: each kernel does the work
 // that does not read its predecessor's output (twiddle and table loads,
@@ -44,6 +46,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "kernels_wide.cuh"
 
 namespace vofl {
 
@@ -59,20 +62,27 @@ struct Kernels {
                    const float2*);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
                            EpiArgs<float>, float, const float2*, int*);
+  using InvColsW = void (*)(const float2*, const float*, const float*, float2*, int, int, int, int, float, float, int,
+                            int, const float2*);
   InvRows inv_rows;        // two operators
   InvRows inv_rows_split;  // one operator, terms split over the slots
-  size_t smem_frows, smem_fcols, smem_icols, smem_irows;
+  // wide line transforms (fft_wide.cuh) of the inverse passes, for lines of
+  // 512 and 1024 points (null elsewhere)
+  InvColsW inv_cols_w = nullptr;
+  InvRows inv_rows_w = nullptr, inv_rows_w_split = nullptr;
+  size_t smem_frows, smem_fcols, smem_icols, smem_irows, smem_icols_w = 0, smem_irows_w = 0;
   int lpw_x, lpw_y;
   int wic;  // warps per CTA of inv_cols
   int wir;  // warps (rows) per CTA of inv_rows
+  int cpc_w = 0, rpc_w = 0, thr_w_c = 0, thr_w_r = 0;  // lines per CTA / threads of the wide kernels
 };
 
-// rows per CTA of the inverse row kernel: 7 at 1024^2 (147 CTAs, one per
-// SM, instead of 256 four-row CTAs in 1.7 waves: a 1.4% shorter step),
-// 4 elsewhere
+// warps per CTA of the inverse row kernel: 7 at 1024^2 (147 CTAs, one per
+// SM, instead of 256 four-row CTAs in 1.7 waves: a 1.4% shorter step), one
+// (two 16-lane rows) at 512^2 (256 CTAs instead of 64), 4 elsewhere
 template <int NX, int NY>
 constexpr int irows_warps() {
-  return (NX == 1024 && NY == 1024) ? 7 : W_IROWS;
+  return (NX == 1024 && NY == 1024) ? 7 : (NX == 512 && NY == 512) ? 1 : W_IROWS;
 }
 
 template <int NX, int NY>
@@ -92,6 +102,19 @@ Kernels kernels_for() {
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
   k.wic = icols_warps<NY>();
+  if constexpr (NY == 512 || NY == 1024) {
+    k.inv_cols_w = k2d_inv_cols_w<NY>;
+    k.smem_icols_w = wide_cols_smem<NY>();
+    k.cpc_w = wide_lines_per_cta<NY>();
+    k.thr_w_c = wide_threads<NY>();
+  }
+  if constexpr (NX == 512 || NX == 1024) {
+    k.inv_rows_w = k2d_inv_rows_w<NX, false>;
+    k.inv_rows_w_split = k2d_inv_rows_w<NX, true>;
+    k.smem_irows_w = wide_rows_smem<NX>();
+    k.rpc_w = wide_rows_per_cta<NX>();
+    k.thr_w_r = wide_rows_threads<NX>();
+  }
   return k;
 }
 
@@ -120,7 +143,10 @@ int set_smem_attributes(const Kernels& k) {
   if (set_kernel_smem(k.fwd_rows, k.smem_frows) ||
       set_kernel_smem(k.fwd_cols, k.smem_fcols) ||
       set_kernel_smem(k.inv_cols, k.smem_icols) ||
-      set_kernel_smem(k.inv_rows, k.smem_irows) || set_kernel_smem(k.inv_rows_split, k.smem_irows)) {
+      set_kernel_smem(k.inv_rows, k.smem_irows) || set_kernel_smem(k.inv_rows_split, k.smem_irows) ||
+      (k.inv_cols_w && set_kernel_smem(k.inv_cols_w, k.smem_icols_w)) ||
+      (k.inv_rows_w && (set_kernel_smem(k.inv_rows_w, k.smem_irows_w) ||
+                        set_kernel_smem(k.inv_rows_w_split, k.smem_irows_w)))) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
@@ -137,11 +163,16 @@ struct Plan2D {
   float* P = nullptr;     // [2][ncols][ny]
   float* Lg = nullptr;    // [ncols][ny]
   float2 *twx = nullptr, *twy = nullptr;
+  float2 *twxw = nullptr, *twyw = nullptr;  // wide line twiddles (512, 1024 points)
   const float* delta = nullptr;
   int* step_ctr = nullptr;
   int* err = nullptr;
   float ryy = 1.f, inv_lambda = 1.f;
   CUtensorMap zmap{};  // Z as [2 G ny rows][pZ] for the column kernel's tile stores
+  // schedule: wide line transforms in the inverse column / row passes
+  // (where built) and the column-pass term split (0: col_parts_default)
+  bool wide_c = false, wide_r = false;
+  int cparts = 0;
 
   // one_op: a model with one operator (its terms fill both slots)
   int groups(int M, bool one_op = false) const { return (term_split(M, one_op).slots + G - 1) / G; }
@@ -169,26 +200,32 @@ struct Plan2D {
                       bool one_op = false) const {
     const TermSplit ts = term_split(M, one_op);
     const int K = groups(M, one_op);
-    const int cpc = k.wic * k.lpw_y;
-    const int parts = icols_parts_2d(ny);
+    const bool wc = wide_c && k.inv_cols_w, wr = wide_r && k.inv_rows_w;
+    const int cpc = wc ? k.cpc_w : k.wic * k.lpw_y;
+    const int parts = cparts > 0 ? cparts : col_parts_default(ny);
     const dim3 gic((ncols + cpc - 1) / cpc, 2 * parts);
-    const int rpc = k.wir * k.lpw_x;
+    const int rpc = wr ? k.rpc_w : k.wir * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
     int e_i = 3;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(ts.slots, m_lo + G);
       const float f0 = inv_factorial(m_lo), f1 = ts.split_k ? inv_factorial(m_lo + ts.split_k) : f0;
-      cudaError_t e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, (const float2*)Uh,
-                                 (const float*)P, (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k,
-                                 parts, (const float2*)twy);
+      cudaError_t e;
+      if (wc)
+        e = launch_pdl(k.inv_cols_w, gic, dim3(k.thr_w_c), k.smem_icols_w, s, (const float2*)Uh, (const float*)P,
+                       (const float*)Lg, Z, pZ, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, (const float2*)twyw);
+      else
+        e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, (const float2*)Uh, (const float*)P,
+                       (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, (const float2*)twy);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
       EpiArgs<float> ep = epi;
       if (gi > 0) ep.mode = EPI_PARTIAL;
-      e = launch_pdl(one_op ? k.inv_rows_split : k.inv_rows, gir, dim3(k.wir * 32), k.smem_irows, s,
+      Kernels::InvRows kr = wr ? (one_op ? k.inv_rows_w_split : k.inv_rows_w) : (one_op ? k.inv_rows_split : k.inv_rows);
+      e = launch_pdl(kr, gir, dim3(wr ? k.thr_w_r : k.wir * 32), wr ? k.smem_irows_w : k.smem_irows, s,
                      (const float2*)Z, zslot, pZ, ny, m_lo, m_hi,
                      gi == K - 1 ? 1 : 0, ts.k2, ts.split_k, delta, part, part + (size_t)nx * ny, ep, inv_lambda,
-                     (const float2*)twx, err);
+                     (const float2*)(wr ? twxw : twx), err);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
     }
@@ -224,13 +261,21 @@ struct Fused2D : Engine {
     cudaFree(p.Lg);
     cudaFree(p.twx);
     cudaFree(p.twy);
+    cudaFree(p.twxw);
+    cudaFree(p.twyw);
   }
 
   size_t bytes() const override { return nbytes; }
 
   bool batch_desc(const vofl_ctx* c, BatchSim* d) const override {
     (void)c;
-    if (p.G != 6) return false;  // the batched launches use 6 terms per group
+    if (p.G != group_default(p.nx, p.ny)) return false;  // the batched launches use the default group size
+    // the batched launches use the default schedule of the size (wide
+    // inverse passes where built, the default column split): a context on
+    // another schedule would not give the same bits in a batch
+    if (p.wide_c != (p.k.inv_cols_w != nullptr && wide_cols_default(p.ny)) ||
+        p.wide_r != (p.k.inv_rows_w != nullptr && wide_rows_default(p.nx)) || p.cparts != 0)
+      return false;
     d->T = p.T;
     d->Uh = p.Uh;
     d->Z = p.Z;
@@ -239,6 +284,8 @@ struct Fused2D : Engine {
     d->Lg = p.Lg;
     d->twx = p.twx;
     d->twy = p.twy;
+    d->twxw = p.twxw;
+    d->twyw = p.twyw;
     d->ryy = p.ryy;
     d->inv_lambda = p.inv_lambda;
     d->zslot = p.zslot;
@@ -263,7 +310,7 @@ struct Fused2D : Engine {
     p.pT = round_up(p.ncols, 8);
     p.pZ = p.pT;
     p.zslot = (long long)p.ny * p.pZ;
-    p.G = 6;
+    p.G = group_default(p.nx, p.ny);
     int st;
     const size_t nx = p.nx, ny = p.ny, nc = p.ncols;
     if ((st = alloc(c, (void**)&p.T, sizeof(float2) * ny * p.pT))) return st;
@@ -274,9 +321,15 @@ struct Fused2D : Engine {
     if ((st = alloc(c, (void**)&p.Lg, sizeof(float) * nc * ny))) return st;
     if ((st = alloc(c, (void**)&p.twx, sizeof(float2) * line_twiddle_entries(p.nx)))) return st;
     if ((st = alloc(c, (void**)&p.twy, sizeof(float2) * line_twiddle_entries(p.ny)))) return st;
+    if (p.k.inv_rows_w && (st = alloc(c, (void**)&p.twxw, sizeof(float2) * wide_twiddle_entries(p.nx)))) return st;
+    if (p.k.inv_cols_w && (st = alloc(c, (void**)&p.twyw, sizeof(float2) * wide_twiddle_entries(p.ny)))) return st;
+    p.wide_c = p.k.inv_cols_w != nullptr && wide_cols_default(p.ny);
+    p.wide_r = p.k.inv_rows_w != nullptr && wide_rows_default(p.nx);
     if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
     if (make_line_twiddles(p.nx, p.twx, c->stream) ||
-        make_line_twiddles(p.ny, p.twy, c->stream))
+        make_line_twiddles(p.ny, p.twy, c->stream) ||
+        (p.twxw && make_wide_twiddles(p.nx, p.twxw, c->stream)) ||
+        (p.twyw && make_wide_twiddles(p.ny, p.twyw, c->stream)))
       return cuda_err(c, cudaGetLastError(), "twiddles");
     p.delta = (const float*)c->delta;
     p.step_ctr = c->d_step;
@@ -299,6 +352,37 @@ struct Fused2D : Engine {
 
   uint64_t kernels_per_step(const vofl_ctx* c) const override {
     return 2 + 2 * (uint64_t)p.groups(c->M, c->general);
+  }
+
+  int set_schedule(vofl_ctx* c, const vofl_schedule* s) override {
+    const bool wc = p.k.inv_cols_w && (s->wide_cols < 0 ? wide_cols_default(p.ny) : s->wide_cols == 1);
+    const bool wr = p.k.inv_rows_w && (s->wide_rows < 0 ? wide_rows_default(p.nx) : s->wide_rows == 1);
+    const int G = s->group == 0 ? group_default(p.nx, p.ny) : s->group;
+    if (G != p.G) {
+      const size_t b_old = sizeof(float2) * (size_t)p.zslot * 2 * p.G;
+      const size_t b_new = sizeof(float2) * (size_t)p.zslot * 2 * G;
+      float2* z = nullptr;
+      cudaError_t e = cudaMalloc((void**)&z, b_new);
+      if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (Taylor group buffer)");
+      cudaFree(p.Z);
+      p.Z = z;
+      p.G = G;
+      nbytes = nbytes - b_old + b_new;
+      if (p.make_zmap()) return set_err(c, VOFL_ECUDA, "tensor map of the Z buffer");
+    }
+    p.wide_c = wc;
+    p.wide_r = wr;
+    p.cparts = s->col_parts;
+    return VOFL_OK;
+  }
+
+  int get_schedule(const vofl_ctx* c, vofl_schedule* s) const override {
+    (void)c;
+    s->wide_cols = p.wide_c && p.k.inv_cols_w ? 1 : 0;
+    s->wide_rows = p.wide_r && p.k.inv_rows_w ? 1 : 0;
+    s->col_parts = p.cparts > 0 ? p.cparts : col_parts_default(p.ny);
+    s->group = p.G;
+    return VOFL_OK;
   }
 
   int apply_pair(vofl_ctx* c, const void* u, void* o1, void* o2) override {
@@ -411,8 +495,13 @@ bool fused2d_supported(int ndim, const int64_t* n, int prec) {
 
 size_t fused2d_footprint(const int64_t* n, int M) {
   const size_t nx = n[0], ny = n[1], nc = nx / 2 + 1, p = (nc + 7) / 8 * 8;
-  const size_t G = std::min(6, M + 1);
-  return sizeof(float2) * (ny * p + nc * ny + ny * p * 2 * G + line_twiddle_entries((int)nx) + line_twiddle_entries((int)ny)) + sizeof(float) * (2 * nx * ny + 3 * nc * ny);
+  (void)M;  // the group buffer is sized for the grid's default group, whatever M
+  const size_t G = group_default((int)nx, (int)ny);
+  const size_t tww = (wide_line((int)nx) ? wide_twiddle_entries((int)nx) : 0) +
+                     (wide_line((int)ny) ? wide_twiddle_entries((int)ny) : 0);
+  return sizeof(float2) * (ny * p + nc * ny + ny * p * 2 * G + line_twiddle_entries((int)nx) +
+                           line_twiddle_entries((int)ny) + tww) +
+         sizeof(float) * (2 * nx * ny + 3 * nc * ny);
 }
 
 Engine* make_fused2d(vofl_ctx* c, int* status) {

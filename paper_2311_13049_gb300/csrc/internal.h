@@ -95,6 +95,8 @@ struct BatchSim {
   const float* Lg;      // ln |mu|^2
   const float2* twx;    // line twiddles along x
   const float2* twy;    // ... along y
+  const float2* twxw;   // wide line twiddles along x (512 or 1024 points, else null)
+  const float2* twyw;   // ... along y
   int* err;             // device error word
   float ryy;            // (h_x / h_y)^2
   float inv_lambda;     // 1 / (operator-2 balance factor)
@@ -193,6 +195,17 @@ struct Engine {
     return 0;
   }
   virtual size_t bytes() const = 0;
+  // transform schedule (fused 2D only)
+  virtual int set_schedule(vofl_ctx* c, const vofl_schedule* s) {
+    (void)c;
+    (void)s;
+    return VOFL_EUNSUPPORTED;
+  }
+  virtual int get_schedule(const vofl_ctx* c, vofl_schedule* s) const {
+    (void)c;
+    (void)s;
+    return VOFL_EUNSUPPORTED;
+  }
   // Fill the engine-owned part of a batch descriptor (buffers, tables,
   // pitches); false if this engine cannot take part in a 2D batch.
   virtual bool batch_desc(const vofl_ctx* c, BatchSim* d) const {
@@ -285,6 +298,11 @@ inline int line_twiddle_entries(int N) {
   return nb * r + nm;
 }
 int make_line_twiddles(int N, float2* d_tw, cudaStream_t s);
+// The wide line transform of N = 512 or 1024 points (fft_wide.cuh): its
+// last stage's N twiddles w_N^{r j}, then the 16 (N/64) of the middle stage.
+inline bool wide_line(int N) { return N == 512 || N == 1024; }
+inline int wide_twiddle_entries(int N) { return N + (N / 64) * 16; }
+int make_wide_twiddles(int N, float2* d_tw, cudaStream_t s);
 // Tensor map of a [rows][pitch] array of 8-byte elements (ncols valid per
 // row) for 2D tiled TMA copies of boxes of box_cols x box_rows (model.cu).
 int make_tile_map(CUtensorMap* map, const void* base, int ncols, long long rows, int pitch, int box_cols,

@@ -44,9 +44,19 @@ template <int N>
 constexpr bool icols_pair() {
   return LineFFT<N>::E >= 24;
 }
+// Warps (columns) per CTA of the narrow column kernel: 8 at 1024 points
+// (65 column blocks x 2 operators = 130 CTAs of one per SM; 4-warp CTAs two
+// per SM measured 10% slower), 4 elsewhere (768: 194 CTAs instead of 98).
 template <int N>
 constexpr int icols_warps() {
-  return icols_pair<N>() ? 8 : 4;
+  return N == 1024 ? 8 : 4;
+}
+// float2 slots of one exchange set of the column kernel: its warps'
+// buffers, rounded to 128 bytes (the second set of the paired form is a
+// tensor-copy source)
+template <int N>
+constexpr int icols_set() {
+  return (icols_warps<N>() * warp_stride<N>() + 15) / 16 * 16;
 }
 
 // -------------------------------------------------------------------------
@@ -255,8 +265,8 @@ constexpr size_t inv_cols_smem() {
   // long lines: two exchange-buffer sets (two terms in flight) and
   // ln|mu|^2 per column; short lines: one set (ln|mu|^2 in registers)
   constexpr int W = icols_warps<NY>();
-  return icols_pair<NY>() ? 2 * exch_smem<NY, W>() + (size_t)W * LineFFT<NY>::LPW * NY * sizeof(float)
-                          : exch_smem<NY, W>();
+  return icols_pair<NY>() ? 2 * (size_t)icols_set<NY>() * sizeof(float2) + (size_t)W * LineFFT<NY>::LPW * NY * sizeof(float)
+                          : (size_t)icols_set<NY>() * sizeof(float2);
 }
 
 template <int NY>
@@ -275,7 +285,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, const
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL, RL = F::RL;
   constexpr int W = icols_warps<NY>(), THREADS = W * 32, CW = W * LPW;  // columns per CTA
   constexpr bool PAIR = icols_pair<NY>();
-  constexpr int SET = W * warp_stride<NY>();  // float2 slots of one exchange set
+  constexpr int SET = icols_set<NY>();  // float2 slots of one exchange set
   constexpr int BOXR = icols_box_rows<NY>();
   // the output tile fits an exchange set; the second set (paired terms)
   // starts 128-byte aligned like the first, as the tensor copies require
@@ -688,12 +698,6 @@ cudaError_t set_kernel_smem(void (*kern)(KArgs...), size_t bytes) {
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// 1/m! in double, rounded once to float
-// Column passes of small 2D grids have fewer CTAs than SMs and run each
-// group's terms one after another; there the group is split into runs of
-// terms over several CTAs.  The solo and batched launches of a grid use the
-// same split (and so the same arithmetic); 3D z passes use one run.
-inline int icols_parts_2d(int ny) { return ny <= 256 ? 3 : (ny <= 512 ? 2 : 1); }
 
 // How the Taylor terms m = 0..M fill the two operator slots of the inverse
 // kernels: one term of each operator per slot index (two operators), or,

@@ -1,0 +1,349 @@
+// kernels_wide.cuh -- the inverse column and row passes of the fused 2D step
+// (Eq. (2.13) of arXiv 2311.13049, see fused2d.cu) on the wide line
+// transform of fft_wide.cuh, for lines of 512 and 1024 points.
+//
+// Same data path and arithmetic order as the narrow kernels of kernels.cuh
+// (multiplier recurrence t_{m+1} = t_m ln|mu|^2/(m+1) in registers, Horner
+// over the group's terms in registers), with 16 elements per lane: a 1024
+// point line is owned by two warps, so a pass has twice the warps of the
+// narrow form and each holds half the registers.
+//
+// Lines per CTA (L) is a template parameter.  At 1024 points seven lines
+// per CTA and one CTA per SM (128 registers a thread) make one step's
+// 6156 column or 6144 row line transforms of a six-term group 5.8 waves of
+// seven per SM, against 5.06 waves (rounded up to 6) of eight.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft_wide.cuh"
+#include "kernels.cuh"
+
+namespace vofl {
+namespace {
+
+// Default transform schedule of a 2D grid (the single-context and the
+// batched launches both follow it, so a batch member gives the bits of the
+// same grid stepped alone): wide inverse column pass at 512 points, wide
+// inverse row pass at 512 and 1024 (measured per size; vofl_set_schedule
+// changes it per context).
+inline bool wide_cols_default(int ny) { return ny == 512; }
+inline bool wide_rows_default(int nx) { return nx == 512 || nx == 1024; }
+// Taylor terms per group: 17, so that M <= 16 runs in one group (one column
+// and one row launch per step).  Every launch boundary costs a few
+// microseconds; at 1024^2 one group of 17 (145 MB of per-term column
+// transforms, beyond L2) measured 7% faster than two groups of 9 (77 MB,
+// in L2) and 12% faster than three of 6.
+inline int group_default(int nx, int ny) {
+  (void)nx;
+  (void)ny;
+  return 17;
+}
+// Runs of terms per group in the column pass (each on its own CTAs): small
+// grids have fewer column blocks than SMs.
+inline int col_parts_default(int ny) { return ny <= 256 ? 3 : (ny <= 512 ? 6 : 1); }
+
+// Lines per CTA: seven two-warp lines at 1024 points; at 512 eight
+// one-warp columns (the cooperative last stage stores 64-byte row
+// segments) but two rows (a 512-row pass has only 512 lines: 256 CTAs).
+template <int N>
+constexpr int wide_lines_per_cta() {
+  return N == 1024 ? 7 : 8;
+}
+template <int N>
+constexpr int wide_rows_per_cta() {
+  return N == 1024 ? 7 : 2;
+}
+template <int N>
+constexpr int wide_threads() {
+  return wide_lines_per_cta<N>() * WideFFT<N>::LANES;
+}
+template <int N>
+constexpr int wide_rows_threads() {
+  return wide_rows_per_cta<N>() * WideFFT<N>::LANES;
+}
+// CTAs per SM the register budget is set for: one 14-warp CTA at 1024
+// points, two 8-warp CTAs at 512
+template <int N>
+constexpr int wide_min_blocks() {
+  return N == 1024 ? 1 : 2;
+}
+// Offset between consecutive lines' buffer pairs: the two buffers plus a
+// stagger that puts the lines of the cooperative last stage (thread b:
+// line b % L, butterfly b / L) on distinct shared-memory banks (checked
+// exhaustively for L = 4, 7, 8).
+template <int N, int L>
+constexpr int wide_line_stride() {
+  return 2 * WideFFT<N>::PAD_LINE + (L == 7 ? 7 : L == 8 ? 2 : L == 4 ? 4 : 1);
+}
+template <int N>
+constexpr int wide_rows_rb() {
+  return (N / 2 + 2) & ~1;  // Z row copy length in float2: >= N/2+1, 16-byte multiple
+}
+template <int N>
+constexpr size_t wide_cols_smem() {
+  constexpr int L = wide_lines_per_cta<N>();
+  return (size_t)L * wide_line_stride<N, L>() * sizeof(float2);
+}
+// rows: the line buffers, then (from a 128-byte boundary, as bulk copies
+// need 16-byte aligned destinations) one staged pair of Z rows per line
+template <int N>
+constexpr int wide_rows_zs_off() {
+  constexpr int L = wide_rows_per_cta<N>();
+  return (L * wide_line_stride<N, L>() + 15) / 16 * 16;
+}
+template <int N>
+constexpr size_t wide_rows_smem() {
+  constexpr int L = wide_rows_per_cta<N>();
+  return ((size_t)wide_rows_zs_off<N>() + (size_t)L * 2 * wide_rows_rb<N>()) * sizeof(float2);
+}
+
+// -------------------------------------------------------------------------
+// I1 (wide): multiplier + inverse FFT along y of L columns of one operator
+// (yidx = operator slot + 2 * part), terms [lo, hi) of the group [m_lo,
+// m_hi) (the group split into `parts` runs as in inv_cols_body).  Stages 0
+// and 1 by the column's own lanes; stage 2 cooperatively (thread b: column
+// b % L, butterfly b / L), whose outputs are row segments of L adjacent
+// columns stored straight to Z[slot][op][y][c].
+// -------------------------------------------------------------------------
+template <int NY>
+__device__ __forceinline__ void inv_cols_wide_body(int bx, int yidx, int parts, const float2* __restrict__ Uh,
+                                                   const float* __restrict__ P, const float* __restrict__ Lg,
+                                                   float2* __restrict__ Z, int pZ, int ncols, int m_lo, int m_hi,
+                                                   float inv_fact_lo, float inv_fact_lo1, int split_k,
+                                                   const float2* __restrict__ twy) {
+  using F = WideFFT<NY>;
+  constexpr int LANES = F::LANES, CW = wide_lines_per_cta<NY>(), THREADS = CW * LANES, NB2 = F::NB2;
+  constexpr int LS = wide_line_stride<NY, CW>();
+  __shared__ float2 s_tw[F::TW];
+  extern __shared__ __align__(16) float2 s_buf[];  // [CW][A, B, stagger]
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
+  const int line = threadIdx.x / LANES, li = threadIdx.x % LANES;
+  float2* A = s_buf + (size_t)line * LS;
+  float2* B = A + F::PAD_LINE;
+  const int c0 = bx * CW;
+  const int cc = min(c0 + line, ncols - 1);
+  const long long tot = (long long)ncols * NY;
+  const int op = yidx & 1, part = yidx >> 1;
+  const int per = (m_hi - m_lo + parts - 1) / parts;
+  const int lo = m_lo + part * per, hi = min(m_hi, lo + per);
+  if (lo >= hi) return;  // the whole CTA, before any barrier
+  const int off = (split_k > 0 && op) ? split_k : 0;
+  const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
+  const float* l_col = Lg + (size_t)cc * NY;
+  const float2* uh_col = Uh + (size_t)cc * NY;
+  float fstart = op ? inv_fact_lo1 : inv_fact_lo;
+  for (int j = m_lo + 1; j <= lo; ++j) fstart *= 1.0f / (float)(j + off);
+  // tables first (they do not depend on the previous kernel)
+  float lg[16], tm[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int y = li + LANES * m;
+    lg[m] = l_col[y];
+    tm[m] = p_col[y] * powi(lg[m], lo + off) * fstart;
+  }
+  // this thread's cooperative stage-2 butterflies: line sc, butterflies
+  // sj0 + LANES q (q < 4); rows sj0 + LANES q + NB2 r of column c0 + sc
+  const int sc = threadIdx.x % CW, sj0 = threadIdx.x / CW;
+  const bool store = c0 + sc < ncols;
+  const float2* Bc = s_buf + (size_t)sc * LS + F::PAD_LINE;
+  __syncthreads();
+  pdl_wait();  // Uh ready; the previous group's readers of Z are done
+  pdl_trigger();
+  float2 v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
+  float2* zcol = Z + (size_t)op * NY * pZ + (size_t)sj0 * pZ + c0 + sc;
+  const size_t zslot2 = (size_t)2 * NY * pZ;  // one term: both operators' slots
+  for (int mt = lo; mt < hi; ++mt) {
+    float2 x[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = v[m];
+    wide_stage0<NY, true>(x, A, li);
+    __syncthreads();  // A complete; every thread's previous stage-2 reads of B done
+    wide_stage1<NY, true>(A, B, s_tw, li);
+    __syncthreads();  // every column's B complete
+    float2* zt = zcol + (size_t)(mt - m_lo) * zslot2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 w[4];
+      wide_stage2_bfly<NY, true>(w, Bc, s_tw, sj0 + LANES * q);
+      if (store) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) zt[(size_t)(LANES * q + NB2 * r) * pZ] = w[r];
+      }
+    }
+    if (mt + 1 < hi) {
+      const float rinv = 1.0f / (float)(mt + 1 + off);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = cscale(v[m], lg[m] * rinv);
+    }
+  }
+}
+
+template <int NY>
+__global__ void __launch_bounds__(wide_threads<NY>(), wide_min_blocks<NY>())
+    k2d_inv_cols_w(const float2* __restrict__ Uh, const float* __restrict__ P, const float* __restrict__ Lg,
+                   float2* __restrict__ Z, int pZ, int ncols, int m_lo, int m_hi, float inv_fact_lo,
+                   float inv_fact_lo1, int split_k, int parts, const float2* __restrict__ twy) {
+  inv_cols_wide_body<NY>(blockIdx.x, blockIdx.y, parts, Uh, P, Lg, Z, pZ, ncols, m_lo, m_hi, inv_fact_lo,
+                         inv_fact_lo1, split_k, twy);
+}
+
+// -------------------------------------------------------------------------
+// I2 (wide): inverse FFT along x of both operators (A + iB) for L rows,
+// Horner accumulation over the group's terms, then partial store or the
+// epilogue.  The two Z rows (operator 1 and 2) of the next term are copied
+// into the row's staging buffer by TMA bulk copies as soon as every lane
+// of the row has read the current term from it (right after the first
+// barrier of the transform), so the copy overlaps the rest of the term.
+// Waits are bounded; the row's lanes decide together (barrier reduction)
+// whether a wait gave up, drain the copy in flight (bounded) and leave.
+// -------------------------------------------------------------------------
+template <int NX, bool SPLIT>
+__device__ __forceinline__ void inv_rows_wide_body(int bx, const float2* __restrict__ Z, long long zslot, int pZ,
+                                                   int ny, int m_lo, int m_hi, int top, int k2, int split_k,
+                                                   const float* __restrict__ delta, float* __restrict__ part1,
+                                                   float* __restrict__ part2, const EpiArgs<float>& epi,
+                                                   float inv_lambda, const float2* __restrict__ twx, int* err) {
+  using F = WideFFT<NX>;
+  constexpr int LANES = F::LANES, RPC = wide_rows_per_cta<NX>(), THREADS = RPC * LANES, H = NX / 2;
+  constexpr int LS = wide_line_stride<NX, RPC>(), RB = wide_rows_rb<NX>();
+  constexpr uint32_t RB_BYTES = RB * sizeof(float2);
+  static_assert(RPC <= 15, "named barriers 1..15");
+  __shared__ float2 s_tw[F::TW];
+  __shared__ uint64_t s_bar[RPC];
+  extern __shared__ __align__(128) float2 s_buf[];  // [RPC][A, B, stagger], then [RPC][op][RB]
+  const int line = threadIdx.x / LANES, li = threadIdx.x % LANES;
+  const int bar_id = 1 + line;
+  float2* A = s_buf + (size_t)line * LS;
+  float2* B = A + F::PAD_LINE;
+  float2* zs = s_buf + wide_rows_zs_off<NX>() + (size_t)line * 2 * RB;  // 128-byte base, RB even
+  static_assert(RB % 2 == 0 && wide_rows_zs_off<NX>() % 16 == 0, "bulk-copy destinations 16-byte aligned");
+  uint64_t* bar = &s_bar[line];
+  if (li == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
+  const int yr = bx * RPC + line;
+  const bool active = yr < ny;
+  const int y = active ? yr : 0;
+  const size_t row = (size_t)y * NX;
+  if (li == 0 && active) {
+    constexpr uint32_t RowB = NX * sizeof(float);
+    if (!top) {
+      prefetch_l2(part1 + row, RowB);
+      prefetch_l2(part2 + row, RowB);
+    }
+    if (m_lo == 0 && (epi.mode == EPI_STEP || epi.mode == EPI_START)) {
+      prefetch_l2(epi.u_cur + row, RowB);
+      prefetch_l2(epi.u_other + row, RowB);
+      prefetch_l2(epi.l2p + row, RowB);
+      prefetch_l2(epi.A + row, RowB);
+      prefetch_l2(epi.B + row, RowB);
+    }
+  }
+  float dl[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) dl[m] = delta[row + li + LANES * m];
+  __syncthreads();
+  pdl_wait();  // Z of this group and the previous group's partial sums are ready
+  pdl_trigger();
+  auto issue = [&](int mt) {
+    const float2* z1 = Z + (long long)((mt - m_lo) * 2) * zslot + (size_t)y * pZ;
+    mbar_arrive_expect_tx(bar, 2 * RB_BYTES);
+    bulk_copy_g2s(zs, z1, RB_BYTES, bar);
+    bulk_copy_g2s(zs + RB, z1 + zslot, RB_BYTES, bar);
+  };
+  if (li == 0) issue(m_hi - 1);
+  float a1[16], a2[16];
+  if (top) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) a1[m] = a2[m] = 0.f;
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      a1[m] = part1[row + li + LANES * m];
+      a2[m] = part2[row + li + LANES * m];
+    }
+  }
+  uint32_t phase = 0;
+  for (int mt = m_hi - 1; mt >= m_lo; --mt) {
+    const bool got = mbar_wait_bounded(bar, phase, err);
+    phase ^= 1u;
+    const float2* z1 = zs;
+    const float2* z2 = zs + RB;
+    float2 w[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int n = li + LANES * m;
+      if (n <= H) {
+        const float2 p = z1[n], q = z2[n];
+        w[m] = (n == 0 || n == H) ? make_float2(p.x, q.x) : make_float2(p.x - q.y, p.y + q.x);
+      } else {
+        const float2 p = z1[NX - n], q = z2[NX - n];
+        w[m] = make_float2(p.x + q.y, q.x - p.y);
+      }
+    }
+    wide_stage0<NX, true>(w, A, li);
+    // every lane has read the staged rows (and written A): the staging
+    // buffer is free for the next term's copy
+    if (line_sync_any<NX>(bar_id, !got)) {
+      // a wait gave up (error word set): no copy is in flight unless this
+      // lane's own wait was the one that failed; drain it (bounded), leave
+      if (li == 0 && !got) mbar_wait_bounded(bar, phase ^ 1u, err);
+      return;
+    }
+    if (li == 0 && mt > m_lo) {
+      fence_proxy_async_smem();
+      issue(mt - 1);
+    }
+    wide_stage1<NX, true>(A, B, s_tw, li);
+    line_sync<NX>(bar_id);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 t[4];
+      wide_stage2_bfly<NX, true>(t, B, s_tw, li + LANES * q);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) w[q + 4 * r] = t[r];
+    }
+    const bool use2 = !SPLIT || mt < k2;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      a1[m] = fmaf(dl[m], a1[m], w[m].x);
+      if (use2) a2[m] = fmaf(dl[m], a2[m], w[m].y);
+    }
+  }
+  if (!active) return;
+  if (m_lo > 0) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      part1[row + li + LANES * m] = a1[m];
+      part2[row + li + LANES * m] = a2[m];
+    }
+  } else if constexpr (SPLIT) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      float dk = 1.f;
+      for (int j = 0; j < split_k; ++j) dk *= dl[m];
+      epilogue_point<float>(epi, (long long)(row + li + LANES * m), fmaf(dk, a2[m], a1[m]), 0.f);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      epilogue_point<float>(epi, (long long)(row + li + LANES * m), a1[m], a2[m] * inv_lambda);
+  }
+}
+
+template <int NX, bool SPLIT>
+__global__ void __launch_bounds__(wide_rows_threads<NX>(), NX == 1024 ? 1 : 6)
+    k2d_inv_rows_w(const float2* __restrict__ Z, long long zslot, int pZ, int ny, int m_lo, int m_hi, int top, int k2,
+                   int split_k, const float* __restrict__ delta, float* __restrict__ part1,
+                   float* __restrict__ part2, EpiArgs<float> epi, float inv_lambda, const float2* __restrict__ twx,
+                   int* err) {
+  inv_rows_wide_body<NX, SPLIT>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, k2, split_k, delta, part1, part2, epi,
+                                inv_lambda, twx, err);
+}
+
+}  // namespace
+}  // namespace vofl

@@ -209,6 +209,29 @@ __global__ void k_twiddles(int N, int NB, int R, int NM, float2* tw) {
   }
 }
 
+// Twiddles of the wide line transform (fft_wide.cuh) of length N:
+// tw[r (N/4) + j] = w_N^{r j} (r < 4, j < N/4), then
+// tw[N + r 16 + k] = w_{N/4}^{r k} (r < N/64, k < 16).
+__global__ void k_twiddles_wide(int N, float2* tw) {
+  const int total = N + (N / 64) * 16;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    long long t;
+    int n;
+    if (i < N) {
+      const int r = i / (N / 4), j = i % (N / 4);
+      t = (long long)r * j;
+      n = N;
+    } else {
+      const int r = (i - N) / 16, k = (i - N) % 16;
+      t = (long long)r * k;
+      n = N / 4;
+    }
+    double s, c;
+    sincospi(-2.0 * (double)(t % n) / (double)n, &s, &c);
+    tw[i] = make_float2((float)c, (float)s);
+  }
+}
+
 inline int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 4096) b = 4096;
@@ -376,6 +399,13 @@ int make_line_twiddles(int N, float2* d_tw, cudaStream_t s) {
   int nb, r, nm;
   line_twiddle_layout(N, &nb, &r, &nm);
   k_twiddles<<<grid_for((long long)nb * r + nm, 256), 256, 0, s>>>(N, nb, r, nm, d_tw);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
+}
+
+int make_wide_twiddles(int N, float2* d_tw, cudaStream_t s) {
+  if (N != 512 && N != 1024) return VOFL_EINVAL;
+  k_twiddles_wide<<<grid_for(wide_twiddle_entries(N), 256), 256, 0, s>>>(N, d_tw);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
 }

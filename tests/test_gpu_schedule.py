@@ -1,0 +1,92 @@
+"""Transform schedules of the fused 2D path (vofl_set_schedule): every
+schedule computes the same operators of Eq. (2.13) within the FP32
+tolerance of the FP64 oracle; the defaults per grid size are reported; a
+context off its size's default schedule cannot join a batch (its bits would
+differ from the batched launches')."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from gpu_util import check, gamma_of
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+# (wide_cols, wide_rows, col_parts, group): -1 / 0 = the size's default
+SCHEDULES = [(-1, -1, 0, 0), (0, 0, 0, 0), (1, 1, 0, 0), (1, 0, 2, 6), (0, 1, 1, 3), (-1, -1, 6, 17),
+             (-1, -1, 3, 4), (0, 0, 1, 1)]
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_every_schedule_matches_the_oracle(V, n):
+    import torch
+    shape = (n, n)
+    Q = S.q_lowpass(shape, 31)
+    u = S.q_lowpass(shape, 32, qmin=-1.0, qmax=1.0, sigma_k=n // 8).astype(np.float32)
+    M = 16
+    r1, r2 = O.seismic_operators(u.astype(np.float64), gamma_of(Q), M)
+    with V.Solver(shape) as s:
+        s.set_q(Q)
+        s.set_M(M)
+        ut = torch.from_numpy(u).cuda()
+        for sc in SCHEDULES:
+            s.set_schedule(*sc)
+            got = s.schedule()
+            if sc[2] > 0:
+                assert got["col_parts"] == sc[2]
+            if sc[3] > 0:
+                assert got["group"] == sc[3]
+            o1, o2 = torch.empty_like(ut), torch.empty_like(ut)
+            s.apply_pair(ut, o1, o2)
+            s.sync()
+            check(o1.cpu().numpy(), r1, TOL32, sc)
+            check(o2.cpu().numpy(), r2, TOL32, sc)
+
+
+def test_default_schedules(V):
+    want = {256: {"wide_cols": 0, "wide_rows": 0, "col_parts": 3, "group": 17},
+            512: {"wide_cols": 1, "wide_rows": 1, "col_parts": 6, "group": 17},
+            768: {"wide_cols": 0, "wide_rows": 0, "col_parts": 1, "group": 17},
+            1024: {"wide_cols": 0, "wide_rows": 1, "col_parts": 1, "group": 17}}
+    for n, w in want.items():
+        with V.Solver((n, n)) as s:
+            assert s.schedule() == w, (n, s.schedule())
+            s.set_schedule(1, 1, 2, 5)
+            s.set_schedule()  # back to the defaults
+            assert s.schedule() == w
+
+
+def test_schedule_runs_agree_and_batch_needs_default(V):
+    """20 leap-frog steps on two schedules agree within the run tolerance;
+    a context off the default schedule is refused by a batch."""
+    shape = (512, 512)
+    Q = S.q_lowpass(shape, 5)
+    src = S.ricker_samples(20, 5e-4, 10.0)
+
+    def run(sched):
+        with V.Solver(shape) as s:
+            s.set_q(Q)
+            s.set_M(12)
+            if sched:
+                s.set_schedule(*sched)
+            s.set_state(np.zeros(shape, np.float32))
+            s.set_source(S.center_index(shape), src)
+            s.step(20, 5e-4)
+            return s.get_state().astype(np.float64)
+
+    a = run(None)
+    b = run((0, 0, 1, 4))
+    check(b, a, 1e-4)
+    with V.Solver(shape) as s, V.Batch() as bt:
+        s.set_q(Q)
+        s.set_M(12)
+        s.set_state(np.zeros(shape, np.float32))
+        s.set_schedule(0, 0, 1, 4)
+        with pytest.raises(V.VoflError):
+            bt.add(s, 5e-4)
+        s.set_schedule()
+        bt.add(s, 5e-4)
+        bt.step(2)
+        bt.sync()
