@@ -759,8 +759,9 @@ def run_gpu(args):
 
     # --- roofline of the dominant kernel (isolated launches, CUDA events on the context stream)
     prof = fused.profile_kernels(reps=20)
-    groups = -(-(M + 1) // 6)
-    launches_per_step = {"k2d_fwd_rows": 1, "k2d_fwd_cols": 1, "k2d_inv_cols": groups, "k2d_inv_rows": groups}
+    sched = fused.schedule()
+    groups = -(-(M + 1) // sched["group"])
+    launches_per_step = {nm: (groups if nm.startswith("k2d_inv") else 1) for nm, _, _ in prof}
     share = {nm: ms * launches_per_step.get(nm, 1) for nm, ms, _ in prof}
     dom = max(share, key=share.get)
     dom_ms, dom_units = [(ms, u) for nm, ms, u in prof if nm == dom][0]
@@ -778,6 +779,7 @@ def run_gpu(args):
             "frac": achieved / fp32_peak, "traffic": traffic, "traffic_note": traffic_note,
             "peak_note": f"derived FP32 FMA peak: {n_sm} SMs (read from the device) x 128 lanes x 2 flop x "
                          f"sm_max_mhz {sm_max:.0f}",
+            "schedule": sched,
             "flops_per_launch": flops, "ms_per_launch": dom_ms,
             "kernels": {nm: {"ms": ms, "units": u, "launches_per_step": launches_per_step.get(nm, 1)}
                         for nm, ms, u in prof}}

@@ -302,6 +302,11 @@ VOFL_API int vofl_profile_kernels(vofl_ctx* ctx, int reps, char* names_out,
  *     transforms are stored between the column and row passes), 1..41;
  *     0 = the default, 17 (M <= 16 in one group).  Changing it re-sizes
  *     that buffer (a device allocation).
+ *   fuse_forward: 1 = the top group's inverse column kernel also does the
+ *     forward transform along y (one launch fewer per step; the same
+ *     arithmetic, so the same bits), 0 = a separate forward column kernel,
+ *     -1 = the default (fused on grids of up to 256 rows); reported 0
+ *     when the column pass is wide.
  * vofl_get_schedule reports the schedule in use, defaults resolved.
  * Only fused 2D contexts have one (VOFL_EUNSUPPORTED elsewhere).  A context
  * whose schedule differs from its size's default cannot join a batch
@@ -311,6 +316,7 @@ typedef struct {
   int wide_rows;
   int col_parts;
   int group;
+  int fuse_forward;
 } vofl_schedule;
 VOFL_API int vofl_set_schedule(vofl_ctx* ctx, const vofl_schedule* sched);
 VOFL_API int vofl_get_schedule(vofl_ctx* ctx, vofl_schedule* sched);

@@ -58,8 +58,8 @@ namespace {
 struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
-  void (*inv_cols)(const float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int,
-                   const float2*);
+  void (*inv_cols)(float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int,
+                   const float2*, const float2*, int, int);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
                            EpiArgs<float>, float, const float2*, int*);
   using InvColsW = void (*)(const float2*, const float*, const float*, float2*, int, int, int, int, float, float, int,
@@ -170,9 +170,13 @@ struct Plan2D {
   float ryy = 1.f, inv_lambda = 1.f;
   CUtensorMap zmap{};  // Z as [2 G ny rows][pZ] for the column kernel's tile stores
   // schedule: wide line transforms in the inverse column / row passes
-  // (where built) and the column-pass term split (0: col_parts_default)
-  bool wide_c = false, wide_r = false;
+  // (where built), the column-pass term split (0: col_parts_default), and
+  // the forward column transform done inside the top group's inverse
+  // column kernel (32-element column kernel only)
+  bool wide_c = false, wide_r = false, fuse_fwd = false;
   int cparts = 0;
+
+  bool fused_forward() const { return fuse_fwd && !(wide_c && k.inv_cols_w); }
 
   // one_op: a model with one operator (its terms fill both slots)
   int groups(int M, bool one_op = false) const { return (term_split(M, one_op).slots + G - 1) / G; }
@@ -188,6 +192,7 @@ struct Plan2D {
                                T, ny, 1, pT, ryy, 0.0f, (const float2*)twx, step_ctr, inc_step ? 1 : 0, err);
     if (e) return e;
     if (ev) cudaEventRecord(ev[1], s);
+    if (fused_forward()) return cudaSuccess;  // the top group's column kernel does F2
     const int cpc = W_FCOLS * k.lpw_y;
     e = launch_pdl(k.fwd_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_FCOLS * 32), k.smem_fcols, s, (const float2*)T,
                    pT, Uh, ncols, (const float2*)twy, 0LL, 0LL);
@@ -195,7 +200,8 @@ struct Plan2D {
     return e;
   }
 
-  // optional events: one after every inverse kernel, from ev[3] on
+  // optional events: one after every inverse kernel, from ev[3] on (ev[2]
+  // when the forward column transform is fused)
   cudaError_t inverse(cudaStream_t s, int M, const EpiArgs<float>& epi, cudaEvent_t* ev = nullptr,
                       bool one_op = false) const {
     const TermSplit ts = term_split(M, one_op);
@@ -206,7 +212,8 @@ struct Plan2D {
     const dim3 gic((ncols + cpc - 1) / cpc, 2 * parts);
     const int rpc = wr ? k.rpc_w : k.wir * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
-    int e_i = 3;
+    const bool ff = fused_forward();
+    int e_i = ff ? 2 : 3;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(ts.slots, m_lo + G);
       const float f0 = inv_factorial(m_lo), f1 = ts.split_k ? inv_factorial(m_lo + ts.split_k) : f0;
@@ -215,8 +222,9 @@ struct Plan2D {
         e = launch_pdl(k.inv_cols_w, gic, dim3(k.thr_w_c), k.smem_icols_w, s, (const float2*)Uh, (const float*)P,
                        (const float*)Lg, Z, pZ, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, (const float2*)twyw);
       else
-        e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, (const float2*)Uh, (const float*)P,
-                       (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, (const float2*)twy);
+        e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, Uh, (const float*)P,
+                       (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, (const float2*)twy,
+                       (const float2*)T, pT, (ff && gi == K - 1) ? 1 : 0);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
       EpiArgs<float> ep = epi;
@@ -325,6 +333,7 @@ struct Fused2D : Engine {
     if (p.k.inv_cols_w && (st = alloc(c, (void**)&p.twyw, sizeof(float2) * wide_twiddle_entries(p.ny)))) return st;
     p.wide_c = p.k.inv_cols_w != nullptr && wide_cols_default(p.ny);
     p.wide_r = p.k.inv_rows_w != nullptr && wide_rows_default(p.nx);
+    p.fuse_fwd = fuse_forward_default(p.ny);
     if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
     if (make_line_twiddles(p.nx, p.twx, c->stream) ||
         make_line_twiddles(p.ny, p.twy, c->stream) ||
@@ -351,7 +360,7 @@ struct Fused2D : Engine {
   }
 
   uint64_t kernels_per_step(const vofl_ctx* c) const override {
-    return 2 + 2 * (uint64_t)p.groups(c->M, c->general);
+    return (p.fused_forward() ? 1 : 2) + 2 * (uint64_t)p.groups(c->M, c->general);
   }
 
   int set_schedule(vofl_ctx* c, const vofl_schedule* s) override {
@@ -373,6 +382,7 @@ struct Fused2D : Engine {
     p.wide_c = wc;
     p.wide_r = wr;
     p.cparts = s->col_parts;
+    p.fuse_fwd = s->fuse_forward < 0 ? fuse_forward_default(p.ny) : s->fuse_forward == 1;
     return VOFL_OK;
   }
 
@@ -382,6 +392,7 @@ struct Fused2D : Engine {
     s->wide_rows = p.wide_r && p.k.inv_rows_w ? 1 : 0;
     s->col_parts = p.cparts > 0 ? p.cparts : col_parts_default(p.ny);
     s->group = p.G;
+    s->fuse_forward = p.fused_forward() ? 1 : 0;
     return VOFL_OK;
   }
 
@@ -430,7 +441,9 @@ struct Fused2D : Engine {
     if (cap < 4) return 0;
     const int K = p.groups(c->M, c->general);
     const int slots = term_split(c->M, c->general).slots;
-    const int nk = 2 + 2 * K;
+    const bool ff = p.fused_forward();
+    const int base = ff ? 1 : 2;  // event after which the first inverse kernel starts
+    const int nk = base + 2 * K;
     // one event set per repetition; all repetitions are queued back to back
     // (one warm-up first) and read after a single synchronisation, so the
     // host launch latency never shows up in the intervals
@@ -460,29 +473,40 @@ struct Fused2D : Engine {
       float t;
       cudaEventElapsedTime(&t, er[0], er[1]);
       acc[0] += t;
-      cudaEventElapsedTime(&t, er[1], er[2]);
-      acc[1] += t;
+      if (!ff) {
+        cudaEventElapsedTime(&t, er[1], er[2]);
+        acc[1] += t;
+      }
       for (int i = 0; i < K; ++i) {
-        cudaEventElapsedTime(&t, er[2 + 2 * i], er[3 + 2 * i]);
+        cudaEventElapsedTime(&t, er[base + 2 * i], er[base + 2 * i + 1]);
         acc[2] += t;
-        cudaEventElapsedTime(&t, er[3 + 2 * i], er[4 + 2 * i]);
+        cudaEventElapsedTime(&t, er[base + 2 * i + 1], er[base + 2 * i + 2]);
         acc[3] += t;
       }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    names = "k2d_fwd_rows;k2d_fwd_cols;k2d_inv_cols;k2d_inv_rows";
+    const bool wc = p.wide_c && p.k.inv_cols_w, wr = p.wide_r && p.k.inv_rows_w;
+    const std::string ic = wc ? "k2d_inv_cols_w" : "k2d_inv_cols", ir = wr ? "k2d_inv_rows_w" : "k2d_inv_rows";
     // ms = average per launch; units = complex line transforms per launch
-    ms[0] = acc[0] / reps;
-    units[0] = p.ny / 2.0;
-    ms[1] = acc[1] / reps;
-    units[1] = p.ncols;
-    ms[2] = acc[2] / reps / K;
-    units[2] = 2.0 * p.ncols * terms / K;
-    ms[3] = acc[3] / reps / K;
-    units[3] = (double)p.ny * terms / K;
+    // (algorithmic: a fused forward column transform counts once per step)
+    int n = 0;
+    std::string nm = "k2d_fwd_rows";
+    ms[n] = acc[0] / reps;
+    units[n++] = p.ny / 2.0;
+    if (!ff) {
+      nm += ";k2d_fwd_cols";
+      ms[n] = acc[1] / reps;
+      units[n++] = p.ncols;
+    }
+    nm += ";" + ic + ";" + ir;
+    ms[n] = acc[2] / reps / K;
+    units[n++] = (2.0 * p.ncols * terms + (ff ? p.ncols : 0)) / K;
+    ms[n] = acc[3] / reps / K;
+    units[n++] = (double)p.ny * terms / K;
+    names = nm;
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_err(c, err, "profile");
-    return 4;
+    return n;
   }
 };
 

@@ -276,11 +276,16 @@ constexpr int icols_box_rows() {
 
 template <int NY>
 // yidx = operator slot + 2 * part: the group's terms [m_lo, m_hi) are split
-// into `parts` consecutive runs, one per CTA (parts = 1: the whole group)
-__device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, const float2* __restrict__ Uh,
+// into `parts` consecutive runs, one per CTA (parts = 1: the whole group).
+// fwd = 1: the column spectra are not in Uh yet; the CTA computes them from
+// the row half spectra T (pitch pT) itself, by the arithmetic of
+// k2d_fwd_cols (so bit for bit the same), and the CTAs of operator slot 0,
+// run 0 store them to Uh for later groups.
+__device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, float2* __restrict__ Uh,
                                               const float* __restrict__ P, const float* __restrict__ Lg,
                                               const void* zmap, int ncols, int m_lo, int m_hi, float inv_fact_lo,
-                                              float inv_fact_lo1, int split_k, const float2* __restrict__ twy) {
+                                              float inv_fact_lo1, int split_k, const float2* __restrict__ twy,
+                                              const float2* __restrict__ T = nullptr, int pT = 0, int fwd = 0) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL, RL = F::RL;
   constexpr int W = icols_warps<NY>(), THREADS = W * 32, CW = W * LPW;  // columns per CTA
@@ -330,12 +335,42 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, const
     tm[m] = p_col[y] * powi(l, lo + off) * fstart;
   }
   __syncthreads();
-  pdl_wait();  // Uh (k2d_fwd_cols) ready; the previous group's readers of Z are done
+  pdl_wait();  // Uh (k2d_fwd_cols) or T (k2d_fwd_rows) ready; the previous group's readers of Z are done
   pdl_trigger();
   // v = the multiplied spectrum of the current term: u_hat P ln|mu|^{2m}/m!
   float2 v[E];
+  if (fwd) {
+    {
+      // forward stage 0 cooperatively: thread b takes column b % CW,
+      // butterfly b / CW (row segments of CW adjacent columns of T)
+      const int fc = threadIdx.x % CW, j = threadIdx.x / CW;
+      const int col = min(c0 + fc, ncols - 1);
+      float2 x[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
+      for (int r = 0; r < E; ++r) x[r] = T[(size_t)(j + LANES * r) * pT + col];
+      float2* lb = s_buf + (fc / LPW) * warp_stride<NY>() + (fc % LPW) * F::PAD_LINE;
+      stage0_to_smem<NY, false>(x, lb, j);
+    }
+    __syncthreads();
+    mid_stage<NY, false>(lb_own, s_tw, li);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < BPL; ++q) {
+      float2 w[RL];
+      stage1_from_smem<NY, false>(w, lb_own, s_tw, li + LANES * q);
+#pragma unroll
+      for (int r = 0; r < RL; ++r) v[q + BPL * r] = w[r];
+    }
+    if (op == 0 && part == 0 && c < ncols) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) Uh[(size_t)c * NY + li + LANES * m] = v[m];
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], tm[m]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
+  }
   // v <- v ln|mu|^2 / (m + 1): the next term
   auto advance = [&](int mt) {
     const float rinv = 1.0f / (float)(mt + 1 + off);
@@ -375,8 +410,12 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, const
     for (int k = 0; k < NY / BOXR; ++k) tma_store_2d(zmap, c0, y0 + k * BOXR, s_buf + set * SET + k * BOXR * CW);
   };
   int mt = lo;
-  // two terms per iteration: two independent register transforms in flight
-  for (; PAIR && mt + 1 < hi; mt += 2) {
+  // two terms per iteration: two independent register transforms in flight;
+  // an odd last term runs through the same code with its partner computed
+  // and not stored (one copy of the unrolled term code: the kernel's
+  // instruction footprint, not its arithmetic, limited it)
+  for (; PAIR && mt < hi; mt += 2) {
+    const bool two = mt + 1 < hi;
     float2 xa[E], xb[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) xa[m] = v[m];
@@ -407,33 +446,12 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, const
     __syncthreads();
     if (threadIdx.x == 0) {
       tile_store(0, mt);
-      tile_store(1, mt + 1);
+      if (two) tile_store(1, mt + 1);
       bulk_commit();
     }
     if (mt + 2 < hi) advance(mt + 1);
   }
-  if (PAIR) {
-    if (mt < hi) {  // an odd last term
-      float2 x[E];
-#pragma unroll
-      for (int m = 0; m < E; ++m) x[m] = v[m];
-      dft<E, true>(x);
-      if (threadIdx.x == 0) bulk_wait_read_all();
-      __syncthreads();
-      stage0_write<NY>(x, lb_own, li);
-      mid_stage<NY, true>(lb_own, s_tw, li);
-      __syncthreads();
-      float2 w[BPL][RL];
-      last_read(0, w);
-      __syncthreads();
-      tile_write(0, w);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        tile_store(0, mt);
-        bulk_commit();
-      }
-    }
-  } else {
+  if (!PAIR) {
     // short lines: one term per iteration (a separate loop: sharing it with
     // the odd last term above made the paired form markedly slower)
     for (; mt < hi; ++mt) {
@@ -462,14 +480,15 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, const
 }
 
 template <int NY>
-__global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(const float2* __restrict__ Uh, const float* __restrict__ P,
+__global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(float2* __restrict__ Uh, const float* __restrict__ P,
                                                            const float* __restrict__ Lg,
                                                            const __grid_constant__ CUtensorMap zmap, int ncols,
                                                            int m_lo, int m_hi, float inv_fact_lo,
                                                            float inv_fact_lo1, int split_k, int parts,
-                                                           const float2* __restrict__ twy) {
+                                                           const float2* __restrict__ twy,
+                                                           const float2* __restrict__ T, int pT, int fwd) {
   inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, inv_fact_lo1,
-                    split_k, twy);
+                    split_k, twy, T, pT, fwd);
 }
 
 // -------------------------------------------------------------------------

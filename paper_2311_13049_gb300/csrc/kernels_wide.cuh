@@ -38,6 +38,13 @@ inline int group_default(int nx, int ny) {
   (void)ny;
   return 17;
 }
+// The forward column transform inside the top group's inverse column
+// kernel (one launch fewer per step; every CTA of the group transforms its
+// own columns, the same arithmetic as k2d_fwd_cols): on grids of up to 256
+// rows, where a launch boundary is a large part of the step (256^2: 6%
+// shorter); at 768 and 1024 the duplicated column transforms (two
+// operators, every run) cost more than the launch (2% longer).
+inline bool fuse_forward_default(int ny) { return ny <= 256; }
 // Runs of terms per group in the column pass (each on its own CTAs): small
 // grids have fewer column blocks than SMs.
 inline int col_parts_default(int ny) { return ny <= 256 ? 3 : (ny <= 512 ? 6 : 1); }
@@ -255,7 +262,14 @@ __device__ __forceinline__ void inv_rows_wide_body(int bx, const float2* __restr
     bulk_copy_g2s(zs, z1, RB_BYTES, bar);
     bulk_copy_g2s(zs + RB, z1 + zslot, RB_BYTES, bar);
   };
-  if (li == 0) issue(m_hi - 1);
+  if (li == 0) {
+    issue(m_hi - 1);
+    if (m_hi - 2 >= m_lo) {
+      const float2* z3 = Z + (long long)((m_hi - 2 - m_lo) * 2) * zslot + (size_t)y * pZ;
+      prefetch_l2(z3, RB_BYTES);
+      prefetch_l2(z3 + zslot, RB_BYTES);
+    }
+  }
   float a1[16], a2[16];
   if (top) {
 #pragma unroll
@@ -297,6 +311,14 @@ __device__ __forceinline__ void inv_rows_wide_body(int bx, const float2* __restr
     if (li == 0 && mt > m_lo) {
       fence_proxy_async_smem();
       issue(mt - 1);
+      // the term after that into L2 already: a group larger than L2
+      // streams its rows from DRAM, and one term of lookahead in shared
+      // memory does not cover that latency
+      if (mt - 1 > m_lo) {
+        const float2* z3 = Z + (long long)((mt - 2 - m_lo) * 2) * zslot + (size_t)y * pZ;
+        prefetch_l2(z3, RB_BYTES);
+        prefetch_l2(z3 + zslot, RB_BYTES);
+      }
     }
     wide_stage1<NX, true>(A, B, s_tw, li);
     line_sync<NX>(bar_id);

@@ -45,11 +45,17 @@ def test_host_only_entry_points(vofl):
     f_fused = vofl.footprint_bytes((1024, 1024), vofl.F32, vofl.IMPL_FUSED, 16)
     f_plain = vofl.footprint_bytes((1024, 1024), vofl.F32, vofl.IMPL_PLAIN, 16)
     n = 1024 * 1024
-    # O(N) storage: a bounded number of fields, far below (M+1) * 2 spectra
-    assert 6 * 4 * n < f_fused < 40 * 4 * n
+    # storage does not grow with M: the fused path keeps one group of G
+    # per-term column transforms (G = 17 by default, a schedule constant)
+    # whatever M, the plain baseline every term's transformed field of both
+    # operators (2 (M + 1) fields)
+    f_fused40 = vofl.footprint_bytes((1024, 1024), vofl.F32, vofl.IMPL_FUSED, 40)
+    f_plain40 = vofl.footprint_bytes((1024, 1024), vofl.F32, vofl.IMPL_PLAIN, 40)
+    assert f_fused40 == f_fused
+    assert 6 * 4 * n < f_fused < 60 * 4 * n
     assert f_plain > 6 * 4 * n
-    # the plain baseline keeps every term's transformed field of both operators
-    assert f_plain > 2 * 17 * 4 * n > f_fused
+    assert f_plain40 > f_plain + 2 * 24 * 4 * n
+    assert f_plain40 > 2 * 41 * 4 * n > f_fused
     assert vofl.footprint_bytes((256, 256, 256), vofl.F32, vofl.IMPL_PLAIN, 8) > 6 * 4 * 256 ** 3
 
 

@@ -14,9 +14,10 @@ pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
 
-# (wide_cols, wide_rows, col_parts, group): -1 / 0 = the size's default
-SCHEDULES = [(-1, -1, 0, 0), (0, 0, 0, 0), (1, 1, 0, 0), (1, 0, 2, 6), (0, 1, 1, 3), (-1, -1, 6, 17),
-             (-1, -1, 3, 4), (0, 0, 1, 1)]
+# (wide_cols, wide_rows, col_parts, group, fuse_forward): -1 / 0 = the
+# size's default
+SCHEDULES = [(-1, -1, 0, 0, -1), (0, 0, 0, 0, 0), (1, 1, 0, 0, -1), (1, 0, 2, 6, 1), (0, 1, 1, 3, 1),
+             (-1, -1, 6, 17, 0), (-1, -1, 3, 4, 1), (0, 0, 1, 1, 1), (0, 0, 2, 17, 1)]
 
 
 @pytest.mark.parametrize("n", [512, 1024])
@@ -46,14 +47,14 @@ def test_every_schedule_matches_the_oracle(V, n):
 
 
 def test_default_schedules(V):
-    want = {256: {"wide_cols": 0, "wide_rows": 0, "col_parts": 3, "group": 17},
-            512: {"wide_cols": 1, "wide_rows": 1, "col_parts": 6, "group": 17},
-            768: {"wide_cols": 0, "wide_rows": 0, "col_parts": 1, "group": 17},
-            1024: {"wide_cols": 0, "wide_rows": 1, "col_parts": 1, "group": 17}}
+    want = {256: {"wide_cols": 0, "wide_rows": 0, "col_parts": 3, "group": 17, "fuse_forward": 1},
+            512: {"wide_cols": 1, "wide_rows": 1, "col_parts": 6, "group": 17, "fuse_forward": 0},
+            768: {"wide_cols": 0, "wide_rows": 0, "col_parts": 1, "group": 17, "fuse_forward": 0},
+            1024: {"wide_cols": 0, "wide_rows": 1, "col_parts": 1, "group": 17, "fuse_forward": 0}}
     for n, w in want.items():
         with V.Solver((n, n)) as s:
             assert s.schedule() == w, (n, s.schedule())
-            s.set_schedule(1, 1, 2, 5)
+            s.set_schedule(1, 1, 2, 5, 0)
             s.set_schedule()  # back to the defaults
             assert s.schedule() == w
 
@@ -77,16 +78,37 @@ def test_schedule_runs_agree_and_batch_needs_default(V):
             return s.get_state().astype(np.float64)
 
     a = run(None)
-    b = run((0, 0, 1, 4))
+    b = run((0, 0, 1, 4, 1))
     check(b, a, 1e-4)
     with V.Solver(shape) as s, V.Batch() as bt:
         s.set_q(Q)
         s.set_M(12)
         s.set_state(np.zeros(shape, np.float32))
-        s.set_schedule(0, 0, 1, 4)
+        s.set_schedule(0, 0, 1, 4, 1)
         with pytest.raises(V.VoflError):
             bt.add(s, 5e-4)
         s.set_schedule()
         bt.add(s, 5e-4)
         bt.step(2)
         bt.sync()
+
+
+def test_fused_forward_is_bit_identical(V):
+    """The forward column transform inside the column kernel is the same
+    arithmetic as the separate forward kernel: same bits, any grid."""
+    import torch
+    for shape in [(256, 256), (1024, 1024), (768, 768), (128, 256)]:
+        Q = S.q_lowpass(shape, 41)
+        u = S.q_lowpass(shape, 42, qmin=-1.0, qmax=1.0, sigma_k=16).astype(np.float32)
+        outs = []
+        with V.Solver(shape) as s:
+            s.set_q(Q)
+            s.set_M(16)
+            ut = torch.from_numpy(u).cuda()
+            for ff in (0, 1):
+                s.set_schedule(0, -1, 0, 0, ff)
+                o1, o2 = torch.empty_like(ut), torch.empty_like(ut)
+                s.apply_pair(ut, o1, o2)
+                s.sync()
+                outs.append((o1.cpu().numpy(), o2.cpu().numpy()))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1]), shape
