@@ -284,6 +284,20 @@ VOFL_API int vofl_profile_kernels(vofl_ctx* ctx, int reps, char* names_out,
                          size_t names_cap, double* ms_out,
                          double* units_out, int cap);
 
+/* Accuracy diagnostics (the relative L2 measure in which every result of
+ * this library is stated): with x, y two fields of the context's grid
+ * (N = prod(n) elements each, device pointers on the context's device,
+ * element type float for VOFL_F32, double for VOFL_F64, chosen per
+ * argument), on the GPU with FP64 accumulation and a fixed reduction order:
+ *   out[0] = ||x - y||_2 / ||y||_2,   out[1] = max|x - y| / max|y|,
+ *   out[2] = ||y||_2,                 out[3] = max|y|
+ * (a ratio is 0 when x = y = 0 and +inf when only y is zero).  Runs on the
+ * context stream after its queued work and waits for the result.  Uses the
+ * context's reduction scratch; needs no model or state.  Returns VOFL_OK,
+ * VOFL_EINVAL or VOFL_ECUDA. */
+VOFL_API int vofl_rel_l2(vofl_ctx* ctx, const void* x_dev, int x_prec, const void* y_dev, int y_prec,
+                         double* out);
+
 /* Transform schedule of the fused 2D path.  The paper has no counterpart:
  * it fixes how the same arithmetic of Eq. (2.13) is laid out on the GPU,
  * not what is computed.  Results of different schedules agree within the
@@ -332,6 +346,17 @@ VOFL_API const char* vofl_version(void);
  * ~1 ms budget; *gave_up is set to 1 when the wait gave up as designed.  It
  * faults and hangs nothing; the device stays usable.  Synchronous. */
 VOFL_API int vofl_selftest_bounded_wait(int* gave_up);
+
+/* Test hook for the out-of-memory paths (no counterpart in the paper).
+ * With k > 0, the k-th device allocation the library makes from now on
+ * (counting every context, batch and solver allocation of the process)
+ * fails as if the device were out of memory, once; k = 0 cancels a pending
+ * failure.  Each entry point that allocates then frees what it allocated
+ * in that call and returns VOFL_ENOMEM, leaving the context (or batch) as
+ * it was.  Process-wide; not for use while other threads allocate.
+ * Returns the number of allocations that were still pending before the
+ * call (0 when none). */
+VOFL_API int64_t vofl_debug_fail_alloc(int64_t k);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent 2D simulations advanced together.

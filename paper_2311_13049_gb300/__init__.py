@@ -70,6 +70,8 @@ SIGNATURES = {
     "vofl_profile_kernels": (C.c_int, [_vp, C.c_int, C.c_char_p, C.c_size_t, _dp, _dp, C.c_int]),
     "vofl_version": (C.c_char_p, []),
     "vofl_set_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
+    "vofl_rel_l2": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _dp]),
+    "vofl_debug_fail_alloc": (C.c_int64, [C.c_int64]),
     "vofl_get_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
     "vofl_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int)]),
     "vofl_apply_pair_2d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp, _vp,
@@ -320,6 +322,21 @@ class Solver:
         sc = Schedule()
         self._check(lib().vofl_get_schedule(self._h, C.byref(sc)))
         return sc.as_dict()
+
+    def rel_l2(self, x, y):
+        """(||x - y|| / ||y||, max|x - y| / max|y|, ||y||, max|y|) of two device
+        tensors of this grid (float32 or float64 each), on the GPU in FP64."""
+        import torch
+        prec = {torch.float32: F32, torch.float64: F64}
+        for t in (x, y):
+            if not (_is_torch(t) and t.is_cuda and t.dtype in prec and t.is_contiguous()):
+                raise TypeError("rel_l2 takes contiguous float32/float64 CUDA tensors")
+            if t.numel() != int(np.prod(self.shape)):
+                raise ValueError(f"rel_l2: {t.numel()} elements, grid has {int(np.prod(self.shape))}")
+        out = (C.c_double * 4)()
+        self._check(lib().vofl_rel_l2(self._h, C.c_void_p(x.data_ptr()), prec[x.dtype],
+                                      C.c_void_p(y.data_ptr()), prec[y.dtype], out))
+        return tuple(out)
 
     def profile_kernels(self, reps=20):
         names = C.create_string_buffer(1024)

@@ -261,7 +261,8 @@ int berr(vofl_batch* b, int code, const std::string& m) {
   return code;
 }
 int bcuda(vofl_batch* b, cudaError_t e, const char* where) {
-  return berr(b, VOFL_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return berr(b, e == cudaErrorMemoryAllocation ? VOFL_ENOMEM : VOFL_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
 }
 
 void drop_bgraphs(vofl_batch* b) {
@@ -293,7 +294,7 @@ int plan(vofl_batch* b) {
     b->d_desc = nullptr;
     b->cap = 0;
     const int cap = std::max(16, n + n / 2);
-    cudaError_t e = cudaMalloc(&b->d_desc, sizeof(BatchSim) * 2 * cap);
+    cudaError_t e = dev_malloc(&b->d_desc, sizeof(BatchSim) * 2 * cap);
     if (e != cudaSuccess) return bcuda(b, e, "cudaMalloc (batch descriptors)");
     b->cap = cap;
   }
@@ -528,7 +529,7 @@ struct Snapshot {
       for (int j = 0; j < 4; ++j) {
         const size_t nb = j < 3 ? bytes : sizeof(int);
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, nb);
+        cudaError_t e = dev_malloc(&p, nb);
         if (e == cudaSuccess) e = cudaMemcpyAsync(p, src[j], nb, cudaMemcpyDeviceToDevice, b->stream);
         buf.push_back(p);
         if (e != cudaSuccess) {

@@ -246,15 +246,15 @@ int vofl_create(vofl_ctx** out, int ndim, const int64_t* n, const double* lo, co
   }
   const size_t r = elem_size(c);
   bool ok = true;
-  ok &= cudaMalloc(&c->delta, r * N) == cudaSuccess;
-  ok &= cudaMalloc(&c->A, r * N) == cudaSuccess;
-  ok &= cudaMalloc(&c->B, r * N) == cudaSuccess;
-  ok &= cudaMalloc(&c->u[0], r * N) == cudaSuccess;
-  ok &= cudaMalloc(&c->u[1], r * N) == cudaSuccess;
-  ok &= cudaMalloc(&c->l2p, r * N) == cudaSuccess;
-  ok &= cudaMalloc(&c->d_gamma, sizeof(double) * N) == cudaSuccess;
-  ok &= cudaMalloc(&c->d_scratch, sizeof(double) * 1024) == cudaSuccess;
-  ok &= cudaMalloc(&c->d_step, sizeof(int) * 4) == cudaSuccess;
+  ok &= dev_malloc(&c->delta, r * N) == cudaSuccess;
+  ok &= dev_malloc(&c->A, r * N) == cudaSuccess;
+  ok &= dev_malloc(&c->B, r * N) == cudaSuccess;
+  ok &= dev_malloc(&c->u[0], r * N) == cudaSuccess;
+  ok &= dev_malloc(&c->u[1], r * N) == cudaSuccess;
+  ok &= dev_malloc(&c->l2p, r * N) == cudaSuccess;
+  ok &= dev_malloc(&c->d_gamma, sizeof(double) * N) == cudaSuccess;
+  ok &= dev_malloc(&c->d_scratch, sizeof(double) * 1024) == cudaSuccess;
+  ok &= dev_malloc(&c->d_step, sizeof(int) * 4) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     vofl_destroy(c);
@@ -355,7 +355,7 @@ int vofl_set_gamma(vofl_ctx* c, const double* gamma, const double* c0_field, int
   if (st) return st;
   double* d_c0 = nullptr;
   if (c0_field) {
-    VOFL_CUDA(c, cudaMalloc(&d_c0, sizeof(double) * c->N));
+    VOFL_CUDA(c, dev_malloc(&d_c0, sizeof(double) * c->N));
     st = upload(c, d_c0, c0_field, sizeof(double) * c->N, on_device);
     if (st) {
       cudaFree(d_c0);
@@ -437,11 +437,16 @@ int vofl_set_source(vofl_ctx* c, const int64_t* idx, const double* samples, int6
     stride *= c->n[i];
   }
   if (nsamples > c->src_cap) {
+    // a new buffer first: a failed allocation leaves the old source in place
+    double* d_new = nullptr;
+    VOFL_CUDA(c, dev_malloc(&d_new, sizeof(double) * nsamples));
     drop_graphs(c);  // graphs hold the old pointer
-    VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {  // queued steps may still read the old samples
+      cudaFree(d_new);
+      return cuda_err(c, cudaGetLastError(), "cudaStreamSynchronize");
+    }
     cudaFree(c->d_src);
-    c->d_src = nullptr;
-    VOFL_CUDA(c, cudaMalloc(&c->d_src, sizeof(double) * nsamples));
+    c->d_src = d_new;
     c->src_cap = nsamples;
   }
   int st = upload(c, c->d_src, samples, sizeof(double) * nsamples, on_device);
@@ -629,6 +634,16 @@ int vofl_load_state(vofl_ctx* c, const void* blob, size_t nbytes) {
       !std::isfinite(h.f1) || !std::isfinite(h.f3))
     return set_err(c, VOFL_EINVAL, "checkpoint: non-finite model constant");
   VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  // the one allocation first, into a new buffer: if it fails the context
+  // is left exactly as it was
+  if (h.nsrc > c->src_cap) {
+    double* d_new = nullptr;
+    VOFL_CUDA(c, dev_malloc(&d_new, sizeof(double) * h.nsrc));
+    drop_graphs(c);  // they hold the old source pointer
+    cudaFree(c->d_src);
+    c->d_src = d_new;
+    c->src_cap = h.nsrc;
+  }
   const unsigned char* p = static_cast<const unsigned char*>(blob) + sizeof(h);
   const size_t b = elem_size(c) * (size_t)c->N;
   for (void* dst : {c->u[0], c->u[1], c->l2p, c->delta, c->A, c->B}) {
@@ -637,13 +652,6 @@ int vofl_load_state(vofl_ctx* c, const void* blob, size_t nbytes) {
   }
   VOFL_CUDA(c, cudaMemcpy(c->d_gamma, p, sizeof(double) * c->N, cudaMemcpyHostToDevice));
   p += sizeof(double) * c->N;
-  if (h.nsrc > c->src_cap) {
-    cudaFree(c->d_src);
-    c->d_src = nullptr;
-    c->src_cap = 0;
-    VOFL_CUDA(c, cudaMalloc(&c->d_src, sizeof(double) * h.nsrc));
-    c->src_cap = h.nsrc;
-  }
   if (h.nsrc > 0) VOFL_CUDA(c, cudaMemcpy(c->d_src, p, sizeof(double) * h.nsrc, cudaMemcpyHostToDevice));
   VOFL_CUDA(c, cudaMemcpy(c->d_step, h.d_step, 2 * sizeof(int), cudaMemcpyHostToDevice));
   drop_graphs(c);  // they may hold the old source pointer
@@ -737,6 +745,17 @@ int vofl_sync(vofl_ctx* c) {
     return set_err(c, VOFL_ETIMEDOUT, "a device wait gave up (asynchronous copy never completed)");
   }
   return VOFL_OK;
+}
+
+int64_t vofl_debug_fail_alloc(int64_t k) { return (int64_t)debug_fail_alloc((long long)k); }
+
+int vofl_rel_l2(vofl_ctx* c, const void* x_dev, int x_prec, const void* y_dev, int y_prec, double* out) {
+  NvtxRange nvtx_range("vofl_rel_l2");
+  if (int st = check_ctx(c)) return st;
+  if (!x_dev || !y_dev || !out) return set_err(c, VOFL_EINVAL, "null diagnostic argument");
+  if ((x_prec != VOFL_F32 && x_prec != VOFL_F64) || (y_prec != VOFL_F32 && y_prec != VOFL_F64))
+    return set_err(c, VOFL_EINVAL, "bad precision");
+  return model_rel_l2(c, x_dev, x_prec, y_dev, y_prec, out);
 }
 
 int vofl_set_schedule(vofl_ctx* c, const vofl_schedule* sched) {

@@ -526,9 +526,9 @@ struct Fused1D : Engine {
   int init(vofl_ctx* c) {
     N = (int)c->n[0];
     const size_t b = sizeof(R) * N;
-    bool ok = cudaMalloc(&P1, b) == cudaSuccess && cudaMalloc(&P2, b) == cudaSuccess &&
-              cudaMalloc(&Lg, b) == cudaSuccess && cudaMalloc(&tw, sizeof(C) * (N / 2)) == cudaSuccess &&
-              cudaMalloc(&d_sim, sizeof(Sim1D<R>)) == cudaSuccess;
+    bool ok = dev_malloc(&P1, b) == cudaSuccess && dev_malloc(&P2, b) == cudaSuccess &&
+              dev_malloc(&Lg, b) == cudaSuccess && dev_malloc(&tw, sizeof(C) * (N / 2)) == cudaSuccess &&
+              dev_malloc(&d_sim, sizeof(Sim1D<R>)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       return set_err(c, VOFL_ENOMEM, "cudaMalloc (fused 1D tables)");
@@ -571,7 +571,7 @@ struct Fused1D : Engine {
       T = nullptr;
       nbytes -= tab_bytes;
       tab_bytes = sizeof(R) * 2 * (size_t)(c->M + 1) * N;
-      const cudaError_t e = cudaMalloc(&T, tab_bytes);
+      const cudaError_t e = dev_malloc(&T, tab_bytes);
       if (e != cudaSuccess) {
         T = nullptr;
         tab_bytes = 0;

@@ -304,7 +304,7 @@ struct Fused2D : Engine {
   }
 
   int alloc(vofl_ctx* c, void** ptr, size_t b) {
-    cudaError_t e = cudaMalloc(ptr, b);
+    cudaError_t e = dev_malloc(ptr, b);
     if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (fused 2D scratch)");
     nbytes += b;
     return VOFL_OK;
@@ -371,7 +371,7 @@ struct Fused2D : Engine {
       const size_t b_old = sizeof(float2) * (size_t)p.zslot * 2 * p.G;
       const size_t b_new = sizeof(float2) * (size_t)p.zslot * 2 * G;
       float2* z = nullptr;
-      cudaError_t e = cudaMalloc((void**)&z, b_new);
+      cudaError_t e = dev_malloc((void**)&z, b_new);
       if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (Taylor group buffer)");
       cudaFree(p.Z);
       p.Z = z;

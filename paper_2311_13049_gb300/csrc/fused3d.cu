@@ -151,7 +151,7 @@ struct Fused3D : Engine {
   size_t bytes() const override { return nbytes; }
 
   int alloc(vofl_ctx* c, void** ptr, size_t b) {
-    cudaError_t e = cudaMalloc(ptr, b);
+    cudaError_t e = dev_malloc(ptr, b);
     if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (fused 3D scratch)");
     nbytes += b;
     return VOFL_OK;

@@ -24,6 +24,17 @@ struct NvtxRange {
 };
 
 extern std::atomic<uint64_t> g_kernel_launches;
+
+// Every device allocation of the library goes through dev_malloc, so that
+// a test can make the k-th one fail as if the device were out of memory
+// (vofl_debug_fail_alloc) and check that each caller frees what it holds
+// and reports VOFL_ENOMEM.
+cudaError_t dev_malloc_bytes(void** p, size_t bytes);
+long long debug_fail_alloc(long long k);  // set the countdown, return the old one
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
 inline void count_launch(uint64_t n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct Engine;
@@ -274,6 +285,8 @@ void epi_model(const vofl_ctx* c, EpiArgs<T>* e) {
   e->f3 = T(c->f3);
 }
 int model_suggest_dt(vofl_ctx* c, double courant, double* dt);
+// rel-L2 / pointwise diagnostics of two fields of the context's grid (model.cu)
+int model_rel_l2(vofl_ctx* c, const void* x, int x_prec, const void* y, int y_prec, double* out);
 int model_suggest_M(vofl_ctx* c, double tol, int M_max, int* M);
 
 // twiddles / tables (model.cu)

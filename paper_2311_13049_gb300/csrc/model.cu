@@ -82,6 +82,65 @@ __global__ void k_sum_pass2(const double* __restrict__ part, double* __restrict_
   if (threadIdx.x == 0) out[0] = s[0];
 }
 
+// rel-L2 diagnostics: per block, in double, over a grid-stride slice:
+// sum (x - y)^2, sum y^2, max |x - y|, max |y|; then one block combines the
+// partials in a fixed order (deterministic for a given launch shape).
+constexpr int DIAG_BLOCKS = 240;  // 4 partials each: 960 doubles of the context scratch
+template <typename TX, typename TY>
+__global__ void k_diff_pass1(const TX* __restrict__ x, const TY* __restrict__ y, long long n,
+                             double* __restrict__ part) {
+  __shared__ double s[4][RED_THREADS];
+  double d2 = 0.0, y2 = 0.0, dm = 0.0, ym = 0.0;
+  for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < n;
+       i += (long long)DIAG_BLOCKS * RED_THREADS) {
+    const double yi = (double)y[i];
+    const double di = (double)x[i] - yi;
+    d2 = fma(di, di, d2);
+    y2 = fma(yi, yi, y2);
+    dm = fmax(dm, fabs(di));
+    ym = fmax(ym, fabs(yi));
+  }
+  s[0][threadIdx.x] = d2;
+  s[1][threadIdx.x] = y2;
+  s[2][threadIdx.x] = dm;
+  s[3][threadIdx.x] = ym;
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + w];
+      s[1][threadIdx.x] += s[1][threadIdx.x + w];
+      s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + w]);
+      s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) part[threadIdx.x * DIAG_BLOCKS + blockIdx.x] = s[threadIdx.x][0];
+}
+
+// out: ||x - y|| / ||y||, max|x - y| / max|y|, ||y||, max|y| (ratios 0 when
+// y is all zero and x equals it, +inf when only y is zero)
+__global__ void k_diff_pass2(const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double s[4][256];
+  for (int k = 0; k < 4; ++k) s[k][threadIdx.x] = threadIdx.x < DIAG_BLOCKS ? part[k * DIAG_BLOCKS + threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + w];
+      s[1][threadIdx.x] += s[1][threadIdx.x + w];
+      s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + w]);
+      s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double dn = sqrt(s[0][0]), yn = sqrt(s[1][0]);
+    out[0] = yn > 0 ? dn / yn : (dn > 0 ? INFINITY : 0.0);
+    out[1] = s[3][0] > 0 ? s[2][0] / s[3][0] : (s[2][0] > 0 ? INFINITY : 0.0);
+    out[2] = yn;
+    out[3] = s[3][0];
+  }
+}
+
 template <typename T>
 __global__ void k_coeffs(const double* __restrict__ g, const double* __restrict__ c0f, double c0s, double w0,
                          double g0, long long n, T* __restrict__ delta, T* __restrict__ A, T* __restrict__ B) {
@@ -243,6 +302,26 @@ inline int grid_for(long long n, int threads) {
 
 std::atomic<uint64_t> g_kernel_launches{0};
 
+// > 0: device allocations left until the injected failure (the last one
+// fails); 0: none pending
+std::atomic<long long> g_fail_alloc{0};
+
+long long debug_fail_alloc(long long k) { return g_fail_alloc.exchange(k < 0 ? 0 : k); }
+
+cudaError_t dev_malloc_bytes(void** p, size_t bytes) {
+  long long k = g_fail_alloc.load();
+  while (k > 0) {
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+      if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 int cuda_err(vofl_ctx* c, cudaError_t e, const char* where) {
   if (c) {
     c->err = std::string(where) + ": " + cudaGetErrorString(e);
@@ -401,6 +480,27 @@ int make_line_twiddles(int N, float2* d_tw, cudaStream_t s) {
   k_twiddles<<<grid_for((long long)nb * r + nm, 256), 256, 0, s>>>(N, nb, r, nm, d_tw);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
+}
+
+int model_rel_l2(vofl_ctx* c, const void* x, int x_prec, const void* y, int y_prec, double* out) {
+  static_assert(4 * DIAG_BLOCKS + 4 <= 1024, "diagnostics fit the context scratch");
+  double* part = c->d_scratch;
+  double* d_out = c->d_scratch + 4 * DIAG_BLOCKS;
+  const long long n = c->N;
+  if (x_prec == VOFL_F32 && y_prec == VOFL_F32)
+    k_diff_pass1<float, float><<<DIAG_BLOCKS, RED_THREADS, 0, c->stream>>>((const float*)x, (const float*)y, n, part);
+  else if (x_prec == VOFL_F32)
+    k_diff_pass1<float, double><<<DIAG_BLOCKS, RED_THREADS, 0, c->stream>>>((const float*)x, (const double*)y, n, part);
+  else if (y_prec == VOFL_F32)
+    k_diff_pass1<double, float><<<DIAG_BLOCKS, RED_THREADS, 0, c->stream>>>((const double*)x, (const float*)y, n, part);
+  else
+    k_diff_pass1<double, double><<<DIAG_BLOCKS, RED_THREADS, 0, c->stream>>>((const double*)x, (const double*)y, n, part);
+  k_diff_pass2<<<1, 256, 0, c->stream>>>(part, d_out);
+  count_launch(2);
+  VOFL_CUDA(c, cudaGetLastError());
+  VOFL_CUDA(c, cudaMemcpyAsync(out, d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  VOFL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VOFL_OK;
 }
 
 int make_wide_twiddles(int N, float2* d_tw, cudaStream_t s) {

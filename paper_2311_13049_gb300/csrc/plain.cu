@@ -564,7 +564,7 @@ struct Plain : Engine {
   size_t bytes() const override { return nbytes; }
 
   int alloc(vofl_ctx* c, void** p, size_t b) {
-    cudaError_t e = cudaMalloc(p, b);
+    cudaError_t e = dev_malloc(p, b);
     if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (plain scratch)");
     nbytes += b;
     return VOFL_OK;
@@ -649,9 +649,12 @@ struct Plain : Engine {
     cufftSetStream(tb.fwd1, c->stream);
     cufftSetStream(tb.inv1, c->stream);
     cufftSetStream(tb.inv2, c->stream);
-    cudaError_t e = cudaMalloc(&tb.X, sizeof(C) * Nh * 2 * B);
-    if (e == cudaSuccess) e = cudaMalloc(&tb.Y, sizeof(T) * N * 2 * B);
-    if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (plain term batch)");
+    cudaError_t e = dev_malloc(&tb.X, sizeof(C) * Nh * 2 * B);
+    if (e == cudaSuccess) e = dev_malloc(&tb.Y, sizeof(T) * N * 2 * B);
+    if (e != cudaSuccess) {
+      tb_free();  // plans and whatever was allocated; the next call starts afresh
+      return cuda_err(c, e, "cudaMalloc (plain term batch)");
+    }
     tb.bytes = (sizeof(C) * Nh + sizeof(T) * N) * 2 * B;
     nbytes += tb.bytes;
     tb.M = c->M;
@@ -752,20 +755,28 @@ struct Plain : Engine {
     }
     if (cn.b) return VOFL_OK;
     auto get = [&](void** q, size_t b) -> int {
-      cudaError_t e = cudaMalloc(q, b);
+      cudaError_t e = dev_malloc(q, b);
       if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (Crank-Nicolson scratch)");
       cn.bytes += b;
       return VOFL_OK;
     };
+    // all or nothing: a failure frees what this call allocated, so that
+    // the next call does not find a half-allocated solver (cn.b set)
+    auto fail = [&](int st) {
+      nbytes += cn.bytes;  // cn_free takes off what was counted
+      cn_free();
+      return st;
+    };
     int st;
     for (T** v : {&cn.b, &cn.x, &cn.r, &cn.z, &cn.p, &cn.w})
-      if ((st = get((void**)v, sizeof(T) * N))) return st;
-    if ((st = get((void**)&cn.pa, sizeof(double) * CN_MAXG))) return st;
-    if ((st = get((void**)&cn.pb, sizeof(double) * CN_MAXG))) return st;
-    if ((st = get((void**)&cn.s, sizeof(double) * S_COUNT))) return st;
+      if ((st = get((void**)v, sizeof(T) * N))) return fail(st);
+    if ((st = get((void**)&cn.pa, sizeof(double) * CN_MAXG))) return fail(st);
+    if ((st = get((void**)&cn.pb, sizeof(double) * CN_MAXG))) return fail(st);
+    if ((st = get((void**)&cn.s, sizeof(double) * S_COUNT))) return fail(st);
     if (cudaMallocHost(&cn.hs, sizeof(double) * S_COUNT) != cudaSuccess) {
       cudaGetLastError();
-      return set_err(c, VOFL_ENOMEM, "cudaMallocHost (solver scalars)");
+      cn.hs = nullptr;
+      return fail(set_err(c, VOFL_ENOMEM, "cudaMallocHost (solver scalars)"));
     }
     VOFL_CUDA(c, cudaMemsetAsync(cn.s, 0, sizeof(double) * S_COUNT, c->stream));
     nbytes += cn.bytes;

@@ -29,7 +29,7 @@ extern "C" int vofl_selftest_bounded_wait(int* gave_up) {
   if (!gave_up) return VOFL_EINVAL;
   *gave_up = 0;
   int* d_err = nullptr;
-  if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) {
+  if (dev_malloc(&d_err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return VOFL_ENOMEM;
   }

@@ -248,3 +248,27 @@ def test_headline_size_nyquist_column_and_top_taylor_group(V):
     t = O.matrix_free_operator(uin.astype(np.float64), order, 11)
     assert rel_l2(t, r) > 100 * TOL32, rel_l2(t, r)
     check(g, r, TOL32)
+
+
+@pytest.mark.parametrize("xp,yp", [("f32", "f32"), ("f32", "f64"), ("f64", "f32"), ("f64", "f64")])
+def test_rel_l2_diagnostic_matches_numpy(V, xp, yp):
+    """vofl_rel_l2 (FP64 accumulation on the GPU, fixed reduction order)
+    against NumPy in FP64 on the same values: the sums to round-off, the
+    maxima exactly; repeated calls give the same bits."""
+    import torch
+    shape = (128, 256)
+    rng = np.random.default_rng(7)
+    dt = {"f32": torch.float32, "f64": torch.float64}
+    y = torch.tensor(rng.standard_normal(shape) * 3.0, dtype=dt[yp]).cuda()
+    x = (y.double() + torch.tensor(rng.standard_normal(shape) * 1e-3).cuda()).to(dt[xp])
+    with V.Solver(shape) as s:
+        got = s.rel_l2(x, y)
+        again = s.rel_l2(x, y)
+        zero = s.rel_l2(y, y)
+    xn, yn = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+    want = (np.linalg.norm(xn - yn) / np.linalg.norm(yn), np.max(np.abs(xn - yn)) / np.max(np.abs(yn)),
+            np.linalg.norm(yn), np.max(np.abs(yn)))
+    assert abs(got[0] - want[0]) <= 1e-13 * want[0] and abs(got[2] - want[2]) <= 1e-13 * want[2]
+    assert got[1] == want[1] and got[3] == want[3]
+    assert got == again
+    assert zero[0] == 0.0 and zero[1] == 0.0
