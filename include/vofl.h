@@ -321,6 +321,10 @@ VOFL_API int vofl_rel_l2(vofl_ctx* ctx, const void* x_dev, int x_prec, const voi
  *     arithmetic, so the same bits), 0 = a separate forward column kernel,
  *     -1 = the default (fused on grids of up to 256 rows); reported 0
  *     when the column pass is wide.
+ *   wide_fwd: 1 = the forward row pass transforms its 512- or 1024-point
+ *     lines with the wide line transform (as wide_rows), 0 = 32 elements
+ *     per lane, -1 = the default (wide at 1024); reported 0 for other line
+ *     lengths.
  * vofl_get_schedule reports the schedule in use, defaults resolved.
  * Only fused 2D contexts have one (VOFL_EUNSUPPORTED elsewhere).  A context
  * whose schedule differs from its size's default cannot join a batch
@@ -331,6 +335,7 @@ typedef struct {
   int col_parts;
   int group;
   int fuse_forward;
+  int wide_fwd;
 } vofl_schedule;
 VOFL_API int vofl_set_schedule(vofl_ctx* ctx, const vofl_schedule* sched);
 VOFL_API int vofl_get_schedule(vofl_ctx* ctx, vofl_schedule* sched);

@@ -67,6 +67,13 @@ __global__ void __launch_bounds__(W_FROWS * 32) kb_fwd_rows(const BatchSim* __re
 }
 
 template <int NX, int NY>
+__global__ void __launch_bounds__(wide_frows_threads<NX>()) kb_fwd_rows_w(const BatchSim* __restrict__ sims) {
+  const BatchSim* s = sims + blockIdx.z;
+  fwd_rows_wide_body<NX>(blockIdx.x, s->epi.u_cur, s->T, NY, s->pT, s->ryy, s->twxw, const_cast<int*>(s->epi.step),
+                         s->inc_step, s->err);
+}
+
+template <int NX, int NY>
 __global__ void __launch_bounds__(W_FCOLS * 32) kb_fwd_cols(const BatchSim* __restrict__ sims) {
   const BatchSim* s = sims + blockIdx.z;
   fwd_cols_body<NY>(blockIdx.x, s->T, s->pT, s->Uh, NX / 2 + 1, s->twy);
@@ -130,6 +137,7 @@ struct BKernels {
   size_t smem_fr, smem_fc, smem_ic, smem_ir;
   int lpw_x, lpw_y;
   int wic;  // warps per CTA of kb_inv_cols
+  int rpf, thr_fr;  // row pairs per CTA and threads of the forward row kernel
   // inverse-kernel launch shapes: lines per CTA and threads per CTA
   int cpc, thr_ic, rpc, thr_ir;
 };
@@ -144,6 +152,16 @@ BKernels bkernels_for() {
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
   k.wic = icols_warps<NY>();
+  k.rpf = W_FROWS * k.lpw_x;
+  k.thr_fr = W_FROWS * 32;
+  if constexpr (NX == 512 || NX == 1024) {
+    if (wide_fwd_default(NX)) {
+      k.fr = kb_fwd_rows_w<NX, NY>;
+      k.smem_fr = wide_frows_smem<NX>();
+      k.rpf = wide_frows_lines<NX>();
+      k.thr_fr = wide_frows_threads<NX>();
+    }
+  }
   bool wc = false, wr = false;
   if constexpr (NY == 512 || NY == 1024) {
     if (wide_cols_default(NY)) {
@@ -385,10 +403,10 @@ cudaError_t enqueue_step(vofl_batch* b, int p) {
       const BatchSim* dc = d + cl.off + c0;
       int Mmax = 0;
       for (int j = 0; j < nz; ++j) Mmax = std::max(Mmax, b->mem[b->order[cl.off + c0 + j]].c->M);
-      const int rpc = W_FROWS * cl.k.lpw_x;
+      const int rpc = cl.k.rpf;
       const dim3 gfr((ny / 2 + rpc - 1) / rpc, 1, nz);
-      e = first ? launch_plain(cl.k.fr, gfr, dim3(W_FROWS * 32), cl.k.smem_fr, s, dc)
-                : launch_pdl(cl.k.fr, gfr, dim3(W_FROWS * 32), cl.k.smem_fr, s, dc);
+      e = first ? launch_plain(cl.k.fr, gfr, dim3(cl.k.thr_fr), cl.k.smem_fr, s, dc)
+                : launch_pdl(cl.k.fr, gfr, dim3(cl.k.thr_fr), cl.k.smem_fr, s, dc);
       if (e) return e;
       first = false;
       const int cpf = W_FCOLS * cl.k.lpw_y;

@@ -70,6 +70,9 @@ struct Kernels {
   // 512 and 1024 points (null elsewhere)
   InvColsW inv_cols_w = nullptr;
   InvRows inv_rows_w = nullptr, inv_rows_w_split = nullptr;
+  void (*fwd_rows_w)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*) = nullptr;
+  size_t smem_frows_w = 0;
+  int rpc_fw = 0, thr_fw = 0;  // row pairs per CTA / threads of the wide forward row kernel
   size_t smem_frows, smem_fcols, smem_icols, smem_irows, smem_icols_w = 0, smem_irows_w = 0;
   int lpw_x, lpw_y;
   int wic;  // warps per CTA of inv_cols
@@ -111,6 +114,10 @@ Kernels kernels_for() {
   if constexpr (NX == 512 || NX == 1024) {
     k.inv_rows_w = k2d_inv_rows_w<NX, false>;
     k.inv_rows_w_split = k2d_inv_rows_w<NX, true>;
+    k.fwd_rows_w = k2d_fwd_rows_w<NX>;
+    k.smem_frows_w = wide_frows_smem<NX>();
+    k.rpc_fw = wide_frows_lines<NX>();
+    k.thr_fw = wide_frows_threads<NX>();
     k.smem_irows_w = wide_rows_smem<NX>();
     k.rpc_w = wide_rows_per_cta<NX>();
     k.thr_w_r = wide_rows_threads<NX>();
@@ -146,7 +153,8 @@ int set_smem_attributes(const Kernels& k) {
       set_kernel_smem(k.inv_rows, k.smem_irows) || set_kernel_smem(k.inv_rows_split, k.smem_irows) ||
       (k.inv_cols_w && set_kernel_smem(k.inv_cols_w, k.smem_icols_w)) ||
       (k.inv_rows_w && (set_kernel_smem(k.inv_rows_w, k.smem_irows_w) ||
-                        set_kernel_smem(k.inv_rows_w_split, k.smem_irows_w)))) {
+                        set_kernel_smem(k.inv_rows_w_split, k.smem_irows_w))) ||
+      (k.fwd_rows_w && set_kernel_smem(k.fwd_rows_w, k.smem_frows_w))) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
@@ -173,7 +181,7 @@ struct Plan2D {
   // (where built), the column-pass term split (0: col_parts_default), and
   // the forward column transform done inside the top group's inverse
   // column kernel (32-element column kernel only)
-  bool wide_c = false, wide_r = false, fuse_fwd = false;
+  bool wide_c = false, wide_r = false, fuse_fwd = false, wide_f = false;
   int cparts = 0;
 
   bool fused_forward() const { return fuse_fwd && !(wide_c && k.inv_cols_w); }
@@ -187,9 +195,15 @@ struct Plan2D {
 
   // optional events: ev[1] after F1, ev[2] after F2 (ev[0] recorded by the caller)
   cudaError_t forward(cudaStream_t s, const float* u, bool inc_step, cudaEvent_t* ev = nullptr) const {
-    const int rpc = W_FROWS * k.lpw_x;  // row pairs per CTA
-    cudaError_t e = launch_pdl(k.fwd_rows, dim3((ny / 2 + rpc - 1) / rpc), dim3(W_FROWS * 32), k.smem_frows, s, u,
-                               T, ny, 1, pT, ryy, 0.0f, (const float2*)twx, step_ctr, inc_step ? 1 : 0, err);
+    cudaError_t e;
+    if (wide_f && k.fwd_rows_w) {
+      e = launch_pdl(k.fwd_rows_w, dim3((ny / 2 + k.rpc_fw - 1) / k.rpc_fw), dim3(k.thr_fw), k.smem_frows_w, s, u, T,
+                     ny, 1, pT, ryy, 0.0f, (const float2*)twxw, step_ctr, inc_step ? 1 : 0, err);
+    } else {
+      const int rpc = W_FROWS * k.lpw_x;  // row pairs per CTA
+      e = launch_pdl(k.fwd_rows, dim3((ny / 2 + rpc - 1) / rpc), dim3(W_FROWS * 32), k.smem_frows, s, u, T, ny, 1,
+                     pT, ryy, 0.0f, (const float2*)twx, step_ctr, inc_step ? 1 : 0, err);
+    }
     if (e) return e;
     if (ev) cudaEventRecord(ev[1], s);
     if (fused_forward()) return cudaSuccess;  // the top group's column kernel does F2
@@ -282,7 +296,8 @@ struct Fused2D : Engine {
     // inverse passes where built, the default column split): a context on
     // another schedule would not give the same bits in a batch
     if (p.wide_c != (p.k.inv_cols_w != nullptr && wide_cols_default(p.ny)) ||
-        p.wide_r != (p.k.inv_rows_w != nullptr && wide_rows_default(p.nx)) || p.cparts != 0)
+        p.wide_r != (p.k.inv_rows_w != nullptr && wide_rows_default(p.nx)) ||
+        p.wide_f != (p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx)) || p.cparts != 0)
       return false;
     d->T = p.T;
     d->Uh = p.Uh;
@@ -334,6 +349,7 @@ struct Fused2D : Engine {
     p.wide_c = p.k.inv_cols_w != nullptr && wide_cols_default(p.ny);
     p.wide_r = p.k.inv_rows_w != nullptr && wide_rows_default(p.nx);
     p.fuse_fwd = fuse_forward_default(p.ny);
+    p.wide_f = p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx);
     if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
     if (make_line_twiddles(p.nx, p.twx, c->stream) ||
         make_line_twiddles(p.ny, p.twy, c->stream) ||
@@ -383,6 +399,7 @@ struct Fused2D : Engine {
     p.wide_r = wr;
     p.cparts = s->col_parts;
     p.fuse_fwd = s->fuse_forward < 0 ? fuse_forward_default(p.ny) : s->fuse_forward == 1;
+    p.wide_f = p.k.fwd_rows_w && (s->wide_fwd < 0 ? wide_fwd_default(p.nx) : s->wide_fwd == 1);
     return VOFL_OK;
   }
 
@@ -393,6 +410,7 @@ struct Fused2D : Engine {
     s->col_parts = p.cparts > 0 ? p.cparts : col_parts_default(p.ny);
     s->group = p.G;
     s->fuse_forward = p.fused_forward() ? 1 : 0;
+    s->wide_fwd = p.wide_f && p.k.fwd_rows_w ? 1 : 0;
     return VOFL_OK;
   }
 
@@ -490,7 +508,7 @@ struct Fused2D : Engine {
     // ms = average per launch; units = complex line transforms per launch
     // (algorithmic: a fused forward column transform counts once per step)
     int n = 0;
-    std::string nm = "k2d_fwd_rows";
+    std::string nm = p.wide_f && p.k.fwd_rows_w ? "k2d_fwd_rows_w" : "k2d_fwd_rows";
     ms[n] = acc[0] / reps;
     units[n++] = p.ny / 2.0;
     if (!ff) {

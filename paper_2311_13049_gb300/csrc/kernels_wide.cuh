@@ -27,6 +27,8 @@ namespace {
 // inverse row pass at 512 and 1024 (measured per size; vofl_set_schedule
 // changes it per context).
 inline bool wide_cols_default(int ny) { return ny == 512; }
+// wide forward row pass at 1024 (1% shorter step; neutral at 512)
+inline bool wide_fwd_default(int nx) { return nx == 1024; }
 inline bool wide_rows_default(int nx) { return nx == 512 || nx == 1024; }
 // Taylor terms per group: 17, so that M <= 16 runs in one group (one column
 // and one row launch per step).  Every launch boundary costs a few
@@ -355,6 +357,116 @@ __device__ __forceinline__ void inv_rows_wide_body(int bx, const float2* __restr
     for (int m = 0; m < 16; ++m)
       epilogue_point<float>(epi, (long long)(row + li + LANES * m), a1[m], a2[m] * inv_lambda);
   }
+}
+
+// -------------------------------------------------------------------------
+// F1 (wide): forward FFT along x of a pair of rows (the complex line
+// w[y0] + i w[y0+1] of the discrete Laplacian w, as k2d_fwd_rows), split
+// into the two half spectra, on the wide line transform: two lines (row
+// pairs) per CTA.  The four rows each line's stencil reads come by TMA bulk
+// copies (bounded wait; the line's lanes decide together whether it gave
+// up).
+// -------------------------------------------------------------------------
+template <int NX>
+constexpr int wide_frows_lines() {
+  return 2;
+}
+template <int NX>
+constexpr int wide_frows_threads() {
+  return wide_frows_lines<NX>() * WideFFT<NX>::LANES;
+}
+template <int NX>
+constexpr size_t wide_frows_smem() {
+  // per line: buffers A, B, then four staged rows of NX floats
+  return (size_t)wide_frows_lines<NX>() * (2 * WideFFT<NX>::PAD_LINE * sizeof(float2) + 4 * NX * sizeof(float));
+}
+
+template <int NX>
+__device__ __forceinline__ void fwd_rows_wide_body(int bx, const float* __restrict__ u, float2* __restrict__ T,
+                                                   int ny, int pT, float ryy, const float2* __restrict__ twx,
+                                                   int* step_ctr, int inc_step, int* err) {
+  using F = WideFFT<NX>;
+  constexpr int LANES = F::LANES, L = wide_frows_lines<NX>(), THREADS = L * LANES, H = NX / 2;
+  constexpr uint32_t ROWB = NX * sizeof(float);
+  constexpr size_t LINE_BYTES = 2 * F::PAD_LINE * sizeof(float2) + 4 * NX * sizeof(float);
+  static_assert(LINE_BYTES % 16 == 0 && (2 * F::PAD_LINE * sizeof(float2)) % 16 == 0, "bulk-copy alignment");
+  __shared__ float2 s_tw[F::TW];
+  __shared__ uint64_t s_bar[L];
+  extern __shared__ __align__(128) unsigned char s_raw[];
+  const int line = threadIdx.x / LANES, li = threadIdx.x % LANES;
+  const int bar_id = 1 + line;
+  float2* A = reinterpret_cast<float2*>(s_raw + (size_t)line * LINE_BYTES);
+  float2* B = A + F::PAD_LINE;
+  float* srow = reinterpret_cast<float*>(B + F::PAD_LINE);  // rows y0-1, y0, y0+1, y0+2
+  uint64_t* bar = &s_bar[line];
+  if (li == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
+  __syncthreads();
+  pdl_wait();  // u is written by the previous step's last kernel
+  pdl_trigger();
+  if (inc_step && bx == 0 && threadIdx.x == 0) *step_ctr += 1;
+  const int pair = bx * L + line;
+  const bool active = pair < ny / 2;
+  const int yy = 2 * (active ? pair : 0);
+  if (li == 0) {
+    const float* r0 = u + (size_t)yy * NX;
+    mbar_arrive_expect_tx(bar, 4 * ROWB);
+    bulk_copy_g2s(srow + 0 * NX, u + (size_t)(yy == 0 ? ny - 1 : yy - 1) * NX, ROWB, bar);
+    bulk_copy_g2s(srow + 1 * NX, r0, ROWB, bar);
+    bulk_copy_g2s(srow + 2 * NX, r0 + NX, ROWB, bar);
+    bulk_copy_g2s(srow + 3 * NX, u + (size_t)(yy + 2 == ny ? 0 : yy + 2) * NX, ROWB, bar);
+  }
+  const bool got = mbar_wait_bounded(bar, 0, err);
+  if (line_sync_any<NX>(bar_id, !got)) {
+    if (li == 0 && !got) mbar_wait_bounded(bar, 0, err);  // drain (bounded), leave
+    return;
+  }
+  // w = D_xx u + (h_x/h_y)^2 D_yy u of rows y0 (real part) and y0+1 (imag)
+  const float* rm = srow;
+  const float* ra = srow + NX;
+  const float* rb = srow + 2 * NX;
+  const float* rp = srow + 3 * NX;
+  float2 v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int x = li + LANES * m;
+    const int xm = x == 0 ? NX - 1 : x - 1, xp = x + 1 == NX ? 0 : x + 1;
+    const float a = ra[x], b = rb[x];
+    const float dxa = (ra[xp] - a) - (a - ra[xm]);
+    const float dxb = (rb[xp] - b) - (b - rb[xm]);
+    const float dya = (b - a) - (a - rm[x]);
+    const float dyb = (rp[x] - b) - (b - a);
+    v[m] = make_float2(dxa + ryy * dya, dxb + ryy * dyb);
+  }
+  wide_fft<NX, false>(v, A, B, s_tw, li, bar_id);
+  // every lane's stage-1 reads of A are done (second barrier of the
+  // transform): A takes the spectrum for the split
+#pragma unroll
+  for (int m = 0; m < 16; ++m) A[F::pad(li + LANES * m)] = v[m];
+  line_sync<NX>(bar_id);
+  float2* t0 = T + (size_t)yy * pT;
+  float2* t1 = t0 + pT;
+  for (int k = li; k <= H; k += LANES) {
+    const float2 a = A[F::pad(k)];
+    const float2 b = A[F::pad(k == 0 ? 0 : NX - k)];
+    // A = (X_k + conj X_{-k})/2 (row y0), B = (X_k - conj X_{-k})/(2i) (row y0+1)
+    if (active) {
+      t0[k] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+      t1[k] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+    }
+  }
+}
+
+template <int NX>
+__global__ void __launch_bounds__(wide_frows_threads<NX>())
+    k2d_fwd_rows_w(const float* __restrict__ u, float2* __restrict__ T, int ny, int nz, int pT, float ryy,
+                   float rzz, const float2* __restrict__ twx, int* step_ctr, int inc_step, int* err) {
+  (void)nz;  // 2D only
+  (void)rzz;
+  fwd_rows_wide_body<NX>(blockIdx.x, u, T, ny, pT, ryy, twx, step_ctr, inc_step, err);
 }
 
 template <int NX, bool SPLIT>

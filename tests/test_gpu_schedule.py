@@ -14,10 +14,11 @@ pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
 
-# (wide_cols, wide_rows, col_parts, group, fuse_forward): -1 / 0 = the
-# size's default
-SCHEDULES = [(-1, -1, 0, 0, -1), (0, 0, 0, 0, 0), (1, 1, 0, 0, -1), (1, 0, 2, 6, 1), (0, 1, 1, 3, 1),
-             (-1, -1, 6, 17, 0), (-1, -1, 3, 4, 1), (0, 0, 1, 1, 1), (0, 0, 2, 17, 1)]
+# (wide_cols, wide_rows, col_parts, group, fuse_forward, wide_fwd): -1 / 0
+# = the size's default
+SCHEDULES = [(-1, -1, 0, 0, -1, -1), (0, 0, 0, 0, 0, 0), (1, 1, 0, 0, -1, 1), (1, 0, 2, 6, 1, 0),
+             (0, 1, 1, 3, 1, 1), (-1, -1, 6, 17, 0, 0), (-1, -1, 3, 4, 1, -1), (0, 0, 1, 1, 1, 0),
+             (0, 0, 2, 17, 1, 1)]
 
 
 @pytest.mark.parametrize("n", [512, 1024])
@@ -47,14 +48,14 @@ def test_every_schedule_matches_the_oracle(V, n):
 
 
 def test_default_schedules(V):
-    want = {256: {"wide_cols": 0, "wide_rows": 0, "col_parts": 3, "group": 17, "fuse_forward": 1},
-            512: {"wide_cols": 1, "wide_rows": 1, "col_parts": 6, "group": 17, "fuse_forward": 0},
-            768: {"wide_cols": 0, "wide_rows": 0, "col_parts": 1, "group": 17, "fuse_forward": 0},
-            1024: {"wide_cols": 0, "wide_rows": 1, "col_parts": 1, "group": 17, "fuse_forward": 0}}
+    want = {256: {"wide_cols": 0, "wide_rows": 0, "col_parts": 3, "group": 17, "fuse_forward": 1, "wide_fwd": 0},
+            512: {"wide_cols": 1, "wide_rows": 1, "col_parts": 6, "group": 17, "fuse_forward": 0, "wide_fwd": 0},
+            768: {"wide_cols": 0, "wide_rows": 0, "col_parts": 1, "group": 17, "fuse_forward": 0, "wide_fwd": 0},
+            1024: {"wide_cols": 0, "wide_rows": 1, "col_parts": 1, "group": 17, "fuse_forward": 0, "wide_fwd": 1}}
     for n, w in want.items():
         with V.Solver((n, n)) as s:
             assert s.schedule() == w, (n, s.schedule())
-            s.set_schedule(1, 1, 2, 5, 0)
+            s.set_schedule(1, 1, 2, 5, 0, 0)
             s.set_schedule()  # back to the defaults
             assert s.schedule() == w
 
