@@ -124,7 +124,7 @@ __device__ __forceinline__ void inv_cols_wide_body(int bx, int yidx, int parts, 
   constexpr int LANES = F::LANES, CW = wide_lines_per_cta<NY>(), THREADS = CW * LANES, NB2 = F::NB2;
   constexpr int LS = wide_line_stride<NY, CW>();
   __shared__ float2 s_tw[F::TW];
-  extern __shared__ __align__(16) float2 s_buf[];  // [CW][A, B, stagger]
+  extern __shared__ __align__(128) float2 s_buf[];  // [CW][A, B, stagger]
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
   const int line = threadIdx.x / LANES, li = threadIdx.x % LANES;
   float2* A = s_buf + (size_t)line * LS;
