@@ -325,6 +325,11 @@ VOFL_API int vofl_rel_l2(vofl_ctx* ctx, const void* x_dev, int x_prec, const voi
  *     lines with the wide line transform (as wide_rows), 0 = 32 elements
  *     per lane, -1 = the default (wide at 1024); reported 0 for other line
  *     lengths.
+ *   row_split: runs of terms each row's group is split into in the
+ *     32-element row pass, one warp per run, the runs' Horner sums joined
+ *     by Horner's rule (1, 2 or 4, dividing that kernel's warps per CTA; 0
+ *     = the default: 4 up to 256^2 points, else 1); reported 1 when the row
+ *     pass is wide.
  * vofl_get_schedule reports the schedule in use, defaults resolved.
  * Only fused 2D contexts have one (VOFL_EUNSUPPORTED elsewhere).  A context
  * whose schedule differs from its size's default cannot join a batch
@@ -336,6 +341,7 @@ typedef struct {
   int group;
   int fuse_forward;
   int wide_fwd;
+  int row_split;
 } vofl_schedule;
 VOFL_API int vofl_set_schedule(vofl_ctx* ctx, const vofl_schedule* sched);
 VOFL_API int vofl_get_schedule(vofl_ctx* ctx, vofl_schedule* sched);

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const Batc
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __restrict__ sims, int g, int BG) {
+__global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __restrict__ sims, int g, int BG, int rsplit) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __re
   // epilogue arguments are read from the descriptor only by group 0
   inv_rows_body<NX, false>(blockIdx.x, s->Z, s->zslot, s->pZ, NY, m_lo, m_hi, m_hi == s->M + 1 ? 1 : 0, s->M + 1, 0, s->delta,
                     s->part,
-                    s->part + (size_t)NX * NY, s->epi, s->inv_lambda, s->twx, s->err);
+                    s->part + (size_t)NX * NY, s->epi, s->inv_lambda, s->twx, s->err, rsplit);
 }
 
 // wide inverse passes (fft_wide.cuh) for 512 and 1024 points, as the
@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(wide_threads<NY>(), wide_min_blocks<NY>()) kb_
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(wide_rows_threads<NX>(), NX == 1024 ? 1 : 6) kb_inv_rows_w(const BatchSim* __restrict__ sims, int g, int BG) {
+__global__ void __launch_bounds__(wide_rows_threads<NX>(), NX == 1024 ? 1 : 6) kb_inv_rows_w(const BatchSim* __restrict__ sims, int g, int BG, int rsplit) {
+  (void)rsplit;
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;
@@ -133,11 +134,12 @@ struct BKernels {
   void (*fr)(const BatchSim*);
   void (*fc)(const BatchSim*);
   void (*ic)(const BatchSim*, int, int, int);
-  void (*ir)(const BatchSim*, int, int);
+  void (*ir)(const BatchSim*, int, int, int);
   size_t smem_fr, smem_fc, smem_ic, smem_ir;
   int lpw_x, lpw_y;
   int wic;  // warps per CTA of kb_inv_cols
   int rpf, thr_fr;  // row pairs per CTA and threads of the forward row kernel
+  int rsplit = 1;   // runs of terms per row in the row kernel
   // inverse-kernel launch shapes: lines per CTA and threads per CTA
   int cpc, thr_ic, rpc, thr_ir;
 };
@@ -190,7 +192,8 @@ BKernels bkernels_for() {
   if (!wr) {
     k.ir = kb_inv_rows<NX, NY>;
     k.smem_ir = inv_rows_smem<NX>();
-    k.rpc = W_IROWS * k.lpw_x;
+    k.rsplit = row_split_default(NX, NY, W_IROWS);
+    k.rpc = (W_IROWS / k.rsplit) * k.lpw_x;
     k.thr_ir = W_IROWS * 32;
   }
   return k;
@@ -419,7 +422,8 @@ cudaError_t enqueue_step(vofl_batch* b, int p) {
         e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2 * parts, nz), dim3(cl.k.thr_ic), cl.k.smem_ic, s,
                        dc, g, parts, BG);
         if (e) return e;
-        e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(cl.k.thr_ir), cl.k.smem_ir, s, dc, g, BG);
+        e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(cl.k.thr_ir), cl.k.smem_ir, s, dc, g, BG,
+                       cl.k.rsplit);
         if (e) return e;
       }
     }

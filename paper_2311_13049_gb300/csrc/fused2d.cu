@@ -61,7 +61,7 @@ struct Kernels {
   void (*inv_cols)(float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int,
                    const float2*, const float2*, int, int);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
-                           EpiArgs<float>, float, const float2*, int*);
+                           EpiArgs<float>, float, const float2*, int*, int);
   using InvColsW = void (*)(const float2*, const float*, const float*, float2*, int, int, int, int, float, float, int,
                             int, const float2*);
   InvRows inv_rows;        // two operators
@@ -183,6 +183,7 @@ struct Plan2D {
   // column kernel (32-element column kernel only)
   bool wide_c = false, wide_r = false, fuse_fwd = false, wide_f = false;
   int cparts = 0;
+  int rsplit = 1;  // runs of terms per row in the (32-element) row kernel
 
   bool fused_forward() const { return fuse_fwd && !(wide_c && k.inv_cols_w); }
 
@@ -224,7 +225,8 @@ struct Plan2D {
     const int cpc = wc ? k.cpc_w : k.wic * k.lpw_y;
     const int parts = cparts > 0 ? cparts : col_parts_default(ny);
     const dim3 gic((ncols + cpc - 1) / cpc, 2 * parts);
-    const int rpc = wr ? k.rpc_w : k.wir * k.lpw_x;
+    const int rsp = wr ? 1 : rsplit;
+    const int rpc = wr ? k.rpc_w : (k.wir / rsp) * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
     const bool ff = fused_forward();
     int e_i = ff ? 2 : 3;
@@ -247,7 +249,7 @@ struct Plan2D {
       e = launch_pdl(kr, gir, dim3(wr ? k.thr_w_r : k.wir * 32), wr ? k.smem_irows_w : k.smem_irows, s,
                      (const float2*)Z, zslot, pZ, ny, m_lo, m_hi,
                      gi == K - 1 ? 1 : 0, ts.k2, ts.split_k, delta, part, part + (size_t)nx * ny, ep, inv_lambda,
-                     (const float2*)(wr ? twxw : twx), err);
+                     (const float2*)(wr ? twxw : twx), err, rsp);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
     }
@@ -297,7 +299,8 @@ struct Fused2D : Engine {
     // another schedule would not give the same bits in a batch
     if (p.wide_c != (p.k.inv_cols_w != nullptr && wide_cols_default(p.ny)) ||
         p.wide_r != (p.k.inv_rows_w != nullptr && wide_rows_default(p.nx)) ||
-        p.wide_f != (p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx)) || p.cparts != 0)
+        p.wide_f != (p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx)) || p.cparts != 0 ||
+        p.rsplit != row_split_default(p.nx, p.ny, p.k.wir))
       return false;
     d->T = p.T;
     d->Uh = p.Uh;
@@ -350,6 +353,7 @@ struct Fused2D : Engine {
     p.wide_r = p.k.inv_rows_w != nullptr && wide_rows_default(p.nx);
     p.fuse_fwd = fuse_forward_default(p.ny);
     p.wide_f = p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx);
+    p.rsplit = row_split_default(p.nx, p.ny, p.k.wir);
     if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
     if (make_line_twiddles(p.nx, p.twx, c->stream) ||
         make_line_twiddles(p.ny, p.twy, c->stream) ||
@@ -380,6 +384,8 @@ struct Fused2D : Engine {
   }
 
   int set_schedule(vofl_ctx* c, const vofl_schedule* s) override {
+    if (s->row_split != 0 && p.k.wir % s->row_split != 0)
+      return set_err(c, VOFL_EINVAL, "row_split must divide the row kernel's warps per CTA");
     const bool wc = p.k.inv_cols_w && (s->wide_cols < 0 ? wide_cols_default(p.ny) : s->wide_cols == 1);
     const bool wr = p.k.inv_rows_w && (s->wide_rows < 0 ? wide_rows_default(p.nx) : s->wide_rows == 1);
     const int G = s->group == 0 ? group_default(p.nx, p.ny) : s->group;
@@ -400,6 +406,7 @@ struct Fused2D : Engine {
     p.cparts = s->col_parts;
     p.fuse_fwd = s->fuse_forward < 0 ? fuse_forward_default(p.ny) : s->fuse_forward == 1;
     p.wide_f = p.k.fwd_rows_w && (s->wide_fwd < 0 ? wide_fwd_default(p.nx) : s->wide_fwd == 1);
+    p.rsplit = s->row_split == 0 ? row_split_default(p.nx, p.ny, p.k.wir) : s->row_split;
     return VOFL_OK;
   }
 
@@ -411,6 +418,7 @@ struct Fused2D : Engine {
     s->group = p.G;
     s->fuse_forward = p.fused_forward() ? 1 : 0;
     s->wide_fwd = p.wide_f && p.k.fwd_rows_w ? 1 : 0;
+    s->row_split = (p.wide_r && p.k.inv_rows_w) ? 1 : p.rsplit;
     return VOFL_OK;
   }
 

@@ -42,7 +42,7 @@ struct Kernels3 {
                 const float2*, const float2*, int, int);
   void (*inv_y)(const float2*, long long, float2*, long long, int, int, const float2*);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
-                           EpiArgs<float>, float, const float2*, int*);
+                           EpiArgs<float>, float, const float2*, int*, int);
   InvRows inv_x;        // two operators
   InvRows inv_x_split;  // one operator, terms split over the slots
   size_t sm_frows, sm_fy, sm_fz, sm_iz, sm_iy, sm_ix;
@@ -256,7 +256,7 @@ struct Fused3D : Engine {
       e = launch_pdl(ts.split_k ? k.inv_x_split : k.inv_x, dim3((rows + rpc - 1) / rpc), dim3(W_IROWS * 32), k.sm_ix,
                      s, (const float2*)Zy, zslot_y,
                      pZ, rows, m_lo, m_hi, gi == K - 1 ? 1 : 0, ts.k2, ts.split_k, (const float*)c->delta, part,
-                     part + (size_t)nx * ny * nz, ep, inv_lambda, (const float2*)twx, c->d_step + 1);
+                     part + (size_t)nx * ny * nz, ep, inv_lambda, (const float2*)twx, c->d_step + 1, 1);
       if (e) return e;
     }
     return cudaSuccess;

@@ -508,14 +508,20 @@ constexpr size_t inv_rows_smem() {
 }
 
 // SPLIT: one operator whose terms fill both slots (TermSplit); k2 and
-// split_k are read only then.  W: warps (rows) per CTA.
+// split_k are read only then.  W: warps per CTA.
+// rsplit (dividing W): the group's terms of each row are split into rsplit
+// runs of per = ceil(G / rsplit) terms, one warp each; every warp sums its
+// run by Horner's rule, and the row's sum is the Horner sum of the runs,
+// T = S_0 + delta^per (S_1 + delta^per (S_2 + ...)), formed through shared
+// memory (short rows have few lines: this shortens each warp's chain of
+// terms).  rsplit = 1: one warp per row takes every term.
 template <int NX, bool SPLIT, int W = W_IROWS>
 __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__ Z, long long zslot, int pZ, int ny,
                                               int m_lo, int m_hi, int top, int k2, int split_k,
                                               const float* __restrict__ delta,
                                               float* __restrict__ part1, float* __restrict__ part2,
                                               const EpiArgs<float>& epi, float inv_lambda,
-                                              const float2* __restrict__ twx, int* err) {
+                                              const float2* __restrict__ twx, int* err, int rsplit = 1) {
   using F = LineFFT<NX>;
   constexpr int E = F::E, LANES = F::LANES, H = NX / 2, LPW = F::LPW, THREADS = W * 32;
   constexpr int RB = rows_rb<NX>();
@@ -535,8 +541,13 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   }
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twx[i];
   float2* wbuf = s_buf + warp * warp_stride<NX>();
-  const int yr = (bx * W + warp) * LPW + line;
+  // this warp's rows and run of terms
+  const int rs = rsplit, sub = warp % rs;
+  const int yr = (bx * (W / rs) + warp / rs) * LPW + line;
   const bool active = yr < ny;
+  const int per = (m_hi - m_lo + rs - 1) / rs;
+  const int r_lo = min(m_hi, m_lo + sub * per), r_hi = min(m_hi, r_lo + per);
+  const bool from_part = !top && r_hi == m_hi && r_lo < r_hi;  // the run that continues the previous group's sum
   const int y = active ? yr : 0;
   const size_t row = (size_t)y * NX;
   // rows this line reads later, produced two or more kernels ago: into L2
@@ -544,7 +555,7 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   // spectrum traffic has usually evicted)
   if (li == 0 && active) {
     constexpr uint32_t RowB = NX * sizeof(float);
-    if (!top) {
+    if (from_part) {
       prefetch_l2(part1 + row, RowB);
       prefetch_l2(part2 + row, RowB);
     }
@@ -571,9 +582,9 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
     bulk_copy_g2s(zbuf + buf * 2 * RB, z1, RB_BYTES, &bar[buf]);
     bulk_copy_g2s(zbuf + buf * 2 * RB + RB, z2, RB_BYTES, &bar[buf]);
   };
-  if (li == 0) issue(0, m_hi - 1);
+  if (li == 0 && r_lo < r_hi) issue(0, r_hi - 1);
   float a1[E], a2[E];
-  if (top) {
+  if (!from_part) {
 #pragma unroll
     for (int m = 0; m < E; ++m) a1[m] = a2[m] = 0.f;
   } else {
@@ -586,9 +597,9 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
   uint32_t phase = 0;  // bit b: parity to wait for on buffer b
   int it = 0;
   bool ok = true;
-  for (int mt = m_hi - 1; mt >= m_lo; --mt, ++it) {
+  for (int mt = r_hi - 1; mt >= r_lo; --mt, ++it) {
     const int b = it & 1;
-    if (mt > m_lo) {
+    if (mt > r_lo) {
       __syncwarp();  // every lane finished reading buffer b^1 (two terms ago)
       if (li == 0) {
         fence_proxy_async_smem();
@@ -599,7 +610,7 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
     phase ^= 1u << b;
     if (!__all_sync(0xffffffffu, got)) {
       // give up: drain the prefetch still in flight (bounded) and leave
-      if (mt > m_lo) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u, err);
+      if (mt > r_lo) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u, err);
       ok = false;
       break;
     }
@@ -623,6 +634,39 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
     for (int m = 0; m < E; ++m) {
       a1[m] = fmaf(dl[m], a1[m], w[m].x);
       if (use2) a2[m] = fmaf(dl[m], a2[m], w[m].y);
+    }
+  }
+  if (rs > 1) {
+    // the runs' sums meet in the row's warps' staging buffers (no copies in
+    // flight any more): run s publishes, run 0 combines, highest first
+    float* pub = reinterpret_cast<float*>(zbuf);  // 2 NX floats fit in 4 RB float2
+    if (sub > 0) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        pub[li + LANES * m] = a1[m];
+        pub[NX + li + LANES * m] = a2[m];
+      }
+    }
+    __syncthreads();
+    if (sub > 0) return;
+    float dp[E];  // delta^per
+#pragma unroll
+    for (int m = 0; m < E; ++m) dp[m] = powi(dl[m], per);
+    float t1[E], t2[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) t1[m] = t2[m] = 0.f;
+    for (int q = rs - 1; q >= 1; --q) {
+      const float* src = reinterpret_cast<const float*>(zbuf + (size_t)q * LPW * 4 * RB);  // warp + q, same line
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        t1[m] = fmaf(dp[m], t1[m], src[li + LANES * m]);
+        t2[m] = fmaf(dp[m], t2[m], src[NX + li + LANES * m]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      a1[m] = fmaf(dp[m], t1[m], a1[m]);
+      a2[m] = fmaf(dp[m], t2[m], a2[m]);
     }
   }
   if (!active || !ok) return;
@@ -652,9 +696,9 @@ __global__ void __launch_bounds__(W * 32) k2d_inv_rows(const float2* __restrict_
                                                            const float* __restrict__ delta, float* __restrict__ part1,
                                                            float* __restrict__ part2, EpiArgs<float> epi,
                                                            float inv_lambda, const float2* __restrict__ twx,
-                                                           int* err) {
+                                                           int* err, int rsplit) {
   inv_rows_body<NX, SPLIT, W>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, k2, split_k, delta, part1, part2, epi,
-                              inv_lambda, twx, err);
+                              inv_lambda, twx, err, rsplit);
 }
 
 // -------------------------------------------------------------------------

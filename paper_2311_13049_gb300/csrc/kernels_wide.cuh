@@ -40,6 +40,13 @@ inline int group_default(int nx, int ny) {
   (void)ny;
   return 17;
 }
+// Runs of terms per row in the 32-element row kernel (dividing its warps
+// per CTA): grids of up to 256^2 points have few row lines (256 rows in
+// 128 warps), so each row's group of 17 terms goes to four warps.
+inline int row_split_default(int nx, int ny, int warps) {
+  const int want = (long long)nx * ny <= 256LL * 256 ? 4 : 1;
+  return warps % want == 0 ? want : 1;
+}
 // The forward column transform inside the top group's inverse column
 // kernel (one launch fewer per step; every CTA of the group transforms its
 // own columns, the same arithmetic as k2d_fwd_cols): on grids of up to 256
@@ -474,7 +481,8 @@ __global__ void __launch_bounds__(wide_rows_threads<NX>(), NX == 1024 ? 1 : 6)
     k2d_inv_rows_w(const float2* __restrict__ Z, long long zslot, int pZ, int ny, int m_lo, int m_hi, int top, int k2,
                    int split_k, const float* __restrict__ delta, float* __restrict__ part1,
                    float* __restrict__ part2, EpiArgs<float> epi, float inv_lambda, const float2* __restrict__ twx,
-                   int* err) {
+                   int* err, int rsplit) {
+  (void)rsplit;  // every row on its own lanes (the wide form has warps enough)
   inv_rows_wide_body<NX, SPLIT>(blockIdx.x, Z, zslot, pZ, ny, m_lo, m_hi, top, k2, split_k, delta, part1, part2, epi,
                                 inv_lambda, twx, err);
 }

@@ -14,11 +14,11 @@ pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
 
-# (wide_cols, wide_rows, col_parts, group, fuse_forward, wide_fwd): -1 / 0
-# = the size's default
-SCHEDULES = [(-1, -1, 0, 0, -1, -1), (0, 0, 0, 0, 0, 0), (1, 1, 0, 0, -1, 1), (1, 0, 2, 6, 1, 0),
-             (0, 1, 1, 3, 1, 1), (-1, -1, 6, 17, 0, 0), (-1, -1, 3, 4, 1, -1), (0, 0, 1, 1, 1, 0),
-             (0, 0, 2, 17, 1, 1)]
+# (wide_cols, wide_rows, col_parts, group, fuse_forward, wide_fwd,
+# row_split): -1 / 0 = the size's default
+SCHEDULES = [(-1, -1, 0, 0, -1, -1, 0), (0, 0, 0, 0, 0, 0, 0), (1, 1, 0, 0, -1, 1, 0), (1, 0, 2, 6, 1, 0, 0),
+             (0, 1, 1, 3, 1, 1, 0), (-1, -1, 6, 17, 0, 0, 0), (-1, -1, 3, 4, 1, -1, 0), (0, 0, 1, 1, 1, 0, 0),
+             (0, 0, 2, 17, 1, 1, 0)]
 
 
 @pytest.mark.parametrize("n", [512, 1024])
@@ -48,10 +48,11 @@ def test_every_schedule_matches_the_oracle(V, n):
 
 
 def test_default_schedules(V):
-    want = {256: {"wide_cols": 0, "wide_rows": 0, "col_parts": 3, "group": 17, "fuse_forward": 1, "wide_fwd": 0},
-            512: {"wide_cols": 1, "wide_rows": 1, "col_parts": 6, "group": 17, "fuse_forward": 0, "wide_fwd": 0},
-            768: {"wide_cols": 0, "wide_rows": 0, "col_parts": 1, "group": 17, "fuse_forward": 0, "wide_fwd": 0},
-            1024: {"wide_cols": 0, "wide_rows": 1, "col_parts": 1, "group": 17, "fuse_forward": 0, "wide_fwd": 1}}
+    base = {"group": 17, "wide_cols": 0, "wide_rows": 0, "fuse_forward": 0, "wide_fwd": 0, "row_split": 1}
+    want = {256: dict(base, col_parts=3, fuse_forward=1, row_split=4),
+            512: dict(base, col_parts=6, wide_cols=1, wide_rows=1),
+            768: dict(base, col_parts=1),
+            1024: dict(base, col_parts=1, wide_rows=1, wide_fwd=1)}
     for n, w in want.items():
         with V.Solver((n, n)) as s:
             assert s.schedule() == w, (n, s.schedule())
@@ -113,3 +114,36 @@ def test_fused_forward_is_bit_identical(V):
                 s.sync()
                 outs.append((o1.cpu().numpy(), o2.cpu().numpy()))
         assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1]), shape
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (128, 128), (64, 64), (128, 256)])
+def test_row_split_matches_the_oracle(V, shape):
+    """Rows whose terms are split over 1, 2 or 4 warps (partial Horner sums
+    joined by Horner's rule), one or more Taylor groups, the seismic pair
+    and the general model's one operator: all within the FP32 tolerance."""
+    import torch
+    Q = S.q_lowpass(shape, 51)
+    u = S.q_lowpass(shape, 52, qmin=-1.0, qmax=1.0, sigma_k=16).astype(np.float32)
+    M = 16
+    r1, r2 = O.seismic_operators(u.astype(np.float64), gamma_of(Q), M)
+    x, y = S.mesh(shape)
+    order = 1.0 - 0.3 * np.cos(x) * np.sin(y)
+    ro = O.matrix_free_operator(u.astype(np.float64), order, M)
+    ut = torch.from_numpy(u).cuda()
+    for rs in (1, 2, 4):
+        for G in (0, 5):
+            with V.Solver(shape) as s:
+                s.set_q(Q)
+                s.set_M(M)
+                s.set_schedule(-1, -1, 0, G, -1, -1, rs)
+                assert s.schedule()["row_split"] == rs
+                o1, o2 = torch.empty_like(ut), torch.empty_like(ut)
+                s.apply_pair(ut, o1, o2)
+                s.sync()
+                check(o1.cpu().numpy(), r1, TOL32, (shape, rs, G))
+                check(o2.cpu().numpy(), r2, TOL32, (shape, rs, G))
+                s.set_order(order)
+                o = torch.empty_like(ut)
+                s.apply(V.OP_S, ut, o)
+                s.sync()
+                check(o.cpu().numpy(), ro, TOL32, (shape, rs, G, "general"))
