@@ -61,8 +61,8 @@ DT = 5e-4
 # reports traffic null (see _ncu_traffic).
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic_2d_1024_M16.txt")
 KERNEL_SOURCES = ["paper_2311_13049_gb300/csrc/kernels.cuh", "paper_2311_13049_gb300/csrc/fft_warp.cuh",
-                  "paper_2311_13049_gb300/csrc/fused2d.cu", "paper_2311_13049_gb300/csrc/tma.cuh",
-                  "paper_2311_13049_gb300/csrc/internal.h"]
+                  "paper_2311_13049_gb300/csrc/kernels_wide.cuh", "paper_2311_13049_gb300/csrc/fft_wide.cuh",
+                  "paper_2311_13049_gb300/csrc/tma.cuh", "paper_2311_13049_gb300/csrc/internal.h"]
 METRIC = "Mpoint-steps/s (2D 1024², M=16) fused vs plain at ≤1e-5 rel L2; serve p50/p99"
 UNIT = "Mpoint-steps/s"
 WORKLOAD = "2D periodic 1024x1024, FP32, M=16, Q low-passed noise in [5,100] (seed 2), Ricker f0=10 at centre, dt=5e-4, 1000 steps"
