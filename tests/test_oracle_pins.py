@@ -488,8 +488,13 @@ def test_paper_table2_cnfp_temporal_errors(golden_dir, col):
     are those of a dt = 2^-12 reference rather than the dt = 1e-4 the text
     names, and the run is on h = 1/8 (J = 512) instead of h = 1/64: the
     spatial error there is at round-off (Table 5), so the temporal errors
-    are the same.  Agreement: 1e-3 relative plus 3e-9 absolute, the spread
-    of such references under round-off (J = 512 against J = 1024)."""
+    are the same.  Agreement: 1e-3 relative on every cell; the ten cells
+    below 5e-7 (the finest steps) also get 3e-9 absolute.  Their deviations
+    from the printed digits are about constant in absolute terms (s = 0.5:
+    1.6e-9, 1.9e-9, 2.7e-9 at dt = 2^-9, 2^-10, 2^-11), not proportional to
+    the cell: a floor in the printed values, as an unstated solver tolerance
+    accumulated over 2^p steps leaves (the k = 0 mode adds each step's solve
+    error), which no choice here can pin tighter."""
     rows = _table2(golden_dir)
     J = 512
     x = S.axis(J, -32.0, 32.0)
@@ -500,7 +505,8 @@ def test_paper_table2_cnfp_temporal_errors(golden_dir, col):
     for p in range(7, 12):
         err = O.l2_error(run(2.0 ** -p, 2 ** p), ref, [64.0 / J])
         printed = rows[p][col]
-        assert abs(err - printed) <= 1e-3 * printed + 3e-9, (col, p, err, printed)
+        floor = 3e-9 if printed < 5e-7 else 0.0
+        assert abs(err - printed) <= 1e-3 * printed + floor, (col, p, err, printed)
 
 
 @pytest.mark.parametrize("s,k", [(0.5, 3), (1.0, 5), (1.3, 2)])
