@@ -104,7 +104,8 @@ def _table2(golden_dir):
 @pytest.mark.parametrize("col,order", [(3, "s1"), (4, "s2"), (1, "one")])
 def test_paper_table2_cnfp_on_the_gpu(V, golden_dir, col, order):
     """Table 2 at the paper's h = 1/64 (J = 4096) with the GPU's FP64 path;
-    agreement 1e-3 relative plus 3e-9 absolute (the oracle pin's rule)."""
+    agreement 1e-3 relative, plus 3e-9 absolute on cells below 5e-7 (the
+    oracle pin's rule: the printed values' floor at the finest steps)."""
     rows = _table2(golden_dir)
     J, lo, hi = 4096, [-32.0], [32.0]
     x = S.axis(J, -32.0, 32.0)
@@ -120,7 +121,8 @@ def test_paper_table2_cnfp_on_the_gpu(V, golden_dir, col, order):
     for p in range(7, 12):
         err = O.l2_error(run(2.0 ** -p, 2 ** p), ref, [1.0 / 64])
         printed = rows[p][col]
-        assert abs(err - printed) <= 1e-3 * printed + 3e-9, (order, p, err, printed)
+        floor = 3e-9 if printed < 5e-7 else 0.0
+        assert abs(err - printed) <= 1e-3 * printed + floor, (order, p, err, printed)
 
 
 def test_cnfp_preconditions_and_solver_limits(V):
