@@ -16,8 +16,9 @@ is Mpoint-steps/s = 1024^2 * 1000 * runs / time.
   plain  the cuFFT + elementwise baseline on the same run;
   batch  64 independent 2D simulations of uneven sizes {256, 512, 768,
          1024}^2 (M = 12, 300 steps each, dt a quarter of the leap-frog bound
-         of each model) advanced together by one batch (vofl_batch_*),
-         autotuned, timed over the whole 300-step run;
+         of each model) advanced together by one batch (vofl_batch_*), the
+         transform schedule of each size and the launch layout autotuned
+         (vofl_batch_tune_transform), timed over the whole 300-step run;
   configs  the 1D 256 FP64 (M = 8, 200 steps) and 3D 256^3 FP32 (M = 8,
          500 steps) runs, fused and plain; the general model of the
          paper's Tables 3 (leap-frog) and 2 (Crank-Nicolson) on the FP64
@@ -306,8 +307,10 @@ def batch_bench(V, torch, stream, flush):
     b.set_schedule(False, {n: 1 for n in sizes})
     ms_serial = b.time(reps=2)
     b.set_schedule(True, {})
-    ms_tuned = b.tune(reps=2)
+    ms_layout = b.tune(reps=2)  # launch layout only (bit-preserving)
+    ms_tuned = b.tune_transform(reps=2)  # transform schedule per size, then the layout
     par, chunks = b.schedule()
+    transforms = {str(n): b.transform(n) for n in sorted({sp["shape"][0] for sp in sims})}
     kps = b.kernels_per_step()
     with torch.cuda.stream(stream):
         flush.zero_()
@@ -333,8 +336,11 @@ def batch_bench(V, torch, stream, flush):
                         + f"; M=12, {nsteps} steps each, dt = 0.25 * 2/omega_max per model",
             "points": pts, "steps": nsteps, "kernels_per_step": kps, "gpu_launches": launches,
             "ms_per_batch_step": {"tuned": ms_tuned, "default_all_per_launch": ms_default,
-                                  "one_sim_per_launch_serial": ms_serial},
-            "schedule": {"parallel_branches": par, "sims_per_launch": {str(k): v for k, v in chunks.items()}},
+                                  "layout_tuned_default_transforms": ms_layout,
+                                  "one_sim_per_launch_serial": ms_serial,
+                                  "tuned_over_default": ms_default / ms_tuned},
+            "schedule": {"parallel_branches": par, "sims_per_launch": {str(k): v for k, v in chunks.items()},
+                         "transforms": transforms},
             "setup_s": t_setup}
 
 

@@ -330,10 +330,11 @@ VOFL_API int vofl_rel_l2(vofl_ctx* ctx, const void* x_dev, int x_prec, const voi
  *     by Horner's rule (1, 2 or 4, dividing that kernel's warps per CTA; 0
  *     = the default: 4 up to 256^2 points, else 1); reported 1 when the row
  *     pass is wide.
- * vofl_get_schedule reports the schedule in use, defaults resolved.
+ * vofl_get_schedule reports the schedule in use, defaults resolved (also
+ * while a batch steps the context).
  * Only fused 2D contexts have one (VOFL_EUNSUPPORTED elsewhere).  A context
- * whose schedule differs from its size's default cannot join a batch
- * (vofl_batch_add returns VOFL_EUNSUPPORTED). */
+ * can join a batch whose members of its size are on the same schedule
+ * (vofl_batch_tune_transform). */
 typedef struct {
   int wide_cols;
   int wide_rows;
@@ -457,6 +458,23 @@ VOFL_API int vofl_batch_get_schedule(const vofl_batch* b, int* parallel, int* si
 
 /* Set the schedule directly (as vofl_batch_get_schedule reports it). */
 VOFL_API int vofl_batch_set_schedule(vofl_batch* b, int parallel, const int* sizes, const int* chunks, int n);
+
+/* Transform schedules of a batch (vofl_set_schedule; no counterpart in the
+ * paper).  The batched launches of one grid size follow one transform
+ * schedule: that of the size's first member; a later member of the size
+ * whose context is on another schedule is refused (VOFL_EUNSUPPORTED), so
+ * every member gives the bits of its context stepped alone.
+ * vofl_batch_tune_transform searches, size by size, the line transforms of
+ * each pass, the column runs, the terms per group (at most the members'
+ * own) and the runs per row, then the launch layout (as vofl_batch_tune),
+ * timing `reps` batch steps per candidate from a saved copy of the state
+ * that is put back; it then gives every member its size's schedule (results
+ * change in the last bits, within the FP32 tolerance; a member stepped alone
+ * afterwards keeps the batch's arithmetic).  *ms_per_step: the best time.
+ * vofl_batch_get_transform reports the schedule of grid edge n (VOFL_EINVAL
+ * when the batch has no member of that size). */
+VOFL_API int vofl_batch_tune_transform(vofl_batch* b, int reps, double* ms_per_step);
+VOFL_API int vofl_batch_get_transform(const vofl_batch* b, int n, vofl_schedule* out);
 
 /* Allocation-free variant of vofl_apply_pair for small 2D grids.  The paper
  * has no counterpart: it is a deployment aid for callers that may not

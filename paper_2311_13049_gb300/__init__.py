@@ -91,6 +91,8 @@ SIGNATURES = {
     "vofl_batch_get_schedule": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.c_int]),
     "vofl_batch_set_schedule": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
+    "vofl_batch_tune_transform": (C.c_int, [_vp, C.c_int, _dp]),
+    "vofl_batch_get_transform": (C.c_int, [_vp, C.c_int, C.POINTER(Schedule)]),
 }
 
 
@@ -399,6 +401,19 @@ class Batch:
         ms = C.c_double()
         self._check(lib().vofl_batch_tune(self._h, int(reps), C.byref(ms)))
         return ms.value
+
+    def tune_transform(self, reps=2):
+        """Search each grid size's transform schedule, then the launch layout;
+        members take the winning schedule.  Returns ms per batch step."""
+        ms = C.c_double(0)
+        self._check(lib().vofl_batch_tune_transform(self._h, int(reps), C.byref(ms)))
+        return ms.value
+
+    def transform(self, n):
+        """The transform schedule of grid edge n (a dict, as Solver.schedule())."""
+        sc = Schedule()
+        self._check(lib().vofl_batch_get_transform(self._h, int(n), C.byref(sc)))
+        return sc.as_dict()
 
     def time(self, reps=2):
         """ms per batch step of the current schedule (state left unchanged)."""

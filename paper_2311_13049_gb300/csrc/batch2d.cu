@@ -131,17 +131,24 @@ __global__ void __launch_bounds__(wide_rows_threads<NX>(), NX == 1024 ? 1 : 6) k
 }
 
 struct BKernels {
+  // 32-element (narrow) kernels, and the wide-line ones where built
+  // (512 and 1024 points; null elsewhere)
   void (*fr)(const BatchSim*);
+  void (*fr_w)(const BatchSim*) = nullptr;
   void (*fc)(const BatchSim*);
   void (*ic)(const BatchSim*, int, int, int);
+  void (*ic_w)(const BatchSim*, int, int, int) = nullptr;
   void (*ir)(const BatchSim*, int, int, int);
-  size_t smem_fr, smem_fc, smem_ic, smem_ir;
+  void (*ir_w)(const BatchSim*, int, int, int) = nullptr;
+  size_t smem_fr, smem_fr_w = 0, smem_fc, smem_ic, smem_ic_w = 0, smem_ir, smem_ir_w = 0;
   int lpw_x, lpw_y;
-  int wic;  // warps per CTA of kb_inv_cols
-  int rpf, thr_fr;  // row pairs per CTA and threads of the forward row kernel
-  int rsplit = 1;   // runs of terms per row in the row kernel
-  // inverse-kernel launch shapes: lines per CTA and threads per CTA
-  int cpc, thr_ic, rpc, thr_ir;
+  int wic;               // warps per CTA of kb_inv_cols
+  int rpf, thr_fr;       // row pairs per CTA and threads: forward rows
+  int rpf_w = 0, thr_fr_w = 0;
+  int cpc, thr_ic;       // columns per CTA and threads: inverse columns
+  int cpc_w = 0, thr_ic_w = 0;
+  int wir, thr_ir;       // warps (rows x runs) per CTA and threads: inverse rows
+  int rpc_w = 0, thr_ir_w = 0;
 };
 
 template <int NX, int NY>
@@ -156,45 +163,29 @@ BKernels bkernels_for() {
   k.wic = icols_warps<NY>();
   k.rpf = W_FROWS * k.lpw_x;
   k.thr_fr = W_FROWS * 32;
-  if constexpr (NX == 512 || NX == 1024) {
-    if (wide_fwd_default(NX)) {
-      k.fr = kb_fwd_rows_w<NX, NY>;
-      k.smem_fr = wide_frows_smem<NX>();
-      k.rpf = wide_frows_lines<NX>();
-      k.thr_fr = wide_frows_threads<NX>();
-    }
-  }
-  bool wc = false, wr = false;
+  k.ic = kb_inv_cols<NX, NY>;
+  k.smem_ic = inv_cols_smem<NY>();
+  k.cpc = k.wic * k.lpw_y;
+  k.thr_ic = k.wic * 32;
+  k.ir = kb_inv_rows<NX, NY>;
+  k.smem_ir = inv_rows_smem<NX>();
+  k.wir = W_IROWS;
+  k.thr_ir = W_IROWS * 32;
   if constexpr (NY == 512 || NY == 1024) {
-    if (wide_cols_default(NY)) {
-      k.ic = kb_inv_cols_w<NX, NY>;
-      k.smem_ic = wide_cols_smem<NY>();
-      k.cpc = wide_lines_per_cta<NY>();
-      k.thr_ic = wide_threads<NY>();
-      wc = true;
-    }
-  }
-  if (!wc) {
-    k.ic = kb_inv_cols<NX, NY>;
-    k.smem_ic = inv_cols_smem<NY>();
-    k.cpc = k.wic * k.lpw_y;
-    k.thr_ic = k.wic * 32;
+    k.ic_w = kb_inv_cols_w<NX, NY>;
+    k.smem_ic_w = wide_cols_smem<NY>();
+    k.cpc_w = wide_lines_per_cta<NY>();
+    k.thr_ic_w = wide_threads<NY>();
   }
   if constexpr (NX == 512 || NX == 1024) {
-    if (wide_rows_default(NX)) {
-      k.ir = kb_inv_rows_w<NX, NY>;
-      k.smem_ir = wide_rows_smem<NX>();
-      k.rpc = wide_rows_per_cta<NX>();
-      k.thr_ir = wide_rows_threads<NX>();
-      wr = true;
-    }
-  }
-  if (!wr) {
-    k.ir = kb_inv_rows<NX, NY>;
-    k.smem_ir = inv_rows_smem<NX>();
-    k.rsplit = row_split_default(NX, NY, W_IROWS);
-    k.rpc = (W_IROWS / k.rsplit) * k.lpw_x;
-    k.thr_ir = W_IROWS * 32;
+    k.fr_w = kb_fwd_rows_w<NX, NY>;
+    k.smem_fr_w = wide_frows_smem<NX>();
+    k.rpf_w = wide_frows_lines<NX>();
+    k.thr_fr_w = wide_frows_threads<NX>();
+    k.ir_w = kb_inv_rows_w<NX, NY>;
+    k.smem_ir_w = wide_rows_smem<NX>();
+    k.rpc_w = wide_rows_per_cta<NX>();
+    k.thr_ir_w = wide_rows_threads<NX>();
   }
   return k;
 }
@@ -216,7 +207,42 @@ bool set_bsmem(const BKernels& k) {
   return set_kernel_smem(k.fr, k.smem_fr) == cudaSuccess &&
          set_kernel_smem(k.fc, k.smem_fc) == cudaSuccess &&
          set_kernel_smem(k.ic, k.smem_ic) == cudaSuccess &&
-         set_kernel_smem(k.ir, k.smem_ir) == cudaSuccess;
+         set_kernel_smem(k.ir, k.smem_ir) == cudaSuccess &&
+         (!k.fr_w || set_kernel_smem(k.fr_w, k.smem_fr_w) == cudaSuccess) &&
+         (!k.ic_w || set_kernel_smem(k.ic_w, k.smem_ic_w) == cudaSuccess) &&
+         (!k.ir_w || set_kernel_smem(k.ir_w, k.smem_ir_w) == cudaSuccess);
+}
+
+// The transform schedule of one size class: the fields of vofl_schedule
+// that decide the arithmetic of the batched launches (its members' own
+// schedule, so a member gives the bits of the same context stepped alone).
+struct TSched {
+  bool wc = false, wr = false, wf = false;
+  int parts = 1, G = 17, rs = 1;
+  bool operator==(const TSched& o) const {
+    return wc == o.wc && wr == o.wr && wf == o.wf && parts == o.parts && G == o.G && rs == o.rs;
+  }
+};
+TSched tsched_of(const vofl_schedule& v) {
+  TSched t;
+  t.wc = v.wide_cols == 1;
+  t.wr = v.wide_rows == 1;
+  t.wf = v.wide_fwd == 1;
+  t.parts = v.col_parts;
+  t.G = v.group;
+  t.rs = v.row_split;
+  return t;
+}
+vofl_schedule schedule_of(const TSched& t) {
+  vofl_schedule v{};
+  v.wide_cols = t.wc ? 1 : 0;
+  v.wide_rows = t.wr ? 1 : 0;
+  v.col_parts = t.parts;
+  v.group = t.G;
+  v.fuse_forward = -1;  // the same bits either way
+  v.wide_fwd = t.wf ? 1 : 0;
+  v.row_split = t.rs;
+  return v;
 }
 
 // plain (non-programmatic) launch, for the first kernel of a graph branch
@@ -253,10 +279,14 @@ struct vofl_batch {
   // and whether classes run on parallel branches
   std::map<int, int> chunk;
   bool parallel = true;
+  // per grid size, the transform schedule of the batched launches (set by
+  // the first member of the size, or by vofl_batch_tune_transform)
+  std::map<int, TSched> tsched;
 
   struct Class {
     int n = 0;  // grid edge
     BKernels k{};
+    TSched ts{};
     int off = 0, count = 0;  // descriptor range
   };
   std::vector<Class> classes;
@@ -286,6 +316,15 @@ int bcuda(vofl_batch* b, cudaError_t e, const char* where) {
               std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// a size whose last member left takes the schedule of its next first member
+void forget_empty_sizes(vofl_batch* b) {
+  for (auto it = b->tsched.begin(); it != b->tsched.end();) {
+    bool used = false;
+    for (auto& m : b->mem) used |= m.c->n[0] == it->first;
+    it = used ? std::next(it) : b->tsched.erase(it);
+  }
+}
+
 void drop_bgraphs(vofl_batch* b) {
   if (b->g1) cudaGraphExecDestroy(b->g1);
   if (b->g2) cudaGraphExecDestroy(b->g2);
@@ -302,6 +341,7 @@ int plan(vofl_batch* b) {
   for (auto& kv : by) {
     vofl_batch::Class cl;
     cl.n = kv.first;
+    cl.ts = b->tsched[cl.n];
     if (!pick_bkernels(cl.n, cl.n, &cl.k)) return berr(b, VOFL_EUNSUPPORTED, "batched kernels: grid size not built");
     if (!set_bsmem(cl.k)) return berr(b, VOFL_ECUDA, "shared-memory attributes of the batched kernels");
     cl.off = (int)b->order.size();
@@ -406,24 +446,31 @@ cudaError_t enqueue_step(vofl_batch* b, int p) {
       const BatchSim* dc = d + cl.off + c0;
       int Mmax = 0;
       for (int j = 0; j < nz; ++j) Mmax = std::max(Mmax, b->mem[b->order[cl.off + c0 + j]].c->M);
-      const int rpc = cl.k.rpf;
+      const TSched& t = cl.ts;
+      const bool wf = t.wf && cl.k.fr_w, wc = t.wc && cl.k.ic_w, wr = t.wr && cl.k.ir_w;
+      const int rpc = wf ? cl.k.rpf_w : cl.k.rpf;
       const dim3 gfr((ny / 2 + rpc - 1) / rpc, 1, nz);
-      e = first ? launch_plain(cl.k.fr, gfr, dim3(cl.k.thr_fr), cl.k.smem_fr, s, dc)
-                : launch_pdl(cl.k.fr, gfr, dim3(cl.k.thr_fr), cl.k.smem_fr, s, dc);
+      auto* fr = wf ? cl.k.fr_w : cl.k.fr;
+      const int thr_fr = wf ? cl.k.thr_fr_w : cl.k.thr_fr;
+      const size_t sm_fr = wf ? cl.k.smem_fr_w : cl.k.smem_fr;
+      e = first ? launch_plain(fr, gfr, dim3(thr_fr), sm_fr, s, dc) : launch_pdl(fr, gfr, dim3(thr_fr), sm_fr, s, dc);
       if (e) return e;
       first = false;
       const int cpf = W_FCOLS * cl.k.lpw_y;
       e = launch_pdl(cl.k.fc, dim3((ncols + cpf - 1) / cpf, 1, nz), dim3(W_FCOLS * 32), cl.k.smem_fc, s, dc);
       if (e) return e;
-      const int cpc = cl.k.cpc, rpi = cl.k.rpc;
-      // the group size and column split of the solo launches of this size
-      const int BG = group_default(nx, ny), parts = col_parts_default(ny);
+      const int cpc = wc ? cl.k.cpc_w : cl.k.cpc;
+      const int rs = wr ? 1 : t.rs;
+      const int rpi = wr ? cl.k.rpc_w : (cl.k.wir / rs) * cl.k.lpw_x;
+      auto* ic = wc ? cl.k.ic_w : cl.k.ic;
+      auto* ir = wr ? cl.k.ir_w : cl.k.ir;
+      const int BG = t.G, parts = t.parts;
       for (int g = Mmax / BG; g >= 0; --g) {
-        e = launch_pdl(cl.k.ic, dim3((ncols + cpc - 1) / cpc, 2 * parts, nz), dim3(cl.k.thr_ic), cl.k.smem_ic, s,
-                       dc, g, parts, BG);
+        e = launch_pdl(ic, dim3((ncols + cpc - 1) / cpc, 2 * parts, nz), dim3(wc ? cl.k.thr_ic_w : cl.k.thr_ic),
+                       wc ? cl.k.smem_ic_w : cl.k.smem_ic, s, dc, g, parts, BG);
         if (e) return e;
-        e = launch_pdl(cl.k.ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(cl.k.thr_ir), cl.k.smem_ir, s, dc, g, BG,
-                       cl.k.rsplit);
+        e = launch_pdl(ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(wr ? cl.k.thr_ir_w : cl.k.thr_ir),
+                       wr ? cl.k.smem_ir_w : cl.k.smem_ir, s, dc, g, BG, rs);
         if (e) return e;
       }
     }
@@ -592,6 +639,7 @@ void vofl::batch_detach(vofl_ctx* c) {
       break;
     }
   c->batch = nullptr;
+  forget_empty_sizes(b);
   drop_bgraphs(b);
 }
 
@@ -646,6 +694,21 @@ int vofl_batch_add(vofl_batch* b, vofl_ctx* c, double dt, int* slot) {
     return berr(b, VOFL_EUNSUPPORTED, "this grid size has no batched kernels");
   if (c->device != b->device) return berr(b, VOFL_EINVAL, "the context lives on another GPU");
   if (c->M > 40) return berr(b, VOFL_EINVAL, "M above 40");
+  // the size's transform schedule: the first member's, which every later
+  // member of the size must share (the batched launches give each member
+  // the bits of its context stepped alone)
+  vofl_schedule vs{};
+  if (c->eng->get_schedule(c, &vs) != VOFL_OK) return berr(b, VOFL_EUNSUPPORTED, "no transform schedule");
+  const TSched ts = tsched_of(vs);
+  if (!ts.wr && W_IROWS % ts.rs != 0)
+    return berr(b, VOFL_EUNSUPPORTED, "row split not available in batched launches");
+  if ((ts.wc && !k.ic_w) || (ts.wr && !k.ir_w) || (ts.wf && !k.fr_w))
+    return berr(b, VOFL_EUNSUPPORTED, "wide line transform not built for batched launches of this size");
+  forget_empty_sizes(b);
+  auto known = b->tsched.find((int)c->n[0]);
+  if (known != b->tsched.end() && !(known->second == ts))
+    return berr(b, VOFL_EUNSUPPORTED,
+                "the context's transform schedule differs from the batch's for this grid size");
   if (int st = prepare_run(c, dt)) return berr(b, st, std::string("context: ") + c->err);
   // the batch stream waits for the context's queued work (set-up, start)
   cudaEvent_t e;
@@ -655,6 +718,7 @@ int vofl_batch_add(vofl_batch* b, vofl_ctx* c, double dt, int* slot) {
   cudaEventDestroy(e);
   if (r != cudaSuccess) return bcuda(b, r, "batch join");
   c->batch = b;
+  b->tsched[(int)c->n[0]] = ts;
   b->mem.push_back({c, dt, b->next_slot});
   if (slot) *slot = b->next_slot;
   ++b->next_slot;
@@ -668,6 +732,7 @@ int vofl_batch_remove(vofl_batch* b, int slot) {
     if (b->mem[i].slot == slot) {
       vofl_ctx* c = b->mem[i].c;
       b->mem.erase(b->mem.begin() + (long)i);
+      forget_empty_sizes(b);
       drop_bgraphs(b);
       return release(b, c);
     }
@@ -771,6 +836,88 @@ int vofl_batch_tune(vofl_batch* b, int reps, double* ms_per_step) {
   snap.restore(b);
   if (st) return st;
   if (ms_per_step) *ms_per_step = best;
+  return VOFL_OK;
+}
+
+int vofl_batch_tune_transform(vofl_batch* b, int reps, double* ms_per_step) {
+  if (!b || reps < 1) return berr(b, VOFL_EINVAL, "bad batch or reps");
+  if (b->mem.empty()) return VOFL_OK;
+  Snapshot snap;
+  if (int st = snap.take(b)) return st;
+  int st = plan(b);
+  double best = 1e300;
+  auto trial = [&](double* ms) -> int {
+    drop_bgraphs(b);
+    return time_schedule(b, reps, ms);
+  };
+  if (!st) st = trial(&best);
+  // coordinate search, size by size: line transforms of each pass, column
+  // runs, terms per group (never above the members' own: their buffers
+  // hold that many), runs per row
+  for (size_t ci = 0; !st && ci < b->classes.size(); ++ci) {
+    const int n = b->classes[ci].n;
+    const BKernels k = b->classes[ci].k;  // a copy: every trial re-plans the classes
+    TSched cur = b->tsched[n];
+    const int gmax = cur.G;
+    auto attempt = [&](TSched t) {
+      if (st || t == cur) return;
+      b->tsched[n] = t;
+      for (auto& cl : b->classes) cl.ts = b->tsched[cl.n];
+      double ms;
+      if ((st = trial(&ms))) return;
+      if (ms < best) {
+        best = ms;
+        cur = t;
+      }
+      b->tsched[n] = cur;
+      for (auto& cl : b->classes) cl.ts = b->tsched[cl.n];
+    };
+    if (k.ic_w) { TSched t = cur; t.wc = !t.wc; attempt(t); }
+    if (k.ir_w) { TSched t = cur; t.wr = !t.wr; if (!t.wr && W_IROWS % t.rs) t.rs = 1; attempt(t); }
+    if (k.fr_w) { TSched t = cur; t.wf = !t.wf; attempt(t); }
+    for (int parts : {1, 2, 3, 6}) { TSched t = cur; t.parts = parts; attempt(t); }
+    for (int G : {17, 9, 6}) if (G <= gmax) { TSched t = cur; t.G = G; attempt(t); }
+    if (!cur.wr)
+      for (int rs : {1, 2, 4}) { TSched t = cur; t.rs = rs; attempt(t); }
+  }
+  // then the launch layout, as vofl_batch_tune
+  for (size_t ci = 0; !st && ci < b->classes.size(); ++ci) {
+    const int n = b->classes[ci].n, count = b->classes[ci].count;
+    int keep = b->chunk.count(n) ? b->chunk[n] : 0;
+    for (int w : {1, 2, 4, 8, 16}) {
+      if (w >= count) break;
+      b->chunk[n] = w;
+      double ms;
+      if ((st = trial(&ms))) break;
+      if (ms < best) {
+        best = ms;
+        keep = w;
+      }
+    }
+    b->chunk[n] = keep;
+  }
+  drop_bgraphs(b);
+  snap.restore(b);
+  if (st) return st;
+  // the members take their size's schedule (a member stepped alone later
+  // keeps the arithmetic it had in the batch)
+  for (auto& m : b->mem) {
+    const vofl_schedule v = schedule_of(b->tsched[(int)m.c->n[0]]);
+    if (int e = m.c->eng->set_schedule(m.c, &v)) return berr(b, e, "member schedule");
+    for (auto& g : m.c->step_graph) {  // captured with the old schedule
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  }
+  if (ms_per_step) *ms_per_step = best;
+  return VOFL_OK;
+}
+
+int vofl_batch_get_transform(const vofl_batch* b, int n, vofl_schedule* out) {
+  if (!b || !out) return VOFL_EINVAL;
+  auto it = b->tsched.find(n);
+  if (it == b->tsched.end()) return VOFL_EINVAL;
+  *out = schedule_of(it->second);
   return VOFL_OK;
 }
 

@@ -275,6 +275,7 @@ struct Fused2D : Engine {
   // round-off up to |mu|_max times its own size.  lambda ~ sqrt(|mu|_max)
   // balances the two; it is divided out exactly in the epilogue.
   double lambda = 1.0;
+  int zcap = 0;  // Taylor terms the group buffer holds (>= p.G)
 
   ~Fused2D() override {
     cudaFree(p.T);
@@ -293,15 +294,9 @@ struct Fused2D : Engine {
 
   bool batch_desc(const vofl_ctx* c, BatchSim* d) const override {
     (void)c;
-    if (p.G != group_default(p.nx, p.ny)) return false;  // the batched launches use the default group size
-    // the batched launches use the default schedule of the size (wide
-    // inverse passes where built, the default column split): a context on
-    // another schedule would not give the same bits in a batch
-    if (p.wide_c != (p.k.inv_cols_w != nullptr && wide_cols_default(p.ny)) ||
-        p.wide_r != (p.k.inv_rows_w != nullptr && wide_rows_default(p.nx)) ||
-        p.wide_f != (p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx)) || p.cparts != 0 ||
-        p.rsplit != row_split_default(p.nx, p.ny, p.k.wir))
-      return false;
+    // the batched launches follow the size class's transform schedule,
+    // which the batch takes from (and checks against) its members'
+    // (vofl_batch_add)
     d->T = p.T;
     d->Uh = p.Uh;
     d->Z = p.Z;
@@ -342,6 +337,7 @@ struct Fused2D : Engine {
     if ((st = alloc(c, (void**)&p.T, sizeof(float2) * ny * p.pT))) return st;
     if ((st = alloc(c, (void**)&p.Uh, sizeof(float2) * nc * ny))) return st;
     if ((st = alloc(c, (void**)&p.Z, sizeof(float2) * (size_t)p.zslot * 2 * p.G))) return st;
+    zcap = p.G;
     if ((st = alloc(c, (void**)&p.part, sizeof(float) * 2 * nx * ny))) return st;
     if ((st = alloc(c, (void**)&p.P, sizeof(float) * 2 * nc * ny))) return st;
     if ((st = alloc(c, (void**)&p.Lg, sizeof(float) * nc * ny))) return st;
@@ -389,16 +385,19 @@ struct Fused2D : Engine {
     const bool wc = p.k.inv_cols_w && (s->wide_cols < 0 ? wide_cols_default(p.ny) : s->wide_cols == 1);
     const bool wr = p.k.inv_rows_w && (s->wide_rows < 0 ? wide_rows_default(p.nx) : s->wide_rows == 1);
     const int G = s->group == 0 ? group_default(p.nx, p.ny) : s->group;
-    if (G != p.G) {
-      const size_t b_old = sizeof(float2) * (size_t)p.zslot * 2 * p.G;
+    if (G > zcap) {  // a larger group buffer; a smaller group uses the one there is
+      const size_t b_old = sizeof(float2) * (size_t)p.zslot * 2 * zcap;
       const size_t b_new = sizeof(float2) * (size_t)p.zslot * 2 * G;
       float2* z = nullptr;
       cudaError_t e = dev_malloc((void**)&z, b_new);
       if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (Taylor group buffer)");
       cudaFree(p.Z);
       p.Z = z;
-      p.G = G;
+      zcap = G;
       nbytes = nbytes - b_old + b_new;
+    }
+    if (G != p.G) {
+      p.G = G;
       if (p.make_zmap()) return set_err(c, VOFL_ECUDA, "tensor map of the Z buffer");
     }
     p.wide_c = wc;

@@ -61,9 +61,10 @@ def test_default_schedules(V):
             assert s.schedule() == w
 
 
-def test_schedule_runs_agree_and_batch_needs_default(V):
+def test_schedule_runs_agree_and_batch_needs_one_schedule_per_size(V):
     """20 leap-frog steps on two schedules agree within the run tolerance;
-    a context off the default schedule is refused by a batch."""
+    the first member of a grid size sets the batch's schedule for the size,
+    and a context of that size on another schedule is refused."""
     shape = (512, 512)
     Q = S.q_lowpass(shape, 5)
     src = S.ricker_samples(20, 5e-4, 10.0)
@@ -82,15 +83,18 @@ def test_schedule_runs_agree_and_batch_needs_default(V):
     a = run(None)
     b = run((0, 0, 1, 4, 1))
     check(b, a, 1e-4)
-    with V.Solver(shape) as s, V.Batch() as bt:
-        s.set_q(Q)
-        s.set_M(12)
-        s.set_state(np.zeros(shape, np.float32))
+    with V.Solver(shape) as s, V.Solver(shape) as s2, V.Batch() as bt:
+        for x in (s, s2):
+            x.set_q(Q)
+            x.set_M(12)
+            x.set_state(np.zeros(shape, np.float32))
         s.set_schedule(0, 0, 1, 4, 1)
+        bt.add(s, 5e-4)  # the size's first member: its schedule is the batch's
+        assert bt.transform(shape[0])["group"] == 4
         with pytest.raises(V.VoflError):
-            bt.add(s, 5e-4)
-        s.set_schedule()
-        bt.add(s, 5e-4)
+            bt.add(s2, 5e-4)  # the default schedule differs
+        s2.set_schedule(0, 0, 1, 4, 1)
+        bt.add(s2, 5e-4)
         bt.step(2)
         bt.sync()
 
@@ -147,3 +151,45 @@ def test_row_split_matches_the_oracle(V, shape):
                 s.apply(V.OP_S, ut, o)
                 s.sync()
                 check(o.cpu().numpy(), ro, TOL32, (shape, rs, G, "general"))
+
+
+def test_batch_transform_tuning_keeps_members_equal_to_solo(V):
+    """vofl_batch_tune_transform: every member takes its size's tuned
+    schedule, and stepping on gives the bits of a context stepped alone on
+    that schedule, within the run tolerance of the default-schedule run."""
+    import synthetic as Sy
+    specs = [(256, 70 + i) for i in range(3)] + [(512, 80 + i) for i in range(2)]
+    nsteps, dt = 12, 5e-4
+
+    def make(n, seed):
+        s = V.Solver((n, n))
+        s.set_q(Sy.q_lowpass((n, n), seed))
+        s.set_M(12)
+        s.set_state(np.zeros((n, n), np.float32))
+        s.set_source(Sy.center_index((n, n)), Sy.ricker_samples(nsteps, dt, 10.0))
+        return s
+
+    members = [make(n, seed) for n, seed in specs]
+    with V.Batch() as b:
+        slots = [b.add(s, dt) for s in members]
+        ms = b.tune_transform(reps=1)
+        assert ms > 0
+        for s, (n, _) in zip(members, specs):
+            assert s.schedule() == dict(b.transform(n), fuse_forward=s.schedule()["fuse_forward"])
+        b.step(nsteps)
+        for slot in slots:
+            b.remove(slot)
+    for s, (n, seed) in zip(members, specs):
+        got = s.get_state().astype(np.float64)
+        sc = s.schedule()
+        solo = make(n, seed)
+        solo.set_schedule(sc["wide_cols"], sc["wide_rows"], sc["col_parts"], sc["group"], -1, sc["wide_fwd"],
+                          sc["row_split"])
+        solo.step(nsteps, dt)
+        assert np.array_equal(solo.get_state().astype(np.float64), got), (n, sc)
+        solo.close()
+        ref = make(n, seed)
+        ref.step(nsteps, dt)
+        check(got, ref.get_state().astype(np.float64), 1e-4, (n, sc))
+        ref.close()
+        s.close()
