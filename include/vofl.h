@@ -370,6 +370,20 @@ VOFL_API int vofl_selftest_bounded_wait(int* gave_up);
  * call (0 when none). */
 VOFL_API int64_t vofl_debug_fail_alloc(int64_t k);
 
+/* Memory-checker stand-in (no counterpart in the paper).  When the
+ * environment holds VOFL_DEBUG_CANARY=1 at the library's first device
+ * allocation, every device buffer the library allocates gets 64 KB pads of
+ * a known byte on both sides; a kernel writing up to 64 KB past either end
+ * of a buffer changes a pad.  Pads are checked when a buffer is freed and
+ * by this call, which synchronises the device and returns the number of
+ * buffers found with changed pads (live ones checked now, freed ones when
+ * they were freed), or -1 when the mode is off.  *live_buffers (may be
+ * NULL): the live padded buffers.  poke = 1 first overwrites one byte of
+ * the newest live buffer's end pad from the host (the test that the check
+ * sees a change).  Debug use only: every allocation and free synchronises
+ * the device. */
+VOFL_API int64_t vofl_debug_canaries(int64_t* live_buffers, int poke);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent 2D simulations advanced together.
  *

@@ -72,6 +72,7 @@ SIGNATURES = {
     "vofl_set_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
     "vofl_rel_l2": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _dp]),
     "vofl_debug_fail_alloc": (C.c_int64, [C.c_int64]),
+    "vofl_debug_canaries": (C.c_int64, [_i64p, C.c_int]),
     "vofl_get_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
     "vofl_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int)]),
     "vofl_apply_pair_2d_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, _vp, _vp, _vp,

@@ -351,7 +351,7 @@ int plan(vofl_batch* b) {
   }
   const int n = (int)b->order.size();
   if (n > b->cap) {
-    cudaFree(b->d_desc);
+    dev_free(b->d_desc);
     b->d_desc = nullptr;
     b->cap = 0;
     const int cap = std::max(16, n + n / 2);
@@ -621,7 +621,7 @@ struct Snapshot {
     release_all();
   }
   void release_all() {
-    for (void* p : buf) cudaFree(p);
+    for (void* p : buf) dev_free(p);
     buf.clear();
   }
   ~Snapshot() { release_all(); }
@@ -674,7 +674,7 @@ void vofl_batch_destroy(vofl_batch* b) {
   drop_bgraphs(b);
   for (auto s : b->aux) cudaStreamDestroy(s);
   for (auto e : b->ev) cudaEventDestroy(e);
-  cudaFree(b->d_desc);
+  dev_free(b->d_desc);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }

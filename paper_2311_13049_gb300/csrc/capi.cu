@@ -288,16 +288,16 @@ void vofl_destroy(vofl_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   delete c->eng;
-  cudaFree(c->delta);
-  cudaFree(c->A);
-  cudaFree(c->B);
-  cudaFree(c->u[0]);
-  cudaFree(c->u[1]);
-  cudaFree(c->l2p);
-  cudaFree(c->d_gamma);
-  cudaFree(c->d_scratch);
-  cudaFree(c->d_step);
-  cudaFree(c->d_src);
+  dev_free(c->delta);
+  dev_free(c->A);
+  dev_free(c->B);
+  dev_free(c->u[0]);
+  dev_free(c->u[1]);
+  dev_free(c->l2p);
+  dev_free(c->d_gamma);
+  dev_free(c->d_scratch);
+  dev_free(c->d_step);
+  dev_free(c->d_src);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -358,14 +358,14 @@ int vofl_set_gamma(vofl_ctx* c, const double* gamma, const double* c0_field, int
     VOFL_CUDA(c, dev_malloc(&d_c0, sizeof(double) * c->N));
     st = upload(c, d_c0, c0_field, sizeof(double) * c->N, on_device);
     if (st) {
-      cudaFree(d_c0);
+      dev_free(d_c0);
       return st;
     }
   }
   st = finish_model(c, d_c0, c0, omega0);
   if (d_c0) {
     cudaStreamSynchronize(c->stream);
-    cudaFree(d_c0);
+    dev_free(d_c0);
   }
   return st;
 }
@@ -442,10 +442,10 @@ int vofl_set_source(vofl_ctx* c, const int64_t* idx, const double* samples, int6
     VOFL_CUDA(c, dev_malloc(&d_new, sizeof(double) * nsamples));
     drop_graphs(c);  // graphs hold the old pointer
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {  // queued steps may still read the old samples
-      cudaFree(d_new);
+      dev_free(d_new);
       return cuda_err(c, cudaGetLastError(), "cudaStreamSynchronize");
     }
-    cudaFree(c->d_src);
+    dev_free(c->d_src);
     c->d_src = d_new;
     c->src_cap = nsamples;
   }
@@ -640,7 +640,7 @@ int vofl_load_state(vofl_ctx* c, const void* blob, size_t nbytes) {
     double* d_new = nullptr;
     VOFL_CUDA(c, dev_malloc(&d_new, sizeof(double) * h.nsrc));
     drop_graphs(c);  // they hold the old source pointer
-    cudaFree(c->d_src);
+    dev_free(c->d_src);
     c->d_src = d_new;
     c->src_cap = h.nsrc;
   }
@@ -748,6 +748,13 @@ int vofl_sync(vofl_ctx* c) {
 }
 
 int64_t vofl_debug_fail_alloc(int64_t k) { return (int64_t)debug_fail_alloc((long long)k); }
+
+int64_t vofl_debug_canaries(int64_t* live_buffers, int poke) {
+  long long live = 0;
+  const long long bad = debug_canaries(&live, poke);
+  if (live_buffers) *live_buffers = (int64_t)live;
+  return (int64_t)bad;
+}
 
 int vofl_rel_l2(vofl_ctx* c, const void* x_dev, int x_prec, const void* y_dev, int y_prec, double* out) {
   NvtxRange nvtx_range("vofl_rel_l2");

@@ -514,12 +514,12 @@ struct Fused1D : Engine {
   }
 
   ~Fused1D() override {
-    cudaFree(P1);
-    cudaFree(P2);
-    cudaFree(Lg);
-    cudaFree(tw);
-    cudaFree(d_sim);
-    cudaFree(T);
+    dev_free(P1);
+    dev_free(P2);
+    dev_free(Lg);
+    dev_free(tw);
+    dev_free(d_sim);
+    dev_free(T);
   }
   size_t bytes() const override { return nbytes; }
 
@@ -567,7 +567,7 @@ struct Fused1D : Engine {
     if (T && tab_M == c->M && tab_gen == model_gen) return VOFL_OK;
     if (tab_M != c->M) {
       VOFL_CUDA(c, cudaStreamSynchronize(c->stream));  // queued work may still read the old table
-      cudaFree(T);
+      dev_free(T);
       T = nullptr;
       nbytes -= tab_bytes;
       tab_bytes = sizeof(R) * 2 * (size_t)(c->M + 1) * N;

@@ -278,16 +278,16 @@ struct Fused2D : Engine {
   int zcap = 0;  // Taylor terms the group buffer holds (>= p.G)
 
   ~Fused2D() override {
-    cudaFree(p.T);
-    cudaFree(p.Uh);
-    cudaFree(p.Z);
-    cudaFree(p.part);
-    cudaFree(p.P);
-    cudaFree(p.Lg);
-    cudaFree(p.twx);
-    cudaFree(p.twy);
-    cudaFree(p.twxw);
-    cudaFree(p.twyw);
+    dev_free(p.T);
+    dev_free(p.Uh);
+    dev_free(p.Z);
+    dev_free(p.part);
+    dev_free(p.P);
+    dev_free(p.Lg);
+    dev_free(p.twx);
+    dev_free(p.twy);
+    dev_free(p.twxw);
+    dev_free(p.twyw);
   }
 
   size_t bytes() const override { return nbytes; }
@@ -391,7 +391,7 @@ struct Fused2D : Engine {
       float2* z = nullptr;
       cudaError_t e = dev_malloc((void**)&z, b_new);
       if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc (Taylor group buffer)");
-      cudaFree(p.Z);
+      dev_free(p.Z);
       p.Z = z;
       zcap = G;
       nbytes = nbytes - b_old + b_new;

@@ -146,7 +146,7 @@ struct Fused3D : Engine {
   ~Fused3D() override {
     for (void* q : {(void*)T, (void*)U2, (void*)U3, (void*)Zz, (void*)Zy, (void*)part, (void*)P, (void*)Lg,
                     (void*)twx, (void*)twy, (void*)twz})
-      cudaFree(q);
+      dev_free(q);
   }
   size_t bytes() const override { return nbytes; }
 

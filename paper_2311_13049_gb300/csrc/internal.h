@@ -31,6 +31,12 @@ extern std::atomic<uint64_t> g_kernel_launches;
 // and reports VOFL_ENOMEM.
 cudaError_t dev_malloc_bytes(void** p, size_t bytes);
 long long debug_fail_alloc(long long k);  // set the countdown, return the old one
+// Frees what dev_malloc gave (cudaFree, or, in the canary mode, the padded
+// allocation after checking its pads).
+cudaError_t dev_free(void* p);
+// Canary mode (VOFL_DEBUG_CANARY=1 in the environment at the first
+// allocation): buffers found with changed pads, -1 when the mode is off.
+long long debug_canaries(long long* live, int poke);
 template <typename T>
 inline cudaError_t dev_malloc(T** p, size_t bytes) {
   return dev_malloc_bytes(reinterpret_cast<void**>(p), bytes);

@@ -8,6 +8,11 @@
 //   FFT twiddles exp(-2 pi i r k / N).
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -308,6 +313,48 @@ std::atomic<long long> g_fail_alloc{0};
 
 long long debug_fail_alloc(long long k) { return g_fail_alloc.exchange(k < 0 ? 0 : k); }
 
+// Canary mode, a stand-in for a memory checker: every buffer gets 64 KB
+// pads of a known byte on both sides; a kernel that writes past either end
+// of a buffer (by up to 64 KB) changes a pad, found when the buffer is freed
+// or by debug_canaries.
+namespace {
+constexpr size_t kCanaryPad = size_t(64) << 10;  // a multiple of 256: the buffer keeps its alignment
+constexpr unsigned char kCanaryByte = 0xA5;
+struct CanaryAlloc {
+  unsigned char* base;
+  size_t bytes;
+  unsigned long long serial;
+};
+std::mutex g_canary_mu;
+std::unordered_map<void*, CanaryAlloc>& canary_live() {
+  static auto* live = new std::unordered_map<void*, CanaryAlloc>();  // outlives static destruction
+  return *live;
+}
+std::atomic<long long> g_canary_bad{0};
+std::atomic<unsigned long long> g_canary_serial{0};
+
+bool canary_mode() {
+  static const bool on = [] {
+    const char* e = std::getenv("VOFL_DEBUG_CANARY");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+bool pads_intact(const CanaryAlloc& a) {
+  std::vector<unsigned char> h(2 * kCanaryPad);
+  if (cudaMemcpy(h.data(), a.base, kCanaryPad, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(h.data() + kCanaryPad, a.base + kCanaryPad + a.bytes, kCanaryPad, cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (unsigned char c : h)
+    if (c != kCanaryByte) return false;
+  return true;
+}
+}  // namespace
+
 cudaError_t dev_malloc_bytes(void** p, size_t bytes) {
   long long k = g_fail_alloc.load();
   while (k > 0) {
@@ -319,7 +366,71 @@ cudaError_t dev_malloc_bytes(void** p, size_t bytes) {
       break;
     }
   }
-  return cudaMalloc(p, bytes);
+  if (!canary_mode()) return cudaMalloc(p, bytes);
+  unsigned char* base = nullptr;
+  cudaError_t e = cudaMalloc((void**)&base, bytes + 2 * kCanaryPad);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  if ((e = cudaMemset(base, kCanaryByte, kCanaryPad)) != cudaSuccess ||
+      (e = cudaMemset(base + kCanaryPad + bytes, kCanaryByte, kCanaryPad)) != cudaSuccess ||
+      (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    cudaFree(base);
+    *p = nullptr;
+    return e;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_canary_mu);
+    canary_live()[base + kCanaryPad] = {base, bytes, g_canary_serial.fetch_add(1)};
+  }
+  *p = base + kCanaryPad;
+  return cudaSuccess;
+}
+
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  if (canary_mode()) {
+    CanaryAlloc a{};
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lock(g_canary_mu);
+      auto it = canary_live().find(p);
+      if (it != canary_live().end()) {
+        a = it->second;
+        canary_live().erase(it);
+        found = true;
+      }
+    }
+    if (found) {
+      cudaDeviceSynchronize();  // kernels still writing the buffer finish first
+      if (!pads_intact(a)) g_canary_bad.fetch_add(1);
+      return cudaFree(a.base);
+    }
+  }
+  return cudaFree(p);
+}
+
+long long debug_canaries(long long* live, int poke) {
+  if (live) *live = 0;
+  if (!canary_mode()) return -1;
+  cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lock(g_canary_mu);
+  if (poke) {  // change one pad byte of the newest live buffer (a check that the check sees it)
+    const CanaryAlloc* newest = nullptr;
+    for (auto& kv : canary_live())
+      if (!newest || kv.second.serial > newest->serial) newest = &kv.second;
+    if (newest) {
+      cudaMemset(newest->base + kCanaryPad + newest->bytes, 0, 1);
+      cudaDeviceSynchronize();
+    }
+  }
+  long long bad = g_canary_bad.load();
+  for (auto& kv : canary_live()) {
+    if (!pads_intact(kv.second)) ++bad;
+    if (live) ++*live;
+  }
+  return bad;
 }
 
 int cuda_err(vofl_ctx* c, cudaError_t e, const char* where) {

@@ -526,7 +526,7 @@ struct Plain : Engine {
     cn_drop_graphs();
     for (void* q : {(void*)cn.b, (void*)cn.x, (void*)cn.r, (void*)cn.z, (void*)cn.p, (void*)cn.w, (void*)cn.pa,
                     (void*)cn.pb, (void*)cn.s})
-      cudaFree(q);
+      dev_free(q);
     if (cn.hs) cudaFreeHost(cn.hs);
     nbytes -= cn.bytes;
     cn = Cn{};
@@ -537,8 +537,8 @@ struct Plain : Engine {
       cufftDestroy(tb.inv1);
       cufftDestroy(tb.inv2);
     }
-    cudaFree(tb.X);
-    cudaFree(tb.Y);
+    dev_free(tb.X);
+    dev_free(tb.Y);
     nbytes -= tb.bytes;
     const int gen = tb.gen;
     tb = Terms{};
@@ -550,16 +550,16 @@ struct Plain : Engine {
     tb_free();
     if (have_fwd) cufftDestroy(fwd);
     if (have_inv) cufftDestroy(inv);
-    cudaFree(uh);
-    cudaFree(X);
-    cudaFree(Y);
-    cudaFree(acc1);
-    cudaFree(acc2);
-    cudaFree(P1);
-    cudaFree(P2);
-    cudaFree(Lg);
-    cudaFree(W);
-    cudaFree(vh);
+    dev_free(uh);
+    dev_free(X);
+    dev_free(Y);
+    dev_free(acc1);
+    dev_free(acc2);
+    dev_free(P1);
+    dev_free(P2);
+    dev_free(Lg);
+    dev_free(W);
+    dev_free(vh);
   }
   size_t bytes() const override { return nbytes; }
 

@@ -45,6 +45,6 @@ extern "C" int vofl_selftest_bounded_wait(int* gave_up) {
     if (cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = VOFL_ECUDA;
     *gave_up = h;
   }
-  cudaFree(d_err);
+  dev_free(d_err);
   return rc;
 }

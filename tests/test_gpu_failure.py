@@ -108,11 +108,11 @@ def test_context_calls_report_enomem_and_stay_usable(V):
         # source stays in place
         longer = S.ricker_samples(400, 1e-3, 5.0)
         assert _each_failure(V, lambda: s.set_source(S.center_index(shape), longer)) == 1
-        # a new Taylor group size re-sizes the group buffer: on failure the
-        # old schedule stays
+        # a Taylor group larger than the group buffer holds re-sizes it: on
+        # failure the old schedule stays
         sched = s.schedule()
-        n = _each_failure(V, lambda: s.set_schedule(-1, -1, 0, 5))
-        assert n == 1 and s.schedule()["group"] == 5
+        n = _each_failure(V, lambda: s.set_schedule(-1, -1, 0, 20))
+        assert n == 1 and s.schedule()["group"] == 20
         s.set_schedule()
         assert s.schedule() == sched
         # the c0 field of set_gamma is staged in a temporary buffer
