@@ -58,12 +58,14 @@ inline bool fuse_forward_default(int ny) { return ny <= 256; }
 // grids have fewer column blocks than SMs.
 inline int col_parts_default(int ny) { return ny <= 256 ? 3 : (ny <= 512 ? 6 : 1); }
 
-// Lines per CTA: seven two-warp lines at 1024 points; at 512 eight
-// one-warp columns (the cooperative last stage stores 64-byte row
-// segments) but two rows (a 512-row pass has only 512 lines: 256 CTAs).
+// Lines per CTA: eight columns (the cooperative last stage stores 64-byte
+// row segments, whole L2 sectors: seven columns' 56-byte segments left
+// partial sectors and measured far slower); rows: seven two-warp lines at
+// 1024 points, two one-warp lines at 512 (a 512-row pass has only 512
+// lines: 256 CTAs).
 template <int N>
 constexpr int wide_lines_per_cta() {
-  return N == 1024 ? 7 : 8;
+  return 8;  // 64-byte row segments: whole 32-byte sectors
 }
 template <int N>
 constexpr int wide_rows_per_cta() {
