@@ -311,7 +311,8 @@ VOFL_API int vofl_rel_l2(vofl_ctx* ctx, const void* x_dev, int x_prec, const voi
  *     (reported 0) for other line lengths.
  *   col_parts: runs of terms per Taylor group in the inverse column pass
  *     (each run starts its multiplier recurrence afresh), 1..41, or 0 for
- *     the size's default (3 at ny <= 256, 2 at ny <= 512, 1 above).
+ *     the size's default (3 at ny <= 256, 6 at ny <= 512, 1 above); not
+ *     used while col_pack > 0.
  *   group: Taylor terms per group G (the terms whose per-term column
  *     transforms are stored between the column and row passes), 1..41;
  *     0 = the default, 17 (M <= 16 in one group).  Changing it re-sizes
@@ -330,6 +331,13 @@ VOFL_API int vofl_rel_l2(vofl_ctx* ctx, const void* x_dev, int x_prec, const voi
  *     by Horner's rule (1, 2 or 4, dividing that kernel's warps per CTA; 0
  *     = the default: 4 up to 256^2 points, else 1); reported 1 when the row
  *     pass is wide.
+ *   col_pack: K > 0 (up to 65535) = the inverse column pass runs on K CTAs
+ *     that share the group's terms of all column blocks evenly (in column
+ *     block order, each CTA takes the tail of one block's terms, whole
+ *     blocks and the head of the next; every run starts its multiplier
+ *     recurrence afresh); 0 = one CTA per column block, operator and
+ *     col_parts run; -1 = the default: K = the device's SMs on square
+ *     grids of 128 and 512 points, twice that at 768, else 0.
  * vofl_get_schedule reports the schedule in use, defaults resolved (also
  * while a batch steps the context).
  * Only fused 2D contexts have one (VOFL_EUNSUPPORTED elsewhere).  A context
@@ -343,6 +351,7 @@ typedef struct {
   int fuse_forward;
   int wide_fwd;
   int row_split;
+  int col_pack;
 } vofl_schedule;
 VOFL_API int vofl_set_schedule(vofl_ctx* ctx, const vofl_schedule* sched);
 VOFL_API int vofl_get_schedule(vofl_ctx* ctx, vofl_schedule* sched);

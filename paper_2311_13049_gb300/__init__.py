@@ -30,7 +30,7 @@ _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5
 class Schedule(C.Structure):
     """vofl_schedule: transform schedule of the fused 2D path."""
     _fields_ = [("wide_cols", C.c_int), ("wide_rows", C.c_int), ("col_parts", C.c_int), ("group", C.c_int),
-                ("fuse_forward", C.c_int), ("wide_fwd", C.c_int), ("row_split", C.c_int)]
+                ("fuse_forward", C.c_int), ("wide_fwd", C.c_int), ("row_split", C.c_int), ("col_pack", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -317,10 +317,10 @@ class Solver:
         return rc == 1
 
     def set_schedule(self, wide_cols=-1, wide_rows=-1, col_parts=0, group=0, fuse_forward=-1, wide_fwd=-1,
-                     row_split=0):
+                     row_split=0, col_pack=-1):
         """Transform schedule of the fused 2D path (-1 / 0: the size's default)."""
         sc = Schedule(int(wide_cols), int(wide_rows), int(col_parts), int(group), int(fuse_forward),
-                      int(wide_fwd), int(row_split))
+                      int(wide_fwd), int(row_split), int(col_pack))
         self._check(lib().vofl_set_schedule(self._h, C.byref(sc)))
 
     def schedule(self):

@@ -81,14 +81,14 @@ __global__ void __launch_bounds__(W_FCOLS * 32) kb_fwd_cols(const BatchSim* __re
 
 template <int NX, int NY>
 __global__ void __launch_bounds__(icols_warps<NY>() * 32) kb_inv_cols(const BatchSim* __restrict__ sims, int g,
-                                                                      int parts, int BG) {
+                                                                      int parts, int pack, int BG) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;  // this simulation has fewer groups
   const int m_hi = min(s->M + 1, m_lo + BG);
   // the descriptor (with its tensor map) was written by a host copy
   if (threadIdx.x == 0) tmap_acquire(&s->zmap);
-  inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, s->Uh, s->P, s->Lg, &s->zmap, NX / 2 + 1, m_lo, m_hi,
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, pack, s->Uh, s->P, s->Lg, &s->zmap, NX / 2 + 1, m_lo, m_hi,
                     (float)c_inv_fact[m_lo], (float)c_inv_fact[m_lo], 0, s->twy);
 }
 
@@ -109,12 +109,12 @@ __global__ void __launch_bounds__(W_IROWS * 32) kb_inv_rows(const BatchSim* __re
 // single-context launches of those sizes use them
 template <int NX, int NY>
 __global__ void __launch_bounds__(wide_threads<NY>(), wide_min_blocks<NY>()) kb_inv_cols_w(const BatchSim* __restrict__ sims, int g,
-                                                                       int parts, int BG) {
+                                                                       int parts, int pack, int BG) {
   const BatchSim* s = sims + blockIdx.z;
   const int m_lo = g * BG;
   if (m_lo > s->M) return;
   const int m_hi = min(s->M + 1, m_lo + BG);
-  inv_cols_wide_body<NY>(blockIdx.x, blockIdx.y, parts, s->Uh, s->P, s->Lg, s->Z, s->pZ, NX / 2 + 1, m_lo, m_hi,
+  inv_cols_wide_body<NY>(blockIdx.x, blockIdx.y, parts, pack, s->Uh, s->P, s->Lg, s->Z, s->pZ, NX / 2 + 1, m_lo, m_hi,
                          (float)c_inv_fact[m_lo], (float)c_inv_fact[m_lo], 0, s->twyw);
 }
 
@@ -136,8 +136,8 @@ struct BKernels {
   void (*fr)(const BatchSim*);
   void (*fr_w)(const BatchSim*) = nullptr;
   void (*fc)(const BatchSim*);
-  void (*ic)(const BatchSim*, int, int, int);
-  void (*ic_w)(const BatchSim*, int, int, int) = nullptr;
+  void (*ic)(const BatchSim*, int, int, int, int);
+  void (*ic_w)(const BatchSim*, int, int, int, int) = nullptr;
   void (*ir)(const BatchSim*, int, int, int);
   void (*ir_w)(const BatchSim*, int, int, int) = nullptr;
   size_t smem_fr, smem_fr_w = 0, smem_fc, smem_ic, smem_ic_w = 0, smem_ir, smem_ir_w = 0;
@@ -218,9 +218,9 @@ bool set_bsmem(const BKernels& k) {
 // schedule, so a member gives the bits of the same context stepped alone).
 struct TSched {
   bool wc = false, wr = false, wf = false;
-  int parts = 1, G = 17, rs = 1;
+  int parts = 1, G = 17, rs = 1, pack = 0;
   bool operator==(const TSched& o) const {
-    return wc == o.wc && wr == o.wr && wf == o.wf && parts == o.parts && G == o.G && rs == o.rs;
+    return wc == o.wc && wr == o.wr && wf == o.wf && parts == o.parts && G == o.G && rs == o.rs && pack == o.pack;
   }
 };
 TSched tsched_of(const vofl_schedule& v) {
@@ -231,6 +231,7 @@ TSched tsched_of(const vofl_schedule& v) {
   t.parts = v.col_parts;
   t.G = v.group;
   t.rs = v.row_split;
+  t.pack = v.col_pack;
   return t;
 }
 vofl_schedule schedule_of(const TSched& t) {
@@ -242,6 +243,7 @@ vofl_schedule schedule_of(const TSched& t) {
   v.fuse_forward = -1;  // the same bits either way
   v.wide_fwd = t.wf ? 1 : 0;
   v.row_split = t.rs;
+  v.col_pack = t.pack;
   return v;
 }
 
@@ -464,10 +466,11 @@ cudaError_t enqueue_step(vofl_batch* b, int p) {
       const int rpi = wr ? cl.k.rpc_w : (cl.k.wir / rs) * cl.k.lpw_x;
       auto* ic = wc ? cl.k.ic_w : cl.k.ic;
       auto* ir = wr ? cl.k.ir_w : cl.k.ir;
-      const int BG = t.G, parts = t.parts;
+      const int BG = t.G, parts = t.parts, pack = t.pack;
+      const dim3 gic = pack > 0 ? dim3(pack, 1, nz) : dim3((ncols + cpc - 1) / cpc, 2 * parts, nz);
       for (int g = Mmax / BG; g >= 0; --g) {
-        e = launch_pdl(ic, dim3((ncols + cpc - 1) / cpc, 2 * parts, nz), dim3(wc ? cl.k.thr_ic_w : cl.k.thr_ic),
-                       wc ? cl.k.smem_ic_w : cl.k.smem_ic, s, dc, g, parts, BG);
+        e = launch_pdl(ic, gic, dim3(wc ? cl.k.thr_ic_w : cl.k.thr_ic), wc ? cl.k.smem_ic_w : cl.k.smem_ic, s, dc, g,
+                       parts, pack, BG);
         if (e) return e;
         e = launch_pdl(ir, dim3((ny + rpi - 1) / rpi, 1, nz), dim3(wr ? cl.k.thr_ir_w : cl.k.thr_ir),
                        wr ? cl.k.smem_ir_w : cl.k.smem_ir, s, dc, g, BG, rs);
@@ -875,7 +878,9 @@ int vofl_batch_tune_transform(vofl_batch* b, int reps, double* ms_per_step) {
     if (k.ic_w) { TSched t = cur; t.wc = !t.wc; attempt(t); }
     if (k.ir_w) { TSched t = cur; t.wr = !t.wr; if (!t.wr && W_IROWS % t.rs) t.rs = 1; attempt(t); }
     if (k.fr_w) { TSched t = cur; t.wf = !t.wf; attempt(t); }
-    for (int parts : {1, 2, 3, 6}) { TSched t = cur; t.parts = parts; attempt(t); }
+    for (int parts : {1, 2, 3, 6}) { TSched t = cur; t.parts = parts; t.pack = 0; attempt(t); }
+    const int sms = device_sm_count();
+    for (int pk : {0, sms, 2 * sms}) { TSched t = cur; t.pack = pk; attempt(t); }
     for (int G : {17, 9, 6}) if (G <= gmax) { TSched t = cur; t.G = G; attempt(t); }
     if (!cur.wr)
       for (int rs : {1, 2, 4}) { TSched t = cur; t.rs = rs; attempt(t); }

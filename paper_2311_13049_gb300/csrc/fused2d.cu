@@ -58,12 +58,12 @@ namespace {
 struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
-  void (*inv_cols)(float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int,
+  void (*inv_cols)(float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int, int,
                    const float2*, const float2*, int, int);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
                            EpiArgs<float>, float, const float2*, int*, int);
   using InvColsW = void (*)(const float2*, const float*, const float*, float2*, int, int, int, int, float, float, int,
-                            int, const float2*);
+                            int, int, const float2*);
   InvRows inv_rows;        // two operators
   InvRows inv_rows_split;  // one operator, terms split over the slots
   // wide line transforms (fft_wide.cuh) of the inverse passes, for lines of
@@ -183,6 +183,7 @@ struct Plan2D {
   // column kernel (32-element column kernel only)
   bool wide_c = false, wide_r = false, fuse_fwd = false, wide_f = false;
   int cparts = 0;
+  int cpack = 0;   // > 0: the column pass's terms dealt out over cpack CTAs (col_run)
   int rsplit = 1;  // runs of terms per row in the (32-element) row kernel
 
   bool fused_forward() const { return fuse_fwd && !(wide_c && k.inv_cols_w); }
@@ -224,7 +225,7 @@ struct Plan2D {
     const bool wc = wide_c && k.inv_cols_w, wr = wide_r && k.inv_rows_w;
     const int cpc = wc ? k.cpc_w : k.wic * k.lpw_y;
     const int parts = cparts > 0 ? cparts : col_parts_default(ny);
-    const dim3 gic((ncols + cpc - 1) / cpc, 2 * parts);
+    const dim3 gic = cpack > 0 ? dim3(cpack) : dim3((ncols + cpc - 1) / cpc, 2 * parts);
     const int rsp = wr ? 1 : rsplit;
     const int rpc = wr ? k.rpc_w : (k.wir / rsp) * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
@@ -236,10 +237,11 @@ struct Plan2D {
       cudaError_t e;
       if (wc)
         e = launch_pdl(k.inv_cols_w, gic, dim3(k.thr_w_c), k.smem_icols_w, s, (const float2*)Uh, (const float*)P,
-                       (const float*)Lg, Z, pZ, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, (const float2*)twyw);
+                       (const float*)Lg, Z, pZ, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, cpack,
+                       (const float2*)twyw);
       else
         e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, Uh, (const float*)P,
-                       (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, (const float2*)twy,
+                       (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, cpack, (const float2*)twy,
                        (const float2*)T, pT, (ff && gi == K - 1) ? 1 : 0);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
@@ -351,6 +353,7 @@ struct Fused2D : Engine {
     p.wide_f = p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx);
     p.rsplit = row_split_default(p.nx, p.ny, p.k.wir);
     if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
+    p.cpack = col_pack_waves(p.nx, p.ny) * device_sm_count();
     if (make_line_twiddles(p.nx, p.twx, c->stream) ||
         make_line_twiddles(p.ny, p.twy, c->stream) ||
         (p.twxw && make_wide_twiddles(p.nx, p.twxw, c->stream)) ||
@@ -403,6 +406,7 @@ struct Fused2D : Engine {
     p.wide_c = wc;
     p.wide_r = wr;
     p.cparts = s->col_parts;
+    p.cpack = s->col_pack < 0 ? col_pack_waves(p.nx, p.ny) * device_sm_count() : s->col_pack;
     p.fuse_fwd = s->fuse_forward < 0 ? fuse_forward_default(p.ny) : s->fuse_forward == 1;
     p.wide_f = p.k.fwd_rows_w && (s->wide_fwd < 0 ? wide_fwd_default(p.nx) : s->wide_fwd == 1);
     p.rsplit = s->row_split == 0 ? row_split_default(p.nx, p.ny, p.k.wir) : s->row_split;
@@ -414,6 +418,7 @@ struct Fused2D : Engine {
     s->wide_cols = p.wide_c && p.k.inv_cols_w ? 1 : 0;
     s->wide_rows = p.wide_r && p.k.inv_rows_w ? 1 : 0;
     s->col_parts = p.cparts > 0 ? p.cparts : col_parts_default(p.ny);
+    s->col_pack = p.cpack;
     s->group = p.G;
     s->fuse_forward = p.fused_forward() ? 1 : 0;
     s->wide_fwd = p.wide_f && p.k.fwd_rows_w ? 1 : 0;

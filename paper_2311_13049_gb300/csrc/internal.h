@@ -320,6 +320,15 @@ int make_line_twiddles(int N, float2* d_tw, cudaStream_t s);
 // The wide line transform of N = 512 or 1024 points (fft_wide.cuh): its
 // last stage's N twiddles w_N^{r j}, then the 16 (N/64) of the middle stage.
 inline bool wide_line(int N) { return N == 512 || N == 1024; }
+// SMs of the current device (0 if it cannot be read)
+inline int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
 inline int wide_twiddle_entries(int N) { return N + (N / 64) * 16; }
 int make_wide_twiddles(int N, float2* d_tw, cudaStream_t s);
 // Tensor map of a [rows][pitch] array of 8-byte elements (ncols valid per

@@ -274,14 +274,58 @@ constexpr int icols_box_rows() {
   return NY < 256 ? NY : 256;
 }
 
+// The runs of Taylor terms one CTA of an inverse column pass transforms.  A
+// unit is (column block cb, operator slot op), numbered u = 2 cb + op; a
+// unit's group terms [m_lo, m_hi) are cut into slots of `step` terms (the
+// paired kernel transforms two terms per iteration: step 2).
+//   pack = 0: CTA (bx, yidx) owns unit (bx, yidx & 1) and run yidx >> 1 of
+//     `parts` equal runs (one run: i = 0 only; it is empty when the runs
+//     outnumber the terms);
+//   pack = K > 0: a grid of K CTAs; the slots of all 2 ncb units, in
+//     unit-major order, are dealt out evenly: CTA bx takes slots
+//     [bx U S / K, (bx + 1) U S / K), i.e. the tail of one unit's terms,
+//     whole units and the head of the next.  Every CTA then has the same
+//     number of slots to within one, where whole units per CTA leave SMs
+//     idle (a 1024-point column pass has 130 units of eight columns for
+//     152 SMs).  Run i is the CTA's i-th unit from the last: a CTA ends on
+//     the top terms of a unit where it can, as the CTAs of pack = 0 all
+//     do, and the row pass, which reads the group's terms from the top
+//     down, finds those most recently written ones in L2.
+// Every run restarts the multiplier recurrence at its first term, so the
+// bits depend on the cut (deterministic for given parts, pack and grid).
+struct ColRun {
+  int cb, op, lo, hi;
+};
+__device__ __forceinline__ bool col_run(int i, int bx, int yidx, int parts, int pack, int ncb, int m_lo, int m_hi,
+                                        int step, ColRun& r) {
+  if (pack <= 0) {
+    if (i > 0) return false;
+    const int part = yidx >> 1, per = (m_hi - m_lo + parts - 1) / parts;
+    r.cb = bx;
+    r.op = yidx & 1;
+    r.lo = m_lo + part * per;
+    r.hi = min(m_hi, r.lo + per);
+    return true;
+  }
+  const long long S = (m_hi - m_lo + step - 1) / step, US = 2LL * ncb * S;
+  const long long s0 = US * bx / pack, s1 = US * (bx + 1) / pack;
+  const long long u = (s1 - 1) / S - i;
+  if (s0 >= s1 || (u + 1) * S <= s0) return false;
+  const long long a = max(s0, u * S) - u * S, b = min(s1, (u + 1) * S) - u * S;
+  r.cb = (int)(u >> 1);
+  r.op = (int)(u & 1);
+  r.lo = m_lo + (int)a * step;
+  r.hi = min(m_hi, m_lo + (int)b * step);
+  return true;
+}
+
 template <int NY>
-// yidx = operator slot + 2 * part: the group's terms [m_lo, m_hi) are split
-// into `parts` consecutive runs, one per CTA (parts = 1: the whole group).
-// fwd = 1: the column spectra are not in Uh yet; the CTA computes them from
-// the row half spectra T (pitch pT) itself, by the arithmetic of
-// k2d_fwd_cols (so bit for bit the same), and the CTAs of operator slot 0,
-// run 0 store them to Uh for later groups.
-__device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, float2* __restrict__ Uh,
+// (bx, yidx, parts, pack): the CTA's runs of terms (col_run).
+// fwd = 1: the column spectra are not in Uh yet; every run computes them
+// from the row half spectra T (pitch pT) itself, by the arithmetic of
+// k2d_fwd_cols (so bit for bit the same), and the run of operator slot 0
+// that starts at m_lo stores them to Uh for later groups.
+__device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, int pack, float2* __restrict__ Uh,
                                               const float* __restrict__ P, const float* __restrict__ Lg,
                                               const void* zmap, int ncols, int m_lo, int m_hi, float inv_fact_lo,
                                               float inv_fact_lo1, int split_k, const float2* __restrict__ twy,
@@ -305,177 +349,182 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, float
   // ln|mu|^2 of the column: shared memory for long lines (registers are
   // short there), registers for short lines
   float* s_lg = reinterpret_cast<float*>(s_buf + 2 * SET) + (size_t)(warp * LPW + line) * NY;
-  const int c0 = bx * CW;
-  const int c = c0 + warp * LPW + line;
-  const int cc = min(c, ncols - 1);
   const long long tot = (long long)ncols * NY;
-  const float2* uh_col = Uh + (size_t)cc * NY;
-  // split_k > 0 (one operator): slot op = 1 carries the terms m + split_k of
-  // operator 1 (multiplier P[0] ln|mu|^{2(m + split_k)} / (m + split_k)!)
-  const int op = yidx & 1, part = yidx >> 1;
-  const int per = (m_hi - m_lo + parts - 1) / parts;
-  const int lo = m_lo + part * per, hi = min(m_hi, lo + per);
-  if (lo >= hi) return;  // the whole CTA, before any barrier
-  const int off = (split_k > 0 && op) ? split_k : 0;
-  const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
-  const float* l_col = Lg + (size_t)cc * NY;
-  float tm[E], lg[PAIR ? 1 : E];
-  // 1 / (lo + off)!: the group's factor advanced to this run's first term
-  float fstart = op ? inv_fact_lo1 : inv_fact_lo;
-  for (int j = m_lo + 1; j <= lo; ++j) fstart *= 1.0f / (float)(j + off);
-  // tables first (they do not depend on the previous kernel)
+  const int ncb = (ncols + CW - 1) / CW;
+  ColRun run;
+  // every condition below is uniform over the CTA (barriers inside)
+  for (int ri = 0; col_run(ri, bx, yidx, parts, pack, ncb, m_lo, m_hi, PAIR ? 2 : 1, run); ++ri) {
+    if (run.lo >= run.hi) continue;
+    const int lo = run.lo, hi = run.hi;
+    const int c0 = run.cb * CW;
+    const int c = c0 + warp * LPW + line;
+    const int cc = min(c, ncols - 1);
+    const float2* uh_col = Uh + (size_t)cc * NY;
+    // split_k > 0 (one operator): slot op = 1 carries the terms m + split_k of
+    // operator 1 (multiplier P[0] ln|mu|^{2(m + split_k)} / (m + split_k)!)
+    const int op = run.op;
+    const int off = (split_k > 0 && op) ? split_k : 0;
+    const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
+    const float* l_col = Lg + (size_t)cc * NY;
+    float tm[E], lg[PAIR ? 1 : E];
+    // 1 / (lo + off)!: the group's factor advanced to this run's first term
+    float fstart = op ? inv_fact_lo1 : inv_fact_lo;
+    for (int j = m_lo + 1; j <= lo; ++j) fstart *= 1.0f / (float)(j + off);
+    // tables first (they do not depend on the previous kernel)
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int y = li + LANES * m;
-    const float l = l_col[y];
-    if constexpr (PAIR)
-      s_lg[y] = l;
-    else
-      lg[m] = l;
-    tm[m] = p_col[y] * powi(l, lo + off) * fstart;
-  }
-  __syncthreads();
-  pdl_wait();  // Uh (k2d_fwd_cols) or T (k2d_fwd_rows) ready; the previous group's readers of Z are done
-  pdl_trigger();
-  // v = the multiplied spectrum of the current term: u_hat P ln|mu|^{2m}/m!
-  float2 v[E];
-  if (fwd) {
-    {
-      // forward stage 0 cooperatively: thread b takes column b % CW,
-      // butterfly b / CW (row segments of CW adjacent columns of T)
-      const int fc = threadIdx.x % CW, j = threadIdx.x / CW;
-      const int col = min(c0 + fc, ncols - 1);
-      float2 x[E];
-#pragma unroll
-      for (int r = 0; r < E; ++r) x[r] = T[(size_t)(j + LANES * r) * pT + col];
-      float2* lb = s_buf + (fc / LPW) * warp_stride<NY>() + (fc % LPW) * F::PAD_LINE;
-      stage0_to_smem<NY, false>(x, lb, j);
+    for (int m = 0; m < E; ++m) {
+      const int y = li + LANES * m;
+      const float l = l_col[y];
+      if constexpr (PAIR)
+        s_lg[y] = l;
+      else
+        lg[m] = l;
+      tm[m] = p_col[y] * powi(l, lo + off) * fstart;
     }
+    if (threadIdx.x == 0) bulk_wait_read_all();  // a previous run's last tiles have left shared memory
     __syncthreads();
-    mid_stage<NY, false>(lb_own, s_tw, li);
-    __syncwarp();
+    pdl_wait();  // Uh (k2d_fwd_cols) or T (k2d_fwd_rows) ready; the previous group's readers of Z are done
+    pdl_trigger();
+    // v = the multiplied spectrum of the current term: u_hat P ln|mu|^{2m}/m!
+    float2 v[E];
+    if (fwd) {
+      {
+        // forward stage 0 cooperatively: thread b takes column b % CW,
+        // butterfly b / CW (row segments of CW adjacent columns of T)
+        const int fc = threadIdx.x % CW, j = threadIdx.x / CW;
+        const int col = min(c0 + fc, ncols - 1);
+        float2 x[E];
 #pragma unroll
-    for (int q = 0; q < BPL; ++q) {
-      float2 w[RL];
-      stage1_from_smem<NY, false>(w, lb_own, s_tw, li + LANES * q);
-#pragma unroll
-      for (int r = 0; r < RL; ++r) v[q + BPL * r] = w[r];
-    }
-    if (op == 0 && part == 0 && c < ncols) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) Uh[(size_t)c * NY + li + LANES * m] = v[m];
-    }
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], tm[m]);
-  } else {
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
-  }
-  // v <- v ln|mu|^2 / (m + 1): the next term
-  auto advance = [&](int mt) {
-    const float rinv = 1.0f / (float)(mt + 1 + off);
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], (PAIR ? s_lg[li + LANES * m] : lg[m]) * rinv);
-  };
-  // last stage of exchange set `set`, cooperatively: thread b takes column
-  // b % CW, butterfly b / CW; results in registers
-  auto last_read = [&](int set, float2 (&w)[BPL][RL]) {
-#pragma unroll
-    for (int q = 0; q < BPL; ++q) {
-      const int b = threadIdx.x + THREADS * q;
-      const int sc = b % CW, sj = b / CW;
-      const float2* lb = s_buf + set * SET + (sc / LPW) * warp_stride<NY>() + (sc % LPW) * F::PAD_LINE;
-      stage1_from_smem<NY, true>(w[q], lb, s_tw, sj);
-    }
-  };
-  // ... written back into the (fully read) set as the output tile
-  // [NY rows][CW columns], made visible to the tensor-copy unit
-  auto tile_write = [&](int set, const float2 (&w)[BPL][RL]) {
-    float2* tile = s_buf + set * SET;
-#pragma unroll
-    for (int q = 0; q < BPL; ++q) {
-      const int b = threadIdx.x + THREADS * q;
-      const int sc = b % CW, sj = b / CW;
-#pragma unroll
-      for (int r = 0; r < RL; ++r) tile[(sj + F::NBL * r) * CW + sc] = w[q][r];
-    }
-    fence_proxy_async_smem();
-  };
-  // one thread stores the tile of `set` to Z slot (mt - m_lo) of operator op
-  // (rows (slot * 2 + op) * NY .. + NY, columns c0 .. c0 + CW; columns past
-  // ncols are clipped by the copy unit)
-  auto tile_store = [&](int set, int mt) {
-    const int y0 = ((mt - m_lo) * 2 + op) * NY;
-#pragma unroll
-    for (int k = 0; k < NY / BOXR; ++k) tma_store_2d(zmap, c0, y0 + k * BOXR, s_buf + set * SET + k * BOXR * CW);
-  };
-  int mt = lo;
-  // two terms per iteration: two independent register transforms in flight;
-  // an odd last term runs through the same code with its partner computed
-  // and not stored (one copy of the unrolled term code: the kernel's
-  // instruction footprint, not its arithmetic, limited it)
-  for (; PAIR && mt < hi; mt += 2) {
-    const bool two = mt + 1 < hi;
-    float2 xa[E], xb[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) xa[m] = v[m];
-    advance(mt);
-#pragma unroll
-    for (int m = 0; m < E; ++m) xb[m] = v[m];
-    dft<E, true>(xa);
-    dft<E, true>(xb);
-    if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tiles have left shared memory
-    __syncthreads();
-    stage0_write<NY>(xa, lb_own, li);
-    stage0_write<NY>(xb, lb_own + SET, li);
-    mid_stage<NY, true>(lb_own, s_tw, li);
-    mid_stage<NY, true>(lb_own + SET, s_tw, li);
-    __syncthreads();
-    {
-      float2 w[BPL][RL];
-      last_read(0, w);
+        for (int r = 0; r < E; ++r) x[r] = T[(size_t)(j + LANES * r) * pT + col];
+        float2* lb = s_buf + (fc / LPW) * warp_stride<NY>() + (fc % LPW) * F::PAD_LINE;
+        stage0_to_smem<NY, false>(x, lb, j);
+      }
       __syncthreads();
-      tile_write(0, w);
-    }
-    {
-      float2 w[BPL][RL];
-      last_read(1, w);
-      __syncthreads();
-      tile_write(1, w);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tile_store(0, mt);
-      if (two) tile_store(1, mt + 1);
-      bulk_commit();
-    }
-    if (mt + 2 < hi) advance(mt + 1);
-  }
-  if (!PAIR) {
-    // short lines: one term per iteration (a separate loop: sharing it with
-    // the odd last term above made the paired form markedly slower)
-    for (; mt < hi; ++mt) {
-      float2 x[E];
+      mid_stage<NY, false>(lb_own, s_tw, li);
+      __syncwarp();
 #pragma unroll
-      for (int m = 0; m < E; ++m) x[m] = v[m];
-      dft<E, true>(x);
-      if (threadIdx.x == 0) bulk_wait_read_all();
+      for (int q = 0; q < BPL; ++q) {
+        float2 w[RL];
+        stage1_from_smem<NY, false>(w, lb_own, s_tw, li + LANES * q);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[q + BPL * r] = w[r];
+      }
+      if (op == 0 && lo == m_lo && c < ncols) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) Uh[(size_t)c * NY + li + LANES * m] = v[m];
+      }
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = cscale(v[m], tm[m]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
+    }
+    // v <- v ln|mu|^2 / (m + 1): the next term
+    auto advance = [&](int mt) {
+      const float rinv = 1.0f / (float)(mt + 1 + off);
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = cscale(v[m], (PAIR ? s_lg[li + LANES * m] : lg[m]) * rinv);
+    };
+    // last stage of exchange set `set`, cooperatively: thread b takes column
+    // b % CW, butterfly b / CW; results in registers
+    auto last_read = [&](int set, float2 (&w)[BPL][RL]) {
+#pragma unroll
+      for (int q = 0; q < BPL; ++q) {
+        const int b = threadIdx.x + THREADS * q;
+        const int sc = b % CW, sj = b / CW;
+        const float2* lb = s_buf + set * SET + (sc / LPW) * warp_stride<NY>() + (sc % LPW) * F::PAD_LINE;
+        stage1_from_smem<NY, true>(w[q], lb, s_tw, sj);
+      }
+    };
+    // ... written back into the (fully read) set as the output tile
+    // [NY rows][CW columns], made visible to the tensor-copy unit
+    auto tile_write = [&](int set, const float2 (&w)[BPL][RL]) {
+      float2* tile = s_buf + set * SET;
+#pragma unroll
+      for (int q = 0; q < BPL; ++q) {
+        const int b = threadIdx.x + THREADS * q;
+        const int sc = b % CW, sj = b / CW;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) tile[(sj + F::NBL * r) * CW + sc] = w[q][r];
+      }
+      fence_proxy_async_smem();
+    };
+    // one thread stores the tile of `set` to Z slot (mt - m_lo) of operator op
+    // (rows (slot * 2 + op) * NY .. + NY, columns c0 .. c0 + CW; columns past
+    // ncols are clipped by the copy unit)
+    auto tile_store = [&](int set, int mt) {
+      const int y0 = ((mt - m_lo) * 2 + op) * NY;
+#pragma unroll
+      for (int k = 0; k < NY / BOXR; ++k) tma_store_2d(zmap, c0, y0 + k * BOXR, s_buf + set * SET + k * BOXR * CW);
+    };
+    int mt = lo;
+    // two terms per iteration: two independent register transforms in flight;
+    // an odd last term runs through the same code with its partner computed
+    // and not stored (one copy of the unrolled term code: the kernel's
+    // instruction footprint, not its arithmetic, limited it)
+    for (; PAIR && mt < hi; mt += 2) {
+      const bool two = mt + 1 < hi;
+      float2 xa[E], xb[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) xa[m] = v[m];
+      advance(mt);
+#pragma unroll
+      for (int m = 0; m < E; ++m) xb[m] = v[m];
+      dft<E, true>(xa);
+      dft<E, true>(xb);
+      if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tiles have left shared memory
       __syncthreads();
-      stage0_write<NY>(x, lb_own, li);
+      stage0_write<NY>(xa, lb_own, li);
+      stage0_write<NY>(xb, lb_own + SET, li);
       mid_stage<NY, true>(lb_own, s_tw, li);
+      mid_stage<NY, true>(lb_own + SET, s_tw, li);
       __syncthreads();
-      float2 w[BPL][RL];
-      last_read(0, w);
-      __syncthreads();
-      tile_write(0, w);
+      {
+        float2 w[BPL][RL];
+        last_read(0, w);
+        __syncthreads();
+        tile_write(0, w);
+      }
+      {
+        float2 w[BPL][RL];
+        last_read(1, w);
+        __syncthreads();
+        tile_write(1, w);
+      }
       __syncthreads();
       if (threadIdx.x == 0) {
         tile_store(0, mt);
+        if (two) tile_store(1, mt + 1);
         bulk_commit();
       }
-      if (mt + 1 < hi) advance(mt);
+      if (mt + 2 < hi) advance(mt + 1);
     }
-  }
+    if (!PAIR) {
+      // short lines: one term per iteration (a separate loop: sharing it with
+      // the odd last term above made the paired form markedly slower)
+      for (; mt < hi; ++mt) {
+        float2 x[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) x[m] = v[m];
+        dft<E, true>(x);
+        if (threadIdx.x == 0) bulk_wait_read_all();
+        __syncthreads();
+        stage0_write<NY>(x, lb_own, li);
+        mid_stage<NY, true>(lb_own, s_tw, li);
+        __syncthreads();
+        float2 w[BPL][RL];
+        last_read(0, w);
+        __syncthreads();
+        tile_write(0, w);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tile_store(0, mt);
+          bulk_commit();
+        }
+        if (mt + 1 < hi) advance(mt);
+      }
+    }
+  }  // runs
   if (threadIdx.x == 0) bulk_wait_all();  // stores complete before the CTA's shared memory goes
 }
 
@@ -485,9 +534,9 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(float2* _
                                                            const __grid_constant__ CUtensorMap zmap, int ncols,
                                                            int m_lo, int m_hi, float inv_fact_lo,
                                                            float inv_fact_lo1, int split_k, int parts,
-                                                           const float2* __restrict__ twy,
+                                                           int pack, const float2* __restrict__ twy,
                                                            const float2* __restrict__ T, int pT, int fwd) {
-  inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, inv_fact_lo1,
+  inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, pack, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, inv_fact_lo1,
                     split_k, twy, T, pT, fwd);
 }
 

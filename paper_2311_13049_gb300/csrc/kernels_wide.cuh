@@ -57,6 +57,20 @@ inline bool fuse_forward_default(int ny) { return ny <= 256; }
 // Runs of terms per group in the column pass (each on its own CTAs): small
 // grids have fewer column blocks than SMs.
 inline int col_parts_default(int ny) { return ny <= 256 ? 3 : (ny <= 512 ? 6 : 1); }
+// The group's terms of all column blocks dealt out evenly over `waves`
+// times the SM count CTAs (col_run, pack > 0) instead of whole column
+// blocks (and col_parts runs) per CTA; 0 = not.  Measured per leap-frog
+// step, M = 16: 128^2 one CTA per SM, 0.0225 -> 0.0195 ms; 512^2 (wide
+// columns, eight warps a CTA) one per SM, 0.0594 -> 0.0483 ms, where two
+// per SM measured 0.0635 (one column CTA per SM leaves room for the row
+// kernel's CTAs to start early); 768^2 (four-warp CTAs) two per SM, 0.1095
+// -> 0.1006 ms; no gain at 256^2 (0.0246 either way) nor at 1024^2
+// (0.1164 vs 0.1158: the 17-term launch's 145 MB of column transforms,
+// not idle SMs, set its time).
+inline int col_pack_waves(int nx, int ny) {
+  if (nx != ny) return 0;
+  return (nx == 128 || nx == 512) ? 1 : nx == 768 ? 2 : 0;
+}
 
 // Lines per CTA: eight columns (the cooperative last stage stores 64-byte
 // row segments, whole L2 sectors: seven columns' 56-byte segments left
@@ -117,14 +131,14 @@ constexpr size_t wide_rows_smem() {
 
 // -------------------------------------------------------------------------
 // I1 (wide): multiplier + inverse FFT along y of L columns of one operator
-// (yidx = operator slot + 2 * part), terms [lo, hi) of the group [m_lo,
-// m_hi) (the group split into `parts` runs as in inv_cols_body).  Stages 0
-// and 1 by the column's own lanes; stage 2 cooperatively (thread b: column
-// b % L, butterfly b / L), whose outputs are row segments of L adjacent
-// columns stored straight to Z[slot][op][y][c].
+// for the CTA's runs of terms of the group [m_lo, m_hi) (col_run: runs of
+// `parts` per unit, or the units' terms dealt out over `pack` CTAs).
+// Stages 0 and 1 by the column's own lanes; stage 2 cooperatively (thread
+// b: column b % L, butterfly b / L), whose outputs are row segments of L
+// adjacent columns stored straight to Z[slot][op][y][c].
 // -------------------------------------------------------------------------
 template <int NY>
-__device__ __forceinline__ void inv_cols_wide_body(int bx, int yidx, int parts, const float2* __restrict__ Uh,
+__device__ __forceinline__ void inv_cols_wide_body(int bx, int yidx, int parts, int pack, const float2* __restrict__ Uh,
                                                    const float* __restrict__ P, const float* __restrict__ Lg,
                                                    float2* __restrict__ Z, int pZ, int ncols, int m_lo, int m_hi,
                                                    float inv_fact_lo, float inv_fact_lo1, int split_k,
@@ -138,62 +152,65 @@ __device__ __forceinline__ void inv_cols_wide_body(int bx, int yidx, int parts, 
   const int line = threadIdx.x / LANES, li = threadIdx.x % LANES;
   float2* A = s_buf + (size_t)line * LS;
   float2* B = A + F::PAD_LINE;
-  const int c0 = bx * CW;
-  const int cc = min(c0 + line, ncols - 1);
   const long long tot = (long long)ncols * NY;
-  const int op = yidx & 1, part = yidx >> 1;
-  const int per = (m_hi - m_lo + parts - 1) / parts;
-  const int lo = m_lo + part * per, hi = min(m_hi, lo + per);
-  if (lo >= hi) return;  // the whole CTA, before any barrier
-  const int off = (split_k > 0 && op) ? split_k : 0;
-  const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
-  const float* l_col = Lg + (size_t)cc * NY;
-  const float2* uh_col = Uh + (size_t)cc * NY;
-  float fstart = op ? inv_fact_lo1 : inv_fact_lo;
-  for (int j = m_lo + 1; j <= lo; ++j) fstart *= 1.0f / (float)(j + off);
-  // tables first (they do not depend on the previous kernel)
-  float lg[16], tm[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int y = li + LANES * m;
-    lg[m] = l_col[y];
-    tm[m] = p_col[y] * powi(lg[m], lo + off) * fstart;
-  }
+  const int ncb = (ncols + CW - 1) / CW;
   // this thread's cooperative stage-2 butterflies: line sc, butterflies
   // sj0 + LANES q (q < 4); rows sj0 + LANES q + NB2 r of column c0 + sc
   const int sc = threadIdx.x % CW, sj0 = threadIdx.x / CW;
-  const bool store = c0 + sc < ncols;
   const float2* Bc = s_buf + (size_t)sc * LS + F::PAD_LINE;
-  __syncthreads();
-  pdl_wait();  // Uh ready; the previous group's readers of Z are done
-  pdl_trigger();
-  float2 v[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
-  float2* zcol = Z + (size_t)op * NY * pZ + (size_t)sj0 * pZ + c0 + sc;
   const size_t zslot2 = (size_t)2 * NY * pZ;  // one term: both operators' slots
-  for (int mt = lo; mt < hi; ++mt) {
-    float2 x[16];
+  ColRun run;
+  // every condition below is uniform over the CTA (barriers inside)
+  for (int ri = 0; col_run(ri, bx, yidx, parts, pack, ncb, m_lo, m_hi, 1, run); ++ri) {
+    if (run.lo >= run.hi) continue;
+    const int lo = run.lo, hi = run.hi, op = run.op;
+    const int c0 = run.cb * CW;
+    const int cc = min(c0 + line, ncols - 1);
+    const int off = (split_k > 0 && op) ? split_k : 0;
+    const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
+    const float* l_col = Lg + (size_t)cc * NY;
+    const float2* uh_col = Uh + (size_t)cc * NY;
+    float fstart = op ? inv_fact_lo1 : inv_fact_lo;
+    for (int j = m_lo + 1; j <= lo; ++j) fstart *= 1.0f / (float)(j + off);
+    // tables first (they do not depend on the previous kernel)
+    float lg[16], tm[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) x[m] = v[m];
-    wide_stage0<NY, true>(x, A, li);
-    __syncthreads();  // A complete; every thread's previous stage-2 reads of B done
-    wide_stage1<NY, true>(A, B, s_tw, li);
-    __syncthreads();  // every column's B complete
-    float2* zt = zcol + (size_t)(mt - m_lo) * zslot2;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float2 w[4];
-      wide_stage2_bfly<NY, true>(w, Bc, s_tw, sj0 + LANES * q);
-      if (store) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) zt[(size_t)(LANES * q + NB2 * r) * pZ] = w[r];
-      }
+    for (int m = 0; m < 16; ++m) {
+      const int y = li + LANES * m;
+      lg[m] = l_col[y];
+      tm[m] = p_col[y] * powi(lg[m], lo + off) * fstart;
     }
-    if (mt + 1 < hi) {
-      const float rinv = 1.0f / (float)(mt + 1 + off);
+    const bool store = c0 + sc < ncols;
+    __syncthreads();  // twiddles; every thread's stage-2 reads of a previous run done
+    pdl_wait();       // Uh ready; the previous group's readers of Z are done
+    pdl_trigger();
+    float2 v[16];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[m] = cscale(v[m], lg[m] * rinv);
+    for (int m = 0; m < 16; ++m) v[m] = cscale(uh_col[li + LANES * m], tm[m]);
+    float2* zcol = Z + (size_t)op * NY * pZ + (size_t)sj0 * pZ + c0 + sc;
+    for (int mt = lo; mt < hi; ++mt) {
+      float2 x[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) x[m] = v[m];
+      wide_stage0<NY, true>(x, A, li);
+      __syncthreads();  // A complete; every thread's previous stage-2 reads of B done
+      wide_stage1<NY, true>(A, B, s_tw, li);
+      __syncthreads();  // every column's B complete
+      float2* zt = zcol + (size_t)(mt - m_lo) * zslot2;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 w[4];
+        wide_stage2_bfly<NY, true>(w, Bc, s_tw, sj0 + LANES * q);
+        if (store) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) zt[(size_t)(LANES * q + NB2 * r) * pZ] = w[r];
+        }
+      }
+      if (mt + 1 < hi) {
+        const float rinv = 1.0f / (float)(mt + 1 + off);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = cscale(v[m], lg[m] * rinv);
+      }
     }
   }
 }
@@ -202,8 +219,8 @@ template <int NY>
 __global__ void __launch_bounds__(wide_threads<NY>(), wide_min_blocks<NY>())
     k2d_inv_cols_w(const float2* __restrict__ Uh, const float* __restrict__ P, const float* __restrict__ Lg,
                    float2* __restrict__ Z, int pZ, int ncols, int m_lo, int m_hi, float inv_fact_lo,
-                   float inv_fact_lo1, int split_k, int parts, const float2* __restrict__ twy) {
-  inv_cols_wide_body<NY>(blockIdx.x, blockIdx.y, parts, Uh, P, Lg, Z, pZ, ncols, m_lo, m_hi, inv_fact_lo,
+                   float inv_fact_lo1, int split_k, int parts, int pack, const float2* __restrict__ twy) {
+  inv_cols_wide_body<NY>(blockIdx.x, blockIdx.y, parts, pack, Uh, P, Lg, Z, pZ, ncols, m_lo, m_hi, inv_fact_lo,
                          inv_fact_lo1, split_k, twy);
 }
 

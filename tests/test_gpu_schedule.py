@@ -15,10 +15,16 @@ pytestmark = pytest.mark.gpu
 TOL32 = 1e-5
 
 # (wide_cols, wide_rows, col_parts, group, fuse_forward, wide_fwd,
-# row_split): -1 / 0 = the size's default
-SCHEDULES = [(-1, -1, 0, 0, -1, -1, 0), (0, 0, 0, 0, 0, 0, 0), (1, 1, 0, 0, -1, 1, 0), (1, 0, 2, 6, 1, 0, 0),
-             (0, 1, 1, 3, 1, 1, 0), (-1, -1, 6, 17, 0, 0, 0), (-1, -1, 3, 4, 1, -1, 0), (0, 0, 1, 1, 1, 0, 0),
-             (0, 0, 2, 17, 1, 1, 0)]
+# row_split, col_pack): -1 / 0 = the size's default
+SCHEDULES = [(-1, -1, 0, 0, -1, -1, 0, -1), (0, 0, 0, 0, 0, 0, 0, 0), (1, 1, 0, 0, -1, 1, 0, 0),
+             (1, 0, 2, 6, 1, 0, 0, 0), (0, 1, 1, 3, 1, 1, 0, 0), (-1, -1, 6, 17, 0, 0, 0, 0),
+             (-1, -1, 3, 4, 1, -1, 0, 0), (0, 0, 1, 1, 1, 0, 0, 0), (0, 0, 2, 17, 1, 1, 0, 0),
+             # the column pass's terms dealt out over K CTAs: one CTA, a
+             # wave, more CTAs than slots, several groups, the forward
+             # column transform in the same kernel, wide columns
+             (0, -1, 0, 0, 0, -1, 0, 1), (0, -1, 0, 0, 0, -1, 0, 152), (0, -1, 0, 0, 0, -1, 0, 5000),
+             (0, -1, 0, 5, 0, -1, 0, 37), (0, -1, 0, 0, 1, -1, 0, 152), (0, -1, 0, 6, 1, -1, 0, 300),
+             (1, -1, 0, 0, -1, -1, 0, 152), (1, -1, 0, 4, -1, -1, 0, 61)]
 
 
 @pytest.mark.parametrize("n", [512, 1024])
@@ -40,6 +46,8 @@ def test_every_schedule_matches_the_oracle(V, n):
                 assert got["col_parts"] == sc[2]
             if sc[3] > 0:
                 assert got["group"] == sc[3]
+            if sc[7] >= 0:
+                assert got["col_pack"] == sc[7]
             o1, o2 = torch.empty_like(ut), torch.empty_like(ut)
             s.apply_pair(ut, o1, o2)
             s.sync()
@@ -48,6 +56,7 @@ def test_every_schedule_matches_the_oracle(V, n):
 
 
 def test_default_schedules(V):
+    import torch
     base = {"group": 17, "wide_cols": 0, "wide_rows": 0, "fuse_forward": 0, "wide_fwd": 0, "row_split": 1}
     want = {256: dict(base, col_parts=3, fuse_forward=1, row_split=4),
             512: dict(base, col_parts=6, wide_cols=1, wide_rows=1),
@@ -55,10 +64,15 @@ def test_default_schedules(V):
             1024: dict(base, col_parts=1, wide_rows=1, wide_fwd=1)}
     for n, w in want.items():
         with V.Solver((n, n)) as s:
-            assert s.schedule() == w, (n, s.schedule())
-            s.set_schedule(1, 1, 2, 5, 0, 0)
+            got = s.schedule()
+            # the column pass's terms over one CTA per SM at 512, two at 768
+            pack = got.pop("col_pack")
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            assert pack == {256: 0, 512: sms, 768: 2 * sms, 1024: 0}[n], (n, pack)
+            assert got == w, (n, got)
+            s.set_schedule(1, 1, 2, 5, 0, 0, 0, 7)
             s.set_schedule()  # back to the defaults
-            assert s.schedule() == w
+            assert s.schedule() == dict(w, col_pack=pack)
 
 
 def test_schedule_runs_agree_and_batch_needs_one_schedule_per_size(V):
@@ -184,7 +198,7 @@ def test_batch_transform_tuning_keeps_members_equal_to_solo(V):
         sc = s.schedule()
         solo = make(n, seed)
         solo.set_schedule(sc["wide_cols"], sc["wide_rows"], sc["col_parts"], sc["group"], -1, sc["wide_fwd"],
-                          sc["row_split"])
+                          sc["row_split"], sc["col_pack"])
         solo.step(nsteps, dt)
         assert np.array_equal(solo.get_state().astype(np.float64), got), (n, sc)
         solo.close()
@@ -193,3 +207,38 @@ def test_batch_transform_tuning_keeps_members_equal_to_solo(V):
         check(got, ref.get_state().astype(np.float64), 1e-4, (n, sc))
         ref.close()
         s.close()
+
+
+@pytest.mark.parametrize("n,wide,units", [(1024, 0, 130), (512, 1, 66)])
+def test_pack_of_one_unit_per_cta_is_bit_identical(V, n, wide, units):
+    """col_pack = the number of (column block, operator) units deals each
+    CTA exactly one unit's terms: the same runs, so the same bits, as one
+    CTA per unit (col_parts = 1).  1024: eight 32-element columns per CTA,
+    65 blocks; 512: eight wide columns per CTA, 33 blocks; M = 16 in one
+    group of 17, for the seismic pair and the general model's one operator."""
+    import torch
+    shape = (n, n)
+    Q = S.q_lowpass(shape, 61)
+    u = torch.from_numpy(S.q_lowpass(shape, 62, qmin=-1.0, qmax=1.0, sigma_k=32).astype(np.float32)).cuda()
+    x, y = S.mesh(shape)
+    order = 1.0 - 0.3 * np.cos(x) * np.sin(y)
+    with V.Solver(shape) as s:
+        s.set_q(Q)
+        s.set_M(16)
+        outs = {}
+        for pack in (0, units):
+            s.set_schedule(wide, -1, 1, 17, 0, -1, 0, pack)
+            o1, o2 = torch.empty_like(u), torch.empty_like(u)
+            s.apply_pair(u, o1, o2)
+            s.sync()
+            outs[pack] = (o1.cpu().numpy(), o2.cpu().numpy())
+        assert np.array_equal(outs[0][0], outs[units][0]) and np.array_equal(outs[0][1], outs[units][1])
+        s.set_order(order)
+        gen = {}
+        for pack in (0, units):
+            s.set_schedule(wide, -1, 1, 17, 0, -1, 0, pack)
+            o = torch.empty_like(u)
+            s.apply(V.OP_S, u, o)
+            s.sync()
+            gen[pack] = o.cpu().numpy()
+        assert np.array_equal(gen[0], gen[units])
