@@ -384,6 +384,7 @@ def configs_bench(V, torch, stream, flush, reps=3):
     out["general_table3_s1_1d_4096_f64"] = table3_bench(V, S, stream)
     out["cnfp_table2_s1_1d_4096_f64"] = cnfp_bench(V, S, stream)
     out["generic_apply_2d_512_M20_f32"] = generic_apply_bench(V, S, torch, stream)
+    out["tsfp2_2d_1024_M16_f32"] = tsfp2_2d_bench(V, S, torch, stream)
     w3 = S.workload_3d_256()
     f, p = run(w3, V.F32, V.IMPL_FUSED), run(w3, V.F32, V.IMPL_PLAIN)
     out["3d_256_f32"] = {"workload": "3D 256^3, FP32, M=8, two-layer Q (10/80), Gaussian pulse sigma = 4 cells, "
@@ -510,6 +511,56 @@ def generic_apply_bench(V, S, torch, stream, reps=20):
             ms = e0.elapsed_time(e1) / reps
         res[nm] = {"ms_per_apply": ms, "value": 512 * 512 / (ms * 1e-3) / 1e6, "unit": "Mpoint/s"}
     res["fused_over_plain"] = res["plain"]["ms_per_apply"] / res["fused"]["ms_per_apply"]
+    return res
+
+
+def tsfp2_2d_bench(V, S, torch, stream, nsteps=100):
+    """The time splitting (Sec. 3.3) of the general model in 2D: 1024^2 on
+    [-8,8]^2, s = 1 - 0.4 cos(pi x/4) cos(pi y/4), kappa = 1, f(u) = u^3,
+    M = 16, dt = 0.25 x the explicit limit 2 / omega_max (vofl_suggest_dt;
+    the kick is explicit), u0 a Gaussian (sigma = 1), v0 = 0; fused FP32 and
+    plain FP32 (cuFFT), CUDA events over `nsteps` steps after a warm-up run;
+    accuracy of both against the plain FP64 run (vofl_rel_l2)."""
+    shape, lo, hi = (1024, 1024), [-8.0, -8.0], [8.0, 8.0]
+    xg, yg = S.mesh(shape, lo, hi)
+    so = 1.0 - 0.4 * np.cos(np.pi * xg / 4) * np.cos(np.pi * yg / 4)
+    u0 = np.exp(-(xg ** 2 + yg ** 2) / 2.0)
+    M = 16
+    with V.Solver(shape, lo, hi) as sv:
+        sv.set_order(so, kappa=1.0, f3=1.0)
+        dt = sv.suggest_dt(0.25)
+    res, finals = {}, {}
+    for nm, im, prec in (("fused", V.IMPL_FUSED, V.F32), ("plain", V.IMPL_PLAIN, V.F32),
+                         ("plain_f64", V.IMPL_PLAIN, V.F64)):
+        ty = torch.float32 if prec == V.F32 else torch.float64
+        u0t = torch.from_numpy(u0).to(ty).cuda()
+        sv = V.Solver(shape, lo, hi, prec, im, stream=stream.cuda_stream)
+        sv.set_order(so, kappa=1.0, f3=1.0)
+        sv.set_M(M)
+        sv.set_scheme(V.SCHEME_TSFP2)
+        with torch.cuda.stream(stream):
+            sv.set_state(u0t)
+            sv.step(3, dt)  # warm-up (tables, graphs)
+            sv.set_state(u0t)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.step(nsteps, dt)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        finals[nm] = (sv, torch.empty_like(u0t))
+        sv.get_state(finals[nm][1])
+        sv.sync()
+        res[nm] = {"ms_per_step": ms, "value": shape[0] * shape[1] / (ms * 1e-3) / 1e6, "unit": UNIT}
+    ref_sv, ref = finals["plain_f64"]
+    for nm in ("fused", "plain"):
+        res[nm]["rel_l2_vs_plain_f64"] = ref_sv.rel_l2(finals[nm][1], ref)[0]
+    for sv, _ in finals.values():
+        sv.close()
+    res["fused_over_plain"] = res["plain"]["ms_per_step"] / res["fused"]["ms_per_step"]
+    res["workload"] = ("1024^2 on [-8,8]^2, s = 1 - 0.4 cos(pi x/4) cos(pi y/4), kappa = 1, f(u) = u^3, M = 16, "
+                       f"dt = {dt:.4g} (0.25 x 2/omega_max), Gaussian u0, v0 = 0, {nsteps} splitting steps")
     return res
 
 

@@ -75,9 +75,9 @@ typedef enum {
 } vofl_op;
 
 /* Time stepping of vofl_step: the leap-frog scheme (Eq. (3.4); both
- * models), the second-order time splitting of Sec. 3.3 or the
- * Crank-Nicolson scheme of Sec. 3.1 (these two: general model only, plain
- * path). */
+ * models), the second-order time splitting of Sec. 3.3 (general model;
+ * plain path, or the fused FP32 2D path) or the Crank-Nicolson scheme of
+ * Sec. 3.1 (general model, plain path). */
 typedef enum {
   VOFL_SCHEME_LFFP = 0,
   VOFL_SCHEME_TSFP2 = 1,
@@ -135,7 +135,10 @@ VOFL_API int vofl_set_gamma(vofl_ctx* ctx, const double* gamma, const double* c0
  * m = 1..M of Eq. (2.13)), and repeats the half rotation; the state is
  * (u, v) with v^0 = the v0 of vofl_set_state, and no point source is
  * applied.  It needs the general model (vofl_set_order) and the plain
- * path (VOFL_IMPL_PLAIN), else vofl_step returns VOFL_EUNSUPPORTED.
+ * path (VOFL_IMPL_PLAIN) or a fused FP32 2D context, else vofl_step
+ * returns VOFL_EUNSUPPORTED.  On the fused 2D path the rotations run on
+ * its own line transforms in FP32 and the m >= 1 terms on the operator
+ * kernels (one operator, Taylor groups of the transform schedule).
  * The Crank-Nicolson scheme (Sec. 3.1, Eq. (3.2)) takes the explicit start
  * step of Eq. (3.3) (that of the leap-frog scheme), then for n >= 1 solves
  *     u^{n+1} + c L u^{n+1} - h f(u^{n+1})
@@ -143,8 +146,8 @@ VOFL_API int vofl_set_gamma(vofl_ctx* ctx, const double* gamma, const double* c0
  * c = kappa dt^2/2, h = dt^2/2, L the operator of Eq. (2.13), by a
  * fixed-point iteration on f around conjugate gradients on the normal
  * equations of A = I + c L (A is not symmetric when s varies), to the
- * tolerance of vofl_set_solver.  It has the same requirements and takes
- * no point source (vofl_step returns VOFL_EUNSUPPORTED while one is set).
+ * tolerance of vofl_set_solver.  It needs the general model and the plain
+ * path, and takes no point source (vofl_step returns VOFL_EUNSUPPORTED while one is set).
  * Returns VOFL_OK, VOFL_EINVAL (unknown scheme) or VOFL_ESTATE (a run is
  * in progress: set the state first). */
 VOFL_API int vofl_set_scheme(vofl_ctx* ctx, int scheme);
@@ -291,7 +294,8 @@ VOFL_API int vofl_profile_kernels(vofl_ctx* ctx, int reps, char* names_out,
  * argument), on the GPU with FP64 accumulation and a fixed reduction order:
  *   out[0] = ||x - y||_2 / ||y||_2,   out[1] = max|x - y| / max|y|,
  *   out[2] = ||y||_2,                 out[3] = max|y|
- * (a ratio is 0 when x = y = 0 and +inf when only y is zero).  Runs on the
+ * (a ratio is 0 when x = y = 0 and +inf when only y is zero; the ratios
+ * and the maxima are NaN when either field holds a NaN).  Runs on the
  * context stream after its queued work and waits for the result.  Uses the
  * context's reduction scratch; needs no model or state.  Returns VOFL_OK,
  * VOFL_EINVAL or VOFL_ECUDA. */

@@ -471,7 +471,8 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
   if (nsteps < 0) return set_err(c, VOFL_EINVAL, "bad nsteps");
   if (c->scheme == VOFL_SCHEME_TSFP2) {
     if (!c->general || !c->eng->can_split())
-      return set_err(c, VOFL_EUNSUPPORTED, "the time splitting needs the general model and the plain path");
+      return set_err(c, VOFL_EUNSUPPORTED,
+                     "the time splitting needs the general model and the plain path or the fused 2D path");
     if (!c->model_set || !c->state_set) return set_err(c, VOFL_ESTATE, "set the model and the state first");
     if (!(dt > 0) || !std::isfinite(dt)) return set_err(c, VOFL_EINVAL, "bad dt");
     if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");

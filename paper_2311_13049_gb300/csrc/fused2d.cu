@@ -46,6 +46,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "kernels_split.cuh"
 #include "kernels_wide.cuh"
 
 namespace vofl {
@@ -59,11 +60,11 @@ struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*inv_cols)(float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int, int,
-                   const float2*, const float2*, int, int);
+                   const float2*, const float2*, int, int, int);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
                            EpiArgs<float>, float, const float2*, int*, int);
   using InvColsW = void (*)(const float2*, const float*, const float*, float2*, int, int, int, int, float, float, int,
-                            int, int, const float2*);
+                            int, int, const float2*, int);
   InvRows inv_rows;        // two operators
   InvRows inv_rows_split;  // one operator, terms split over the slots
   // wide line transforms (fft_wide.cuh) of the inverse passes, for lines of
@@ -78,6 +79,11 @@ struct Kernels {
   int wic;  // warps per CTA of inv_cols
   int wir;  // warps (rows) per CTA of inv_rows
   int cpc_w = 0, rpc_w = 0, thr_w_c = 0, thr_w_r = 0;  // lines per CTA / threads of the wide kernels
+  // the exact flow of the time splitting (kernels_split.cuh)
+  void (*rot_rows)(const float*, const float*, float2*, float2*, int, int, const float2*);
+  void (*rot_cols)(const float2*, const float2*, const float*, float, float, float2*, float2*, int, int, const float2*);
+  void (*rot_irows)(const float2*, const float2*, float*, float*, int, int, const float2*);
+  size_t smem_rot_rows, smem_rot_cols;
 };
 
 // warps per CTA of the inverse row kernel: 7 at 1024^2 (147 CTAs, one per
@@ -105,6 +111,11 @@ Kernels kernels_for() {
   k.lpw_x = LineFFT<NX>::LPW;
   k.lpw_y = LineFFT<NY>::LPW;
   k.wic = icols_warps<NY>();
+  k.rot_rows = k2d_rot_fwd_rows<NX>;
+  k.rot_cols = k2d_rot_cols<NY>;
+  k.rot_irows = k2d_rot_inv_rows<NX>;
+  k.smem_rot_rows = rot_rows_smem<NX>();
+  k.smem_rot_cols = rot_cols_smem<NY>();
   if constexpr (NY == 512 || NY == 1024) {
     k.inv_cols_w = k2d_inv_cols_w<NY>;
     k.smem_icols_w = wide_cols_smem<NY>();
@@ -154,7 +165,9 @@ int set_smem_attributes(const Kernels& k) {
       (k.inv_cols_w && set_kernel_smem(k.inv_cols_w, k.smem_icols_w)) ||
       (k.inv_rows_w && (set_kernel_smem(k.inv_rows_w, k.smem_irows_w) ||
                         set_kernel_smem(k.inv_rows_w_split, k.smem_irows_w))) ||
-      (k.fwd_rows_w && set_kernel_smem(k.fwd_rows_w, k.smem_frows_w))) {
+      (k.fwd_rows_w && set_kernel_smem(k.fwd_rows_w, k.smem_frows_w)) ||
+      set_kernel_smem(k.rot_rows, k.smem_rot_rows) || set_kernel_smem(k.rot_irows, k.smem_rot_rows) ||
+      set_kernel_smem(k.rot_cols, k.smem_rot_cols)) {
     cudaGetLastError();
     return VOFL_ECUDA;
   }
@@ -172,6 +185,7 @@ struct Plan2D {
   float* Lg = nullptr;    // [ncols][ny]
   float2 *twx = nullptr, *twy = nullptr;
   float2 *twxw = nullptr, *twyw = nullptr;  // wide line twiddles (512, 1024 points)
+  float* Wrot = nullptr;  // time splitting: sqrt(kappa) |mu|^{s0}, [ncols][ny] (general model)
   const float* delta = nullptr;
   int* step_ctr = nullptr;
   int* err = nullptr;
@@ -218,10 +232,13 @@ struct Plan2D {
 
   // optional events: one after every inverse kernel, from ev[3] on (ev[2]
   // when the forward column transform is fused)
+  // base > 0 (one operator only): the terms base..M of the expansion (the
+  // splitting's remainder, Sec. 3.3: base = 1), the epilogue's L1 carrying
+  // the factor delta^base (epi.dpow = base)
   cudaError_t inverse(cudaStream_t s, int M, const EpiArgs<float>& epi, cudaEvent_t* ev = nullptr,
-                      bool one_op = false) const {
-    const TermSplit ts = term_split(M, one_op);
-    const int K = groups(M, one_op);
+                      bool one_op = false, int base = 0) const {
+    const TermSplit ts = term_split(M - base, one_op);
+    const int K = groups(M - base, one_op);
     const bool wc = wide_c && k.inv_cols_w, wr = wide_r && k.inv_rows_w;
     const int cpc = wc ? k.cpc_w : k.wic * k.lpw_y;
     const int parts = cparts > 0 ? cparts : col_parts_default(ny);
@@ -233,16 +250,16 @@ struct Plan2D {
     int e_i = ff ? 2 : 3;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(ts.slots, m_lo + G);
-      const float f0 = inv_factorial(m_lo), f1 = ts.split_k ? inv_factorial(m_lo + ts.split_k) : f0;
+      const float f0 = inv_factorial(m_lo + base), f1 = ts.split_k ? inv_factorial(m_lo + base + ts.split_k) : f0;
       cudaError_t e;
       if (wc)
         e = launch_pdl(k.inv_cols_w, gic, dim3(k.thr_w_c), k.smem_icols_w, s, (const float2*)Uh, (const float*)P,
                        (const float*)Lg, Z, pZ, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, cpack,
-                       (const float2*)twyw);
+                       (const float2*)twyw, base);
       else
         e = launch_pdl(k.inv_cols, gic, dim3(k.wic * 32), k.smem_icols, s, Uh, (const float*)P,
                        (const float*)Lg, zmap, ncols, m_lo, m_hi, f0, f1, ts.split_k, parts, cpack, (const float2*)twy,
-                       (const float2*)T, pT, (ff && gi == K - 1) ? 1 : 0);
+                       (const float2*)T, pT, (ff && gi == K - 1) ? 1 : 0, base);
       if (e) return e;
       if (ev) cudaEventRecord(ev[e_i++], s);
       EpiArgs<float> ep = epi;
@@ -256,6 +273,34 @@ struct Plan2D {
       if (ev) cudaEventRecord(ev[e_i++], s);
     }
     return cudaSuccess;
+  }
+
+  // The exact flow of the splitting over time t (Sec. 3.3) on u, v in place
+  // (kernels_split.cuh).  Scratch: the row spectra in the Z buffer (two
+  // [ny][pT] planes; Z holds at least that), the column spectra in Uh and,
+  // for v, in T (its ny x pT slots hold ncols x ny).
+  cudaError_t rotate(cudaStream_t s, float* u, float* v, float t) const {
+    float2* Su = Z;
+    float2* Sv = Z + (size_t)ny * pT;
+    float2* Uv = T;
+    const float invN = (float)(1.0 / ((double)nx * (double)ny));
+    const int rpc = W_ROT * k.lpw_x, cpc = W_ROT * k.lpw_y, cpf = W_FCOLS * k.lpw_y;
+    cudaError_t e = launch_pdl(k.rot_rows, dim3((ny + rpc - 1) / rpc), dim3(W_ROT * 32), k.smem_rot_rows, s,
+                               (const float*)u, (const float*)v, Su, Sv, ny, pT, (const float2*)twx);
+    if (!e)
+      e = launch_pdl(k.fwd_cols, dim3((ncols + cpf - 1) / cpf), dim3(W_FCOLS * 32), k.smem_fcols, s,
+                     (const float2*)Su, pT, Uh, ncols, (const float2*)twy, 0LL, 0LL);
+    if (!e)
+      e = launch_pdl(k.fwd_cols, dim3((ncols + cpf - 1) / cpf), dim3(W_FCOLS * 32), k.smem_fcols, s,
+                     (const float2*)Sv, pT, Uv, ncols, (const float2*)twy, 0LL, 0LL);
+    if (!e)
+      e = launch_pdl(k.rot_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_ROT * 32), k.smem_rot_cols, s,
+                     (const float2*)Uh, (const float2*)Uv, (const float*)Wrot, t, invN, Su, Sv, pT, ncols,
+                     (const float2*)twy);
+    if (!e)
+      e = launch_pdl(k.rot_irows, dim3((ny + rpc - 1) / rpc), dim3(W_ROT * 32), k.smem_rot_rows, s,
+                     (const float2*)Su, (const float2*)Sv, u, v, ny, pT, (const float2*)twx);
+    return e;
   }
 };
 
@@ -290,6 +335,7 @@ struct Fused2D : Engine {
     dev_free(p.twy);
     dev_free(p.twxw);
     dev_free(p.twyw);
+    dev_free(p.Wrot);
   }
 
   size_t bytes() const override { return nbytes; }
@@ -375,6 +421,47 @@ struct Fused2D : Engine {
     if (make_fused2d_tables(p.nx, p.ny, lx, ly, c->s01, c->s02, lambda, (double)p.ryy, p.P, p.Lg,
                             c->stream))
       return cuda_err(c, cudaGetLastError(), "fused 2D tables");
+    if (c->general) {  // the time splitting's frequencies (Sec. 3.3)
+      if (!p.Wrot) {
+        const size_t b = sizeof(float) * (size_t)p.ncols * p.ny;
+        if (int st = alloc(c, (void**)&p.Wrot, b)) return st;
+      }
+      if (make_fused2d_omega(p.nx, p.ny, lx, ly, c->s01, c->kappa, p.Wrot, c->stream))
+        return cuda_err(c, cudaGetLastError(), "splitting frequency table");
+    }
+    return VOFL_OK;
+  }
+
+  // Second-order time splitting (Sec. 3.3) of the general model: the exact
+  // half-step flow of the constant-order part, the kick with the
+  // variable-order remainder (terms 1..M of Eq. (2.13), on the operator
+  // kernels) and f(u), the half-step flow again.
+  bool can_split() const override { return true; }
+  int step_split(vofl_ctx* c) override {
+    if (!p.Wrot) return set_err(c, VOFL_ESTATE, "set the general model first");
+    float* u = (float*)c->u[c->cur];
+    float* v = (float*)c->u[1 - c->cur];
+    const float half = (float)(0.5 * c->dt);
+    cudaError_t err = p.rotate(c->stream, u, v, half);
+    if (!err && c->M >= 1) {
+      EpiArgs<float> e{};
+      e.mode = EPI_KICK;
+      e.u_cur = u;
+      e.u_other = v;
+      e.A = (const float*)c->A;
+      e.dt1 = (float)c->dt;
+      e.src_flat = -1;
+      e.dpow = 1;
+      epi_model(c, &e);
+      err = p.forward(c->stream, u, false);
+      if (!err) err = p.inverse(c->stream, c->M, e, nullptr, true, 1);
+    } else if (!err) {
+      const long long n = (long long)p.nx * p.ny;
+      err = launch_pdl(k2d_kick_f, dim3((unsigned)std::min<long long>((n + 255) / 256, 4096)), dim3(256), 0,
+                       c->stream, (const float*)u, v, n, (float)c->dt, (float)c->f1, (float)c->f3);
+    }
+    if (!err) err = p.rotate(c->stream, u, v, half);
+    if (err) return cuda_err(c, err, "fused 2D splitting step");
     return VOFL_OK;
   }
 

@@ -39,7 +39,7 @@ struct Kernels3 {
   void (*fwd_ycols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*fwd_zcols)(const float2*, int, float2*, int, const float2*, long long, long long);
   void (*inv_z)(float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int, int,
-                const float2*, const float2*, int, int);
+                const float2*, const float2*, int, int, int);
   void (*inv_y)(const float2*, long long, float2*, long long, int, int, const float2*);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
                            EpiArgs<float>, float, const float2*, int*, int);
@@ -244,7 +244,7 @@ struct Fused3D : Engine {
       const int cz = k.wiz * k.lpw_z;
       cudaError_t e = launch_pdl(k.inv_z, dim3((c3 + cz - 1) / cz, 2), dim3(k.wiz * 32), k.sm_iz, s, U3,
                                  (const float*)P, (const float*)Lg, zmap, c3, m_lo, m_hi, f0, f1, ts.split_k, 1, 0,
-                                 (const float2*)twz, (const float2*)nullptr, 0, 0);
+                                 (const float2*)twz, (const float2*)nullptr, 0, 0, 0);
       if (e) return e;
       const int cy = W_YCOLS * k.lpw_y;
       e = launch_pdl(k.inv_y, dim3((c2 + cy - 1) / cy, 2 * (m_hi - m_lo) * nz), dim3(W_YCOLS * 32), k.sm_iy, s,

@@ -47,7 +47,9 @@ struct Engine;
 
 
 // Epilogue of the last inverse pass: what to do with L1 u, L2 u at a point.
-enum EpiMode { EPI_PARTIAL = 0, EPI_APPLY = 1, EPI_STEP = 2, EPI_START = 3 };
+// EPI_KICK: the kick of the time splitting (Sec. 3.3), v += dt (A L1 + f(u))
+// with v = u_other, u = u_cur (L2 unused, l2p untouched).
+enum EpiMode { EPI_PARTIAL = 0, EPI_APPLY = 1, EPI_STEP = 2, EPI_START = 3, EPI_KICK = 4 };
 
 template <typename T>
 struct EpiArgs {
@@ -67,6 +69,7 @@ struct EpiArgs {
   double src_scale;   // dt^2 / h^d
   int nonlin;         // general model with a source term f(u) = f1 u + f3 u^3
   T f1, f3;
+  int dpow;           // one-operator sums of terms dpow..M: L1 = delta^dpow (slot sums)
 };
 
 // Pointwise update of Eq. (3.4) extended to Eq. (1.1) (see vofl.h).
@@ -79,6 +82,12 @@ __device__ __forceinline__ void epilogue_point(const EpiArgs<T>& e, long long id
   }
   const T un = e.u_cur[idx];
   const T other = e.u_other[idx];
+  if (e.mode == EPI_KICK) {
+    T f = e.A[idx] * L1;
+    if (e.nonlin) f += e.f1 * un + e.f3 * un * un * un;
+    e.u_other[idx] = other + e.dt1 * f;
+    return;
+  }
   const T l2o = e.l2p[idx];
   T unew;
   if (e.mode == EPI_STEP) {
@@ -337,6 +346,9 @@ int make_tile_map(CUtensorMap* map, const void* base, int ncols, long long rows,
                   int box_rows);
 int make_fused2d_tables(int nx, int ny, double lx, double ly, double s01, double s02, double scale2, double ryy,
                         float* P, float* Lg, cudaStream_t s);
+// sqrt(kappa) |mu_k|^{s0} on the fused 2D column-spectrum layout [H+1][ny]
+// (the time splitting's exact flow, Sec. 3.3)
+int make_fused2d_omega(int nx, int ny, double lx, double ly, double s0, double kappa, float* W, cudaStream_t s);
 template <typename T>
 int make_plain_tables(int ndim, const int64_t* n, const double* lo, const double* hi, double s01, double s02,
                       T* P1, T* P2, T* Lg, cudaStream_t s);

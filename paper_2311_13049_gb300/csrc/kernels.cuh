@@ -321,6 +321,8 @@ __device__ __forceinline__ bool col_run(int i, int bx, int yidx, int parts, int 
 
 template <int NY>
 // (bx, yidx, parts, pack): the CTA's runs of terms (col_run).
+// base > 0: slot index m stands for the term m + base (the splitting's
+// remainder of terms 1..M, Sec. 3.3: base = 1).
 // fwd = 1: the column spectra are not in Uh yet; every run computes them
 // from the row half spectra T (pitch pT) itself, by the arithmetic of
 // k2d_fwd_cols (so bit for bit the same), and the run of operator slot 0
@@ -329,7 +331,8 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, int p
                                               const float* __restrict__ P, const float* __restrict__ Lg,
                                               const void* zmap, int ncols, int m_lo, int m_hi, float inv_fact_lo,
                                               float inv_fact_lo1, int split_k, const float2* __restrict__ twy,
-                                              const float2* __restrict__ T = nullptr, int pT = 0, int fwd = 0) {
+                                              const float2* __restrict__ T = nullptr, int pT = 0, int fwd = 0,
+                                              int base = 0) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL, RL = F::RL;
   constexpr int W = icols_warps<NY>(), THREADS = W * 32, CW = W * LPW;  // columns per CTA
@@ -363,7 +366,7 @@ __device__ __forceinline__ void inv_cols_body(int bx, int yidx, int parts, int p
     // split_k > 0 (one operator): slot op = 1 carries the terms m + split_k of
     // operator 1 (multiplier P[0] ln|mu|^{2(m + split_k)} / (m + split_k)!)
     const int op = run.op;
-    const int off = (split_k > 0 && op) ? split_k : 0;
+    const int off = base + ((split_k > 0 && op) ? split_k : 0);
     const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
     const float* l_col = Lg + (size_t)cc * NY;
     float tm[E], lg[PAIR ? 1 : E];
@@ -535,9 +538,9 @@ __global__ void __launch_bounds__(icols_warps<NY>() * 32) k2d_inv_cols(float2* _
                                                            int m_lo, int m_hi, float inv_fact_lo,
                                                            float inv_fact_lo1, int split_k, int parts,
                                                            int pack, const float2* __restrict__ twy,
-                                                           const float2* __restrict__ T, int pT, int fwd) {
+                                                           const float2* __restrict__ T, int pT, int fwd, int base) {
   inv_cols_body<NY>(blockIdx.x, blockIdx.y, parts, pack, Uh, P, Lg, &zmap, ncols, m_lo, m_hi, inv_fact_lo, inv_fact_lo1,
-                    split_k, twy, T, pT, fwd);
+                    split_k, twy, T, pT, fwd, base);
 }
 
 // -------------------------------------------------------------------------
@@ -730,7 +733,9 @@ __device__ __forceinline__ void inv_rows_body(int bx, const float2* __restrict__
     for (int m = 0; m < E; ++m) {
       float dk = 1.f;
       for (int j = 0; j < split_k; ++j) dk *= dl[m];
-      epilogue_point<float>(epi, (long long)(row + li + LANES * m), fmaf(dk, a2[m], a1[m]), 0.f);
+      float L = fmaf(dk, a2[m], a1[m]);
+      for (int j = 0; j < epi.dpow; ++j) L *= dl[m];  // terms from dpow on
+      epilogue_point<float>(epi, (long long)(row + li + LANES * m), L, 0.f);
     }
   } else {
 #pragma unroll

@@ -142,7 +142,7 @@ __device__ __forceinline__ void inv_cols_wide_body(int bx, int yidx, int parts, 
                                                    const float* __restrict__ P, const float* __restrict__ Lg,
                                                    float2* __restrict__ Z, int pZ, int ncols, int m_lo, int m_hi,
                                                    float inv_fact_lo, float inv_fact_lo1, int split_k,
-                                                   const float2* __restrict__ twy) {
+                                                   const float2* __restrict__ twy, int base = 0) {
   using F = WideFFT<NY>;
   constexpr int LANES = F::LANES, CW = wide_lines_per_cta<NY>(), THREADS = CW * LANES, NB2 = F::NB2;
   constexpr int LS = wide_line_stride<NY, CW>();
@@ -166,7 +166,7 @@ __device__ __forceinline__ void inv_cols_wide_body(int bx, int yidx, int parts, 
     const int lo = run.lo, hi = run.hi, op = run.op;
     const int c0 = run.cb * CW;
     const int cc = min(c0 + line, ncols - 1);
-    const int off = (split_k > 0 && op) ? split_k : 0;
+    const int off = base + ((split_k > 0 && op) ? split_k : 0);  // base: as in inv_cols_body
     const float* p_col = P + (split_k > 0 ? 0 : op) * tot + (size_t)cc * NY;
     const float* l_col = Lg + (size_t)cc * NY;
     const float2* uh_col = Uh + (size_t)cc * NY;
@@ -219,9 +219,10 @@ template <int NY>
 __global__ void __launch_bounds__(wide_threads<NY>(), wide_min_blocks<NY>())
     k2d_inv_cols_w(const float2* __restrict__ Uh, const float* __restrict__ P, const float* __restrict__ Lg,
                    float2* __restrict__ Z, int pZ, int ncols, int m_lo, int m_hi, float inv_fact_lo,
-                   float inv_fact_lo1, int split_k, int parts, int pack, const float2* __restrict__ twy) {
+                   float inv_fact_lo1, int split_k, int parts, int pack, const float2* __restrict__ twy,
+                   int base) {
   inv_cols_wide_body<NY>(blockIdx.x, blockIdx.y, parts, pack, Uh, P, Lg, Z, pZ, ncols, m_lo, m_hi, inv_fact_lo,
-                         inv_fact_lo1, split_k, twy);
+                         inv_fact_lo1, split_k, twy, base);
 }
 
 // -------------------------------------------------------------------------
@@ -376,7 +377,9 @@ __device__ __forceinline__ void inv_rows_wide_body(int bx, const float2* __restr
     for (int m = 0; m < 16; ++m) {
       float dk = 1.f;
       for (int j = 0; j < split_k; ++j) dk *= dl[m];
-      epilogue_point<float>(epi, (long long)(row + li + LANES * m), fmaf(dk, a2[m], a1[m]), 0.f);
+      float L = fmaf(dk, a2[m], a1[m]);
+      for (int j = 0; j < epi.dpow; ++j) L *= dl[m];  // terms from dpow on
+      epilogue_point<float>(epi, (long long)(row + li + LANES * m), L, 0.f);
     }
   } else {
 #pragma unroll

@@ -91,6 +91,8 @@ __global__ void k_sum_pass2(const double* __restrict__ part, double* __restrict_
 // sum (x - y)^2, sum y^2, max |x - y|, max |y|; then one block combines the
 // partials in a fixed order (deterministic for a given launch shape).
 constexpr int DIAG_BLOCKS = 240;  // 4 partials each: 960 doubles of the context scratch
+// max that keeps a NaN (fmax drops it): a field with a NaN reports NaN
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
 template <typename TX, typename TY>
 __global__ void k_diff_pass1(const TX* __restrict__ x, const TY* __restrict__ y, long long n,
                              double* __restrict__ part) {
@@ -102,8 +104,8 @@ __global__ void k_diff_pass1(const TX* __restrict__ x, const TY* __restrict__ y,
     const double di = (double)x[i] - yi;
     d2 = fma(di, di, d2);
     y2 = fma(yi, yi, y2);
-    dm = fmax(dm, fabs(di));
-    ym = fmax(ym, fabs(yi));
+    dm = nan_max(dm, fabs(di));
+    ym = nan_max(ym, fabs(yi));
   }
   s[0][threadIdx.x] = d2;
   s[1][threadIdx.x] = y2;
@@ -114,8 +116,8 @@ __global__ void k_diff_pass1(const TX* __restrict__ x, const TY* __restrict__ y,
     if (threadIdx.x < w) {
       s[0][threadIdx.x] += s[0][threadIdx.x + w];
       s[1][threadIdx.x] += s[1][threadIdx.x + w];
-      s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + w]);
-      s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + w]);
+      s[2][threadIdx.x] = nan_max(s[2][threadIdx.x], s[2][threadIdx.x + w]);
+      s[3][threadIdx.x] = nan_max(s[3][threadIdx.x], s[3][threadIdx.x + w]);
     }
     __syncthreads();
   }
@@ -123,7 +125,8 @@ __global__ void k_diff_pass1(const TX* __restrict__ x, const TY* __restrict__ y,
 }
 
 // out: ||x - y|| / ||y||, max|x - y| / max|y|, ||y||, max|y| (ratios 0 when
-// y is all zero and x equals it, +inf when only y is zero)
+// y is all zero and x equals it, +inf when only y is zero, NaN when either
+// field holds a NaN)
 __global__ void k_diff_pass2(const double* __restrict__ part, double* __restrict__ out) {
   __shared__ double s[4][256];
   for (int k = 0; k < 4; ++k) s[k][threadIdx.x] = threadIdx.x < DIAG_BLOCKS ? part[k * DIAG_BLOCKS + threadIdx.x] : 0.0;
@@ -132,15 +135,16 @@ __global__ void k_diff_pass2(const double* __restrict__ part, double* __restrict
     if (threadIdx.x < w) {
       s[0][threadIdx.x] += s[0][threadIdx.x + w];
       s[1][threadIdx.x] += s[1][threadIdx.x + w];
-      s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + w]);
-      s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + w]);
+      s[2][threadIdx.x] = nan_max(s[2][threadIdx.x], s[2][threadIdx.x + w]);
+      s[3][threadIdx.x] = nan_max(s[3][threadIdx.x], s[3][threadIdx.x + w]);
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     const double dn = sqrt(s[0][0]), yn = sqrt(s[1][0]);
-    out[0] = yn > 0 ? dn / yn : (dn > 0 ? INFINITY : 0.0);
-    out[1] = s[3][0] > 0 ? s[2][0] / s[3][0] : (s[2][0] > 0 ? INFINITY : 0.0);
+    auto ratio = [](double a, double b) { return b > 0 ? a / b : (a > 0 ? INFINITY : (a == 0 ? 0.0 : NAN)); };
+    out[0] = (dn != dn || yn != yn) ? NAN : ratio(dn, yn);
+    out[1] = (s[2][0] != s[2][0] || s[3][0] != s[3][0]) ? NAN : ratio(s[2][0], s[3][0]);
     out[2] = yn;
     out[3] = s[3][0];
   }
@@ -650,6 +654,24 @@ int make_fused2d_tables(int nx, int ny, double lx, double ly, double s01, double
                         float* P, float* Lg, cudaStream_t s) {
   const long long total = (long long)(nx / 2 + 1) * ny;
   k_tables_fused2d<<<grid_for(total, 256), 256, 0, s>>>(nx, ny, lx, ly, s01, s02, scale2, ryy, P, Lg);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
+}
+
+__global__ void k_omega_fused2d(int nx, int ny, double lx, double ly, double s0, double kappa, float* __restrict__ W) {
+  const long long total = (long long)(nx / 2 + 1) * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / ny), k2 = (int)(i % ny);
+    const int k2s = (k2 < ny / 2) ? k2 : k2 - ny;
+    const double m1 = 2.0 * M_PI * (double)c / lx, m2 = 2.0 * M_PI * (double)k2s / ly;
+    const double mu2 = m1 * m1 + m2 * m2;
+    W[i] = (float)(mu2 > 0.0 ? sqrt(kappa) * pow(mu2, 0.5 * s0) : 0.0);
+  }
+}
+
+int make_fused2d_omega(int nx, int ny, double lx, double ly, double s0, double kappa, float* W, cudaStream_t s) {
+  const long long total = (long long)(nx / 2 + 1) * ny;
+  k_omega_fused2d<<<grid_for(total, 256), 256, 0, s>>>(nx, ny, lx, ly, s0, kappa, W);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? VOFL_OK : VOFL_ECUDA;
 }

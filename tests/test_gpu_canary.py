@@ -70,6 +70,16 @@ for shape, prec, impl in (((256,), V.F64, V.IMPL_FUSED), ((4096,), V.F32, V.IMPL
     s.step(3, s.suggest_dt(0.25))
     s.sync()
     keep.append(s)
+for shape, M in (((256, 256), 6), ((768, 768), 0), ((1024, 1024), 3)):  # fused time splitting
+    xg, yg = S.mesh(shape, [-8.0, -8.0], [8.0, 8.0])
+    s = V.Solver(shape, [-8.0, -8.0], [8.0, 8.0])
+    s.set_order(1.0 - 0.4 * np.cos(np.pi * xg / 4) * np.cos(np.pi * yg / 4), kappa=1.0, f3=1.0)
+    s.set_M(M)
+    s.set_scheme(V.SCHEME_TSFP2)
+    s.set_state(np.exp(-(xg ** 2 + yg ** 2) / 2.0).astype(np.float32))
+    s.step(3, 1e-3)
+    s.sync()
+    keep.append(s)
 x = S.axis(256, -16.0, 16.0)
 s = V.Solver((256,), [-16.0], [16.0], V.F64, V.IMPL_PLAIN)
 s.set_order(1.0 + 0.3 * np.sin(np.pi * x / 8), kappa=1.0, f3=1.0)

@@ -165,9 +165,11 @@ def _table4(golden_dir):
     return rows
 
 
-def _gpu_split(V, shape, s, u0, dt, nsteps, M, f3, prec, lo=None, hi=None, v0=None):
+def _gpu_split(V, shape, s, u0, dt, nsteps, M, f3, prec, lo=None, hi=None, v0=None, impl=None, group=0):
     ty = np.float32 if prec == V.F32 else np.float64
-    with V.Solver(shape, lo, hi, prec, V.IMPL_PLAIN) as sv:
+    with V.Solver(shape, lo, hi, prec, V.IMPL_PLAIN if impl is None else impl) as sv:
+        if group:
+            sv.set_schedule(group=group)
         sv.set_order(np.ascontiguousarray(np.broadcast_to(s, shape), dtype=np.float64), kappa=1.0, f3=f3)
         sv.set_M(M)
         sv.set_scheme(V.SCHEME_TSFP2)
@@ -200,22 +202,55 @@ def test_paper_table4_tsfp2_on_the_gpu(V, golden_dir, col, order):
             assert abs(err - printed) <= 0.0006 * printed, (order, p, err, printed)
 
 
-def test_tsfp2_fp32_2d_against_oracle(V):
-    """A 2D splitting run in FP32 with a non-zero initial velocity."""
+@pytest.mark.parametrize("impl", ["plain", "fused"])
+def test_tsfp2_fp32_2d_against_oracle(V, impl):
+    """A 2D splitting run in FP32 with a non-zero initial velocity, on the
+    cuFFT path and on the fused path (rotations on its own line transforms,
+    the m >= 1 remainder on the operator kernels, the kick in their
+    epilogue)."""
     shape, lo, hi = (128, 128), [-8.0, -8.0], [8.0, 8.0]
     s = _s2d(shape, lo, hi)
     u0 = S.gaussian_pulse(shape, 6.0).astype(np.float32)
     xg, yg = S.mesh(shape, lo, hi)
     v0 = (0.3 * np.sin(np.pi * xg / 4) * np.cos(np.pi * yg / 8)).astype(np.float32)
-    g = _gpu_split(V, shape, s, u0, 2e-3, 50, 20, 1.0, V.F32, lo, hi, v0)
+    im = V.IMPL_PLAIN if impl == "plain" else V.IMPL_FUSED
+    g = _gpu_split(V, shape, s, u0, 2e-3, 50, 20, 1.0, V.F32, lo, hi, v0, impl=im)
     r = O.general_tsfp2(s, 1.0, lambda u: u ** 3, u0.astype(np.float64), v0.astype(np.float64), 2e-3, 50, 20, lo, hi)
     check(g, r, 1e-4)
 
 
+@pytest.mark.parametrize("shape,M,group", [((256, 256), 12, 0), ((512, 512), 8, 3), ((768, 768), 6, 0),
+                                           ((1024, 1024), 16, 0), ((256, 128), 0, 0), ((64, 64), 1, 0)])
+def test_tsfp2_fused_2d_sizes(V, shape, M, group):
+    """The fused splitting on every line-transform kind (32-element lines,
+    wide lines at 512 and 1024, the three-stage 768-point line), several
+    Taylor groups (partial sums across groups, the delta factor of the
+    remainder), a rectangular grid, M = 0 (the kick alone: no remainder)
+    and M = 1 (one remainder term), against the FP64 oracle.  The kick is
+    explicit: dt is a quarter of 2 / |mu_max|^{max s} (the leap-frog rule;
+    at 2e-3 the 768^2 and 1024^2 runs are unstable, in FP64 too)."""
+    lo, hi = [-8.0, -8.0], [8.0, 8.0]
+    s = _s2d(shape, lo, hi)
+    xg, yg = S.mesh(shape, lo, hi)
+    u0 = np.exp(-(xg ** 2 + yg ** 2) / 2.0).astype(np.float32)
+    v0 = (0.2 * np.cos(np.pi * xg / 8) * np.sin(np.pi * yg / 4)).astype(np.float32)
+    mu_max = np.pi * np.hypot(shape[0] / 16.0, shape[1] / 16.0)
+    dt, n = 0.25 * 2.0 / mu_max ** s.max(), 6
+    g = _gpu_split(V, shape, s, u0, dt, n, M, 1.0, V.F32, lo, hi, v0, impl=V.IMPL_FUSED, group=group)
+    r = O.general_tsfp2(s, 1.0, lambda u: u ** 3, u0.astype(np.float64), v0.astype(np.float64), dt, n, M, lo, hi)
+    check(g, r, 1e-4, (shape, M, group))
+
+
 def test_tsfp2_needs_general_model_and_plain_path(V):
     shape = (64, 64)
-    with V.Solver(shape) as sv:  # fused path
-        sv.set_order(np.ones(shape))
+    with V.Solver((64, 64, 64)) as sv:  # fused 3D path: no splitting
+        sv.set_order(np.ones((64, 64, 64)))
+        sv.set_scheme(V.SCHEME_TSFP2)
+        sv.set_state(np.zeros((64, 64, 64), np.float32))
+        with pytest.raises(V.VoflError):
+            sv.step(1, 1e-3)
+    with V.Solver(shape) as sv:  # fused 2D path, seismic model
+        sv.set_q(S.q_lowpass(shape, 1))
         sv.set_scheme(V.SCHEME_TSFP2)
         sv.set_state(np.zeros(shape, np.float32))
         with pytest.raises(V.VoflError):

@@ -265,6 +265,10 @@ def test_rel_l2_diagnostic_matches_numpy(V, xp, yp):
         got = s.rel_l2(x, y)
         again = s.rel_l2(x, y)
         zero = s.rel_l2(y, y)
+        bad = x.clone()
+        bad[77, 131] = float("nan")  # a blown-up field never reads as a match
+        nan_x, nan_y = s.rel_l2(bad, y), s.rel_l2(y, bad)
+    assert all(np.isnan(v) for v in nan_x[:2]) and all(np.isnan(v) for v in nan_y)
     xn, yn = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
     want = (np.linalg.norm(xn - yn) / np.linalg.norm(yn), np.max(np.abs(xn - yn)) / np.max(np.abs(yn)),
             np.linalg.norm(yn), np.max(np.abs(yn)))
