@@ -138,7 +138,10 @@ VOFL_API int vofl_set_gamma(vofl_ctx* ctx, const double* gamma, const double* c0
  * path (VOFL_IMPL_PLAIN) or a fused FP32 2D context, else vofl_step
  * returns VOFL_EUNSUPPORTED.  On the fused 2D path the rotations run on
  * its own line transforms in FP32 and the m >= 1 terms on the operator
- * kernels (one operator, Taylor groups of the transform schedule).
+ * kernels (one operator, Taylor groups of the transform schedule), and
+ * the two half-step rotations that meet between consecutive steps of one
+ * call are one rotation over dt (the call's first and last rotations over
+ * dt/2 and -dt/2 bracket them): the same scheme, one rotation per step.
  * The Crank-Nicolson scheme (Sec. 3.1, Eq. (3.2)) takes the explicit start
  * step of Eq. (3.3) (that of the leap-frog scheme), then for n >= 1 solves
  *     u^{n+1} + c L u^{n+1} - h f(u^{n+1})

@@ -478,8 +478,14 @@ int vofl_step(vofl_ctx* c, int64_t nsteps, double dt) {
     if (c->steps > 0 && dt != c->dt) return set_err(c, VOFL_EINVAL, "dt must stay fixed during a run");
     if (int st = c->eng->prepare(c)) return st;
     c->dt = dt;
+    // merged flows: S(dt/2) [K S(dt)]^n S(-dt/2) = [S(dt/2) K S(dt/2)]^n
+    const bool merged = c->eng->split_merged() && nsteps > 0;
+    if (merged)
+      if (int st = c->eng->split_flow(c, 0.5 * dt)) return st;
     for (int64_t i = 0; i < nsteps; ++i)
       if (int st = split_step(c)) return st;
+    if (merged)
+      if (int st = c->eng->split_flow(c, -0.5 * dt)) return st;
     return VOFL_OK;
   }
   if (c->scheme == VOFL_SCHEME_CNFP) {

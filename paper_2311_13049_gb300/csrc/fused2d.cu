@@ -81,7 +81,7 @@ struct Kernels {
   int cpc_w = 0, rpc_w = 0, thr_w_c = 0, thr_w_r = 0;  // lines per CTA / threads of the wide kernels
   // the exact flow of the time splitting (kernels_split.cuh)
   void (*rot_rows)(const float*, const float*, float2*, float2*, int, int, const float2*);
-  void (*rot_cols)(const float2*, const float2*, const float*, float, float, float2*, float2*, int, int, const float2*);
+  void (*rot_cols)(float2*, float2*, const float*, float, float, int, int, const float2*);
   void (*rot_irows)(const float2*, const float2*, float*, float*, int, int, const float2*);
   size_t smem_rot_rows, smem_rot_cols;
 };
@@ -276,27 +276,18 @@ struct Plan2D {
   }
 
   // The exact flow of the splitting over time t (Sec. 3.3) on u, v in place
-  // (kernels_split.cuh).  Scratch: the row spectra in the Z buffer (two
-  // [ny][pT] planes; Z holds at least that), the column spectra in Uh and,
-  // for v, in T (its ny x pT slots hold ncols x ny).
+  // (kernels_split.cuh), three launches.  Scratch: the row spectra in the Z
+  // buffer (two [ny][pT] planes; Z holds at least that).
   cudaError_t rotate(cudaStream_t s, float* u, float* v, float t) const {
     float2* Su = Z;
     float2* Sv = Z + (size_t)ny * pT;
-    float2* Uv = T;
     const float invN = (float)(1.0 / ((double)nx * (double)ny));
-    const int rpc = W_ROT * k.lpw_x, cpc = W_ROT * k.lpw_y, cpf = W_FCOLS * k.lpw_y;
+    const int rpc = W_ROT * k.lpw_x, cpc = W_ROT * k.lpw_y;
     cudaError_t e = launch_pdl(k.rot_rows, dim3((ny + rpc - 1) / rpc), dim3(W_ROT * 32), k.smem_rot_rows, s,
                                (const float*)u, (const float*)v, Su, Sv, ny, pT, (const float2*)twx);
     if (!e)
-      e = launch_pdl(k.fwd_cols, dim3((ncols + cpf - 1) / cpf), dim3(W_FCOLS * 32), k.smem_fcols, s,
-                     (const float2*)Su, pT, Uh, ncols, (const float2*)twy, 0LL, 0LL);
-    if (!e)
-      e = launch_pdl(k.fwd_cols, dim3((ncols + cpf - 1) / cpf), dim3(W_FCOLS * 32), k.smem_fcols, s,
-                     (const float2*)Sv, pT, Uv, ncols, (const float2*)twy, 0LL, 0LL);
-    if (!e)
-      e = launch_pdl(k.rot_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_ROT * 32), k.smem_rot_cols, s,
-                     (const float2*)Uh, (const float2*)Uv, (const float*)Wrot, t, invN, Su, Sv, pT, ncols,
-                     (const float2*)twy);
+      e = launch_pdl(k.rot_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_ROT * 32), k.smem_rot_cols, s, Su, Sv,
+                     (const float*)Wrot, t, invN, pT, ncols, (const float2*)twy);
     if (!e)
       e = launch_pdl(k.rot_irows, dim3((ny + rpc - 1) / rpc), dim3(W_ROT * 32), k.smem_rot_rows, s,
                      (const float2*)Su, (const float2*)Sv, u, v, ny, pT, (const float2*)twx);
@@ -433,17 +424,25 @@ struct Fused2D : Engine {
   }
 
   // Second-order time splitting (Sec. 3.3) of the general model: the exact
-  // half-step flow of the constant-order part, the kick with the
-  // variable-order remainder (terms 1..M of Eq. (2.13), on the operator
-  // kernels) and f(u), the half-step flow again.
+  // flow of the constant-order part, the kick with the variable-order
+  // remainder (terms 1..M of Eq. (2.13), on the operator kernels) and f(u).
+  // Consecutive half-step flows are merged: a step is the kick followed by
+  // the flow over dt, and a run is bracketed by the flows over +dt/2 and
+  // -dt/2 (vofl_step), one flow per step instead of two.
   bool can_split() const override { return true; }
+  bool split_merged() const override { return true; }
+  int split_flow(vofl_ctx* c, double t) override {
+    if (!p.Wrot) return set_err(c, VOFL_ESTATE, "set the general model first");
+    cudaError_t err = p.rotate(c->stream, (float*)c->u[c->cur], (float*)c->u[1 - c->cur], (float)t);
+    if (err) return cuda_err(c, err, "fused 2D splitting flow");
+    return VOFL_OK;
+  }
   int step_split(vofl_ctx* c) override {
     if (!p.Wrot) return set_err(c, VOFL_ESTATE, "set the general model first");
     float* u = (float*)c->u[c->cur];
     float* v = (float*)c->u[1 - c->cur];
-    const float half = (float)(0.5 * c->dt);
-    cudaError_t err = p.rotate(c->stream, u, v, half);
-    if (!err && c->M >= 1) {
+    cudaError_t err = cudaSuccess;
+    if (c->M >= 1) {
       EpiArgs<float> e{};
       e.mode = EPI_KICK;
       e.u_cur = u;
@@ -455,12 +454,12 @@ struct Fused2D : Engine {
       epi_model(c, &e);
       err = p.forward(c->stream, u, false);
       if (!err) err = p.inverse(c->stream, c->M, e, nullptr, true, 1);
-    } else if (!err) {
+    } else {
       const long long n = (long long)p.nx * p.ny;
       err = launch_pdl(k2d_kick_f, dim3((unsigned)std::min<long long>((n + 255) / 256, 4096)), dim3(256), 0,
                        c->stream, (const float*)u, v, n, (float)c->dt, (float)c->f1, (float)c->f3);
     }
-    if (!err) err = p.rotate(c->stream, u, v, half);
+    if (!err) err = p.rotate(c->stream, u, v, (float)c->dt);
     if (err) return cuda_err(c, err, "fused 2D splitting step");
     return VOFL_OK;
   }

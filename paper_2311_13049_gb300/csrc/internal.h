@@ -250,6 +250,15 @@ struct Engine {
     (void)c;
     return VOFL_EUNSUPPORTED;
   }
+  // engines whose step_split is the kick followed by the flow over the whole
+  // step (consecutive half-step flows merged): a run of n steps is then
+  // split_flow(+dt/2), n x step_split, split_flow(-dt/2)
+  virtual bool split_merged() const { return false; }
+  virtual int split_flow(vofl_ctx* c, double t) {
+    (void)c;
+    (void)t;
+    return VOFL_EUNSUPPORTED;
+  }
   // size M-dependent scratch before stepping or applying (outside any graph
   // capture: allocations and plans are not stream operations)
   virtual int prepare(vofl_ctx* c) {

@@ -13,11 +13,11 @@
 //   S1 k2d_rot_fwd_rows   u, v -> row half spectra Su, Sv ([ny][pT] c64):
 //        one complex FFT along x of u[y] + i v[y] per row, split into the
 //        two half spectra;
-//   (k2d_fwd_cols of kernels.cuh: Su -> Uu, Sv -> Uv, column-major)
-//   S2 k2d_rot_cols       per column k_x: the flow above on (Uu, Uv), the
-//        1/(nx ny) of the unnormalised transforms, then the inverse FFT
-//        along y of both, back to Su, Sv (row segments of the CTA's
-//        columns, the last stage done cooperatively as in k2d_inv_cols);
+//   S2 k2d_rot_cols       per column k_x: the forward FFT along y of Su
+//        and Sv, the flow above, the 1/(nx ny) of the unnormalised
+//        transforms, the inverse FFT along y of both, back to Su, Sv (loads
+//        and stores are row segments of the CTA's columns: the first and
+//        last stages are done cooperatively as in k2d_inv_cols);
 //   S3 k2d_rot_inv_rows   per row: one complex inverse FFT along x of the
 //        Hermitian extensions A + iB of (Su[y], Sv[y]) gives u[y] + i v[y].
 #pragma once
@@ -78,18 +78,24 @@ __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_fwd_rows(const float* __re
   }
 }
 
-// S2: columns c0 .. c0 + CW of the column spectra (Uu, Uv: [ncols][NY]):
-// the flow over time t (omega table W, same layout), scaled by invN, then
-// the inverse transforms along y into Su, Sv ([NY][pT]).
+// S2: columns c0 .. c0 + CW of the row spectra Su, Sv ([NY][pT]): forward
+// FFT along y of both (stage 0 cooperatively: thread q takes column q % CW,
+// butterfly q / CW, so loads are row segments of CW adjacent columns; the
+// other stages by the column's own lanes, leaving the column's spectrum in
+// natural order in registers), the flow over time t (omega table W,
+// [ncols][NY]), the 1/(nx ny) of the unnormalised transforms, then the
+// inverse FFT along y of both back into Su, Sv (last stage cooperatively:
+// stores are row segments too).  Each CTA reads and writes only its own
+// columns, so the pass runs in place.
 template <int NY>
-__global__ void __launch_bounds__(W_ROT * 32) k2d_rot_cols(const float2* __restrict__ Uu, const float2* __restrict__ Uv,
-                                                           const float* __restrict__ W, float t, float invN,
-                                                           float2* __restrict__ Su, float2* __restrict__ Sv, int pT,
+__global__ void __launch_bounds__(W_ROT * 32) k2d_rot_cols(float2* __restrict__ Su, float2* __restrict__ Sv,
+                                                           const float* __restrict__ W, float t, float invN, int pT,
                                                            int ncols, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL, RL = F::RL, NBL = F::NBL;
   constexpr int THREADS = W_ROT * 32, CW = W_ROT * LPW;  // columns per CTA
   constexpr int SET = W_ROT * warp_stride<NY>();
+  static_assert(CW * LANES == THREADS, "one stage-0 butterfly per thread");
   __shared__ float2 s_tw[F::TW];
   extern __shared__ __align__(128) float2 s_buf[];  // [field][warp] exchange buffers
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
@@ -97,18 +103,45 @@ __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_cols(const float2* __restr
   const int li = lane % LANES, line = lane / LANES;
   const int c0 = blockIdx.x * CW;
   const int cc = min(c0 + warp * LPW + line, ncols - 1);
-  const size_t col = (size_t)cc * NY;
   // the table does not depend on the previous kernel
   float wk[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) wk[m] = W[col + li + LANES * m];
-  __syncthreads();
-  pdl_wait();  // Uu, Uv are written by the forward column kernels
+  for (int m = 0; m < E; ++m) wk[m] = W[(size_t)cc * NY + li + LANES * m];
+  pdl_wait();  // Su, Sv are written by k2d_rot_fwd_rows
   pdl_trigger();
+  float2* lbu = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
+  float2* lbv = lbu + SET;
+  {
+    const int fc = threadIdx.x % CW, j = threadIdx.x / CW;
+    const int col = min(c0 + fc, ncols - 1);
+    float2* lb = s_buf + (fc / LPW) * warp_stride<NY>() + (fc % LPW) * F::PAD_LINE;
+    float2 x[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) x[r] = Su[(size_t)(j + LANES * r) * pT + col];
+    stage0_to_smem<NY, false>(x, lb, j);
+#pragma unroll
+    for (int r = 0; r < E; ++r) x[r] = Sv[(size_t)(j + LANES * r) * pT + col];
+    stage0_to_smem<NY, false>(x, lb + SET, j);
+  }
+  __syncthreads();  // twiddles; every column's stage 0 in place
+  mid_stage<NY, false>(lbu, s_tw, li);
+  mid_stage<NY, false>(lbv, s_tw, li);
+  __syncwarp();
   float2 a[E], b[E];
 #pragma unroll
+  for (int q = 0; q < BPL; ++q) {
+    float2 w[RL];
+    stage1_from_smem<NY, false>(w, lbu, s_tw, li + LANES * q);
+#pragma unroll
+    for (int r = 0; r < RL; ++r) a[q + BPL * r] = w[r];
+    stage1_from_smem<NY, false>(w, lbv, s_tw, li + LANES * q);
+#pragma unroll
+    for (int r = 0; r < RL; ++r) b[q + BPL * r] = w[r];
+  }
+  // the flow, element y = li + LANES m of the column (natural order)
+#pragma unroll
   for (int m = 0; m < E; ++m) {
-    const float2 p = Uu[col + li + LANES * m], q = Uv[col + li + LANES * m];
+    const float2 p = a[m], q = b[m];
     float2 p2, q2;
     if (wk[m] > 0.f) {
       float sn, cs;
@@ -123,15 +156,13 @@ __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_cols(const float2* __restr
     a[m] = cscale(p2, invN);
     b[m] = cscale(q2, invN);
   }
-  float2* lbu = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
-  float2* lbv = lbu + SET;
+  __syncwarp();  // the line's stage-1 reads are done before its buffers are rewritten
   stage0_to_smem<NY, true>(a, lbu, li);
   mid_stage<NY, true>(lbu, s_tw, li);
   stage0_to_smem<NY, true>(b, lbv, li);
   mid_stage<NY, true>(lbv, s_tw, li);
   __syncthreads();
-  // last stage cooperatively: thread q takes column q % CW, butterfly q / CW,
-  // so each store instruction writes row segments of CW adjacent columns
+  // last stage cooperatively: thread q takes column q % CW, butterfly q / CW
 #pragma unroll
   for (int q = 0; q < BPL; ++q) {
     const int bb = threadIdx.x + THREADS * q;
