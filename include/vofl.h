@@ -326,13 +326,16 @@ VOFL_API int vofl_rel_l2(vofl_ctx* ctx, const void* x_dev, int x_prec, const voi
  *     that buffer (a device allocation).
  *   fuse_forward: 1 = the top group's inverse column kernel also does the
  *     forward transform along y (one launch fewer per step; the same
- *     arithmetic, so the same bits), 0 = a separate forward column kernel,
- *     -1 = the default (fused on grids of up to 256 rows); reported 0
- *     when the column pass is wide.
+ *     arithmetic, so the same bits), 2 = both forward passes (32-element
+ *     lines) in one cooperative launch with a grid-wide barrier between
+ *     them (the same bits as the two kernels; not with wide_fwd = 1),
+ *     0 = separate forward row and column kernels, -1 = the default (1 on
+ *     grids of up to 256 rows, 2 on square grids of 512, 768 and 1024);
+ *     reported 0 when the column pass is wide (1), or when the forward
+ *     rows are wide or the device cannot launch it (2).
  *   wide_fwd: 1 = the forward row pass transforms its 512- or 1024-point
  *     lines with the wide line transform (as wide_rows), 0 = 32 elements
- *     per lane, -1 = the default (wide at 1024); reported 0 for other line
- *     lengths.
+ *     per lane, -1 = the default (0); reported 0 for other line lengths.
  *   row_split: runs of terms each row's group is split into in the
  *     32-element row pass, one warp per run, the runs' Horner sums joined
  *     by Horner's rule (1, 2 or 4, dividing that kernel's warps per CTA; 0

@@ -778,7 +778,7 @@ int vofl_set_schedule(vofl_ctx* c, const vofl_schedule* sched) {
   if (!sched) return set_err(c, VOFL_EINVAL, "null schedule");
   if (sched->wide_cols < -1 || sched->wide_cols > 1 || sched->wide_rows < -1 || sched->wide_rows > 1 ||
       sched->col_parts < 0 || sched->col_parts > 41 || sched->group < 0 || sched->group > 41 ||
-      sched->fuse_forward < -1 || sched->fuse_forward > 1 || sched->wide_fwd < -1 || sched->wide_fwd > 1 ||
+      sched->fuse_forward < -1 || sched->fuse_forward > 2 || sched->wide_fwd < -1 || sched->wide_fwd > 1 ||
       sched->row_split < 0 || sched->row_split > 16 || sched->col_pack < -1 || sched->col_pack > 65535)
     return set_err(c, VOFL_EINVAL, "schedule field out of range");
   VOFL_CUDA(c, cudaStreamSynchronize(c->stream));  // queued work may use the buffers being re-sized

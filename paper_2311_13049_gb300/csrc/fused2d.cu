@@ -59,6 +59,10 @@ namespace {
 struct Kernels {
   void (*fwd_rows)(const float*, float2*, int, int, int, float, float, const float2*, int*, int, int*);
   void (*fwd_cols)(const float2*, int, float2*, int, const float2*, long long, long long);
+  // both forward passes in one cooperative launch
+  void (*fwd_both)(const float*, float2*, float2*, int, int, int, float, const float2*, const float2*, int*, int, int*,
+                   unsigned long long*);
+  size_t smem_fboth;
   void (*inv_cols)(float2*, const float*, const float*, CUtensorMap, int, int, int, float, float, int, int, int,
                    const float2*, const float2*, int, int, int);
   using InvRows = void (*)(const float2*, long long, int, int, int, int, int, int, int, const float*, float*, float*,
@@ -101,6 +105,8 @@ Kernels kernels_for() {
   k.wir = WR;
   k.fwd_rows = k2d_fwd_rows<NX, false>;
   k.fwd_cols = k2d_fwd_cols<NY>;
+  k.fwd_both = k2d_fwd_both<NX, NY>;
+  k.smem_fboth = fboth_smem<NX, NY>();
   k.inv_cols = k2d_inv_cols<NY>;
   k.inv_rows = k2d_inv_rows<NX, false, WR>;
   k.inv_rows_split = k2d_inv_rows<NX, true, WR>;
@@ -159,7 +165,7 @@ bool pick_kernels(int nx, int ny, Kernels* k) {
 
 int set_smem_attributes(const Kernels& k) {
   if (set_kernel_smem(k.fwd_rows, k.smem_frows) ||
-      set_kernel_smem(k.fwd_cols, k.smem_fcols) ||
+      set_kernel_smem(k.fwd_cols, k.smem_fcols) || set_kernel_smem(k.fwd_both, k.smem_fboth) ||
       set_kernel_smem(k.inv_cols, k.smem_icols) ||
       set_kernel_smem(k.inv_rows, k.smem_irows) || set_kernel_smem(k.inv_rows_split, k.smem_irows) ||
       (k.inv_cols_w && set_kernel_smem(k.inv_cols_w, k.smem_icols_w)) ||
@@ -195,12 +201,19 @@ struct Plan2D {
   // (where built), the column-pass term split (0: col_parts_default), and
   // the forward column transform done inside the top group's inverse
   // column kernel (32-element column kernel only)
-  bool wide_c = false, wide_r = false, fuse_fwd = false, wide_f = false;
+  bool wide_c = false, wide_r = false, wide_f = false;
+  // forward passes: 0 two kernels, 1 the column transform inside the top
+  // group's column kernel, 2 both passes in one cooperative launch
+  int fuse_fwd = 0;
+  int both_grid = 0;                   // CTAs of that launch (0: not resident-safe here)
+  unsigned long long* gbar = nullptr;  // its grid-barrier counter
   int cparts = 0;
   int cpack = 0;   // > 0: the column pass's terms dealt out over cpack CTAs (col_run)
   int rsplit = 1;  // runs of terms per row in the (32-element) row kernel
 
-  bool fused_forward() const { return fuse_fwd && !(wide_c && k.inv_cols_w); }
+  bool fused_forward() const { return fuse_fwd == 1 && !(wide_c && k.inv_cols_w); }
+  bool forward_both() const { return fuse_fwd == 2 && both_grid > 0 && !(wide_f && k.fwd_rows_w); }
+  bool one_forward_launch() const { return fused_forward() || forward_both(); }
 
   // one_op: a model with one operator (its terms fill both slots)
   int groups(int M, bool one_op = false) const { return (term_split(M, one_op).slots + G - 1) / G; }
@@ -209,9 +222,21 @@ struct Plan2D {
     return make_tile_map(&zmap, Z, ncols, 2LL * G * ny, pZ, k.wic * k.lpw_y, std::min(ny, 256));
   }
 
-  // optional events: ev[1] after F1, ev[2] after F2 (ev[0] recorded by the caller)
-  cudaError_t forward(cudaStream_t s, const float* u, bool inc_step, cudaEvent_t* ev = nullptr) const {
+  // optional events: ev[1] after F1, ev[2] after F2 (ev[0] recorded by the
+  // caller).  coop = false: the two forward kernels even where the schedule
+  // has the cooperative launch (same bits), for eagerly launched applies:
+  // there the cooperative launch cost more than the boundary it saves (the
+  // generic 512^2 apply, M = 20: 0.0395 ms with it, 0.0365 without), while
+  // steps replay it from a graph
+  cudaError_t forward(cudaStream_t s, const float* u, bool inc_step, cudaEvent_t* ev = nullptr,
+                      bool coop = true) const {
     cudaError_t e;
+    if (coop && forward_both()) {
+      e = launch_coop(k.fwd_both, dim3(both_grid), dim3(W_FBOTH * 32), k.smem_fboth, s, u, T, Uh, ny, pT, ncols, ryy,
+                      (const float2*)twx, (const float2*)twy, step_ctr, inc_step ? 1 : 0, err, gbar);
+      if (!e && ev) cudaEventRecord(ev[1], s);
+      return e;
+    }
     if (wide_f && k.fwd_rows_w) {
       e = launch_pdl(k.fwd_rows_w, dim3((ny / 2 + k.rpc_fw - 1) / k.rpc_fw), dim3(k.thr_fw), k.smem_frows_w, s, u, T,
                      ny, 1, pT, ryy, 0.0f, (const float2*)twxw, step_ctr, inc_step ? 1 : 0, err);
@@ -236,7 +261,7 @@ struct Plan2D {
   // splitting's remainder, Sec. 3.3: base = 1), the epilogue's L1 carrying
   // the factor delta^base (epi.dpow = base)
   cudaError_t inverse(cudaStream_t s, int M, const EpiArgs<float>& epi, cudaEvent_t* ev = nullptr,
-                      bool one_op = false, int base = 0) const {
+                      bool one_op = false, int base = 0, bool coop = true) const {
     const TermSplit ts = term_split(M - base, one_op);
     const int K = groups(M - base, one_op);
     const bool wc = wide_c && k.inv_cols_w, wr = wide_r && k.inv_rows_w;
@@ -247,7 +272,7 @@ struct Plan2D {
     const int rpc = wr ? k.rpc_w : (k.wir / rsp) * k.lpw_x;
     const dim3 gir((ny + rpc - 1) / rpc);
     const bool ff = fused_forward();
-    int e_i = ff ? 2 : 3;
+    int e_i = (fused_forward() || (coop && forward_both())) ? 2 : 3;
     for (int gi = K - 1; gi >= 0; --gi) {
       const int m_lo = gi * G, m_hi = std::min(ts.slots, m_lo + G);
       const float f0 = inv_factorial(m_lo + base), f1 = ts.split_k ? inv_factorial(m_lo + base + ts.split_k) : f0;
@@ -327,6 +352,7 @@ struct Fused2D : Engine {
     dev_free(p.twxw);
     dev_free(p.twyw);
     dev_free(p.Wrot);
+    dev_free(p.gbar);
   }
 
   size_t bytes() const override { return nbytes; }
@@ -386,11 +412,29 @@ struct Fused2D : Engine {
     if (p.k.inv_cols_w && (st = alloc(c, (void**)&p.twyw, sizeof(float2) * wide_twiddle_entries(p.ny)))) return st;
     p.wide_c = p.k.inv_cols_w != nullptr && wide_cols_default(p.ny);
     p.wide_r = p.k.inv_rows_w != nullptr && wide_rows_default(p.nx);
-    p.fuse_fwd = fuse_forward_default(p.ny);
+    p.fuse_fwd = fuse_forward_default(p.nx, p.ny);
     p.wide_f = p.k.fwd_rows_w != nullptr && wide_fwd_default(p.nx);
     p.rsplit = row_split_default(p.nx, p.ny, p.k.wir);
     if (set_smem_attributes(p.k)) return set_err(c, VOFL_ECUDA, "shared-memory attributes of the fused kernels");
     p.cpack = col_pack_waves(p.nx, p.ny) * device_sm_count();
+    // the two-pass forward launch: one block of rows and one of columns per
+    // CTA where one wave holds them all, never more CTAs than fit at once
+    if ((st = alloc(c, (void**)&p.gbar, sizeof(unsigned long long)))) return st;
+    if (cudaMemsetAsync(p.gbar, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+      return cuda_err(c, cudaGetLastError(), "grid-barrier counter");
+    {
+      int dev = 0, coop = 0, per = 0;
+      const int sms = device_sm_count();
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, p.k.fwd_both, W_FBOTH * 32, p.k.smem_fboth) ==
+              cudaSuccess) {
+        const int rb = W_FBOTH * p.k.lpw_x, cb = W_FBOTH * p.k.lpw_y;
+        const int want = std::max((p.ny / 2 + rb - 1) / rb, (p.ncols + cb - 1) / cb);
+        p.both_grid = std::min(want, sms * per);
+      }
+      cudaGetLastError();
+    }
     if (make_line_twiddles(p.nx, p.twx, c->stream) ||
         make_line_twiddles(p.ny, p.twy, c->stream) ||
         (p.twxw && make_wide_twiddles(p.nx, p.twxw, c->stream)) ||
@@ -465,7 +509,7 @@ struct Fused2D : Engine {
   }
 
   uint64_t kernels_per_step(const vofl_ctx* c) const override {
-    return (p.fused_forward() ? 1 : 2) + 2 * (uint64_t)p.groups(c->M, c->general);
+    return (p.one_forward_launch() ? 1 : 2) + 2 * (uint64_t)p.groups(c->M, c->general);
   }
 
   int set_schedule(vofl_ctx* c, const vofl_schedule* s) override {
@@ -493,7 +537,7 @@ struct Fused2D : Engine {
     p.wide_r = wr;
     p.cparts = s->col_parts;
     p.cpack = s->col_pack < 0 ? col_pack_waves(p.nx, p.ny) * device_sm_count() : s->col_pack;
-    p.fuse_fwd = s->fuse_forward < 0 ? fuse_forward_default(p.ny) : s->fuse_forward == 1;
+    p.fuse_fwd = s->fuse_forward < 0 ? fuse_forward_default(p.nx, p.ny) : s->fuse_forward;
     p.wide_f = p.k.fwd_rows_w && (s->wide_fwd < 0 ? wide_fwd_default(p.nx) : s->wide_fwd == 1);
     p.rsplit = s->row_split == 0 ? row_split_default(p.nx, p.ny, p.k.wir) : s->row_split;
     return VOFL_OK;
@@ -506,7 +550,7 @@ struct Fused2D : Engine {
     s->col_parts = p.cparts > 0 ? p.cparts : col_parts_default(p.ny);
     s->col_pack = p.cpack;
     s->group = p.G;
-    s->fuse_forward = p.fused_forward() ? 1 : 0;
+    s->fuse_forward = p.forward_both() ? 2 : p.fused_forward() ? 1 : 0;
     s->wide_fwd = p.wide_f && p.k.fwd_rows_w ? 1 : 0;
     s->row_split = (p.wide_r && p.k.inv_rows_w) ? 1 : p.rsplit;
     return VOFL_OK;
@@ -518,8 +562,8 @@ struct Fused2D : Engine {
     e.out1 = (float*)o1;
     e.out2 = (float*)o2;
     e.src_flat = -1;
-    cudaError_t err = p.forward(c->stream, (const float*)u, false);
-    if (!err) err = p.inverse(c->stream, c->M, e, nullptr, c->general);
+    cudaError_t err = p.forward(c->stream, (const float*)u, false, nullptr, false);
+    if (!err) err = p.inverse(c->stream, c->M, e, nullptr, c->general, 0, false);
     if (err) return cuda_err(c, err, "fused 2D launch");
     return VOFL_OK;
   }
@@ -557,8 +601,8 @@ struct Fused2D : Engine {
     if (cap < 4) return 0;
     const int K = p.groups(c->M, c->general);
     const int slots = term_split(c->M, c->general).slots;
-    const bool ff = p.fused_forward();
-    const int base = ff ? 1 : 2;  // event after which the first inverse kernel starts
+    const bool ff = p.fused_forward(), one = p.one_forward_launch();
+    const int base = one ? 1 : 2;  // event after which the first inverse kernel starts
     const int nk = base + 2 * K;
     // one event set per repetition; all repetitions are queued back to back
     // (one warm-up first) and read after a single synchronisation, so the
@@ -589,7 +633,7 @@ struct Fused2D : Engine {
       float t;
       cudaEventElapsedTime(&t, er[0], er[1]);
       acc[0] += t;
-      if (!ff) {
+      if (!one) {
         cudaEventElapsedTime(&t, er[1], er[2]);
         acc[1] += t;
       }
@@ -606,10 +650,10 @@ struct Fused2D : Engine {
     // ms = average per launch; units = complex line transforms per launch
     // (algorithmic: a fused forward column transform counts once per step)
     int n = 0;
-    std::string nm = p.wide_f && p.k.fwd_rows_w ? "k2d_fwd_rows_w" : "k2d_fwd_rows";
+    std::string nm = p.forward_both() ? "k2d_fwd_both" : p.wide_f && p.k.fwd_rows_w ? "k2d_fwd_rows_w" : "k2d_fwd_rows";
     ms[n] = acc[0] / reps;
-    units[n++] = p.ny / 2.0;
-    if (!ff) {
+    units[n++] = p.ny / 2.0 + (p.forward_both() ? p.ncols : 0);
+    if (!one) {
       nm += ";k2d_fwd_cols";
       ms[n] = acc[1] / reps;
       units[n++] = p.ncols;

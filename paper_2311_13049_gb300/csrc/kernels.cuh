@@ -70,28 +70,29 @@ template <bool Z3>
 constexpr int frows_nrows() {
   return Z3 ? 8 : 4;
 }
-template <int NX, bool Z3>
+template <int NX, bool Z3, int W = W_FROWS>
 constexpr size_t frows_smem() {
-  return exch_smem<NX, W_FROWS>() + (size_t)W_FROWS * LineFFT<NX>::LPW * frows_nrows<Z3>() * NX * sizeof(float);
+  return exch_smem<NX, W>() + (size_t)W * LineFFT<NX>::LPW * frows_nrows<Z3>() * NX * sizeof(float);
 }
 
-template <int NX, bool Z3>
+// W: warps per CTA (bx counts blocks of W warps)
+template <int NX, bool Z3, int W = W_FROWS>
 __device__ __forceinline__ void fwd_rows_body(int bx, const float* __restrict__ u, float2* __restrict__ T, int ny,
                                               int nz, int pT, float ryy, float rzz, const float2* __restrict__ twx,
                                               int* step_ctr, int inc_step, int* err) {
   using F = LineFFT<NX>;
-  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, H = NX / 2, THREADS = W_FROWS * 32;
+  constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, H = NX / 2, THREADS = W * 32;
   constexpr int NR = frows_nrows<Z3>();
   constexpr uint32_t ROWB = NX * sizeof(float);
   __shared__ float2 s_tw[F::TW];
-  __shared__ uint64_t s_rbar[W_FROWS * LPW];
+  __shared__ uint64_t s_rbar[W * LPW];
   extern __shared__ __align__(128) float2 s_buf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = lane % LANES, line = lane / LANES;
   const int lid = warp * LPW + line;
   uint64_t* bar = &s_rbar[lid];
   // rows of this line: 0 y-1, 1 y0, 2 y0+1, 3 y0+2 [, 4-5 the pair at z-1, 6-7 at z+1]
-  float* srow = reinterpret_cast<float*>(s_buf + W_FROWS * warp_stride<NX>()) + (size_t)lid * NR * NX;
+  float* srow = reinterpret_cast<float*>(s_buf + W * warp_stride<NX>()) + (size_t)lid * NR * NX;
   if (li == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -104,7 +105,7 @@ __device__ __forceinline__ void fwd_rows_body(int bx, const float* __restrict__ 
   float2* wbuf = s_buf + warp * warp_stride<NX>();
   // rows are flattened over planes: row = z * ny + y (nz = 1 in 2D); a
   // pair of rows never straddles two planes (ny is even)
-  const int pair = (bx * W_FROWS + warp) * LPW + line;
+  const int pair = (bx * W + warp) * LPW + line;
   const bool active = pair < (ny / 2) * nz;
   const int r0i = 2 * (active ? pair : 0);
   const int yy = r0i % ny, zz = r0i / ny;
@@ -196,12 +197,14 @@ __global__ void __launch_bounds__(W_FROWS * 32) k2d_fwd_rows(const float* __rest
 // the column, whose output is a contiguous column of Uh.  blockIdx.y runs
 // over independent planes (strides in_plane, out_plane).
 // -------------------------------------------------------------------------
-template <int NY>
+// COHERENT: T was written earlier in the same launch by other CTAs (the
+// two-pass forward kernel): its loads bypass L1 (ld.global.cg).
+template <int NY, int W = W_FCOLS, bool COHERENT = false>
 __device__ __forceinline__ void fwd_cols_body(int bx, const float2* __restrict__ T, int pT, float2* __restrict__ Uh,
                                               int ncols, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL;
-  constexpr int THREADS = W_FCOLS * 32, CW = W_FCOLS * LPW;  // columns per CTA
+  constexpr int THREADS = W * 32, CW = W * LPW;  // columns per CTA
   __shared__ float2 s_tw[F::TW];
   extern __shared__ __align__(128) float2 s_buf[];
   for (int i = threadIdx.x; i < F::TW; i += THREADS) s_tw[i] = twy[i];
@@ -214,7 +217,10 @@ __device__ __forceinline__ void fwd_cols_body(int bx, const float2* __restrict__
     const int col = min(c0 + cc, ncols - 1);
     float2 v[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = T[(size_t)(j + LANES * r) * pT + col];
+    for (int r = 0; r < E; ++r) {
+      const float2* src = T + (size_t)(j + LANES * r) * pT + col;
+      v[r] = COHERENT ? __ldcg(src) : *src;
+    }
     float2* lb = s_buf + (cc / LPW) * warp_stride<NY>() + (cc % LPW) * F::PAD_LINE;
     stage0_to_smem<NY, false>(v, lb, j);
   }
@@ -244,6 +250,37 @@ __global__ void __launch_bounds__(W_FCOLS * 32) k2d_fwd_cols(const float2* __res
                                                              long long out_plane) {
   // blockIdx.y: independent planes (3D: one per z)
   fwd_cols_body<NY>(blockIdx.x, T + blockIdx.y * in_plane, pT, Uh + blockIdx.y * out_plane, ncols, twy);
+}
+
+// -------------------------------------------------------------------------
+// F1 + F2 in one cooperative launch (every CTA resident at once): the
+// forward row pass over blocks of W_FBOTH warps, a grid-wide barrier
+// (bounded), then the forward column pass over blocks of W_FBOTH columns.
+// The arithmetic of k2d_fwd_rows and k2d_fwd_cols, so the same bits, with
+// one kernel boundary (launch ramp and drain) fewer per step.
+// -------------------------------------------------------------------------
+constexpr int W_FBOTH = 4;
+template <int NX, int NY>
+constexpr size_t fboth_smem() {
+  return std::max(frows_smem<NX, false, W_FBOTH>(), exch_smem<NY, W_FBOTH>());
+}
+template <int NX, int NY>
+__global__ void __launch_bounds__(W_FBOTH * 32) k2d_fwd_both(const float* __restrict__ u, float2* __restrict__ T,
+                                                             float2* __restrict__ Uh, int ny, int pT, int ncols,
+                                                             float ryy, const float2* __restrict__ twx,
+                                                             const float2* __restrict__ twy, int* step_ctr,
+                                                             int inc_step, int* err, unsigned long long* gbar) {
+  constexpr int RB = W_FBOTH * LineFFT<NX>::LPW, CB = W_FBOTH * LineFFT<NY>::LPW;
+  const int nrb = (ny / 2 + RB - 1) / RB, ncb = (ncols + CB - 1) / CB;
+  for (int b = blockIdx.x; b < nrb; b += gridDim.x) {
+    fwd_rows_body<NX, false, W_FBOTH>(b, u, T, ny, 1, pT, ryy, 0.f, twx, step_ctr, inc_step, err);
+    __syncthreads();  // shared buffers free for the next block
+  }
+  grid_barrier_bounded(gbar, err);
+  for (int b = blockIdx.x; b < ncb; b += gridDim.x) {
+    fwd_cols_body<NY, W_FBOTH, true>(b, T, pT, Uh, ncols, twy);
+    __syncthreads();
+  }
 }
 
 // -------------------------------------------------------------------------
@@ -835,6 +872,24 @@ inline float inv_factorial(int m) {
   double f = 1.0;
   for (int i = 2; i <= m; ++i) f *= i;
   return (float)(1.0 / f);
+}
+
+// Cooperative launch (every CTA resident at once, for kernels with a
+// grid-wide barrier); the grid must not exceed the resident capacity.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
 // Launch with programmatic stream serialisation: the kernel may start while

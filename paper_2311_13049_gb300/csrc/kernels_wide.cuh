@@ -27,8 +27,13 @@ namespace {
 // inverse row pass at 512 and 1024 (measured per size; vofl_set_schedule
 // changes it per context).
 inline bool wide_cols_default(int ny) { return ny == 512; }
-// wide forward row pass at 1024 (1% shorter step; neutral at 512)
-inline bool wide_fwd_default(int nx) { return nx == 1024; }
+// wide forward row pass: an option only (at 1024 it made the two-kernel
+// forward 1% shorter, but both forward passes in one launch, which use
+// 32-element lines, are 2% shorter still)
+inline bool wide_fwd_default(int nx) {
+  (void)nx;
+  return false;
+}
 inline bool wide_rows_default(int nx) { return nx == 512 || nx == 1024; }
 // Taylor terms per group: 17, so that M <= 16 runs in one group (one column
 // and one row launch per step).  Every launch boundary costs a few
@@ -47,13 +52,20 @@ inline int row_split_default(int nx, int ny, int warps) {
   const int want = (long long)nx * ny <= 256LL * 256 ? 4 : 1;
   return warps % want == 0 ? want : 1;
 }
-// The forward column transform inside the top group's inverse column
-// kernel (one launch fewer per step; every CTA of the group transforms its
-// own columns, the same arithmetic as k2d_fwd_cols): on grids of up to 256
-// rows, where a launch boundary is a large part of the step (256^2: 6%
-// shorter); at 768 and 1024 the duplicated column transforms (two
-// operators, every run) cost more than the launch (2% longer).
-inline bool fuse_forward_default(int ny) { return ny <= 256; }
+// Forward passes.  1: the forward column transform inside the top group's
+// inverse column kernel (one launch fewer per step; every CTA of the group
+// transforms its own columns, the same arithmetic as k2d_fwd_cols): on
+// grids of up to 256 rows, where a launch boundary is a large part of the
+// step (256^2: 6% shorter); at 768 and 1024 the duplicated column
+// transforms (two operators, every run) cost more than the launch (2%
+// longer).  2: both forward passes in one cooperative launch
+// (k2d_fwd_both): per leap-frog step, M = 16, 512^2 0.0486 -> 0.0471 ms,
+// 768^2 0.1008 -> 0.0985, 1024^2 0.1166 -> 0.1142; at 256^2 and 128^2 it
+// loses to 1 (0.0266 vs 0.0246, 0.0233 vs 0.0205).
+inline int fuse_forward_default(int nx, int ny) {
+  if (ny <= 256) return 1;
+  return (nx == ny && (nx == 512 || nx == 768 || nx == 1024)) ? 2 : 0;
+}
 // Runs of terms per group in the column pass (each on its own CTAs): small
 // grids have fewer column blocks than SMs.
 inline int col_parts_default(int ny) { return ny <= 256 ? 3 : (ny <= 512 ? 6 : 1); }

@@ -76,6 +76,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
   return true;
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident), bounded:
+// `ctr` is a per-context counter that only this barrier touches and only
+// grows; each launch of gridDim.x CTAs advances it by gridDim.x, and a CTA
+// waits until the count reaches the end of its launch's round.  Writes
+// before the barrier are visible to every CTA after it (fences around the
+// arrival and the wait).  A wait past the budget sets the error word and
+// lets the CTA go on (the launch's results are then reported invalid).
+__device__ __forceinline__ void grid_barrier_bounded(unsigned long long* ctr, int* err,
+                                                     long long budget = kWaitBudgetCycles) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long n = gridDim.x;
+    __threadfence();
+    const unsigned long long ticket = atomicAdd(ctr, 1ULL);
+    const unsigned long long target = (ticket / n + 1) * n;
+    const volatile unsigned long long* vc = ctr;
+    const long long t0 = clock64();
+    while (*vc < target) {
+      if (clock64() - t0 > budget) {
+        if (err) atomicExch(err, 1);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 // Hint: bring `bytes` (a multiple of 16) at the 16-byte aligned global
 // address p into L2 (no completion to wait for; data may change later).
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {

@@ -49,6 +49,8 @@ run2d((512, 512), (0, 0, 2, 5, 1, 1, 0))
 run2d((1024, 1024), (1, 0, 2, 4, 1, 0, 0))
 run2d((256, 256), (-1, -1, 1, 3, 0, -1, 2))
 run2d((1024, 1024), (0, -1, 0, 6, 1, -1, 0, 300))
+run2d((1024, 1024), (0, -1, 0, 0, 2, 0, 0, -1))
+run2d((256, 256), (0, -1, 0, 0, 2, 0, 0, -1))
 run2d((512, 512), (1, -1, 0, 0, -1, -1, 0, 5000))
 run2d((128, 256))
 run2d((256, 1024))

@@ -24,7 +24,9 @@ SCHEDULES = [(-1, -1, 0, 0, -1, -1, 0, -1), (0, 0, 0, 0, 0, 0, 0, 0), (1, 1, 0, 
              # column transform in the same kernel, wide columns
              (0, -1, 0, 0, 0, -1, 0, 1), (0, -1, 0, 0, 0, -1, 0, 152), (0, -1, 0, 0, 0, -1, 0, 5000),
              (0, -1, 0, 5, 0, -1, 0, 37), (0, -1, 0, 0, 1, -1, 0, 152), (0, -1, 0, 6, 1, -1, 0, 300),
-             (1, -1, 0, 0, -1, -1, 0, 152), (1, -1, 0, 4, -1, -1, 0, 61)]
+             (1, -1, 0, 0, -1, -1, 0, 152), (1, -1, 0, 4, -1, -1, 0, 61),
+             # both forward passes in one cooperative launch
+             (0, -1, 0, 0, 2, 0, 0, -1), (1, 1, 0, 5, 2, -1, 0, 0), (0, 0, 3, 17, 2, 1, 0, 152)]
 
 
 @pytest.mark.parametrize("n", [512, 1024])
@@ -57,11 +59,11 @@ def test_every_schedule_matches_the_oracle(V, n):
 
 def test_default_schedules(V):
     import torch
-    base = {"group": 17, "wide_cols": 0, "wide_rows": 0, "fuse_forward": 0, "wide_fwd": 0, "row_split": 1}
+    base = {"group": 17, "wide_cols": 0, "wide_rows": 0, "fuse_forward": 2, "wide_fwd": 0, "row_split": 1}
     want = {256: dict(base, col_parts=3, fuse_forward=1, row_split=4),
             512: dict(base, col_parts=6, wide_cols=1, wide_rows=1),
             768: dict(base, col_parts=1),
-            1024: dict(base, col_parts=1, wide_rows=1, wide_fwd=1)}
+            1024: dict(base, col_parts=1, wide_rows=1)}
     for n, w in want.items():
         with V.Solver((n, n)) as s:
             got = s.schedule()
@@ -114,24 +116,33 @@ def test_schedule_runs_agree_and_batch_needs_one_schedule_per_size(V):
 
 
 def test_fused_forward_is_bit_identical(V):
-    """The forward column transform inside the column kernel is the same
-    arithmetic as the separate forward kernel: same bits, any grid."""
+    """The forward column transform inside the column kernel, and both
+    forward passes in one cooperative launch, are the same arithmetic as
+    the separate forward kernels: same bits, any grid (also over a run of
+    steps, whose step counter the cooperative launch advances)."""
     import torch
-    for shape in [(256, 256), (1024, 1024), (768, 768), (128, 256)]:
+    for shape in [(256, 256), (1024, 1024), (768, 768), (128, 256), (512, 512), (512, 64)]:
         Q = S.q_lowpass(shape, 41)
         u = S.q_lowpass(shape, 42, qmin=-1.0, qmax=1.0, sigma_k=16).astype(np.float32)
-        outs = []
+        outs, runs = [], []
         with V.Solver(shape) as s:
             s.set_q(Q)
             s.set_M(16)
             ut = torch.from_numpy(u).cuda()
-            for ff in (0, 1):
-                s.set_schedule(0, -1, 0, 0, ff)
+            for ff in (0, 1, 2):
+                s.set_schedule(0, -1, 0, 0, ff, 0)
+                assert s.schedule()["fuse_forward"] == ff, (shape, ff, s.schedule())
                 o1, o2 = torch.empty_like(ut), torch.empty_like(ut)
                 s.apply_pair(ut, o1, o2)
                 s.sync()
                 outs.append((o1.cpu().numpy(), o2.cpu().numpy()))
-        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1]), shape
+                s.set_state(np.zeros(shape, np.float32))
+                s.set_source(S.center_index(shape), S.ricker_samples(12, 5e-4, 10.0))
+                s.step(12, 5e-4)
+                runs.append(s.get_state())
+        for o, r in zip(outs[1:], runs[1:]):
+            assert np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1]), shape
+            assert np.array_equal(runs[0], r), shape
 
 
 @pytest.mark.parametrize("shape", [(256, 256), (128, 128), (64, 64), (128, 256)])
