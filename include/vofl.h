@@ -370,12 +370,14 @@ VOFL_API int vofl_get_schedule(vofl_ctx* ctx, vofl_schedule* sched);
 VOFL_API const char* vofl_version(void);
 
 /* Self-test of the failure path of device waits (no counterpart in the
- * paper).  Every wait inside the kernels (on TMA copy completion) is bounded
- * by a clock budget: when it runs out the kernel sets an error word, drains
+ * paper).  Every wait inside the kernels (on TMA copy completion, and the
+ * grid-wide barrier of the cooperative forward launch) is bounded by a
+ * clock budget: when it runs out the kernel sets an error word, drains
  * what it issued and returns, and vofl_sync() reports VOFL_ETIMEDOUT.  This
- * launches one kernel that waits on a barrier nothing completes, with a
- * ~1 ms budget; *gave_up is set to 1 when the wait gave up as designed.  It
- * faults and hangs nothing; the device stays usable.  Synchronous. */
+ * launches one kernel that waits on an mbarrier nothing completes and one
+ * of two CTAs whose second CTA never reaches the grid barrier, each with a
+ * ~1 ms budget; *gave_up is set to 1 when both waits gave up as designed.
+ * It faults and hangs nothing; the device stays usable.  Synchronous. */
 VOFL_API int vofl_selftest_bounded_wait(int* gave_up);
 
 /* Test hook for the out-of-memory paths (no counterpart in the paper).

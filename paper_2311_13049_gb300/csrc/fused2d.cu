@@ -206,7 +206,7 @@ struct Plan2D {
   // group's column kernel, 2 both passes in one cooperative launch
   int fuse_fwd = 0;
   int both_grid = 0;                   // CTAs of that launch (0: not resident-safe here)
-  unsigned long long* gbar = nullptr;  // its grid-barrier counter
+  unsigned long long* gbar = nullptr;  // its grid barrier's count and generation
   int cparts = 0;
   int cpack = 0;   // > 0: the column pass's terms dealt out over cpack CTAs (col_run)
   int rsplit = 1;  // runs of terms per row in the (32-element) row kernel
@@ -419,8 +419,8 @@ struct Fused2D : Engine {
     p.cpack = col_pack_waves(p.nx, p.ny) * device_sm_count();
     // the two-pass forward launch: one block of rows and one of columns per
     // CTA where one wave holds them all, never more CTAs than fit at once
-    if ((st = alloc(c, (void**)&p.gbar, sizeof(unsigned long long)))) return st;
-    if (cudaMemsetAsync(p.gbar, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+    if ((st = alloc(c, (void**)&p.gbar, 2 * sizeof(unsigned long long)))) return st;
+    if (cudaMemsetAsync(p.gbar, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
       return cuda_err(c, cudaGetLastError(), "grid-barrier counter");
     {
       int dev = 0, coop = 0, per = 0;

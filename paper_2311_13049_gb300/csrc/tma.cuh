@@ -76,29 +76,36 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
   return true;
 }
 
-// Grid-wide barrier of a cooperative launch (every CTA resident), bounded:
-// `ctr` is a per-context counter that only this barrier touches and only
-// grows; each launch of gridDim.x CTAs advances it by gridDim.x, and a CTA
-// waits until the count reaches the end of its launch's round.  Writes
-// before the barrier are visible to every CTA after it (fences around the
-// arrival and the wait).  A wait past the budget sets the error word and
-// lets the CTA go on (the launch's results are then reported invalid).
-__device__ __forceinline__ void grid_barrier_bounded(unsigned long long* ctr, int* err,
+// Grid-wide barrier of a cooperative launch (every CTA resident), bounded.
+// bar[0] counts the CTAs that arrived, bar[1] is the generation: each CTA
+// reads the generation, then arrives; the last of the grid's CTAs resets
+// the count and advances the generation, which releases the others.  (Any
+// grid size per launch; launches that use the same counter pair run one
+// after another.)  Writes before the barrier are visible to every CTA
+// after it (fences around the arrival and the wait).  A wait past the
+// budget sets the error word and lets the CTA go on (the launch's results
+// are then reported invalid).
+__device__ __forceinline__ void grid_barrier_bounded(unsigned long long* bar, int* err,
                                                      long long budget = kWaitBudgetCycles) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned long long n = gridDim.x;
+    const unsigned long long n = (unsigned long long)gridDim.x * gridDim.y * gridDim.z;
+    const volatile unsigned long long* vgen = bar + 1;
+    const unsigned long long g0 = *vgen;
     __threadfence();
-    const unsigned long long ticket = atomicAdd(ctr, 1ULL);
-    const unsigned long long target = (ticket / n + 1) * n;
-    const volatile unsigned long long* vc = ctr;
-    const long long t0 = clock64();
-    while (*vc < target) {
-      if (clock64() - t0 > budget) {
-        if (err) atomicExch(err, 1);
-        break;
+    if (atomicAdd(bar, 1ULL) + 1 == n) {
+      atomicExch(bar, 0ULL);
+      __threadfence();
+      atomicAdd(bar + 1, 1ULL);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g0) {
+        if (clock64() - t0 > budget) {
+          if (err) atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(32);
       }
-      __nanosleep(32);
     }
     __threadfence();
   }
