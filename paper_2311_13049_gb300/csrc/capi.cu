@@ -749,6 +749,7 @@ int vofl_sync(vofl_ctx* c) {
   VOFL_CUDA(c, cudaMemcpy(&werr, c->d_step + 1, sizeof(int), cudaMemcpyDeviceToHost));
   if (werr) {
     VOFL_CUDA(c, cudaMemset(c->d_step + 1, 0, sizeof(int)));
+    c->eng->reset_waits(c);
     return set_err(c, VOFL_ETIMEDOUT, "a device wait gave up (asynchronous copy never completed)");
   }
   return VOFL_OK;

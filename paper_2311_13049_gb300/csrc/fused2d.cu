@@ -508,6 +508,12 @@ struct Fused2D : Engine {
     return VOFL_OK;
   }
 
+  // a grid barrier that timed out leaves its count short of a full round
+  void reset_waits(vofl_ctx* c) override {
+    (void)c;
+    if (p.gbar && cudaMemset(p.gbar, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) cudaGetLastError();
+  }
+
   uint64_t kernels_per_step(const vofl_ctx* c) const override {
     return (p.one_forward_launch() ? 1 : 2) + 2 * (uint64_t)p.groups(c->M, c->general);
   }

@@ -259,6 +259,10 @@ struct Engine {
     (void)t;
     return VOFL_EUNSUPPORTED;
   }
+  // after a device wait gave up (the error word was set): put back the
+  // device-side state of the engine's waits (grid-barrier counters), so
+  // later launches start from a clean barrier; called with the stream idle
+  virtual void reset_waits(vofl_ctx* c) { (void)c; }
   // size M-dependent scratch before stepping or applying (outside any graph
   // capture: allocations and plans are not stream operations)
   virtual int prepare(vofl_ctx* c) {
