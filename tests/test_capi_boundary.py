@@ -83,3 +83,16 @@ def test_no_gpu_means_a_clean_error(vofl):
         pytest.skip("a GPU is present")
     with pytest.raises(vofl.VoflError):
         vofl.Solver((64, 64), impl=vofl.IMPL_PLAIN)
+
+
+def test_schedule_struct_matches_the_header(vofl):
+    """The binding's Schedule mirrors vofl_schedule field by field (all
+    int, in the header's order): a field added on one side only would shift
+    every later field across the C ABI."""
+    src = open(os.path.join(ROOT, "include", "vofl.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\}\s*vofl_schedule;", src).group(1)
+    fields = re.findall(r"\bint\s+(\w+)\s*;", body)
+    assert fields and len(fields) == body.count(";")
+    assert [f for f, _ in vofl.Schedule._fields_] == fields
+    assert all(t is C.c_int for _, t in vofl.Schedule._fields_)
+    assert C.sizeof(vofl.Schedule) == 4 * len(fields)
