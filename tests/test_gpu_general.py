@@ -365,3 +365,32 @@ def test_batches_take_seismic_contexts_only(V):
         sv.set_state(np.zeros(shape, np.float32))
         with pytest.raises(V.VoflError):
             b.add(sv, 1e-3)
+
+
+def test_tsfp2_fused_split_calls_agree(V):
+    """On the fused path one vofl_step call brackets its steps by the flows
+    over +dt/2 and -dt/2; a run split over several calls differs from one
+    call only by those extra (exactly cancelling) flows: FP32 round-off,
+    far below the run tolerance; both match the oracle."""
+    shape, lo, hi = (256, 256), [-8.0, -8.0], [8.0, 8.0]
+    s = _s2d(shape, lo, hi)
+    xg, yg = S.mesh(shape, lo, hi)
+    u0 = np.exp(-(xg ** 2 + yg ** 2) / 2.0).astype(np.float32)
+    v0 = (0.2 * np.cos(np.pi * xg / 8) * np.sin(np.pi * yg / 4)).astype(np.float32)
+    dt, M = 1e-3, 10
+    outs = []
+    for calls in ([12], [5, 7], [1] * 12):
+        with V.Solver(shape, lo, hi) as sv:
+            sv.set_order(s, kappa=1.0, f3=1.0)
+            sv.set_M(M)
+            sv.set_scheme(V.SCHEME_TSFP2)
+            sv.set_state(u0, v0)
+            for n in calls:
+                sv.step(n, dt)
+            assert sv.steps_taken() == 12
+            outs.append(sv.get_state().astype(np.float64))
+    r = O.general_tsfp2(s, 1.0, lambda u: u ** 3, u0.astype(np.float64), v0.astype(np.float64), dt, 12, M, lo, hi)
+    for g in outs:
+        check(g, r, 1e-4)
+    for g in outs[1:]:
+        check(g, outs[0], 1e-5)
