@@ -689,9 +689,12 @@ size_t fused2d_footprint(const int64_t* n, int M) {
   const size_t G = group_default((int)nx, (int)ny);
   const size_t tww = (wide_line((int)nx) ? wide_twiddle_entries((int)nx) : 0) +
                      (wide_line((int)ny) ? wide_twiddle_entries((int)ny) : 0);
+  // float tables: P (two), ln|mu|^2 and, for the general model, the time
+  // splitting's frequencies (counted always: an upper bound); then the
+  // grid barrier's two words
   return sizeof(float2) * (ny * p + nc * ny + ny * p * 2 * G + line_twiddle_entries((int)nx) +
                            line_twiddle_entries((int)ny) + tww) +
-         sizeof(float) * (2 * nx * ny + 3 * nc * ny);
+         sizeof(float) * (2 * nx * ny + 4 * nc * ny) + 2 * sizeof(unsigned long long);
 }
 
 Engine* make_fused2d(vofl_ctx* c, int* status) {
