@@ -385,6 +385,7 @@ def configs_bench(V, torch, stream, flush, reps=3):
     out["cnfp_table2_s1_1d_4096_f64"] = cnfp_bench(V, S, stream)
     out["generic_apply_2d_512_M20_f32"] = generic_apply_bench(V, S, torch, stream)
     out["tsfp2_2d_1024_M16_f32"] = tsfp2_2d_bench(V, S, torch, stream)
+    out["small_grids_2d_f32"] = small_grids_bench(V, S, torch, stream)
     w3 = S.workload_3d_256()
     f, p = run(w3, V.F32, V.IMPL_FUSED), run(w3, V.F32, V.IMPL_PLAIN)
     out["3d_256_f32"] = {"workload": "3D 256^3, FP32, M=8, two-layer Q (10/80), Gaussian pulse sigma = 4 cells, "
@@ -561,6 +562,42 @@ def tsfp2_2d_bench(V, S, torch, stream, nsteps=100):
     res["fused_over_plain"] = res["plain"]["ms_per_step"] / res["fused"]["ms_per_step"]
     res["workload"] = ("1024^2 on [-8,8]^2, s = 1 - 0.4 cos(pi x/4) cos(pi y/4), kappa = 1, f(u) = u^3, M = 16, "
                        f"dt = {dt:.4g} (0.25 x 2/omega_max), Gaussian u0, v0 = 0, {nsteps} splitting steps")
+    return res
+
+
+def small_grids_bench(V, S, torch, stream, nsteps=200, reps=3):
+    """The seismic leap-frog step on the smaller grids of the batch and
+    serve workloads: the headline's model and source (Q low-passed noise,
+    Ricker f0 = 10 at the centre, dt = 5e-4) at 256^2 and 512^2, M = 12 and
+    16, fused FP32 against the plain (cuFFT) FP32 path; per step, CUDA events
+    over `nsteps` graph-replayed steps after 10, best of `reps`."""
+    res = {}
+    for n in (256, 512):
+        for M in (12, 16):
+            w = S.workload_2d_1024(nsteps=nsteps + 10, n=n, M=M)
+            row = {}
+            for nm, im in (("fused", V.IMPL_FUSED), ("plain", V.IMPL_PLAIN)):
+                best = 1e9
+                with V.Solver(w["shape"], prec=V.F32, impl=im, stream=stream.cuda_stream) as sv:
+                    sv.set_q(w["Q"], w["c0"], w["omega0"])
+                    sv.set_M(M)
+                    for _ in range(reps):
+                        with torch.cuda.stream(stream):
+                            sv.set_state(np.zeros(w["shape"], np.float32))
+                            sv.set_source(w["src_idx"], w["src"])
+                            sv.step(10, w["dt"])
+                            stream.synchronize()
+                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            e0.record(stream)
+                            sv.step(nsteps, w["dt"])
+                            e1.record(stream)
+                            e1.synchronize()
+                        best = min(best, e0.elapsed_time(e1) / nsteps)
+                row[nm + "_ms_per_step"] = best
+            row["fused_over_plain"] = row["plain_ms_per_step"] / row["fused_ms_per_step"]
+            res[f"{n}x{n}_M{M}"] = row
+    res["workload"] = ("seismic model of the headline (Q low-passed noise seed 2, Ricker f0 = 10 at the centre, "
+                       "dt = 5e-4) at 256^2 and 512^2, M = 12 and 16; per leap-frog step")
     return res
 
 
