@@ -644,8 +644,9 @@ def serve_bench(nreq, check=3):
 def profile_run(V, S, stream, args):
     """Short runs for profilers (print nothing): set-up, then ncu_steps steps
     of the 3D 256^3 workload, of the 64-simulation batch, of the Table 2
-    CNFP problem (1D 4096 FP64, dt = 2^-9), of the 1D 256 FP64 run, or
-    ncu_steps applies of the generic 512^2 operator (M = 20)."""
+    CNFP problem (1D 4096 FP64, dt = 2^-9), of the 1D 256 FP64 run, of the
+    fused 2D time splitting (1024^2, M = 16), or ncu_steps applies of the
+    generic 512^2 operator (M = 20)."""
     if args.ncu_workload == "cnfp":
         J = 4096
         x = S.axis(J, -32.0, 32.0)
@@ -664,6 +665,17 @@ def profile_run(V, S, stream, args):
             sv.set_q(w["Q"], w["c0"], w["omega0"])
             sv.set_state(w["u0"])
             sv.step(args.ncu_steps, w["dt"])
+            sv.sync()
+        return 0
+    if args.ncu_workload == "tsfp2":
+        shape, lo, hi = (1024, 1024), [-8.0, -8.0], [8.0, 8.0]
+        xg, yg = S.mesh(shape, lo, hi)
+        with V.Solver(shape, lo, hi, V.F32, V.IMPL_FUSED, stream=stream.cuda_stream) as sv:
+            sv.set_order(1.0 - 0.4 * np.cos(np.pi * xg / 4) * np.cos(np.pi * yg / 4), kappa=1.0, f3=1.0)
+            sv.set_M(16)
+            sv.set_scheme(V.SCHEME_TSFP2)
+            sv.set_state(np.exp(-(xg ** 2 + yg ** 2) / 2.0).astype(np.float32))
+            sv.step(args.ncu_steps, sv.suggest_dt(0.25))
             sv.sync()
         return 0
     if args.ncu_workload == "generic":
@@ -943,7 +955,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the 600-request serving stream to serve (0: skip)")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving measurement")
-    ap.add_argument("--ncu-workload", default="2d", choices=["2d", "3d", "batch", "cnfp", "generic", "1d"],
+    ap.add_argument("--ncu-workload", default="2d", choices=["2d", "3d", "batch", "cnfp", "generic", "1d", "tsfp2"],
                     help="workload of the --ncu-steps profiling mode")
     ap.add_argument("--ncu-steps", type=int, default=0,
                     help="profiling mode: set up the workload, run this many leap-frog steps, print nothing")

@@ -192,6 +192,10 @@ struct Plan2D {
   float2 *twx = nullptr, *twy = nullptr;
   float2 *twxw = nullptr, *twyw = nullptr;  // wide line twiddles (512, 1024 points)
   float* Wrot = nullptr;  // time splitting: sqrt(kappa) |mu|^{s0}, [ncols][ny] (general model)
+  // flow tables over dt and over dt/2 ([2][3][ncols][ny], k_flow_table) and
+  // the dt they were built for (NaN: none)
+  float* flow = nullptr;
+  double flow_dt = std::nan("");
   const float* delta = nullptr;
   int* step_ctr = nullptr;
   int* err = nullptr;
@@ -303,21 +307,24 @@ struct Plan2D {
   // The exact flow of the splitting over time t (Sec. 3.3) on u, v in place
   // (kernels_split.cuh), three launches.  Scratch: the row spectra in the Z
   // buffer (two [ny][pT] planes; Z holds at least that).
-  cudaError_t rotate(cudaStream_t s, float* u, float* v, float t) const {
+  // half: the flow over dt/2 (else over dt); sign -1: backwards
+  cudaError_t rotate(cudaStream_t s, float* u, float* v, bool half, float sign) const {
     float2* Su = Z;
     float2* Sv = Z + (size_t)ny * pT;
     const float invN = (float)(1.0 / ((double)nx * (double)ny));
     const int rpc = W_ROT * k.lpw_x, cpc = W_ROT * k.lpw_y;
+    const float* tab = flow + (half ? (size_t)3 * ncols * ny : 0);
     cudaError_t e = launch_pdl(k.rot_rows, dim3((ny + rpc - 1) / rpc), dim3(W_ROT * 32), k.smem_rot_rows, s,
                                (const float*)u, (const float*)v, Su, Sv, ny, pT, (const float2*)twx);
     if (!e)
-      e = launch_pdl(k.rot_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_ROT * 32), k.smem_rot_cols, s, Su, Sv,
-                     (const float*)Wrot, t, invN, pT, ncols, (const float2*)twy);
+      e = launch_pdl(k.rot_cols, dim3((ncols + cpc - 1) / cpc), dim3(W_ROT * 32), k.smem_rot_cols, s, Su, Sv, tab,
+                     sign, invN, pT, ncols, (const float2*)twy);
     if (!e)
       e = launch_pdl(k.rot_irows, dim3((ny + rpc - 1) / rpc), dim3(W_ROT * 32), k.smem_rot_rows, s,
                      (const float2*)Su, (const float2*)Sv, u, v, ny, pT, (const float2*)twx);
     return e;
   }
+
 };
 
 // constants of a model on an nx * ny box of size lx * ly
@@ -352,6 +359,7 @@ struct Fused2D : Engine {
     dev_free(p.twxw);
     dev_free(p.twyw);
     dev_free(p.Wrot);
+    dev_free(p.flow);
     dev_free(p.gbar);
   }
 
@@ -461,8 +469,13 @@ struct Fused2D : Engine {
         const size_t b = sizeof(float) * (size_t)p.ncols * p.ny;
         if (int st = alloc(c, (void**)&p.Wrot, b)) return st;
       }
+      if (!p.flow) {
+        const size_t b = sizeof(float) * 6 * (size_t)p.ncols * p.ny;
+        if (int st = alloc(c, (void**)&p.flow, b)) return st;
+      }
       if (make_fused2d_omega(p.nx, p.ny, lx, ly, c->s01, c->kappa, p.Wrot, c->stream))
         return cuda_err(c, cudaGetLastError(), "splitting frequency table");
+      p.flow_dt = std::nan("");  // the flow tables follow the frequencies
     }
     return VOFL_OK;
   }
@@ -476,13 +489,25 @@ struct Fused2D : Engine {
   bool can_split() const override { return true; }
   bool split_merged() const override { return true; }
   int split_flow(vofl_ctx* c, double t) override {
-    if (!p.Wrot) return set_err(c, VOFL_ESTATE, "set the general model first");
-    cudaError_t err = p.rotate(c->stream, (float*)c->u[c->cur], (float*)c->u[1 - c->cur], (float)t);
+    if (!p.Wrot || !p.flow) return set_err(c, VOFL_ESTATE, "set the general model first");
+    if (!(p.flow_dt == c->dt)) {  // flow tables for this dt (outside any capture: a run starts here)
+      const long long n = (long long)p.ncols * p.ny;
+      const unsigned g = (unsigned)std::min<long long>((n + 255) / 256, 4096);
+      k_flow_table<<<g, 256, 0, c->stream>>>(p.Wrot, c->dt, p.flow, n);
+      k_flow_table<<<g, 256, 0, c->stream>>>(p.Wrot, 0.5 * c->dt, p.flow + 3 * n, n);
+      count_launch(2);
+      if (cudaGetLastError() != cudaSuccess) return set_err(c, VOFL_ECUDA, "splitting flow tables");
+      p.flow_dt = c->dt;
+    }
+    // the bracketing flows of a run: over +dt/2 and -dt/2
+    cudaError_t err = p.rotate(c->stream, (float*)c->u[c->cur], (float*)c->u[1 - c->cur], true, t < 0 ? -1.f : 1.f);
     if (err) return cuda_err(c, err, "fused 2D splitting flow");
     return VOFL_OK;
   }
   int step_split(vofl_ctx* c) override {
-    if (!p.Wrot) return set_err(c, VOFL_ESTATE, "set the general model first");
+    // the flow tables of c->dt were built by split_flow, which every run
+    // starts with
+    if (!p.Wrot || !p.flow || !(p.flow_dt == c->dt)) return set_err(c, VOFL_ESTATE, "set the general model first");
     float* u = (float*)c->u[c->cur];
     float* v = (float*)c->u[1 - c->cur];
     cudaError_t err = cudaSuccess;
@@ -503,7 +528,7 @@ struct Fused2D : Engine {
       err = launch_pdl(k2d_kick_f, dim3((unsigned)std::min<long long>((n + 255) / 256, 4096)), dim3(256), 0,
                        c->stream, (const float*)u, v, n, (float)c->dt, (float)c->f1, (float)c->f3);
     }
-    if (!err) err = p.rotate(c->stream, u, v, (float)c->dt);
+    if (!err) err = p.rotate(c->stream, u, v, false, 1.f);
     if (err) return cuda_err(c, err, "fused 2D splitting step");
     return VOFL_OK;
   }

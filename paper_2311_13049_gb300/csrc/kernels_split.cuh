@@ -87,10 +87,13 @@ __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_fwd_rows(const float* __re
 // inverse FFT along y of both back into Su, Sv (last stage cooperatively:
 // stores are row segments too).  Each CTA reads and writes only its own
 // columns, so the pass runs in place.
+// The flow over t comes from a table of (c, r, q) = (cos wt, sin(wt)/w,
+// w sin wt) per mode (k_flow_table; t for w = 0 in r), [3][ncols][NY];
+// sign = -1 runs it backwards (the flow over -t: r and q change sign).
 template <int NY>
 __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_cols(float2* __restrict__ Su, float2* __restrict__ Sv,
-                                                           const float* __restrict__ W, float t, float invN, int pT,
-                                                           int ncols, const float2* __restrict__ twy) {
+                                                           const float* __restrict__ tab, float sign, float invN,
+                                                           int pT, int ncols, const float2* __restrict__ twy) {
   using F = LineFFT<NY>;
   constexpr int E = F::E, LANES = F::LANES, LPW = F::LPW, BPL = F::BPL, RL = F::RL, NBL = F::NBL;
   constexpr int THREADS = W_ROT * 32, CW = W_ROT * LPW;  // columns per CTA
@@ -103,10 +106,7 @@ __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_cols(float2* __restrict__ 
   const int li = lane % LANES, line = lane / LANES;
   const int c0 = blockIdx.x * CW;
   const int cc = min(c0 + warp * LPW + line, ncols - 1);
-  // the table does not depend on the previous kernel
-  float wk[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) wk[m] = W[(size_t)cc * NY + li + LANES * m];
+  const long long tsz = (long long)ncols * NY;
   pdl_wait();  // Su, Sv are written by k2d_rot_fwd_rows
   pdl_trigger();
   float2* lbu = s_buf + warp * warp_stride<NY>() + line * F::PAD_LINE;
@@ -141,18 +141,11 @@ __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_cols(float2* __restrict__ 
   // the flow, element y = li + LANES m of the column (natural order)
 #pragma unroll
   for (int m = 0; m < E; ++m) {
+    const size_t i = (size_t)cc * NY + li + LANES * m;
+    const float cs = tab[i], r = sign * tab[tsz + i], ws = sign * tab[2 * tsz + i];
     const float2 p = a[m], q = b[m];
-    float2 p2, q2;
-    if (wk[m] > 0.f) {
-      float sn, cs;
-      sincosf(wk[m] * t, &sn, &cs);
-      const float r = sn / wk[m], ws = wk[m] * sn;
-      p2 = make_float2(fmaf(p.x, cs, q.x * r), fmaf(p.y, cs, q.y * r));
-      q2 = make_float2(fmaf(q.x, cs, -p.x * ws), fmaf(q.y, cs, -p.y * ws));
-    } else {
-      p2 = make_float2(fmaf(t, q.x, p.x), fmaf(t, q.y, p.y));
-      q2 = q;
-    }
+    const float2 p2 = make_float2(fmaf(p.x, cs, q.x * r), fmaf(p.y, cs, q.y * r));
+    const float2 q2 = make_float2(fmaf(q.x, cs, -p.x * ws), fmaf(q.y, cs, -p.y * ws));
     a[m] = cscale(p2, invN);
     b[m] = cscale(q2, invN);
   }
@@ -223,6 +216,25 @@ __global__ void __launch_bounds__(W_ROT * 32) k2d_rot_inv_rows(const float2* __r
   for (int m = 0; m < E; ++m) {
     u[row + li + LANES * m] = x[m].x;
     v[row + li + LANES * m] = x[m].y;
+  }
+}
+
+// The flow table over time t from the frequencies W (float, [ncols][ny]),
+// in double: (cos wt, sin(wt)/w, w sin wt), and (1, t, 0) where w = 0.
+__global__ void k_flow_table(const float* __restrict__ W, double t, float* __restrict__ tab, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double w = (double)W[i];
+    if (w > 0.0) {
+      double sn, cs;
+      sincos(w * t, &sn, &cs);
+      tab[i] = (float)cs;
+      tab[n + i] = (float)(sn / w);
+      tab[2 * n + i] = (float)(w * sn);
+    } else {
+      tab[i] = 1.f;
+      tab[n + i] = (float)t;
+      tab[2 * n + i] = 0.f;
+    }
   }
 }
 
