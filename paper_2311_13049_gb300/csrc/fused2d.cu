@@ -27,15 +27,21 @@
 // the operator-1 slot and K..M in the operator-2 slot (K = ceil((M+1)/2)),
 // summed as sum_0 + delta^K sum_1 in the epilogue: half the line
 // transforms.  The schedule (kernels_wide.cuh: group_default,
-// col_parts_default, wide_cols_default, wide_rows_default) sets per grid
-// size the terms per group, the runs of terms the column pass splits a
-// group into, and whether the 512/1024-point inverse passes use the wide
-// line transform (fft_wide.cuh); vofl_set_schedule overrides it.
+// col_parts_default, col_pack_waves, wide_cols_default, wide_rows_default,
+// fuse_forward_default) sets per grid size the terms per group, how the
+// column pass deals a group's terms to CTAs, whether the 512/1024-point
+// inverse passes use the wide line transform (fft_wide.cuh), and whether
+// F2 runs inside the top group's I1 or F1 and F2 share one cooperative
+// launch (k2d_fwd_both); vofl_set_schedule overrides it.
+// The second-order time splitting of the general model (Sec. 3.3) runs the
+// exact flow of its constant-order part on the kernels of kernels_split.cuh
+// and the kick with the remainder (terms 1..M) on F1, F2, I1, I2.
 //
 // Launches use programmatic dependent launch: each kernel does the work
 // that does not read its predecessor's output (twiddle and table loads,
 // barrier set-up) before griddepcontrol.wait, so it overlaps the tail of
-// the previous kernel.
+// the previous kernel.  The cooperative launch does not (it is launched
+// after its predecessor ends); its successor still overlaps it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
