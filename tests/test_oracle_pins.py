@@ -587,6 +587,20 @@ def test_tsfp2_constant_order_linear_mode_is_exact(s, k):
     assert np.max(np.abs(u - (np.cos(w * t) + b * np.sin(w * t) / w) * np.cos(k * x))) < 1e-12
 
 
+@pytest.mark.parametrize("s,k1,k2", [(0.8, 2, 1), (1.3, 1, 3)])
+def test_tsfp2_constant_order_linear_mode_is_exact_2d(s, k1, k2):
+    """The same exact single-mode solution on a 2D box with unequal sides
+    and unequal point counts (ny x nx = 24 x 32, Lx = 2 pi, Ly = 4 pi): the
+    mode cos(k1 x + (k2/2) y) has |mu|^2 = k1^2 + (k2/2)^2, so a swapped axis
+    or a dropped y term in the oracle's 2D path changes w."""
+    shape, lo, hi, kappa, dt, n, b = (24, 32), [-np.pi, -2 * np.pi], [np.pi, 2 * np.pi], 0.9, 0.11, 30, -0.3
+    x, y = S.mesh(shape, lo, hi)
+    mode = np.cos(k1 * x + 0.5 * k2 * y)
+    u = O.general_tsfp2(s, kappa, lambda v: 0.0 * v, mode, b * mode, dt, n, 3, lo, hi)
+    w, t = np.sqrt(kappa) * (k1 ** 2 + (0.5 * k2) ** 2) ** (s / 2), n * dt
+    assert np.max(np.abs(u - (np.cos(w * t) + b * np.sin(w * t) / w) * mode)) < 1e-12
+
+
 @pytest.mark.parametrize("s,k", [(0.6, 2), (1.2, 3)])
 def test_general_lffp_single_mode_recurrence(s, k):
     """Constant order and f = 0 (Eq. (3.4)): a1 = (1 - dt^2 kappa lambda/2)
