@@ -14,7 +14,9 @@
 //        one complex FFT along x of u[y] + i v[y] per row, split into the
 //        two half spectra;
 //   S2 k2d_rot_cols       per column k_x: the forward FFT along y of Su
-//        and Sv, the flow above, the 1/(nx ny) of the unnormalised
+//        and Sv, the flow above (c, s / w, w s per mode from a table that
+//        k_flow_table builds in double for a run's dt and dt/2), the
+//        1/(nx ny) of the unnormalised
 //        transforms, the inverse FFT along y of both, back to Su, Sv (loads
 //        and stores are row segments of the CTA's columns: the first and
 //        last stages are done cooperatively as in k2d_inv_cols);
