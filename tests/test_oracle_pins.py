@@ -144,6 +144,39 @@ def test_matrix_free_converges_to_dense_within_remainder(shape):
 
 
 # --------------------------------------------------------------------------
+# P8: the matrix-free scheme against the dense definition on the configs'
+# full grids, at sampled points (the dense sum is O(N) per point)
+# --------------------------------------------------------------------------
+def test_matrix_free_matches_dense_on_the_headline_grid():
+    """1024^2, s = 1 + gamma of the headline Q field (seed 2), M = 16, a
+    smooth seeded field: |delta| ln|mu|^2 stays below ~0.5 over the field's
+    modes, so the Taylor remainder at M = 16 is far below round-off and
+    Eq. (2.13) must equal Eq. (2.12) to FFT round-off at every sampled
+    point."""
+    w = S.workload_2d_1024(nsteps=1)
+    s = 1.0 + O.seismic_coefficients(w["Q"], 1.0, 2 * np.pi)["gamma"]
+    u = S.q_lowpass((1024, 1024), 7, qmin=-1.0, qmax=1.0, sigma_k=16.0)
+    pts = np.random.default_rng(8).choice(u.size, 64, replace=False)
+    dense = O.dense_operator(u, s, points=pts)
+    mf = O.matrix_free_operator(u, s, 16).ravel()[pts]
+    assert np.max(np.abs(mf - dense)) <= 1e-12 * np.max(np.abs(dense))
+
+
+def test_matrix_free_matches_dense_on_the_3d_grid():
+    """256^3, s = 1 + gamma of the two-layer Q, M = 8, the config's Gaussian
+    pulse: twelve seeded points and four around the pulse."""
+    w = S.workload_3d_256()
+    s = 1.0 + O.seismic_coefficients(w["Q"], 1.0, 2 * np.pi)["gamma"]
+    u = w["u0"]
+    c = (128 * 256 + 128) * 256 + 128
+    pts = np.concatenate([np.random.default_rng(9).choice(u.size, 12, replace=False),
+                          [c, c + 3, c + 256 * 2, c + 256 * 256 * 5]])
+    dense = O.dense_operator(u, s, points=pts)
+    mf = O.matrix_free_operator(u, s, 8).ravel()[pts]
+    assert np.max(np.abs(mf - dense)) <= 1e-12 * np.max(np.abs(dense))
+
+
+# --------------------------------------------------------------------------
 # P4: special cases
 # --------------------------------------------------------------------------
 def test_constant_order_is_the_plain_multiplier():
